@@ -1,0 +1,710 @@
+/*
+ * oracle.c -- plain, slow, single-threaded FP64 reference implementation of
+ * the interval reachability methods of PIRK (Devonport, Khaled, Arcak, Zamani:
+ * "PIRK: Scalable Interval Reachability Analysis for High-Dimensional
+ * Nonlinear Systems", 2020).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  The CUDA library
+ * neither links nor calls it, and the two share no source, header, table or
+ * constant generator.  Build: gcc -O2 -ffp-contract=off -fPIC -shared (no
+ * fast-math, no threads, no FMA contraction).
+ *
+ * Every function below names the passage of the paper it follows.  Where the
+ * paper is silent, garbled or inconsistent the reading taken is stated next
+ * to the code:
+ *
+ *  R1 (Sec. 3.1, Algorithm 1).  The printed listing is read as classic
+ *     fourth-order Runge-Kutta: the third stage is evaluated at y + h*k3 (the
+ *     listing writes h/2), the update carries the factor h, and the loop runs
+ *     N = round((t1 - t0)/h) steps (the listing's time set has N+1 elements).
+ *     Only this reading is fourth order, which the section title claims.
+ *  R2 (Sec. 2.1, CGB; Algorithm 2).  Center and radius are integrated as one
+ *     coupled 2n-dimensional system with the same RK4.  When the contraction
+ *     matrix C is constant this equals the paper's two sequential runs; when C
+ *     is evaluated on the current box (R3) it is the natural reading.
+ *  R3 (Sec. 2.1, CGB).  The paper does not say over which domain C must bound
+ *     the Jacobian.  Systems with globally valid constant bounds (traffic,
+ *     linear) use a constant C; the KS grid and the oscillator chain use the
+ *     supremum of the Jacobian over the current stage box [c - r, c + r].
+ *  R4 (Sec. 2.1, MC).  The text samples the initial set and the input set;
+ *     Algorithm 4 samples only x0.  The text is followed: inputs are sampled
+ *     too, once per trajectory and constant in time (Sec. 2).
+ *  R5 (Sec. 2.1, MC).  "log" in the sample bound is the natural logarithm.
+ *  R6 (Sec. 5.1).  The printed traffic equations are garbled (the first cell
+ *     lacks its outflow, indices disagree).  The chain is: cells 0..n-1,
+ *     flux out of cell i  f_i = min(c, v x_i, w (xbar - x_{i+1})) for i<n-1,
+ *     f_{n-1} = min(c, v x_{n-1}), inflow of cell 0 is the input d, and
+ *     dx_i/dt = f_{i-1} - f_i (beta = T = 1).
+ *  R7 (Sec. 2.1, MM).  The paper leaves the decomposition function to its
+ *     references; each system below documents the one used.
+ *
+ * Random numbers of the MC method come from Philox4x32-10 (Salmon, Moraes,
+ * Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3", SC'11),
+ * implemented here from that definition.  Sample j, component i, stream tag t
+ * uses counter (i, j, t, 0) and key (seed mod 2^32, seed div 2^32); the first
+ * two output words w0, w1 give U = ((w0 << 32 | w1) >> 11) * 2^-53 in [0,1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_MM = 0, ORC_CGB = 1, ORC_MC = 2 };
+enum { ORC_TRAFFIC = 0, ORC_KS = 1, ORC_OSC = 2, ORC_LINEAR = 3 };
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ENONFINITE = -4 };
+
+/* ---------------------------------------------------------------------- */
+/* System description                                                      */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int kind;
+    int64_t n;          /* state dimension */
+    int64_t nw;         /* input dimension */
+    /* traffic (Sec. 5.1): capacity c, free-flow speed v, congestion wave
+       speed w, jam density xbar */
+    double cap, v, w, xbar;
+    /* KS grid: u_t = -g_nl u u_x - g_2 u_xx - g_4 u_xxxx, spacing dx */
+    double dx, g_nl, g_2, g_4;
+    double a0, a1, a2;  /* 5-point stencil of -g_2 u_xx - g_4 u_xxxx */
+    /* oscillator chain: xdd_i = -ka x_i - kb x_i^3 + kc (x_{i-1} - 2 x_i + x_{i+1}) + w_i */
+    double ka, kb, kc;
+    /* linear: dx/dt = A x + p, A row-major n x n */
+    const double *A;
+} orc_sys;
+
+static int64_t input_dim(int kind, int64_t n)
+{
+    switch (kind) {
+    case ORC_TRAFFIC: return 1;
+    case ORC_KS: return 0;
+    case ORC_OSC: return n / 2;
+    case ORC_LINEAR: return n;
+    }
+    return -1;
+}
+
+int64_t orc_input_dim(int kind, int64_t n) { return input_dim(kind, n); }
+
+static int make_sys(orc_sys *s, int kind, const double *prm, const double *A, int64_t n)
+{
+    memset(s, 0, sizeof *s);
+    s->kind = kind;
+    s->n = n;
+    s->nw = input_dim(kind, n);
+    if (n < 1 || s->nw < 0) return ORC_EINVAL;
+    switch (kind) {
+    case ORC_TRAFFIC:
+        s->cap = prm[0]; s->v = prm[1]; s->w = prm[2]; s->xbar = prm[3];
+        break;
+    case ORC_KS: {
+        double d2, d4;
+        s->dx = prm[0]; s->g_nl = prm[1]; s->g_2 = prm[2]; s->g_4 = prm[3];
+        d2 = 1.0 / (s->dx * s->dx);
+        d4 = d2 * d2;
+        /* -g_2 (u_{i+1} - 2u_i + u_{i-1})/dx^2
+           -g_4 (u_{i+2} - 4u_{i+1} + 6u_i - 4u_{i-1} + u_{i-2})/dx^4 */
+        s->a0 = 2.0 * s->g_2 * d2 - 6.0 * s->g_4 * d4;
+        s->a1 = -s->g_2 * d2 + 4.0 * s->g_4 * d4;
+        s->a2 = -s->g_4 * d4;
+        break;
+    }
+    case ORC_OSC:
+        if (n % 2) return ORC_EINVAL;
+        s->ka = prm[0]; s->kb = prm[1]; s->kc = prm[2];
+        break;
+    case ORC_LINEAR:
+        if (!A) return ORC_EINVAL;
+        s->A = A;
+        break;
+    default:
+        return ORC_EINVAL;
+    }
+    return ORC_OK;
+}
+
+static double min2(double a, double b) { return a < b ? a : b; }
+static double max2(double a, double b) { return a > b ? a : b; }
+static double posp(double a) { return a > 0.0 ? a : 0.0; }
+static double negp(double a) { return a < 0.0 ? a : 0.0; }
+
+/* periodic index for the KS grid */
+static int64_t wrap(int64_t i, int64_t n) { i %= n; return i < 0 ? i + n : i; }
+
+/* ---------------------------------------------------------------------- */
+/* Right-hand sides f(t, x, p)  (Sec. 2: dx/dt = f(t, x, p))               */
+/* ---------------------------------------------------------------------- */
+
+/* traffic flux out of cell i (reading R6) */
+static double traffic_flux(const orc_sys *s, const double *x, int64_t i)
+{
+    if (i == s->n - 1) return min2(s->cap, s->v * x[i]);
+    return min2(s->cap, min2(s->v * x[i], s->w * (s->xbar - x[i + 1])));
+}
+
+static void f_traffic(const orc_sys *s, const double *x, const double *p, double *dx)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double in = (i == 0) ? p[0] : traffic_flux(s, x, i - 1);
+        dx[i] = in - traffic_flux(s, x, i);
+    }
+}
+
+/* KS, second-order central differences on a periodic grid */
+static void f_ks(const orc_sys *s, const double *u, double *du)
+{
+    int64_t n = s->n;
+    for (int64_t i = 0; i < n; ++i) {
+        double um2 = u[wrap(i - 2, n)], um1 = u[wrap(i - 1, n)];
+        double up1 = u[wrap(i + 1, n)], up2 = u[wrap(i + 2, n)];
+        double lin = s->a0 * u[i] + s->a1 * (um1 + up1) + s->a2 * (um2 + up2);
+        double ux = (up1 - um1) / (2.0 * s->dx);
+        du[i] = lin - s->g_nl * u[i] * ux;
+    }
+}
+
+/* oscillator chain, state [x_1..x_m | v_1..v_m], fixed ends x_0 = x_{m+1} = 0 */
+static void f_osc(const orc_sys *s, const double *y, const double *w, double *dy)
+{
+    int64_t m = s->n / 2;
+    const double *x = y, *v = y + m;
+    for (int64_t i = 0; i < m; ++i) {
+        double xl = (i > 0) ? x[i - 1] : 0.0;
+        double xr = (i < m - 1) ? x[i + 1] : 0.0;
+        dy[i] = v[i];
+        dy[m + i] = -s->ka * x[i] - s->kb * x[i] * x[i] * x[i]
+                    + s->kc * (xl - 2.0 * x[i] + xr) + w[i];
+    }
+}
+
+static void f_linear(const orc_sys *s, const double *x, const double *p, double *dx)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < s->n; ++j) acc += s->A[i * s->n + j] * x[j];
+        dx[i] = acc + p[i];
+    }
+}
+
+static void f_sys(const orc_sys *s, const double *x, const double *p, double *dx)
+{
+    switch (s->kind) {
+    case ORC_TRAFFIC: f_traffic(s, x, p, dx); break;
+    case ORC_KS: f_ks(s, x, dx); break;
+    case ORC_OSC: f_osc(s, x, p, dx); break;
+    case ORC_LINEAR: f_linear(s, x, p, dx); break;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Decomposition functions d(t, x, p, xh, ph)  (Sec. 2.1, MM)              */
+/* d(x,p,x,p) = f(x,p); d_i nondecreasing in x_j (j != i) and p,           */
+/* nonincreasing in xh_j (j != i) and ph.                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Traffic is cooperative (every off-diagonal Jacobian entry is >= 0) and
+   increasing in the inflow, so d(x, p, xh, ph) = f(x, p). */
+static void d_traffic(const orc_sys *s, const double *x, const double *p,
+                      const double *xh, const double *ph, double *dx)
+{
+    (void)xh; (void)ph;
+    f_traffic(s, x, p, dx);
+}
+
+/* KS: the linear stencil is split by coefficient sign; the product
+   -g_nl u_i D_i, D_i = (u_{i+1} - u_{i-1})/(2 dx), is bounded with u_i held at
+   its own argument x_i and D_i ranging over the interval its neighbours span:
+   Da = (x_{i+1} - xh_{i-1})/(2dx), Db = (xh_{i+1} - x_{i-1})/(2dx).  When x is
+   the lower end (Da <= Db) the minimum over that interval is taken, otherwise
+   the maximum: this is the tight decomposition of the product on ordered
+   boxes, and it reduces to f when xh = x. */
+static void d_ks(const orc_sys *s, const double *x, const double *xh, double *dx)
+{
+    int64_t n = s->n;
+    double a1p = posp(s->a1), a1m = negp(s->a1), a2p = posp(s->a2), a2m = negp(s->a2);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t im2 = wrap(i - 2, n), im1 = wrap(i - 1, n);
+        int64_t ip1 = wrap(i + 1, n), ip2 = wrap(i + 2, n);
+        double lin = s->a0 * x[i]
+                   + (a1p * x[im1] + a1m * xh[im1]) + (a1p * x[ip1] + a1m * xh[ip1])
+                   + (a2p * x[im2] + a2m * xh[im2]) + (a2p * x[ip2] + a2m * xh[ip2]);
+        double Da = (x[ip1] - xh[im1]) / (2.0 * s->dx);
+        double Db = (xh[ip1] - x[im1]) / (2.0 * s->dx);
+        double ea = -s->g_nl * x[i] * Da, eb = -s->g_nl * x[i] * Db;
+        double nl = (Da <= Db) ? min2(ea, eb) : max2(ea, eb);
+        dx[i] = lin + nl;
+    }
+}
+
+/* Oscillator: dv_i/dt is decreasing in x_i (an off-diagonal entry for the
+   v_i row, slope -ka - 2kc - 3kb x_i^2 < 0) and increasing in x_{i+-1}, v_i
+   and w_i; so x_i enters through the hatted argument. */
+static void d_osc(const orc_sys *s, const double *y, const double *w,
+                  const double *yh, const double *wh, double *dy)
+{
+    int64_t m = s->n / 2;
+    const double *x = y, *v = y + m, *xh = yh;
+    (void)wh;
+    for (int64_t i = 0; i < m; ++i) {
+        double xl = (i > 0) ? x[i - 1] : 0.0;
+        double xr = (i < m - 1) ? x[i + 1] : 0.0;
+        double z = xh[i];
+        dy[i] = v[i];
+        dy[m + i] = -s->ka * z - s->kb * z * z * z + s->kc * (xl - 2.0 * z + xr) + w[i];
+    }
+}
+
+/* Linear: off-diagonal entries split by sign, diagonal at its own argument. */
+static void d_linear(const orc_sys *s, const double *x, const double *p,
+                     const double *xh, double *dx)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < s->n; ++j) {
+            double a = s->A[i * s->n + j];
+            if (j == i) acc += a * x[j];
+            else acc += posp(a) * x[j] + negp(a) * xh[j];
+        }
+        dx[i] = acc + p[i];
+    }
+}
+
+static void d_sys(const orc_sys *s, const double *x, const double *p,
+                  const double *xh, const double *ph, double *dx)
+{
+    switch (s->kind) {
+    case ORC_TRAFFIC: d_traffic(s, x, p, xh, ph, dx); break;
+    case ORC_KS: d_ks(s, x, xh, dx); break;
+    case ORC_OSC: d_osc(s, x, p, xh, ph, dx); break;
+    case ORC_LINEAR: d_linear(s, x, p, xh, dx); break;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Growth dynamics g(r) = C r + [p]  (Sec. 2.1, CGB)                        */
+/* C_ii >= J_ii and C_ij >= |J_ij| (i != j).  c is the current center and  */
+/* r the current radius (used only by the box-evaluated bounds, R3).       */
+/* ---------------------------------------------------------------------- */
+
+static void g_traffic(const orc_sys *s, const double *c, const double *r,
+                      const double *hp, double *dr)
+{
+    /* dx_i/dx_{i-1} in {0, v}, dx_i/dx_{i+1} in {0, w}, dx_i/dx_i in [-v-w, 0]:
+       C_{i,i-1} = v, C_{i,i+1} = w, C_ii = 0, valid for every x.  The inflow
+       enters cell 0 with coefficient 1. */
+    (void)c;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double acc = 0.0;
+        if (i > 0) acc += s->v * r[i - 1];
+        if (i < s->n - 1) acc += s->w * r[i + 1];
+        dr[i] = acc + ((i == 0) ? hp[0] : 0.0);
+    }
+}
+
+static void g_ks(const orc_sys *s, const double *c, const double *r, double *dr)
+{
+    /* J_ii = a0 - g_nl D_i,  J_{i,i+1} = a1 - g_nl u_i/(2dx),
+       J_{i,i-1} = a1 + g_nl u_i/(2dx),  J_{i,i+-2} = a2.
+       Suprema over the box u in [c - r, c + r]. */
+    int64_t n = s->n;
+    double k = s->g_nl / (2.0 * s->dx);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t im2 = wrap(i - 2, n), im1 = wrap(i - 1, n);
+        int64_t ip1 = wrap(i + 1, n), ip2 = wrap(i + 2, n);
+        double lo_i = c[i] - r[i], hi_i = c[i] + r[i];
+        /* D_i ranges over [(lo_{i+1} - hi_{i-1}), (hi_{i+1} - lo_{i-1})]/(2dx) */
+        double dmin = (c[ip1] - r[ip1]) - (c[im1] + r[im1]);
+        double dmax = (c[ip1] + r[ip1]) - (c[im1] - r[im1]);
+        double Cii = max2(s->a0 - k * dmin, s->a0 - k * dmax);
+        double Cip = max2(fabs(s->a1 - k * lo_i), fabs(s->a1 - k * hi_i));
+        double Cim = max2(fabs(s->a1 + k * lo_i), fabs(s->a1 + k * hi_i));
+        double C2 = fabs(s->a2);
+        dr[i] = Cii * r[i] + Cim * r[im1] + Cip * r[ip1] + C2 * (r[im2] + r[ip2]);
+    }
+}
+
+static void g_osc(const orc_sys *s, const double *c, const double *r,
+                  const double *hp, double *dr)
+{
+    /* rows x_i: J[x_i, v_i] = 1.  rows v_i: J[v_i, x_i] = -ka - 2kc - 3kb x_i^2,
+       J[v_i, x_{i+-1}] = kc, diagonal entries 0. */
+    int64_t m = s->n / 2;
+    const double *cx = c, *rx = r, *rv = r + m;
+    for (int64_t i = 0; i < m; ++i) {
+        double amax = fabs(cx[i]) + rx[i];
+        double cxx = s->ka + 2.0 * s->kc + 3.0 * s->kb * amax * amax;
+        double rl = (i > 0) ? rx[i - 1] : 0.0;
+        double rr = (i < m - 1) ? rx[i + 1] : 0.0;
+        dr[i] = rv[i];
+        dr[m + i] = cxx * rx[i] + fabs(s->kc) * (rl + rr) + hp[i];
+    }
+}
+
+static void g_linear(const orc_sys *s, const double *r, const double *hp, double *dr)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < s->n; ++j) {
+            double a = s->A[i * s->n + j];
+            acc += ((j == i) ? a : fabs(a)) * r[j];
+        }
+        dr[i] = acc + hp[i];
+    }
+}
+
+static void g_sys(const orc_sys *s, const double *c, const double *r,
+                  const double *hp, double *dr)
+{
+    switch (s->kind) {
+    case ORC_TRAFFIC: g_traffic(s, c, r, hp, dr); break;
+    case ORC_KS: g_ks(s, c, r, dr); break;
+    case ORC_OSC: g_osc(s, c, r, hp, dr); break;
+    case ORC_LINEAR: g_linear(s, r, hp, dr); break;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 (Sec. 3.1): fourth-order Runge-Kutta, reading R1           */
+/* ---------------------------------------------------------------------- */
+
+typedef void (*rhs_fn)(const void *ctx, double t, const double *y, double *dy);
+
+static int rk4(rhs_fn F, const void *ctx, int64_t dim, double *y,
+               double t0, double h, int64_t N)
+{
+    double *k1 = malloc(sizeof(double) * dim), *k2 = malloc(sizeof(double) * dim);
+    double *k3 = malloc(sizeof(double) * dim), *k4 = malloc(sizeof(double) * dim);
+    double *tmp = malloc(sizeof(double) * dim);
+    if (!k1 || !k2 || !k3 || !k4 || !tmp) {
+        free(k1); free(k2); free(k3); free(k4); free(tmp);
+        return ORC_ENOMEM;
+    }
+    for (int64_t k = 0; k < N; ++k) {
+        double t = t0 + (double)k * h;
+        F(ctx, t, y, k1);
+        for (int64_t i = 0; i < dim; ++i) tmp[i] = y[i] + (h / 2.0) * k1[i];
+        F(ctx, t + h / 2.0, tmp, k2);
+        for (int64_t i = 0; i < dim; ++i) tmp[i] = y[i] + (h / 2.0) * k2[i];
+        F(ctx, t + h / 2.0, tmp, k3);
+        for (int64_t i = 0; i < dim; ++i) tmp[i] = y[i] + h * k3[i];
+        F(ctx, t + h, tmp, k4);
+        for (int64_t i = 0; i < dim; ++i)
+            y[i] = y[i] + (h / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    free(k1); free(k2); free(k3); free(k4); free(tmp);
+    return ORC_OK;
+}
+
+/* number of RK4 steps for [0, t_final] with step dt (reading R1) */
+int orc_nsteps(double t_final, double dt, int64_t *N)
+{
+    double q;
+    if (!(dt > 0.0) || !(t_final >= 0.0) || !isfinite(dt) || !isfinite(t_final))
+        return ORC_EINVAL;
+    q = nearbyint(t_final / dt);
+    if (fabs(q * dt - t_final) > 1e-9 * t_final) return ORC_EINVAL;
+    *N = (int64_t)q;
+    return ORC_OK;
+}
+
+/* ---- plain system:  dy/dt = f(y, p) ---- */
+typedef struct { const orc_sys *s; const double *p; } flow_ctx;
+
+static void flow_rhs(const void *ctx, double t, const double *y, double *dy)
+{
+    const flow_ctx *c = ctx;
+    (void)t;
+    f_sys(c->s, y, c->p, dy);
+}
+
+/* ---- embedding system (Sec. 2.1):  [x; xh]' = [d(x,p,xh,ph); d(xh,ph,x,p)] ---- */
+typedef struct { const orc_sys *s; const double *p, *ph; } mm_ctx;
+
+static void mm_rhs(const void *ctx, double t, const double *z, double *dz)
+{
+    const mm_ctx *c = ctx;
+    int64_t n = c->s->n;
+    (void)t;
+    d_sys(c->s, z, c->p, z + n, c->ph, dz);
+    d_sys(c->s, z + n, c->ph, z, c->p, dz + n);
+}
+
+/* ---- center/radius system (Sec. 2.1, R2):  [c; r]' = [f(c,p*); C r + [p]] ---- */
+typedef struct { const orc_sys *s; const double *pc, *hp; } cgb_ctx;
+
+static void cgb_rhs(const void *ctx, double t, const double *z, double *dz)
+{
+    const cgb_ctx *c = ctx;
+    int64_t n = c->s->n;
+    (void)t;
+    f_sys(c->s, z, c->pc, dz);
+    g_sys(c->s, z, z + n, c->hp, dz + n);
+}
+
+static int all_finite(const double *a, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) if (!isfinite(a[i])) return 0;
+    return 1;
+}
+
+static int check_box(const double *lo, const double *hi, int64_t n)
+{
+    if (n > 0 && (!lo || !hi)) return ORC_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(lo[i]) || !isfinite(hi[i]) || lo[i] > hi[i]) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* one trajectory of f from x0 under constant input p (Sec. 2: Phi(t1; t0, x0, p)) */
+int orc_flow(int kind, const double *prm, const double *A, int64_t n,
+             const double *x0, const double *p, double t_final, double dt, double *x1)
+{
+    orc_sys s;
+    flow_ctx c;
+    int64_t N;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    if ((rc = orc_nsteps(t_final, dt, &N))) return rc;
+    memcpy(x1, x0, sizeof(double) * n);
+    c.s = &s; c.p = p;
+    if ((rc = rk4(flow_rhs, &c, n, x1, 0.0, dt, N))) return rc;
+    return all_finite(x1, n) ? ORC_OK : ORC_ENONFINITE;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 3: mixed monotonicity.  If pipe_lo is given, the box after    */
+/* every `every` steps is written to row q of pipe_lo / pipe_hi (the reach */
+/* pipe of Sec. 5.5); otherwise every == N.                                 */
+/* ---------------------------------------------------------------------- */
+static int reach_mm(const orc_sys *s, const double *xlo, const double *xhi,
+                    const double *wlo, const double *whi, double h, int64_t N,
+                    int64_t every, double *pipe_lo, double *pipe_hi,
+                    double *lo, double *hi)
+{
+    int64_t n = s->n;
+    mm_ctx c;
+    int rc = ORC_OK;
+    double *z = malloc(sizeof(double) * 2 * n);
+    if (!z) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n; ++i) { z[i] = xlo[i]; z[n + i] = xhi[i]; }
+    c.s = s; c.p = wlo; c.ph = whi;
+    for (int64_t done = 0, q = 0; done < N && !rc; done += every, ++q) {
+        rc = rk4(mm_rhs, &c, 2 * n, z, (double)done * h, h, every);
+        if (!rc && pipe_lo) {
+            memcpy(pipe_lo + q * n, z, sizeof(double) * n);
+            memcpy(pipe_hi + q * n, z + n, sizeof(double) * n);
+        }
+    }
+    if (!rc) {
+        for (int64_t i = 0; i < n; ++i) { lo[i] = z[i]; hi[i] = z[n + i]; }
+        if (!all_finite(z, 2 * n)) rc = ORC_ENONFINITE;
+    }
+    free(z);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 2: contraction / growth bound (pipe output as in reach_mm)     */
+/* ---------------------------------------------------------------------- */
+static int reach_cgb(const orc_sys *s, const double *xlo, const double *xhi,
+                     const double *wlo, const double *whi, double h, int64_t N,
+                     int64_t every, double *pipe_lo, double *pipe_hi,
+                     double *lo, double *hi)
+{
+    int64_t n = s->n, nw = s->nw;
+    cgb_ctx c;
+    int rc = ORC_OK;
+    double *z = malloc(sizeof(double) * 2 * n);
+    double *pc = malloc(sizeof(double) * (nw > 0 ? nw : 1));
+    double *hp = malloc(sizeof(double) * (nw > 0 ? nw : 1));
+    if (!z || !pc || !hp) { free(z); free(pc); free(hp); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < n; ++i) {
+        z[i] = (xlo[i] + xhi[i]) / 2.0;      /* center, Sec. 2 */
+        z[n + i] = (xhi[i] - xlo[i]) / 2.0;  /* half-width */
+    }
+    for (int64_t k = 0; k < nw; ++k) {
+        pc[k] = (wlo[k] + whi[k]) / 2.0;
+        hp[k] = (whi[k] - wlo[k]) / 2.0;
+    }
+    c.s = s; c.pc = pc; c.hp = hp;
+    for (int64_t done = 0, q = 0; done < N && !rc; done += every, ++q) {
+        rc = rk4(cgb_rhs, &c, 2 * n, z, (double)done * h, h, every);
+        if (!rc && pipe_lo) {
+            for (int64_t i = 0; i < n; ++i) {
+                pipe_lo[q * n + i] = z[i] - z[n + i];
+                pipe_hi[q * n + i] = z[i] + z[n + i];
+            }
+        }
+    }
+    if (!rc) {
+        for (int64_t i = 0; i < n; ++i) { lo[i] = z[i] - z[n + i]; hi[i] = z[i] + z[n + i]; }
+        if (!all_finite(z, 2 * n)) rc = ORC_ENONFINITE;
+    }
+    free(z); free(pc); free(hp);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11)                                     */
+/* ---------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_uniform(uint64_t seed, int64_t j, int64_t i, uint32_t tag)
+{
+    uint32_t ctr[4] = { (uint32_t)i, (uint32_t)j, tag, 0u };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t o[4];
+    uint64_t bits;
+    orc_philox4x32_10(ctr, key, o);
+    bits = ((uint64_t)o[0] << 32) | o[1];
+    return (double)(bits >> 11) * 0x1.0p-53;
+}
+
+/* Sec. 2.1: m >= (2n/eps) log(2n/delta), natural log (reading R5) */
+int64_t orc_mc_samples(int64_t n, double eps, double delta)
+{
+    double q = 2.0 * (double)n;
+    return (int64_t)ceil((q / eps) * log(q / delta));
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 4: Monte Carlo.  prec == 32: each sample is rounded to FP32   */
+/* (the value an FP32 trajectory starts from) and integrated in FP64.      */
+/* finals (optional) receives every sample's final state, row j = sample j. */
+/* ---------------------------------------------------------------------- */
+static int reach_mc(const orc_sys *s, const double *xlo, const double *xhi,
+                    const double *wlo, const double *whi, double h, int64_t N,
+                    int64_t m, uint64_t seed, int prec,
+                    double *lo, double *hi, double *finals)
+{
+    int64_t n = s->n, nw = s->nw;
+    flow_ctx c;
+    int rc = ORC_OK;
+    double *x = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * (nw > 0 ? nw : 1));
+    if (!x || !p) { free(x); free(p); return ORC_ENOMEM; }
+    if (m < 1) { free(x); free(p); return ORC_EINVAL; }
+    for (int64_t i = 0; i < n; ++i) { lo[i] = INFINITY; hi[i] = -INFINITY; }
+    c.s = s; c.p = p;
+    for (int64_t j = 0; j < m && !rc; ++j) {
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] = xlo[i] + (xhi[i] - xlo[i]) * orc_uniform(seed, j, i, 0u);
+            if (prec == 32) x[i] = (double)(float)x[i];
+        }
+        for (int64_t k = 0; k < nw; ++k) {
+            p[k] = wlo[k] + (whi[k] - wlo[k]) * orc_uniform(seed, j, k, 1u);
+            if (prec == 32) p[k] = (double)(float)p[k];
+        }
+        rc = rk4(flow_rhs, &c, n, x, 0.0, h, N);
+        if (rc) break;
+        if (!all_finite(x, n)) { rc = ORC_ENONFINITE; break; }
+        for (int64_t i = 0; i < n; ++i) {
+            lo[i] = min2(lo[i], x[i]);
+            hi[i] = max2(hi[i], x[i]);
+        }
+        if (finals) memcpy(finals + j * n, x, sizeof(double) * n);
+    }
+    free(x); free(p);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Entry point                                                              */
+/* ---------------------------------------------------------------------- */
+int orc_reach(int method, int kind, const double *prm, const double *A, int64_t n,
+              const double *x_lo, const double *x_hi,
+              const double *w_lo, const double *w_hi,
+              double t_final, double dt, int64_t m, uint64_t seed, int prec,
+              double *lo, double *hi, double *finals)
+{
+    orc_sys s;
+    int64_t N;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    if ((rc = orc_nsteps(t_final, dt, &N))) return rc;
+    if ((rc = check_box(x_lo, x_hi, n))) return rc;
+    if ((rc = check_box(w_lo, w_hi, s.nw))) return rc;
+    switch (method) {
+    case ORC_MM: return reach_mm(&s, x_lo, x_hi, w_lo, w_hi, dt, N, N > 0 ? N : 1, NULL, NULL, lo, hi);
+    case ORC_CGB: return reach_cgb(&s, x_lo, x_hi, w_lo, w_hi, dt, N, N > 0 ? N : 1, NULL, NULL, lo, hi);
+    case ORC_MC:
+        if (prec != 32 && prec != 64) return ORC_EINVAL;
+        return reach_mc(&s, x_lo, x_hi, w_lo, w_hi, dt, N, m, seed, prec, lo, hi, finals);
+    }
+    return ORC_EINVAL;
+}
+
+/* The reach pipe (Sec. 5.5): the box after every `every` RK4 steps.
+   pipe_lo / pipe_hi receive N/every rows of n values; lo / hi the final box. */
+int orc_reach_pipe(int method, int kind, const double *prm, const double *A, int64_t n,
+                   const double *x_lo, const double *x_hi,
+                   const double *w_lo, const double *w_hi,
+                   double t_final, double dt, int64_t every,
+                   double *pipe_lo, double *pipe_hi, double *lo, double *hi)
+{
+    orc_sys s;
+    int64_t N;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    if ((rc = orc_nsteps(t_final, dt, &N))) return rc;
+    if (every < 1 || N % every) return ORC_EINVAL;
+    if ((rc = check_box(x_lo, x_hi, n))) return rc;
+    if ((rc = check_box(w_lo, w_hi, s.nw))) return rc;
+    if (method == ORC_MM)
+        return reach_mm(&s, x_lo, x_hi, w_lo, w_hi, dt, N, every, pipe_lo, pipe_hi, lo, hi);
+    if (method == ORC_CGB)
+        return reach_cgb(&s, x_lo, x_hi, w_lo, w_hi, dt, N, every, pipe_lo, pipe_hi, lo, hi);
+    return ORC_EINVAL;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Single evaluations of f, d and g, so that tests can check the defining  */
+/* properties of Sec. 2.1 (d(x,p,x,p) = f(x,p), monotonicity of d,         */
+/* C_ii >= J_ii and C_ij >= |J_ij|) against f directly.                    */
+/* ---------------------------------------------------------------------- */
+int orc_rhs(int kind, const double *prm, const double *A, int64_t n,
+            const double *x, const double *p, double *dx)
+{
+    orc_sys s;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    f_sys(&s, x, p, dx);
+    return ORC_OK;
+}
+
+int orc_decomp(int kind, const double *prm, const double *A, int64_t n,
+               const double *x, const double *p, const double *xh, const double *ph,
+               double *dx)
+{
+    orc_sys s;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    d_sys(&s, x, p, xh, ph, dx);
+    return ORC_OK;
+}
+
+int orc_growth(int kind, const double *prm, const double *A, int64_t n,
+               const double *c, const double *r, const double *hp, double *dr)
+{
+    orc_sys s;
+    int rc = make_sys(&s, kind, prm, A, n);
+    if (rc) return rc;
+    g_sys(&s, c, r, hp, dr);
+    return ORC_OK;
+}

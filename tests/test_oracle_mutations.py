@@ -1,0 +1,73 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/oracle.c`` (on the CPU),
+builds it, and runs the pin suite against that copy: the suite must fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+# (name, text in oracle.c, replacement)
+MUTATIONS = [
+    ("rk4 third stage at h/2 (the printed listing)",
+     "tmp[i] = y[i] + h * k3[i];", "tmp[i] = y[i] + (h / 2.0) * k3[i];"),
+    ("rk4 weight of k3", "2.0 * k3[i] + k4[i]", "k3[i] + k4[i]"),
+    ("rk4 update without h", "y[i] = y[i] + (h / 6.0) *", "y[i] = y[i] + (1.0 / 6.0) *"),
+    ("traffic congestion term reads own cell",
+     "s->w * (s->xbar - x[i + 1])", "s->w * (s->xbar - x[i])"),
+    ("traffic inflow dropped", "double in = (i == 0) ? p[0] :", "double in = (i == 0) ? 0.0 :"),
+    ("traffic last cell has no outflow",
+     "if (i == s->n - 1) return min2(s->cap, s->v * x[i]);", "if (i == s->n - 1) return 0.0;"),
+    ("ks second-derivative sign", "s->a1 = -s->g_2 * d2 + 4.0", "s->a1 = s->g_2 * d2 + 4.0"),
+    ("ks a2 coefficient", "s->a2 = -s->g_4 * d4;", "s->a2 = -2.0 * s->g_4 * d4;"),
+    ("ks advection direction", "double ux = (up1 - um1)", "double ux = (um1 - up1)"),
+    ("ks decomposition min/max swapped", "(Da <= Db) ? min2(ea, eb) : max2(ea, eb)",
+     "(Da <= Db) ? max2(ea, eb) : min2(ea, eb)"),
+    ("ks decomposition neighbour transposed",
+     "double Da = (x[ip1] - xh[im1])", "double Da = (xh[ip1] - x[im1])"),
+    ("osc decomposition uses own x", "double z = xh[i];", "double z = x[i];"),
+    ("osc cubic power", "s->kb * x[i] * x[i] * x[i]", "s->kb * x[i] * x[i]"),
+    ("osc fixed end", "double xr = (i < m - 1) ? x[i + 1] : 0.0;\n        dy[i] = v[i];\n        dy[m + i] = -s->ka * x[i]",
+     "double xr = (i < m - 1) ? x[i + 1] : x[i];\n        dy[i] = v[i];\n        dy[m + i] = -s->ka * x[i]"),
+    ("linear decomposition sign split swapped",
+     "else acc += posp(a) * x[j] + negp(a) * xh[j];", "else acc += negp(a) * x[j] + posp(a) * xh[j];"),
+    ("traffic growth bound entries swapped", "if (i > 0) acc += s->v * r[i - 1];",
+     "if (i > 0) acc += s->w * r[i - 1];"),
+    ("traffic growth bound without input", "dr[i] = acc + ((i == 0) ? hp[0] : 0.0);", "dr[i] = acc;"),
+    ("ks growth diagonal uses the infimum", "double Cii = max2(s->a0 - k * dmin, s->a0 - k * dmax);",
+     "double Cii = min2(s->a0 - k * dmin, s->a0 - k * dmax);"),
+    ("osc growth bound drops the radius", "double amax = fabs(cx[i]) + rx[i];", "double amax = fabs(cx[i]);"),
+    ("linear growth bound keeps the sign", "acc += ((j == i) ? a : fabs(a)) * r[j];", "acc += a * r[j];"),
+    ("mm inputs swapped", "c.s = s; c.p = wlo; c.ph = whi;", "c.s = s; c.p = whi; c.ph = wlo;"),
+    ("cgb center is the lower corner", "z[i] = (xlo[i] + xhi[i]) / 2.0;", "z[i] = xlo[i];"),
+    ("mc samples the input stream for x0", "orc_uniform(seed, j, i, 0u);", "orc_uniform(seed, j, i, 1u);"),
+    ("mc inputs not sampled", "p[k] = wlo[k] + (whi[k] - wlo[k]) * orc_uniform(seed, j, k, 1u);",
+     "p[k] = wlo[k];"),
+    ("philox multiplier", "0xD2511F53u", "0xD2511F55u"),
+    ("philox key schedule", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;"),
+    ("uniform uses 52 bits", "(bits >> 11) * 0x1.0p-53", "(bits >> 12) * 0x1.0p-52"),
+]
+
+
+@pytest.mark.parametrize("mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_mutation(mut, tmp_path):
+    name, old, new = mut
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    mutated = tmp_path / "oracle.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, REACH_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(HERE, "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"

@@ -1,0 +1,545 @@
+"""Pins of the FP64 oracle against facts other than itself.
+
+Each test checks the oracle against a closed form, an invariant, a published
+known-answer table, the defining inequalities of the paper's methods (Sec. 2.1)
+evaluated by brute force, or exhaustive sampling on tiny systems.  A dropped
+term, a wrong sign or index, a transposed operand or a wrong RK4 weight in
+``oracle/oracle.c`` makes at least one of them fail.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rk4_poly(Z):
+    """RK4 applied to y' = Z y / h gives y <- p(Z) y with p the degree-4 Taylor
+    polynomial of exp (Butcher, Numerical Methods for ODEs, Sec. 23)."""
+    Z = np.atleast_2d(Z)
+    I = np.eye(Z.shape[0])
+    return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+def rk4_input_poly(Z):
+    """For y' = A y + p with constant p, one RK4 step adds h * phi(hA) p with
+    phi(Z) = I + Z/2 + Z^2/6 + Z^3/24."""
+    Z = np.atleast_2d(Z)
+    I = np.eye(Z.shape[0])
+    return I + Z / 2 + Z @ Z / 6 + Z @ Z @ Z / 24
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v, 16) for v in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert O.philox4x32_10(r[0:4], r[4:6]) == tuple(r[6:10])
+
+
+def test_uniform_stream_properties():
+    u = np.array([O.uniform(7, j, i, 0) for j in range(200) for i in range(50)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert np.all(u * 2.0**53 == np.floor(u * 2.0**53))  # 53-bit grid
+    assert abs(u.mean() - 0.5) < 0.01
+    assert abs(u.var() - 1.0 / 12.0) < 0.005
+    # the tag, the sample index, the component index and the seed all change the draw
+    assert O.uniform(7, 3, 4, 0) != O.uniform(7, 3, 4, 1)
+    assert O.uniform(7, 3, 4, 0) != O.uniform(7, 4, 3, 0)
+    assert O.uniform(7, 3, 4, 0) != O.uniform(8, 3, 4, 0)
+    assert O.uniform(1 << 32, 0, 0, 0) != O.uniform(0, 0, 0, 0)
+    # all 53 bits are used: the lowest one is set about half the time
+    assert 0.45 < np.mean((u * 2.0**53).astype(np.int64) & 1) < 0.55
+
+
+def test_uniform_is_the_stated_conversion_of_philox():
+    # counter (i, j, tag, 0), key (seed mod 2^32, seed div 2^32), U = top 53 bits of w0:w1
+    seed, j, i, tag = (5 << 32) + 77, 12, 345, 1
+    w = O.philox4x32_10([i, j, tag, 0], [seed & 0xFFFFFFFF, seed >> 32])
+    assert O.uniform(seed, j, i, tag) == (((w[0] << 32) | w[1]) >> 11) * 2.0**-53
+
+
+def test_mc_sample_bound_values():
+    # Sec. 2.1 / Algorithm 4, m = ceil((2n/eps) ln(2n/delta)), evaluated by hand:
+    # 20 ln 20 = 59.91; 640 ln 3200 = 5165.38 (a base-10 log would give 2244)
+    assert O.mc_samples(1, 0.1, 0.1) == 60
+    assert O.mc_samples(16, 0.05, 0.01) == 5166
+
+
+def test_nsteps_reading():
+    assert O.nsteps(10.0, 0.01) == 1000
+    assert O.nsteps(0.05, 1e-4) == 500
+    assert O.nsteps(2.0, 0.01) == 200
+    assert O.nsteps(0.0, 0.1) == 0
+    for bad in [(1.0, 0.3), (1.0, 0.0), (1.0, -0.1), (float("nan"), 0.1), (-1.0, 0.1)]:
+        with pytest.raises(O.OracleError):
+            O.nsteps(*bad)
+
+
+# ------------------------------------------------------------------ RK4 (Algorithm 1, reading R1)
+@pytest.mark.parametrize("lam", [-1.3, 0.7, -20.0])
+def test_rk4_scalar_stability_polynomial(lam):
+    h, T = 0.05, 2.0
+    N = O.nsteps(T, h)
+    y = O.flow("linear", [1.0], [0.0], t_final=T, dt=h, A=[[lam]])
+    expect = rk4_poly(h * lam)[0, 0] ** N
+    assert y[0] == pytest.approx(expect, rel=1e-13)
+
+
+def test_rk4_exact_on_nilpotent_system():
+    # A^5 = 0 -> exp(hA) equals its degree-4 Taylor polynomial, so RK4 is exact
+    A = W.linear_nilpotent(5, seed=3)
+    x0 = np.array([0.3, -1.0, 2.0, 0.5, 1.5])
+    T = 1.7
+    y = O.flow("linear", x0, np.zeros(5), t_final=T, dt=0.1, A=A)
+    np.testing.assert_allclose(y, scipy.linalg.expm(A * T) @ x0, rtol=0, atol=1e-12)
+
+
+def test_rk4_fourth_order_convergence():
+    m = 3
+    x0 = np.array([0.4, -0.7, 0.9, 0.1, 0.0, -0.2])
+    w = np.array([0.01, -0.005, 0.0])
+    T = 2.0
+    ref = O.flow("osc", x0, w, t_final=T, dt=0.00125)
+    errs = [np.abs(O.flow("osc", x0, w, t_final=T, dt=h) - ref).max() for h in (0.04, 0.02, 0.01)]
+    assert 13.0 < errs[0] / errs[1] < 19.0
+    assert 13.0 < errs[1] / errs[2] < 19.0
+
+
+# ------------------------------------------------------------------ linear test system (C5)
+def _exact_linear_hull(A, lo, hi, plo, phi, T):
+    n = A.shape[0]
+    aug = np.zeros((2 * n, 2 * n))
+    aug[:n, :n] = A
+    aug[:n, n:] = np.eye(n)
+    E2 = scipy.linalg.expm(aug * T)
+    E, G = E2[:n, :n], E2[:n, n:]
+    Ep, Em = np.maximum(E, 0), np.minimum(E, 0)
+    Gp, Gm = np.maximum(G, 0), np.minimum(G, 0)
+    return Ep @ lo + Em @ hi + Gp @ plo + Gm @ phi, Ep @ hi + Em @ lo + Gp @ phi + Gm @ plo
+
+
+def _discrete_linear_hull(A, lo, hi, plo, phi, h, N):
+    """Exact reachable set of the RK4 map itself: x_N = P^N x0 + S p."""
+    n = A.shape[0]
+    P = rk4_poly(h * A)
+    Q = h * rk4_input_poly(h * A)
+    PN = np.linalg.matrix_power(P, N)
+    S = np.zeros((n, n))
+    Pk = np.eye(n)
+    for _ in range(N):
+        S += Pk @ Q
+        Pk = Pk @ P
+    Pp, Pm = np.maximum(PN, 0), np.minimum(PN, 0)
+    Sp, Sm = np.maximum(S, 0), np.minimum(S, 0)
+    return Pp @ lo + Pm @ hi + Sp @ plo + Sm @ phi, Pp @ hi + Pm @ lo + Sp @ phi + Sm @ plo
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_linear_metzler_matches_expm_hull(method):
+    n, T, h = 4, 1.0, 0.01
+    A = W.linear_metzler(n, seed=11)
+    lo, hi = W.random_box(n, seed=12)
+    plo, phi = W.random_box(n, seed=13, centre=(-0.2, 0.2), width=(0.0, 0.1))
+    glo, ghi = O.reach(method, "linear", lo, hi, plo, phi, t_final=T, dt=h, A=A)
+    elo, ehi = _exact_linear_hull(A, lo, hi, plo, phi, T)
+    np.testing.assert_allclose(glo, elo, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(ghi, ehi, rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_linear_metzler_equals_discrete_rk4_hull(method):
+    # P = p(hA) >= 0 elementwise when h max|a_ii| <= 1, so both bounds are the
+    # exact reachable set of the RK4 map
+    n, h, N = 4, 0.01, 150
+    A = W.linear_metzler(n, seed=21)
+    lo, hi = W.random_box(n, seed=22)
+    plo, phi = W.random_box(n, seed=23, centre=(-0.2, 0.2), width=(0.0, 0.1))
+    assert (rk4_poly(h * A) >= 0).all()
+    glo, ghi = O.reach(method, "linear", lo, hi, plo, phi, t_final=N * h, dt=h, A=A)
+    dlo, dhi = _discrete_linear_hull(A, lo, hi, plo, phi, h, N)
+    np.testing.assert_allclose(glo, dlo, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(ghi, dhi, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_linear_general_contains_discrete_hull(method):
+    n, h, N = 4, 0.02, 100
+    A = W.linear_general(n, seed=31)
+    assert (A - np.diag(np.diag(A)) < 0).any()  # not Metzler
+    lo, hi = W.random_box(n, seed=32)
+    plo, phi = W.random_box(n, seed=33, centre=(-0.2, 0.2), width=(0.0, 0.1))
+    glo, ghi = O.reach(method, "linear", lo, hi, plo, phi, t_final=N * h, dt=h, A=A)
+    dlo, dhi = _discrete_linear_hull(A, lo, hi, plo, phi, h, N)
+    assert (glo <= dlo + 1e-12).all() and (ghi >= dhi - 1e-12).all()
+
+
+# ------------------------------------------------------------------ traffic (Sec. 5.1, reading R6)
+def test_traffic_free_flow_fixed_point():
+    # x_i = 70, d = 35: every flux equals 35 (= v x < c, < w (xbar - x)), so x stays put
+    n = 9
+    x = np.full(n, 70.0)
+    assert np.all(O.rhs("traffic", x, [35.0]) == 0.0)
+    lo, hi = O.reach("mm", "traffic", x, x, [35.0], [35.0], t_final=3.0, dt=0.01)
+    assert np.all(lo == 70.0) and np.all(hi == 70.0)
+
+
+def test_traffic_mass_balance():
+    # Interior fluxes telescope: sum_i dx_i/dt = d - f_{n-1}.  While the last cell
+    # stays above c/v = 80 its outflow is the capacity 40, so the total density
+    # changes by exactly (d - 40) T; RK4 preserves this linear invariant.
+    n, T, h, d = 8, 2.0, 0.01, 35.0
+    x0 = np.full(n, 150.0)
+    plo, phi = O.reach_pipe("mm", "traffic", x0, x0, [d], [d], t_final=T, dt=h, every=1)
+    assert plo[:, -1].min() > 85.0
+    xT = O.flow("traffic", x0, [d], t_final=T, dt=h)
+    assert xT.sum() == pytest.approx(x0.sum() + (d - 40.0) * T, abs=1e-9)
+    assert np.all(plo[-1] == xT)
+
+
+def test_traffic_mm_is_corner_trajectories():
+    wl = W.traffic_small(16)
+    lo, hi = O.reach("mm", "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"],
+                     t_final=wl["t_final"], dt=wl["dt"])
+    flo = O.flow("traffic", wl["x_lo"], wl["w_lo"], t_final=wl["t_final"], dt=wl["dt"])
+    fhi = O.flow("traffic", wl["x_hi"], wl["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    assert np.array_equal(lo, flo) and np.array_equal(hi, fhi)
+    assert lo[0] == pytest.approx(83.333, abs=1e-3) and hi[0] == pytest.approx(236.667, abs=1e-3)
+
+
+def test_traffic_cgb_radius_closed_form():
+    # the traffic contraction matrix is constant, so the radius obeys the linear
+    # ODE r' = C r + [p]; with C read off g by unit probes the radius must match
+    # expm of that ODE (RK4 error O(h^4))
+    n, T, h = 6, 2.0, 0.01
+    c0 = np.linspace(60, 200, n)
+    C = np.column_stack([O.growth("traffic", c0, np.eye(n)[j], [0.0]) for j in range(n)])
+    hp = O.growth("traffic", c0, np.zeros(n), [1.0])
+    lo, hi = c0 - 3.0, c0 + 3.0
+    glo, ghi = O.reach("cgb", "traffic", lo, hi, [35.0], [45.0], t_final=T, dt=h)
+    aug = np.zeros((n + 1, n + 1))
+    aug[:n, :n] = C
+    aug[:n, n] = hp * 5.0
+    E = scipy.linalg.expm(aug * T)
+    r = E[:n, :n] @ np.full(n, 3.0) + E[:n, n]
+    np.testing.assert_allclose((ghi - glo) / 2, r, rtol=1e-9)
+
+
+# ------------------------------------------------------------------ KS grid (C8, C9)
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_ks_linear_part_fourier_symbol(k):
+    # -u_xx - u_xxxx by central differences has the symbol
+    # 4 sin^2(th/2)/dx^2 - 16 sin^4(th/2)/dx^4 on the mode cos(th i)
+    n, dx = 32, math.pi / 4
+    th = 2 * math.pi * k / n
+    u = np.cos(th * np.arange(n))
+    f = O.rhs("ks", u, params=(dx, 0.0, 1.0, 1.0))
+    lam = 4 * math.sin(th / 2) ** 2 / dx**2 - 16 * math.sin(th / 2) ** 4 / dx**4
+    np.testing.assert_allclose(f, lam * u, rtol=0, atol=1e-12)
+
+
+def test_ks_nonlinear_term_closed_form():
+    # -u u_x with u = sin(th i): -sin(th i) cos(th i) sin(th)/dx
+    n, dx, k = 24, 0.3, 2
+    th = 2 * math.pi * k / n
+    i = np.arange(n)
+    u = np.sin(th * i)
+    f = O.rhs("ks", u, params=(dx, 1.0, 0.0, 0.0))
+    np.testing.assert_allclose(f, -np.sin(th * i) * np.cos(th * i) * math.sin(th) / dx, atol=1e-13)
+
+
+def test_ks_mean_is_conserved():
+    n = 128
+    wl = W.ks_grid(n)
+    u0 = 0.5 * (wl["x_lo"] + wl["x_hi"])
+    uT = O.flow("ks", u0, t_final=0.05, dt=1e-4, params=wl["params"])
+    assert abs(uT.sum() - u0.sum()) < 1e-12 * n
+    assert np.abs(uT - u0).max() > 1e-5  # it did move
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_ks_shift_invariance(method):
+    n, k = 40, 7
+    wl = W.ks_grid(n, t_final=0.01)
+    a = O.reach(method, "ks", wl["x_lo"], wl["x_hi"], t_final=0.01, dt=1e-4, params=wl["params"])
+    b = O.reach(method, "ks", np.roll(wl["x_lo"], k), np.roll(wl["x_hi"], k), t_final=0.01,
+                dt=1e-4, params=wl["params"])
+    assert np.array_equal(np.roll(a[0], k), b[0]) and np.array_equal(np.roll(a[1], k), b[1])
+
+
+# ------------------------------------------------------------------ oscillator chain (C10)
+def _osc_as_linear(m, ka, kc):
+    n = 2 * m
+    A = np.zeros((n, n))
+    for i in range(m):
+        A[i, m + i] = 1.0
+        A[m + i, i] = -ka - 2 * kc
+        if i > 0:
+            A[m + i, i - 1] = kc
+        if i < m - 1:
+            A[m + i, i + 1] = kc
+    return A
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_osc_without_cubic_term_is_the_linear_chain(method):
+    m = 4
+    q = W.osc_query(m, seed=5, half_width=1e-2, t_final=2.0)
+    prm = (1.0, 0.0, 0.5)
+    wlo = np.concatenate([np.zeros(m), q["w_lo"]])
+    whi = np.concatenate([np.zeros(m), q["w_hi"]])
+    a = O.reach(method, "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=2.0,
+                dt=q["dt"], params=prm)
+    b = O.reach(method, "linear", q["x_lo"], q["x_hi"], wlo, whi, t_final=2.0, dt=q["dt"],
+                A=_osc_as_linear(m, 1.0, 0.5))
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ defining properties (Sec. 2.1)
+def _systems():
+    g = np.random.default_rng(99)
+    A = W.linear_general(5, seed=41)
+    return [
+        ("traffic", 6, None, None, lambda n: (g.uniform(0, 320, n), g.uniform(0, 30, n)), 1),
+        ("ks", 8, (math.pi / 4, 1.0, 1.0, 1.0), None,
+         lambda n: (g.uniform(-1, 1, n), g.uniform(0, 0.5, n)), 0),
+        ("osc", 6, None, None, lambda n: (g.uniform(-1.5, 1.5, n), g.uniform(0, 0.5, n)), 3),
+        ("linear", 5, None, A, lambda n: (g.uniform(-1, 1, n), g.uniform(0, 0.5, n)), 5),
+    ]
+
+
+@pytest.mark.parametrize("sysdef", _systems(), ids=lambda s: s[0])
+def test_decomposition_properties(sysdef):
+    kind, n, prm, A, draw, nw = sysdef
+    g = np.random.default_rng(7)
+    for trial in range(20):
+        c, hw = draw(n)
+        x, xh = c - hw, c + hw
+        p = g.uniform(30, 40, nw) if kind == "traffic" else g.uniform(-0.1, 0.0, nw)
+        ph = p + g.uniform(0, 0.05, nw)
+        kw = dict(params=prm, A=A)
+        # d(x, p, x, p) = f(x, p)
+        np.testing.assert_allclose(O.decomp(kind, x, p, x, p, **kw), O.rhs(kind, x, p, **kw),
+                                   rtol=1e-13, atol=1e-12)
+        d0 = O.decomp(kind, x, p, xh, ph, **kw)
+        u0 = O.decomp(kind, xh, ph, x, p, **kw)
+        # monotone in the off-diagonal arguments (finite increases, box kept ordered)
+        for j in range(n):
+            e = np.zeros(n)
+            e[j] = 0.5 * hw[j] + 1e-3
+            d1 = O.decomp(kind, x + e, p, xh + e, ph, **kw)
+            for i in range(n):
+                if i == j:
+                    continue
+                # raising x_j (lower argument) may not lower d_i(x, ., xh, .)
+                dx_only = O.decomp(kind, x + np.where(np.arange(n) == j, min(e[j], xh[j] - x[j]), 0),
+                                   p, xh, ph, **kw)
+                assert dx_only[i] >= d0[i] - 1e-12 * (1 + abs(d0[i]))
+                dxh_only = O.decomp(kind, x, p, xh + e, ph, **kw)
+                assert dxh_only[i] <= d0[i] + 1e-12 * (1 + abs(d0[i]))
+            del d1
+        # the decomposition bounds f over the box with the diagonal argument held
+        for _ in range(30):
+            y = x + g.random(n) * (xh - x)
+            q = p + g.random(nw) * (ph - p)
+            fy_lo = O.rhs(kind, np.where(np.eye(n, dtype=bool), x[:, None], y[None, :]).diagonal()
+                          if False else y, q, **kw)
+            for i in range(n):
+                yl = y.copy()
+                yl[i] = x[i]
+                yu = y.copy()
+                yu[i] = xh[i]
+                assert d0[i] <= O.rhs(kind, yl, q, **kw)[i] + 1e-12 * (1 + abs(d0[i]))
+                assert u0[i] >= O.rhs(kind, yu, q, **kw)[i] - 1e-12 * (1 + abs(u0[i]))
+            del fy_lo
+
+
+def _num_jacobian(kind, y, p, kw, eps=1e-6):
+    n = y.size
+    J = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = eps
+        J[:, j] = (O.rhs(kind, y + e, p, **kw) - O.rhs(kind, y - e, p, **kw)) / (2 * eps)
+    return J
+
+
+@pytest.mark.parametrize("sysdef", _systems(), ids=lambda s: s[0])
+def test_contraction_matrix_is_the_box_supremum(sysdef):
+    # Sec. 2.1: C_ii >= J_ii, C_ij >= |J_ij|.  Every Jacobian entry of these
+    # systems is affine or monotone in |x| on each coordinate, so its supremum
+    # over the box is attained at a corner: g(c, r) - [p] must equal
+    # sum_j sup_corners(J_ij) r_j, not merely exceed it.
+    kind, n, prm, A, draw, nw = sysdef
+    kw = dict(params=prm, A=A)
+    g = np.random.default_rng(5)
+    for trial in range(4):
+        c, r = draw(n)
+        if kind == "traffic":
+            c = g.uniform(20, 300, n)
+            r = g.uniform(0, 2, n)
+            p = np.array([40.0])
+        else:
+            p = np.zeros(nw)
+        corners = np.array(list(itertools.product([-1.0, 1.0], repeat=n)))
+        Csup = np.full((n, n), -np.inf)
+        for s in corners:
+            J = _num_jacobian(kind, c + s * r, p, kw)
+            Jb = np.abs(J)
+            Jb[np.diag_indices(n)] = J.diagonal()
+            Csup = np.maximum(Csup, Jb)
+        gr = O.growth(kind, c, r, np.zeros(max(nw, 0)), **kw)
+        expect = Csup @ r
+        if kind == "traffic":
+            # piecewise-linear fluxes: corners need not hit every regime; the
+            # constant C must dominate the sampled supremum
+            assert (gr >= expect - 1e-8).all()
+        else:
+            np.testing.assert_allclose(gr, expect, rtol=1e-7, atol=1e-7)
+
+
+def test_traffic_contraction_matrix_is_tight_over_all_states():
+    # random states in [0, 320] visit every regime of the min; the sampled
+    # supremum of the Jacobian then equals the constant bound exactly
+    n = 5
+    g = np.random.default_rng(3)
+    C = np.column_stack([O.growth("traffic", np.zeros(n), np.eye(n)[j], [0.0]) for j in range(n)])
+    Csup = np.full((n, n), -np.inf)
+    for _ in range(3000):
+        J = _num_jacobian("traffic", g.uniform(1, 319, n), np.array([40.0]), {}, eps=1e-7)
+        Jb = np.abs(J)
+        Jb[np.diag_indices(n)] = J.diagonal()
+        Csup = np.maximum(Csup, Jb)
+    np.testing.assert_allclose(C, Csup, atol=1e-6)
+
+
+# ------------------------------------------------------------------ brute force (C11)
+BRUTE = [
+    ("traffic", np.array([100.0, 110.0, 95.0]), np.array([110.0, 120.0, 100.0]),
+     np.array([35.0]), np.array([45.0]), 3.0, 0.01, None, None),
+    ("ks", np.array([0.1, -0.2, 0.3, 0.0]), np.array([0.15, -0.1, 0.35, 0.1]),
+     np.zeros(0), np.zeros(0), 0.1, 1e-3, (math.pi / 4, 1.0, 1.0, 1.0), None),
+    ("osc", np.array([0.5, -0.3, 0.0, 0.1]), np.array([0.52, -0.28, 0.02, 0.12]),
+     np.array([-0.01, -0.01]), np.array([0.01, 0.01]), 2.0, 0.005, None, None),
+    ("linear", np.array([-0.1, 0.2, 0.5]), np.array([0.1, 0.3, 0.6]),
+     np.array([-0.1, 0.0, 0.1]), np.array([0.1, 0.05, 0.1]), 1.5, 0.01, None,
+     W.linear_general(3, seed=51)),
+]
+
+
+@pytest.mark.parametrize("case", BRUTE, ids=lambda c: c[0])
+def test_brute_force_samples_inside_mm_and_cgb(case):
+    kind, lo, hi, wlo, whi, T, h, prm, A = case
+    kw = dict(params=prm, A=A)
+    n, nw = lo.size, wlo.size
+    mm = O.reach("mm", kind, lo, hi, wlo, whi, t_final=T, dt=h, **kw)
+    cg = O.reach("cgb", kind, lo, hi, wlo, whi, t_final=T, dt=h, **kw)
+    g = np.random.default_rng(17)
+    pts = [np.array(c) for c in itertools.product(*[np.linspace(0, 1, 4)] * n)]
+    pts += [g.random(n) for _ in range(300)]
+    worst = np.inf
+    for k, u in enumerate(pts):
+        x0 = lo + u * (hi - lo)
+        w = wlo + (g.random(nw) if k % 2 else (k // 2) % 2 * np.ones(nw)) * (whi - wlo)
+        xT = O.flow(kind, x0, w, t_final=T, dt=h, **kw)
+        for blo, bhi in (mm, cg):
+            worst = min(worst, (xT - blo).min(), (bhi - xT).min())
+    assert worst >= 0.0, f"a trajectory left the box by {-worst}"
+
+
+# ------------------------------------------------------------------ Monte Carlo (Algorithm 4)
+def test_mc_box_is_elementwise_min_max_of_samples():
+    wl = W.traffic_small(16)
+    lo, hi, fin = O.reach("mc", "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"],
+                          t_final=1.0, dt=0.01, m=64, seed=3, return_finals=True)
+    assert np.array_equal(lo, fin.min(axis=0)) and np.array_equal(hi, fin.max(axis=0))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_mc_samples_are_uniform_in_the_initial_box(prec):
+    n, m = 5, 4000
+    lo, hi = W.random_box(n, seed=61, width=(0.1, 1.0))
+    _, _, fin = O.reach("mc", "linear", lo, hi, np.zeros(n), np.zeros(n), t_final=0.0, dt=0.1,
+                        A=np.zeros((n, n)), m=m, seed=9, prec=prec, return_finals=True)
+    u = (fin - lo) / (hi - lo)
+    assert (u >= -1e-7).all() and (u < 1 + 1e-7).all()
+    assert np.abs(u.mean(axis=0) - 0.5).max() < 0.02
+    if prec == 32:
+        assert np.array_equal(fin, fin.astype(np.float32).astype(np.float64))
+    else:
+        j, i = 17, 3
+        assert fin[j, i] == lo[i] + (hi[i] - lo[i]) * O.uniform(9, j, i, 0)
+
+
+def test_mc_samples_the_inputs_too():
+    # reading R4: with A = 0 the final state is x0 + T p, which recovers every
+    # sampled input; they must follow the input stream (tag 1)
+    n, m, T = 3, 500, 2.0
+    lo, hi = np.zeros(n), np.zeros(n)
+    plo, phi = np.array([-1.0, 0.0, 2.0]), np.array([1.0, 0.5, 2.0])
+    _, _, fin = O.reach("mc", "linear", lo, hi, plo, phi, t_final=T, dt=0.5, A=np.zeros((n, n)),
+                        m=m, seed=4, return_finals=True)
+    p = fin / T
+    assert p[:, 0].min() < -0.9 and p[:, 0].max() > 0.9 and np.all(p[:, 2] == 2.0)
+    assert p[7, 1] == pytest.approx(0.5 * O.uniform(4, 7, 1, 1), rel=1e-14)
+
+
+def test_mc_inside_mm_traffic_config():
+    wl = W.traffic_small(16)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    kw = dict(t_final=wl["t_final"], dt=wl["dt"])
+    mlo, mhi = O.reach("mm", "traffic", *args, **kw)
+    clo, chi = O.reach("mc", "traffic", *args, **kw, m=1000, seed=0)
+    assert (clo >= mlo).all() and (chi <= mhi).all()
+
+
+# ------------------------------------------------------------------ degenerate boxes (C13)
+@pytest.mark.parametrize("kind", ["traffic", "ks", "osc", "linear"])
+def test_zero_width_box_is_one_trajectory(kind):
+    g = np.random.default_rng(2)
+    n = 6
+    prm = None
+    A = W.linear_general(n, seed=71) if kind == "linear" else None
+    if kind == "traffic":
+        x = g.uniform(50, 200, n)
+        w = np.array([40.0])
+    elif kind == "ks":
+        x = g.uniform(-0.5, 0.5, n)
+        w = np.zeros(0)
+    else:
+        x = g.uniform(-1, 1, n)
+        w = g.uniform(-0.01, 0.01, O.input_dim(kind, n))
+    kw = dict(t_final=0.5, dt=0.005, params=prm, A=A)
+    traj = O.flow(kind, x, w, **kw)
+    mlo, mhi = O.reach("mm", kind, x, x, w, w, **kw)
+    np.testing.assert_allclose(mlo, traj, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(mhi, traj, rtol=1e-12, atol=1e-12)
+    clo, chi = O.reach("cgb", kind, x, x, w, w, **kw)
+    assert np.array_equal(clo, traj) and np.array_equal(chi, traj)  # r stays exactly 0
+    slo, shi = O.reach("mc", kind, x, x, w, w, **kw, m=8, seed=1)
+    assert np.array_equal(slo, traj) and np.array_equal(shi, traj)
+
+
+# ------------------------------------------------------------------ reach pipe (Sec. 5.5)
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_pipe_rows_are_intermediate_boxes(method):
+    wl = W.traffic_small(8)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    plo, phi = O.reach_pipe(method, "traffic", *args, t_final=1.0, dt=0.01, every=25)
+    assert plo.shape == (4, 8)
+    for q in range(4):
+        lo, hi = O.reach(method, "traffic", *args, t_final=0.25 * (q + 1), dt=0.01)
+        np.testing.assert_allclose(plo[q], lo, rtol=1e-14)
+        np.testing.assert_allclose(phi[q], hi, rtol=1e-14)

@@ -1,0 +1,190 @@
+"""Seeded synthetic inputs for the interval-reachability workloads.
+
+This module only draws initial boxes, input boxes and query mixes from fixed
+seeds; it holds none of the reachability arithmetic.  Both the FP64 oracle
+(through the tests) and the CUDA library (through the tests and the benchmark)
+take their inputs from here, so both sides see bit-identical data.
+
+Workloads (all synthetic; the paper prints no datasets or reachable boxes):
+
+* traffic chain (Sec. 5.1 of the paper, cell transmission model): n=16 with
+  x0 in [100,120]^n, and n=2^26 with box centres 80 + 80 U_i, width 10;
+  inflow d in [35, 45], dt = 0.01.
+* Kuramoto-Sivashinsky periodic grid: spacing pi/4 (so 128 cells span one
+  32*pi period of the initial profile), u0(x) = 0.1 cos(x/16)(1 + sin(x/16))
+  +- 1e-3, dt = 1e-4, T = 0.05.
+* oscillator-chain queries: m log-uniform in [4, 4096], positions U[-1,1],
+  velocities 0, half-width 1e-4, disturbance w in [-0.01, 0.01], dt = 0.005,
+  T = 5.
+* linear test systems (Metzler, general, nilpotent).
+* a Poisson arrival trace mixing traffic and KS queries for the serving loop.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(seed))
+
+
+# ---------------------------------------------------------------- traffic
+TRAFFIC_DT = 0.01
+TRAFFIC_D = (35.0, 45.0)
+
+
+def traffic_small(n: int = 16):
+    """Traffic chain, n cells, x0 in [100, 120]^n, d in [35, 45], T = 10."""
+    return dict(kind="traffic", x_lo=np.full(n, 100.0), x_hi=np.full(n, 120.0),
+                w_lo=np.array([TRAFFIC_D[0]]), w_hi=np.array([TRAFFIC_D[1]]),
+                t_final=10.0, dt=TRAFFIC_DT)
+
+
+def traffic_large(n: int = 1 << 26, seed: int = 0, t_final: float = 2.0, half_width: float = 5.0):
+    """Traffic chain with box centres 80 + 80 U_i (U uniform from `seed`), width 10."""
+    u = _rng(seed).random(n)
+    c = 80.0 + 80.0 * u
+    return dict(kind="traffic", x_lo=c - half_width, x_hi=c + half_width,
+                w_lo=np.array([TRAFFIC_D[0]]), w_hi=np.array([TRAFFIC_D[1]]),
+                t_final=t_final, dt=TRAFFIC_DT)
+
+
+# ---------------------------------------------------------------- KS
+KS_DX = math.pi / 4.0
+KS_DT = 1e-4
+
+
+def ks_profile(n: int, dx: float = KS_DX) -> np.ndarray:
+    x = np.arange(n, dtype=np.float64) * dx
+    return 0.1 * np.cos(x / 16.0) * (1.0 + np.sin(x / 16.0))
+
+
+def ks_grid(n: int = 1 << 20, half_width: float = 1e-3, t_final: float = 0.05, dx: float = KS_DX):
+    u = ks_profile(n, dx)
+    return dict(kind="ks", x_lo=u - half_width, x_hi=u + half_width,
+                w_lo=np.zeros(0), w_hi=np.zeros(0), t_final=t_final, dt=KS_DT,
+                params=(dx, 1.0, 1.0, 1.0))
+
+
+# ---------------------------------------------------------------- oscillator chain
+OSC_DT = 0.005
+OSC_T = 5.0
+OSC_W = 0.01
+
+
+def osc_query(m: int, seed: int, half_width: float = 1e-4, t_final: float = OSC_T):
+    """One oscillator-chain query: state [x_1..x_m | v_1..v_m]."""
+    pos = _rng(seed).uniform(-1.0, 1.0, m)
+    c = np.concatenate([pos, np.zeros(m)])
+    return dict(kind="osc", x_lo=c - half_width, x_hi=c + half_width,
+                w_lo=np.full(m, -OSC_W), w_hi=np.full(m, OSC_W),
+                t_final=t_final, dt=OSC_DT)
+
+
+def osc_sizes(count: int = 4096, seed: int = 0, lo: int = 4, hi: int = 4096) -> np.ndarray:
+    """m_q log-uniform in [lo, hi], rounded to integers."""
+    u = _rng(seed).random(count)
+    return np.rint(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
+
+
+def osc_batch(count: int = 4096, seed: int = 0, t_final: float = OSC_T):
+    sizes = osc_sizes(count, seed)
+    return [osc_query(int(m), seed=1000003 * (seed + 1) + q, t_final=t_final)
+            for q, m in enumerate(sizes)]
+
+
+# ---------------------------------------------------------------- linear test systems
+def linear_metzler(n: int, seed: int, diag=(-2.0, -0.5), off=(0.0, 0.4)):
+    g = _rng(seed)
+    A = g.uniform(*off, (n, n))
+    A[np.diag_indices(n)] = g.uniform(*diag, n)
+    return A
+
+
+def linear_general(n: int, seed: int, scale: float = 0.6):
+    g = _rng(seed)
+    A = g.uniform(-scale, scale, (n, n))
+    A[np.diag_indices(n)] = g.uniform(-2.0, -0.5, n)
+    return A
+
+
+def linear_nilpotent(n: int, seed: int):
+    """Strictly upper-triangular A (A^n = 0)."""
+    g = _rng(seed)
+    return np.triu(g.uniform(-1.0, 1.0, (n, n)), k=1)
+
+
+def random_box(n: int, seed: int, centre=(-1.0, 1.0), width=(0.0, 0.2)):
+    g = _rng(seed)
+    c = g.uniform(*centre, n)
+    h = g.uniform(*width, n)
+    return c - h, c + h
+
+
+# ---------------------------------------------------------------- serving trace
+@dataclass
+class Query:
+    qid: int
+    arrival: float
+    kind: str
+    method: str
+    n: int
+    steps: int
+    x_lo: np.ndarray = field(repr=False)
+    x_hi: np.ndarray = field(repr=False)
+    w_lo: np.ndarray = field(repr=False)
+    w_hi: np.ndarray = field(repr=False)
+    dt: float = 0.0
+    params: tuple = ()
+    m: int = 0
+    prec: int = 64
+    seed: int = 0
+
+
+def _logu(g, lo, hi):
+    return math.exp(math.log(lo) + g.random() * (math.log(hi) - math.log(lo)))
+
+
+def serving_trace(count: int = 4000, rate: float = 2000.0, seed: int = 0,
+                  traffic_n=(100, 10_000_000), ks_k=(10, 20), steps=(100, 20000),
+                  mc_samples: int = 256, scale_steps: float = 1.0, max_n: int | None = None):
+    """Poisson arrivals at `rate` queries/s mixing traffic chains and KS grids.
+
+    Box width ~ logU[1e-4, 1e-1] * scale (100 for traffic, 0.1 for KS); method
+    uniform over MM / CGB / MC(256 samples, FP32); horizon logU[100, 20000]
+    RK4 steps (times `scale_steps`)."""
+    g = _rng(seed)
+    t = 0.0
+    out = []
+    for q in range(count):
+        t += g.exponential(1.0 / rate)
+        kind = "traffic" if g.random() < 0.5 else "ks"
+        method = ("mm", "cgb", "mc")[int(g.integers(0, 3))]
+        nsteps = max(1, int(round(_logu(g, *steps) * scale_steps)))
+        width = _logu(g, 1e-4, 1e-1)
+        if kind == "traffic":
+            n = int(round(_logu(g, *traffic_n)))
+            if max_n:
+                n = min(n, max_n)
+            c = 80.0 + 80.0 * g.random(n)
+            hw = 0.5 * width * 100.0
+            x_lo, x_hi = c - hw, c + hw
+            w_lo, w_hi = np.array([TRAFFIC_D[0]]), np.array([TRAFFIC_D[1]])
+            dt, params = TRAFFIC_DT, ()
+        else:
+            n = 1 << int(g.integers(ks_k[0], ks_k[1] + 1))
+            if max_n:
+                n = min(n, max_n)
+            u = ks_profile(n)
+            hw = 0.5 * width * 0.1
+            x_lo, x_hi = u - hw, u + hw
+            w_lo = w_hi = np.zeros(0)
+            dt, params = KS_DT, (KS_DX, 1.0, 1.0, 1.0)
+        out.append(Query(qid=q, arrival=t, kind=kind, method=method, n=n, steps=nsteps,
+                         x_lo=x_lo, x_hi=x_hi, w_lo=w_lo, w_hi=w_hi, dt=dt, params=params,
+                         m=mc_samples if method == "mc" else 0,
+                         prec=32 if method == "mc" else 64, seed=q))
+    return out
