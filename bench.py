@@ -1,0 +1,289 @@
+"""Benchmark: RK4 interval reachability on the 2^26-cell traffic chain.
+
+One step = one pass of the hot path over the workload: the mixed-monotonicity
+box (Algorithm 3) and the contraction/growth-bound box (Algorithm 2) of the
+traffic cell-transmission chain with n = 2^26 cells, x0 box centres
+80 + 80 U_i (seed 0) of width 10, inflow d in [35, 45], dt = 0.01, T = 2
+(200 RK4 steps each).  Metric: state-component RK4 updates per second
+(MM and CGB integrate 2n components each).
+
+  value  inputs resident in HBM (device tensors), CUDA events on the stream
+  e2e    the same through the public API with host (numpy) buffers: the
+         library's host->device copies and the result readback are inside
+         the timed region
+  roofline  the dominant kernel (stencil_rk4): FP64-pipe operations per
+         launch / its average launch time, against the FP64 issue rate of
+         148 SMs x 2 ops/clk x 2.032 GHz
+  cpu_baseline / --impl reference  the FP64 oracle on one host core, on the
+         first 2^20 cells of the same workload (full horizon)
+
+Multi-GPU: the path is run as independent replicas, one per rank (weak
+scaling); ranks meet only in a barrier and the max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_CELLS = 1 << 26
+T_FINAL, DT = 2.0, 0.01
+NSTEPS = 200
+# FP64 pipe operations per component-step of the fused kernel (add, mul and
+# fma each count one): traffic MM 19 (per cell-stage: v x, w (xbar - x'),
+# flux difference, stage input, accumulator; minus the first accumulator and
+# the last stage input, plus the final update); traffic CGB: center 19,
+# radius 15 (v r_l + w r_r is 2 per stage)
+FP64_OPS = {"mm": 19.0, "cgb": 17.0}
+SM_COUNT, FP64_PER_SM_CLK, SM_MAX_MHZ = 148, 2, 2032.0
+FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
+CPU_SAMPLE_CELLS = 1 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_oracle_rate(cells: int = CPU_SAMPLE_CELLS):
+    """The FP64 oracle (single thread) on the first `cells` cells, both methods."""
+    import oracle as O
+    wl = W.traffic_large(N_CELLS, seed=0) if cells == N_CELLS else None
+    if wl is None:
+        full = W.traffic_large(N_CELLS, seed=0)
+        wl = dict(full, x_lo=full["x_lo"][:cells].copy(), x_hi=full["x_hi"][:cells].copy())
+    t0 = time.perf_counter()
+    for method in ("mm", "cgb"):
+        O.reach(method, "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=T_FINAL, dt=DT)
+    sec = time.perf_counter() - t0
+    comp_steps = 2 * 2 * cells * NSTEPS
+    return comp_steps / sec, sec, comp_steps
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rates = []
+    for _ in range(max(args.warmup, 0)):
+        pass   # the oracle has no warm state; warm-up steps are not needed
+    for _ in range(args.steps):
+        r, sec, cs = cpu_oracle_rate()
+        rates.append(r)
+    value = statistics.median(rates)
+    sample = f"first {CPU_SAMPLE_CELLS} cells of the 2^26-cell chain, MM + CGB, 200 RK4 steps, per step"
+    line = {"metric": "state-component RK4 updates/s", "value": value, "unit": "comp-steps/s",
+            "impl": "reference", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "traffic chain n=2^26, MM+CGB, dt=0.01, T=2 (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "comp-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2001_10635_b300 as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = W.traffic_large(N_CELLS, seed=0)
+    dev = torch.device("cuda", local)
+    host = {k: np.ascontiguousarray(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    lo = torch.empty(N_CELLS, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    stream = torch.cuda.current_stream(dev)
+    sysm = R.System("traffic", N_CELLS)
+    R.reach_set_option(R.OPT_KERNEL, 0)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+
+    method_ms = {"mm": [], "cgb": []}
+
+    def step(record=False):
+        for method, fn in (("mm", R.reach_mm), ("cgb", R.reach_cgb)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(sysm, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=T_FINAL, dt=DT, lo=lo, hi=hi,
+               stream=stream)
+            e1.record(stream)
+            if record:
+                e1.synchronize()
+                method_ms[method].append(e0.elapsed_time(e1))
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    launches0 = R.reach_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = R.reach_kernel_launches() - launches0
+    ms = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    comp_steps = 2 * 2 * N_CELLS * NSTEPS * args.steps * world
+    value = comp_steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers
+    hlo = np.empty(N_CELLS)
+    hhi = np.empty(N_CELLS)
+    for _ in range(1):
+        R.reach_mm(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
+                   lo=hlo, hi=hhi)
+    barrier()
+    te = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 2))
+    for _ in range(e2e_steps):
+        R.reach_mm(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
+                   lo=hlo, hi=hhi)
+        R.reach_cgb(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
+                    lo=hlo, hi=hhi)
+    barrier()
+    e2e_sec = time.perf_counter() - te
+    if dist is not None:
+        tt = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_sec = float(tt.item())
+    e2e_value = 2 * 2 * N_CELLS * NSTEPS * e2e_steps * world / e2e_sec
+    h2d = 2 * (2 * N_CELLS + 2) * 8
+    d2h = 2 * 2 * N_CELLS * 8
+
+    # dominant kernel: the streaming RK4 kernel, 200 launches per call
+    per_launch_ms = {m: statistics.median(v) / NSTEPS for m, v in method_ms.items()}
+    ops = {m: FP64_OPS[m] * 2 * N_CELLS for m in method_ms}          # per launch
+    achieved = {m: ops[m] / (per_launch_ms[m] * 1e-3) for m in method_ms}
+    mm_achieved = achieved["mm"]
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    eff_gbs = 16.0 * value / world / 1e9
+    line = {
+        "metric": "state-component RK4 updates/s", "value": value, "unit": "comp-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "traffic chain n=2^26, MM + CGB, dt=0.01, T=2 (200 RK4 steps each)",
+                   "n": N_CELLS, "rk4_steps": NSTEPS, "methods": ["mm", "cgb"],
+                   "l2": "inputs larger than L2 (2 x 512 MiB state per call)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": mm_achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
+                     "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": None,
+                     "kernel": "stencil_rk4<traffic, MM>",
+                     "per_launch_ms": per_launch_ms, "fp64_ops_per_comp_step": FP64_OPS,
+                     "cgb_frac": achieved["cgb"] / FP64_PEAK_OPS,
+                     "peak_source": "148 SMs x 2 FP64 ops/clk x 2032 MHz (recipe nominal FP64 1.25 TFLOP/s)",
+                     "hbm_effective_gbs": eff_gbs, "hbm_frac_of_measured": eff_gbs / hbm},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, sec, cs = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {CPU_SAMPLE_CELLS} cells, MM + CGB, 200 steps ({sec:.1f} s)"}
+    sysm.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * reach.h -- C ABI of libreach.so, interval reachability on one B300 GPU.
+ *
+ * The library computes interval over-approximations (MM, CGB) and sampled
+ * approximations (MC) of the finite-time reachable set of dx/dt = f(x, p):
+ *
+ *     R = { Phi(t1; 0, x0, p) : x0 in [x0_lo, x0_hi], p in [w_lo, w_hi] }
+ *
+ * (Devonport, Khaled, Arcak, Zamani, "PIRK", 2020: Sec. 2 for the problem,
+ * Sec. 2.1 for the three methods, Algorithms 1-4 for their parallel form).
+ * Integration is fixed-step classic fourth-order Runge-Kutta (Algorithm 1
+ * read as RK4: stages at t, t+h/2, t+h/2, t+h with weights 1,2,2,1 / 6) with
+ * N = round(t_final/dt) steps of size dt from t0 = 0.  All arithmetic of MM
+ * and CGB is IEEE binary64; MC trajectories run in binary64 or binary32.
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument may be host memory (pageable or pinned) or CUDA
+ *     device memory of the current device; the library asks the driver which
+ *     (cudaPointerGetAttributes).  Host data is copied in and out by the
+ *     call.  All buffers stay owned by the caller.
+ *   - Vectors are dense, contiguous binary64 arrays.  A state vector has the
+ *     system's dimension n, an input vector its input dimension nw
+ *     (reach_input_dim).  Inputs are constant in time (Sec. 2).
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream).  Work is
+ *     ordered on that stream, and every computing reach_* call returns only
+ *     after its results are complete (it synchronises the stream), so that
+ *     it can report data-dependent errors.
+ *   - Return value: REACH_OK (0) or a negative REACH_E* code.  No C++
+ *     exception crosses the ABI.  On error the outputs are unspecified.
+ *   - Scratch memory comes from the device's stream-ordered memory pool
+ *     (cudaMallocAsync) and is returned before the call ends.
+ */
+#ifndef REACH_H
+#define REACH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define REACH_API __attribute__((visibility("default")))
+#else
+#define REACH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define REACH_OK 0
+#define REACH_EINVAL (-1)     /* bad argument: size, lo > hi, non-finite input,
+                                 dt <= 0, t_final/dt not an integer (within
+                                 1e-9 t_final), unknown kind or method */
+#define REACH_ENOMEM (-2)     /* device allocation failed */
+#define REACH_EADMIT (-3)     /* serving: query can never fit the HBM budget */
+#define REACH_ENONFINITE (-4) /* a result (or an MC sample) became NaN or Inf */
+#define REACH_ETIMEOUT (-5)   /* a bounded device or host wait ran out */
+#define REACH_ECUDA (-6)      /* a CUDA runtime call failed */
+#define REACH_ENODEV (-7)     /* no usable CUDA device */
+
+/* ---- built-in systems ---- */
+typedef enum {
+    /* Cell-transmission traffic chain (Sec. 5.1).  Cells i = 0..n-1, flux out
+       of cell i  f_i = min(cap, v x_i, w (xbar - x_{i+1})) for i < n-1,
+       f_{n-1} = min(cap, v x_{n-1}); inflow of cell 0 is the input d (nw = 1);
+       dx_i/dt = f_{i-1} - f_i.  Params: reach_traffic_params. */
+    REACH_TRAFFIC = 0,
+    /* Kuramoto-Sivashinsky u_t = -g_nl u u_x - g_2 u_xx - g_4 u_xxxx on a
+       periodic grid of n >= 5 points with spacing dx, second-order central
+       differences (3-point u_x, u_xx; 5-point u_xxxx).  nw = 0.
+       Params: reach_ks_params. */
+    REACH_KS = 1,
+    /* Chain of m = n/2 nonlinear oscillators, state [x_1..x_m | v_1..v_m]:
+       dx_i/dt = v_i, dv_i/dt = -ka x_i - kb x_i^3 + kc (x_{i-1} - 2 x_i +
+       x_{i+1}) + w_i with x_0 = x_{m+1} = 0.  nw = m.
+       Params: reach_osc_params. */
+    REACH_OSC = 2,
+    /* Dense linear test system dx/dt = A x + p, nw = n, n <= 256.
+       Params: reach_linear_params. */
+    REACH_LINEAR = 3
+} reach_kind;
+
+typedef struct { double cap, v, w, xbar; } reach_traffic_params;   /* 40, 0.5, 1/6, 320 */
+typedef struct { double dx, g_nl, g_2, g_4; } reach_ks_params;     /* pi/4, 1, 1, 1 */
+typedef struct { double ka, kb, kc; } reach_osc_params;            /* 1, 0.1, 0.5 */
+typedef struct { const double *A; } reach_linear_params;           /* n x n, row-major */
+
+typedef struct reach_system reach_system;   /* opaque; parameters live on the device */
+
+/* Create a system of dimension n.  `params` points to the kind's parameter
+   struct (params_bytes = its sizeof), or is NULL for the defaults noted
+   above (REACH_LINEAR requires params).  The parameters, including A, are
+   copied to the current device; the caller's buffers may be freed
+   afterwards.  REACH_EINVAL for n < 1, odd n with REACH_OSC, n < 5 with
+   REACH_KS, n > 256 with REACH_LINEAR, a wrong params_bytes or non-finite
+   params (traffic additionally needs v, w >= 0; KS dx > 0; osc kb >= 0). */
+REACH_API int reach_system_create(int kind, int64_t n, const void *params, size_t params_bytes,
+                        reach_system **out);
+REACH_API int reach_system_destroy(reach_system *sys);
+REACH_API int64_t reach_system_dim(const reach_system *sys);
+REACH_API int64_t reach_input_dim(const reach_system *sys);
+
+/* Mixed monotonicity (Sec. 2.1, Algorithm 3).  Integrates the embedding
+   system [x; xh]' = [d(x, p, xh, ph); d(xh, ph, x, p)] from
+   [x0_lo; x0_hi] with p = w_lo, ph = w_hi and returns [lo, hi] = [x(T), xh(T)].
+   The decomposition function d of each built-in system is the tight one:
+   cooperative traffic uses d = f; KS splits the linear stencil by coefficient
+   sign and bounds u_i u_x with u_i held at its own argument; the oscillator
+   feeds x_i into the v_i row through the hatted argument; linear splits
+   off-diagonal entries of A by sign.
+   x0_lo, x0_hi, lo, hi: n values.  w_lo, w_hi: nw values (may be NULL if
+   nw = 0).  lo/hi may not alias x0_lo/x0_hi. */
+REACH_API int reach_mm(const reach_system *sys, const double *x0_lo, const double *x0_hi,
+             const double *w_lo, const double *w_hi, double t_final, double dt,
+             double *lo, double *hi, void *stream);
+
+/* Contraction / growth bound (Sec. 2.1, Algorithm 2).  Integrates the
+   center c' = f(c, p*) and the radius r' = C(c, r) r + [p] as one coupled
+   2n-dimensional system from c = (x0_lo + x0_hi)/2, r = (x0_hi - x0_lo)/2,
+   p* = (w_lo + w_hi)/2, [p] = (w_hi - w_lo)/2 (entering as the input enters
+   f), and returns [lo, hi] = [c(T) - r(T), c(T) + r(T)].  C satisfies
+   C_ii >= J_ii and C_ij >= |J_ij|: a constant bound valid for every state
+   (traffic, linear) or the supremum of the Jacobian over the current stage
+   box [c - r, c + r] (KS, oscillator).  Arguments as reach_mm. */
+REACH_API int reach_cgb(const reach_system *sys, const double *x0_lo, const double *x0_hi,
+              const double *w_lo, const double *w_hi, double t_final, double dt,
+              double *lo, double *hi, void *stream);
+
+/* Monte Carlo (Sec. 2.1, Algorithm 4).  Draws m initial states and m input
+   vectors uniformly from the boxes with Philox4x32-10 (Salmon et al., SC'11):
+   for sample j and component i, counter (i, j, tag, 0) with tag 0 for the
+   state and 1 for the input, key (seed mod 2^32, seed div 2^32), and
+   U = ((w0 << 32 | w1) >> 11) 2^-53; x0_i = lo_i + (hi_i - lo_i) U computed in
+   binary64.  Each sample is integrated with RK4 in binary64 (precision = 64)
+   or, after rounding the sample to binary32, in binary32 (precision = 32).
+   Returns the elementwise minimum and maximum over the samples of the
+   final states, as binary64.  REACH_ENONFINITE if any sample trajectory
+   ends NaN or Inf.  1 <= m < 2^32. */
+REACH_API int reach_mc(const reach_system *sys, const double *x0_lo, const double *x0_hi,
+             const double *w_lo, const double *w_hi, double t_final, double dt,
+             int64_t m, uint64_t seed, int precision,
+             double *lo, double *hi, void *stream);
+
+/* Sample count for an (eps, delta) guarantee (Sec. 2.1):
+   m = ceil((2n/eps) ln(2n/delta)).  Returns REACH_EINVAL for n < 1 or
+   eps, delta outside (0, 1). */
+REACH_API int64_t reach_mc_samples(int64_t n, double eps, double delta);
+
+/* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
+#define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
+#define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming stencil: RK4 steps fused per launch, 1..8 */
+#define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
+REACH_API int reach_set_option(int key, int64_t value);
+REACH_API int64_t reach_get_option(int key);
+
+/* Human-readable name of a status code. */
+REACH_API const char *reach_strerror(int code);
+
+/* Number of kernels this library has launched in the process (benchmark
+   bookkeeping; a graph launch counts each kernel node it runs). */
+REACH_API int64_t reach_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REACH_H */

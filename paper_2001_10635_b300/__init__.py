@@ -1,0 +1,226 @@
+"""Interval reachability on one B300 GPU: Python binding of libreach.so.
+
+A thin ctypes layer over the C ABI declared in ``include/reach.h``; every
+function here has the name of the C entry point it calls and only marshals
+arguments.  All computation happens in the CUDA kernels of ``csrc/``.  Arrays
+may be numpy float64 arrays (host memory, copied by the library) or contiguous
+float64 CUDA tensors (device memory, used in place).
+
+Methods (Devonport, Khaled, Arcak, Zamani, "PIRK", 2020, Sec. 2.1):
+``reach_mm`` (mixed monotonicity, Algorithm 3), ``reach_cgb`` (contraction /
+growth bound, Algorithm 2), ``reach_mc`` (Monte Carlo, Algorithm 4), all over
+fixed-step RK4 (Algorithm 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libreach.so")
+
+TRAFFIC, KS, OSC, LINEAR = 0, 1, 2, 3
+KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR}
+OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK = 1, 2, 3
+STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
+          -4: "REACH_ENONFINITE", -5: "REACH_ETIMEOUT", -6: "REACH_ECUDA", -7: "REACH_ENODEV"}
+
+_lib = None
+
+
+class ReachError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(self.code, self.code)} ({strerror(self.code)})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libreach.so; there is no fallback when it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run python -m paper_2001_10635_b300.build")
+        try:   # share the CUDA runtime PyTorch loads, when it is present
+            import torch  # noqa: F401
+        except Exception:
+            pass
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.reach_system_create.argtypes = [ctypes.c_int, i64, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.reach_system_destroy.argtypes = [vp]
+        L.reach_system_dim.argtypes = [vp]
+        L.reach_system_dim.restype = i64
+        L.reach_input_dim.argtypes = [vp]
+        L.reach_input_dim.restype = i64
+        box = [vp, vp, vp, vp, vp, dbl, dbl]
+        L.reach_mm.argtypes = box + [vp, vp, vp]
+        L.reach_cgb.argtypes = box + [vp, vp, vp]
+        L.reach_mc.argtypes = box + [i64, ctypes.c_uint64, ctypes.c_int, vp, vp, vp]
+        L.reach_mc_samples.argtypes = [i64, dbl, dbl]
+        L.reach_mc_samples.restype = i64
+        L.reach_set_option.argtypes = [ctypes.c_int, i64]
+        L.reach_get_option.argtypes = [ctypes.c_int]
+        L.reach_get_option.restype = i64
+        L.reach_strerror.argtypes = [ctypes.c_int]
+        L.reach_strerror.restype = ctypes.c_char_p
+        L.reach_kernel_launches.restype = i64
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().reach_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise ReachError(rc, where)
+
+
+# ------------------------------------------------------------------ arrays
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, n: int, name: str):
+    """Address and keep-alive reference of a float64 contiguous vector."""
+    if a is None:
+        if n:
+            raise ValueError(f"{name} is required")
+        return None, None
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"{name}: need a contiguous float64 tensor of {n} values")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if arr.size != n:
+        raise ValueError(f"{name}: need {n} values, got {arr.size}")
+    return arr.ctypes.data, arr
+
+
+def _out(like, given, n: int, name: str):
+    if given is not None:
+        return given
+    if _is_torch(like):
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=like.device)
+    return np.empty(n, dtype=np.float64)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+# ------------------------------------------------------------------ systems
+class System:
+    """reach_system_create / reach_system_destroy."""
+
+    _PARAM_FIELDS = {TRAFFIC: 4, KS: 4, OSC: 3}
+
+    def __init__(self, kind, n: int, params=None, A=None):
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.handle = ctypes.c_void_p()
+        buf, nbytes = None, 0
+        if self.kind == LINEAR:
+            self._A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(n, n))
+            buf = (ctypes.c_void_p * 1)(self._A.ctypes.data)
+            nbytes = ctypes.sizeof(ctypes.c_void_p)
+        elif params is not None:
+            vals = [float(v) for v in params]
+            if len(vals) != self._PARAM_FIELDS[self.kind]:
+                raise ValueError("wrong number of parameters")
+            buf = (ctypes.c_double * len(vals))(*vals)
+            nbytes = ctypes.sizeof(buf)
+        rc = lib().reach_system_create(self.kind, int(n), ctypes.cast(buf, ctypes.c_void_p) if buf is not None
+                                       else None, nbytes, ctypes.byref(self.handle))
+        _check(rc, "reach_system_create")
+        self.n = int(lib().reach_system_dim(self.handle))
+        self.nw = int(lib().reach_input_dim(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().reach_system_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _box_args(sys: System, x0_lo, x0_hi, w_lo, w_hi):
+    a = _ptr(x0_lo, sys.n, "x0_lo")
+    b = _ptr(x0_hi, sys.n, "x0_hi")
+    c = _ptr(w_lo, sys.nw, "w_lo") if sys.nw else (None, None)
+    d = _ptr(w_hi, sys.nw, "w_hi") if sys.nw else (None, None)
+    return a, b, c, d
+
+
+def reach_mm(sys: System, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final: float, dt: float,
+             lo=None, hi=None, stream=None):
+    """Mixed-monotonicity box (Algorithm 3).  Returns (lo, hi)."""
+    a, b, c, d = _box_args(sys, x0_lo, x0_hi, w_lo, w_hi)
+    lo = _out(x0_lo, lo, sys.n, "lo")
+    hi = _out(x0_lo, hi, sys.n, "hi")
+    pl, _ = _ptr(lo, sys.n, "lo")
+    ph, _ = _ptr(hi, sys.n, "hi")
+    rc = lib().reach_mm(sys.handle, a[0], b[0], c[0], d[0], float(t_final), float(dt), pl, ph, _stream(stream))
+    _check(rc, "reach_mm")
+    return lo, hi
+
+
+def reach_cgb(sys: System, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final: float, dt: float,
+              lo=None, hi=None, stream=None):
+    """Contraction / growth-bound box (Algorithm 2).  Returns (lo, hi)."""
+    a, b, c, d = _box_args(sys, x0_lo, x0_hi, w_lo, w_hi)
+    lo = _out(x0_lo, lo, sys.n, "lo")
+    hi = _out(x0_lo, hi, sys.n, "hi")
+    pl, _ = _ptr(lo, sys.n, "lo")
+    ph, _ = _ptr(hi, sys.n, "hi")
+    rc = lib().reach_cgb(sys.handle, a[0], b[0], c[0], d[0], float(t_final), float(dt), pl, ph, _stream(stream))
+    _check(rc, "reach_cgb")
+    return lo, hi
+
+
+def reach_mc(sys: System, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final: float, dt: float, m: int,
+             seed: int = 0, precision: int = 64, lo=None, hi=None, stream=None):
+    """Monte Carlo box of m Philox samples (Algorithm 4).  Returns (lo, hi)."""
+    a, b, c, d = _box_args(sys, x0_lo, x0_hi, w_lo, w_hi)
+    lo = _out(x0_lo, lo, sys.n, "lo")
+    hi = _out(x0_lo, hi, sys.n, "hi")
+    pl, _ = _ptr(lo, sys.n, "lo")
+    ph, _ = _ptr(hi, sys.n, "hi")
+    rc = lib().reach_mc(sys.handle, a[0], b[0], c[0], d[0], float(t_final), float(dt), int(m),
+                        int(seed) & (2**64 - 1), int(precision), pl, ph, _stream(stream))
+    _check(rc, "reach_mc")
+    return lo, hi
+
+
+def reach_mc_samples(n: int, eps: float, delta: float) -> int:
+    return int(lib().reach_mc_samples(int(n), float(eps), float(delta)))
+
+
+def reach_set_option(key: int, value: int):
+    _check(lib().reach_set_option(int(key), int(value)), "reach_set_option")
+
+
+def reach_get_option(key: int) -> int:
+    return int(lib().reach_get_option(int(key)))
+
+
+def reach_kernel_launches() -> int:
+    return int(lib().reach_kernel_launches())

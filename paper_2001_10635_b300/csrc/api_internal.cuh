@@ -1,0 +1,64 @@
+// api_internal.cuh -- host-side internals shared by the ABI translation units.
+#pragma once
+
+#include "common.cuh"
+#include "onchip.cuh"
+
+struct reach_system {
+    int kind;
+    int64_t n, nw;
+    double prm[8];    // host copy of the device parameter block (not for linear)
+    double *dprm;     // device parameters (linear: A, n x n)
+};
+
+namespace reach {
+
+// per-call device staging: input copies, output buffers, scratch, status word
+struct Staging {
+    cudaStream_t st;
+    void *owned[16];
+    int nowned = 0;
+    double *back_dst[4];
+    double *back_src[4];
+    int64_t back_n[4];
+    int nback = 0;
+    int *status = nullptr;
+
+    explicit Staging(cudaStream_t s) : st(s) {}
+    ~Staging();
+    int in(const double *src, int64_t count, const double **dev);
+    int out(double *dst, int64_t count, double **dev);
+    int scratch(size_t bytes, void **dev);
+    int begin_status();
+    int finish();
+    void release();
+};
+
+int pool_init();
+int dalloc(void **p, size_t bytes, cudaStream_t st);
+void dfree(void *p, cudaStream_t st);
+bool is_device_ptr(const void *p);
+int nsteps(double t_final, double dt, int64_t *N);
+int check_host_box(const double *lo, const double *hi, int64_t count);
+int64_t opt_kernel();
+int64_t opt_steps();
+int64_t opt_block();
+
+// kernels
+int64_t onchip_smem_bytes(int64_t n, int64_t nw);
+int onchip_max_smem();
+int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st);
+int onchip_launch_batch(int kind, const void *items, const void *slots, const void *bins, int nbins,
+                        int *counter, int grid, size_t smem, cudaStream_t st);
+int onchip_batch_threads();
+size_t onchip_slot_bytes();
+size_t onchip_bin_bytes();
+size_t onchip_item_bytes();
+int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+                    double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
+                    int *status, cudaStream_t st);
+int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
+               double *hi, double *sA, double *sB, double h, int64_t N, int S, int *status,
+               cudaStream_t st);
+
+}  // namespace reach

@@ -1,0 +1,91 @@
+// common.cuh -- shared internals of libreach.so (device parameter blocks,
+// status plumbing, launch bookkeeping).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "reach.h"
+
+namespace reach {
+
+enum Method : int { MM = 0, CGB = 1 };
+
+// Per-kind parameters as the kernels see them: derived constants are
+// computed on the host once per call, never per element.
+struct TrafficK {
+    double cap, v, w, xbar;
+    double wxbar;        // w * xbar
+    double d_lo, d_hi;   // MM inputs (p, ph)
+    double d_c, d_r;     // CGB input center and half-width
+};
+
+struct KsK {
+    double a0, a1, a2;   // 5-point stencil of -g_2 u_xx - g_4 u_xxxx
+    double k;            // g_nl / (2 dx)
+};
+
+struct OscK {
+    double ka, kb, kc;
+};
+
+// bit flags written by kernels into a per-call status word
+enum : int {
+    ST_NONFINITE = 1,   // a result became NaN / Inf
+    ST_BADINPUT = 2,    // lo > hi or a non-finite input seen on the device
+    ST_NEGRADIUS = 4,   // CGB radius went negative (cannot happen for valid C)
+    ST_TIMEOUT = 8,     // a bounded wait ran out
+};
+
+// process-wide launch counter (bench bookkeeping); host side only
+void count_launch(int64_t k = 1);
+
+// map a cudaError_t into a status code
+int cuda_fail(cudaError_t e, const char *where);
+
+#define REACH_CUDA(call)                                               \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return ::reach::cuda_fail(e__, #call); \
+    } while (0)
+
+#define REACH_LAUNCHED(where)                                          \
+    do {                                                               \
+        ::reach::count_launch();                                       \
+        cudaError_t e__ = cudaPeekAtLastError();                       \
+        if (e__ != cudaSuccess) return ::reach::cuda_fail(e__, where); \
+    } while (0)
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the paper's
+// definition: 10 rounds of (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+// lo(M0 c0)) with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t a = c[0], b = c[2];
+        uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
+        uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
+        c[0] = hi_b ^ c[1] ^ k0;
+        c[1] = lo_b;
+        c[2] = hi_a ^ c[3] ^ k1;
+        c[3] = lo_a;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// uniform double in [0,1) for (sample j, component i, tag) under `seed`:
+// counter (i, j, tag, 0), key (seed lo, seed hi), top 53 bits of w0:w1
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint32_t j, uint32_t i, uint32_t tag) {
+    uint32_t c[4] = {i, j, tag, 0u};
+    philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    uint64_t bits = ((uint64_t)c[0] << 32) | c[1];
+    return (double)(bits >> 11) * 0x1.0p-53;
+}
+
+// sample lo + (hi - lo) U without contraction, exactly as the definition reads
+__device__ __forceinline__ double box_sample(double lo, double hi, double u) {
+    return __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), u));
+}
+
+}  // namespace reach

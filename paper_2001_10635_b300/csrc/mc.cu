@@ -1,0 +1,489 @@
+// mc.cu -- Monte Carlo reachability (Sec. 2.1, Algorithm 4).
+//
+// Samples are drawn on the device with Philox4x32-10 (common.cuh) and
+// integrated with RK4 in binary64 or binary32.  Lane = sample: a warp holds 32
+// samples of the same components, so the stencil never crosses lanes and the
+// final per-component minimum / maximum over samples is a warp shuffle.
+//   mc_onchip : small n, one block = 32 samples x the whole state, all N steps
+//               in shared memory.
+//   mc_stream : large stencil systems; state in HBM, sample-fastest layout
+//               x[i * M + j]; one launch per RK4 step over tiles of 32 samples x
+//               TC components plus a 4R-cell halo; sampling fused into the first
+//               launch and the min/max into the last.
+// Per-block partial minima / maxima are combined by mc_reduce (no atomics, so
+// the result does not depend on scheduling).
+#include <cmath>
+
+#include "api_internal.cuh"
+
+namespace reach {
+
+constexpr int MC_WARPS = 16;            // warps per block
+constexpr int MC_THREADS = 32 * MC_WARPS;
+constexpr int MC_Q = 8;                 // component rows per thread (on-chip)
+
+// ------------------------------------------------------------------ plain f
+// Y: rows of 32 samples (row c at Y + 32 c), P: input rows.  `g` is the
+// global component of row c; rows c +- R exist in Y (halo or wrapped).
+template <int SYS, class T>
+struct Plain;
+
+template <class T>
+struct Plain<REACH_TRAFFIC, T> {
+    static constexpr int R = 1;
+    // flux out of global cell g given its row value y and right neighbour yr
+    static __device__ __forceinline__ T flux(const T *q, T y, T yr, int64_t g, int64_t n, T d) {
+        T f = fmin(q[0], fmin(q[1] * y, fma(-q[2], yr, q[3])));
+        T fl = fmin(q[0], q[1] * y);
+        f = (g == n - 1) ? fl : f;
+        f = (g == -1) ? d : f;
+        f = (g < -1 || g >= n) ? T(0) : f;
+        return f;
+    }
+    template <class Row>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t g, int64_t n, const T *P, int lane) {
+        T d = P[lane];
+        T fin = flux(q, row(c - 1), row(c), g - 1, n, d);
+        T fout = flux(q, row(c), row(c + 1), g, n, d);
+        return fin - fout;
+    }
+};
+
+template <class T>
+struct Plain<REACH_KS, T> {
+    static constexpr int R = 2;
+    template <class Row>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
+        T um2 = row(c - 2), um1 = row(c - 1), u = row(c), up1 = row(c + 1), up2 = row(c + 2);
+        T lin = fma(q[2], um2 + up2, fma(q[1], um1 + up1, q[0] * u));
+        return fma(-q[3] * u, up1 - um1, lin);
+    }
+};
+
+template <class T>
+struct Plain<REACH_OSC, T> {
+    static constexpr int R = 0;
+    // whole state on chip: rows 0..m-1 positions, m..2m-1 velocities
+    template <class Row>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t n, const T *P, int lane) {
+        const int m = (int)(n >> 1);
+        if (c < m) return row(m + c);
+        const int j = c - m;
+        T z = row(j);
+        T xl = (j > 0) ? row(j - 1) : T(0), xr = (j < m - 1) ? row(j + 1) : T(0);
+        T t = fma(q[1] * z, z, q[0]);
+        T r = fma(q[2], fma(T(-2), z, xl + xr), P[j * 32 + lane]);
+        return fma(-t, z, r);
+    }
+};
+
+template <class T>
+struct Plain<REACH_LINEAR, T> {
+    static constexpr int R = 0;
+    template <class Row>
+    static __device__ __forceinline__ T rhs(const T *, Row row, int c, int64_t, int64_t n, const T *P, int lane,
+                                            const double *A) {
+        T acc = T(0);
+        const double *Ar = A + (int64_t)c * n;
+        for (int j = 0; j < (int)n; ++j) acc = fma((T)__ldg(Ar + j), row(j), acc);
+        return acc + P[c * 32 + lane];
+    }
+};
+
+template <int SYS, class T>
+__device__ __forceinline__ void mc_consts(const double *prm, T (&q)[4]) {
+    q[0] = q[1] = q[2] = q[3] = T(0);
+    if (SYS == REACH_TRAFFIC) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)(prm[2] * prm[3]); }
+    if (SYS == REACH_KS) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)prm[3]; }
+    if (SYS == REACH_OSC) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; }
+}
+
+// sample value rounded to the run precision (binary32 runs start from the
+// binary64 sample rounded to nearest)
+template <class T>
+__device__ __forceinline__ T as_run(double v) { return (T)v; }
+
+// warp min / max over the valid lanes of one component row; lane 0 writes
+template <class T>
+__device__ __forceinline__ void warp_minmax(T v, bool valid, double *plo, double *phi, int *status) {
+    double a = valid ? (double)v : INFINITY, b = valid ? (double)v : -INFINITY;
+    bool bad = valid && !isfinite((double)v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+    if ((threadIdx.x & 31) == 0) { *plo = a; *phi = b; }
+}
+
+struct McArgs {
+    int64_t n, nw, m, N;
+    double h;
+    uint64_t seed;
+    const double *xlo, *xhi, *wlo, *whi, *prm;
+    double *plo, *phi;   // partials [block][n]
+    int *status;
+};
+
+// ------------------------------------------------------------------ on-chip
+template <int SYS, class T>
+__global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
+    extern __shared__ unsigned char smraw[];
+    T *Y = (T *)smraw;                    // [n][32]
+    T *P = Y + a.n * 32;                  // [nw][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;   // sample
+    const bool valid = j < a.m;
+    const int n = (int)a.n;
+    T q[4];
+    mc_consts<SYS, T>(a.prm, q);
+    int flags = 0;
+
+    for (int k = warp; k < (int)a.nw; k += MC_WARPS) {
+        double lo = a.wlo[k], hi = a.whi[k];
+        if (lane == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+        P[k * 32 + lane] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)k, 1u)));
+    }
+    T z[MC_Q], acc[MC_Q], kk[MC_Q];
+#pragma unroll
+    for (int s = 0; s < MC_Q; ++s) {
+        int c = warp + s * MC_WARPS;
+        z[s] = acc[s] = T(0);
+        if (c < n) {
+            double lo = a.xlo[c], hi = a.xhi[c];
+            if (lane == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+            z[s] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)c, 0u)));
+            Y[c * 32 + lane] = z[s];
+        }
+    }
+    __syncthreads();
+    const bool wrap = (SYS == REACH_KS);
+    auto row = [&](int c) -> T {
+        if (wrap) c = c < 0 ? c + n : (c >= n ? c - n : c);
+        else if (c < 0 || c >= n) return T(0);
+        return Y[c * 32 + lane];
+    };
+    const T h = (T)a.h, hh = (T)(0.5 * a.h), h6 = (T)(a.h / 6.0);
+    for (int64_t step = 0; step < a.N; ++step) {
+#pragma unroll 1
+        for (int stage = 0; stage < 4; ++stage) {
+#pragma unroll
+            for (int s = 0; s < MC_Q; ++s) {
+                int c = warp + s * MC_WARPS;
+                if (c < n) {
+                    if constexpr (SYS == REACH_LINEAR)
+                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, P, lane, a.prm);
+                    else
+                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, P, lane);
+                }
+            }
+            __syncthreads();
+            const T cst = (stage == 2) ? h : hh;
+#pragma unroll
+            for (int s = 0; s < MC_Q; ++s) {
+                int c = warp + s * MC_WARPS;
+                if (c < n) {
+                    T y;
+                    if (stage == 0) acc[s] = kk[s];
+                    else if (stage < 3) acc[s] = fma(T(2), kk[s], acc[s]);
+                    else acc[s] += kk[s];
+                    if (stage < 3) y = fma(cst, kk[s], z[s]);
+                    else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
+                    Y[c * 32 + lane] = y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < MC_Q; ++s) {
+        int c = warp + s * MC_WARPS;
+        if (c < n) warp_minmax<T>(z[s], valid, a.plo + blockIdx.x * a.n + c, a.phi + blockIdx.x * a.n + c, a.status);
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// ------------------------------------------------------------------ streaming
+struct McStep {
+    int64_t n, M, m;          // M: padded sample count (row stride)
+    int TC, H;                // owned rows per tile, halo rows per side
+    double h;
+    uint64_t seed;
+    const double *xlo, *xhi;  // first launch: the initial box
+    double dlo, dhi;          // traffic inflow box
+    const void *in;           // state (T) of the previous launch
+    void *out;
+    double *plo, *phi;        // last launch: partials [sample block][n]
+    int first, last;
+    int step;                 // 1: advance one RK4 step, 0: only sample (t_final = 0)
+    int *status;
+};
+
+template <int SYS, class T, int TCMAX>
+__global__ void __launch_bounds__(MC_THREADS) mc_stream(McStep a, const double *__restrict__ prm) {
+    extern __shared__ unsigned char smraw[];
+    constexpr int R = Plain<SYS, T>::R;
+    const int rows = a.TC + 2 * a.H;
+    T *Y = (T *)smraw;                                    // [rows][32]
+    T *K = Y + rows * 32;                                 // [rows][32]
+    __shared__ T Pd[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ntile = (a.n + a.TC - 1) / a.TC;
+    const int64_t nsb = a.M / 32;
+    const int64_t tile = blockIdx.x % ntile, sb = blockIdx.x / ntile;
+    if (sb >= nsb) return;
+    const int64_t j = sb * 32 + lane;
+    const bool valid = j < a.m;
+    const int64_t n = a.n;
+    const int64_t i0 = tile * a.TC - a.H;   // global component of row 0
+    T q[4];
+    mc_consts<SYS, T>(prm, q);
+    int flags = 0;
+    if (warp == 0) {
+        double d = (SYS == REACH_TRAFFIC) ? box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j, 0u, 1u)) : 0.0;
+        Pd[lane] = as_run<T>(d);
+    }
+    for (int c = warp; c < rows; c += MC_WARPS) {
+        int64_t g = i0 + c;
+        int64_t gi = g;
+        bool in = true;
+        if (SYS == REACH_KS) gi = ((g % n) + n) % n;
+        else in = g >= 0 && g < n;
+        T v = T(0);
+        if (in) {
+            if (a.first) {
+                double lo = a.xlo[gi], hi = a.xhi[gi];
+                if (lane == 0 && c >= a.H && c < a.H + a.TC && !(lo <= hi && isfinite(lo) && isfinite(hi)))
+                    flags |= ST_BADINPUT;
+                v = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)gi, 0u)));
+            } else {
+                v = ((const T *)a.in)[gi * a.M + j];
+            }
+        }
+        Y[c * 32 + lane] = v;
+    }
+    __syncthreads();
+    // z and acc for this thread's rows
+    constexpr int QS = (TCMAX + 2 * 4 * R + MC_WARPS - 1) / MC_WARPS;
+    T z[QS], acc[QS];
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+        int c = warp + s * MC_WARPS;
+        z[s] = (c < rows) ? Y[c * 32 + lane] : T(0);
+        acc[s] = T(0);
+    }
+    auto row = [&](int c) -> T { return (c >= 0 && c < rows) ? Y[c * 32 + lane] : T(0); };
+    const T h = (T)a.h, hh = (T)(0.5 * a.h), h6 = (T)(a.h / 6.0);
+#pragma unroll 1
+    for (int stage = 0; stage < 4 * a.step; ++stage) {
+#pragma unroll
+        for (int s = 0; s < QS; ++s) {
+            int c = warp + s * MC_WARPS;
+            if (c < rows) K[c * 32 + lane] = Plain<SYS, T>::rhs(q, row, c, i0 + c, n, Pd, lane);
+        }
+        __syncthreads();
+        const T cst = (stage == 2) ? h : hh;
+#pragma unroll
+        for (int s = 0; s < QS; ++s) {
+            int c = warp + s * MC_WARPS;
+            if (c < rows) {
+                T k = K[c * 32 + lane], y;
+                if (stage == 0) acc[s] = k;
+                else if (stage < 3) acc[s] = fma(T(2), k, acc[s]);
+                else acc[s] += k;
+                if (stage < 3) y = fma(cst, k, z[s]);
+                else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
+                Y[c * 32 + lane] = y;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+        int c = warp + s * MC_WARPS;
+        int64_t g = i0 + c;
+        if (c < a.H || c >= a.H + a.TC || g >= n) continue;
+        if (a.last) warp_minmax<T>(z[s], valid, a.plo + sb * n + g, a.phi + sb * n + g, a.status);
+        else ((T *)a.out)[g * a.M + j] = z[s];
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// ------------------------------------------------------------------ reduce
+__global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, int64_t n, double *lo,
+                          double *hi) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = INFINITY, b = -INFINITY;
+        for (int64_t k = 0; k < nblk; ++k) {
+            a = fmin(a, plo[k * n + i]);
+            b = fmax(b, phi[k * n + i]);
+        }
+        lo[i] = a;
+        hi[i] = b;
+    }
+}
+
+// ------------------------------------------------------------------ host
+template <int SYS, class T>
+static int launch_onchip(const McArgs &a, cudaStream_t st) {
+    int64_t nblk = (a.m + 31) / 32;
+    size_t smem = (size_t)(a.n + a.nw) * 32 * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        REACH_CUDA(cudaFuncSetAttribute(mc_onchip<SYS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        onchip_max_smem()));
+        attr = true;
+    }
+    mc_onchip<SYS, T><<<(unsigned)nblk, MC_THREADS, smem, st>>>(a);
+    REACH_LAUNCHED("mc_onchip");
+    return REACH_OK;
+}
+
+constexpr int MC_TC = 256;
+
+template <int SYS, class T>
+static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
+    constexpr int R = Plain<SYS, T>::R;
+    a.TC = MC_TC;
+    a.H = 4 * R;
+    int rows = a.TC + 2 * a.H;
+    size_t smem = (size_t)rows * 32 * sizeof(T) * 2;
+    static bool attr = false;
+    if (!attr) {
+        REACH_CUDA(cudaFuncSetAttribute(mc_stream<SYS, T, MC_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        onchip_max_smem()));
+        attr = true;
+    }
+    int64_t ntile = (a.n + a.TC - 1) / a.TC;
+    int64_t grid = ntile * (a.M / 32);
+    if (grid > 0x7fffffffLL) return REACH_EINVAL;
+    void *buf[2] = {bufA, bufB};
+    const int64_t L = N > 0 ? N : 1;
+    for (int64_t s = 0; s < L; ++s) {
+        a.first = (s == 0);
+        a.last = (s == L - 1);
+        a.step = N > 0;
+        a.in = buf[s % 2];
+        a.out = buf[(s + 1) % 2];
+        mc_stream<SYS, T, MC_TC><<<(unsigned)grid, MC_THREADS, smem, st>>>(a, prm);
+        REACH_LAUNCHED("mc_stream");
+    }
+    return REACH_OK;
+}
+
+int64_t mc_onchip_limit(int kind, int prec) {
+    // rows per thread x warps, and shared memory for [n + nw][32]
+    int64_t by_regs = (int64_t)MC_Q * MC_WARPS;
+    int64_t elt = prec == 32 ? 4 : 8;
+    int64_t smem = onchip_max_smem();
+    int64_t by_smem = smem / (32 * elt);   // n + nw rows
+    if (kind == REACH_OSC) by_smem = by_smem * 2 / 3;        // nw = n / 2
+    if (kind == REACH_LINEAR || kind == REACH_TRAFFIC) by_smem = by_smem - 1;
+    if (kind == REACH_LINEAR) by_smem /= 2;
+    return by_regs < by_smem ? by_regs : by_smem;
+}
+
+}  // namespace reach
+
+using namespace reach;
+
+template <class T>
+static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base, double *dlo, double *dhi,
+                       double wl, double wh) {
+    const int64_t n = sys->n;
+    int rc;
+    bool onchip = n <= mc_onchip_limit(sys->kind, sizeof(T) == 4 ? 32 : 64);
+    if (opt_kernel() == 1 && (sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS) && n >= 16) onchip = false;
+    if (!onchip && !(sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS)) return REACH_EINVAL;
+    int64_t nblk = (base.m + 31) / 32;
+    McArgs a = base;
+    if ((rc = sg.scratch(2 * nblk * n * sizeof(double), (void **)&a.plo))) return rc;
+    a.phi = a.plo + nblk * n;
+    if (onchip) {
+        switch (sys->kind) {
+        case REACH_TRAFFIC: rc = launch_onchip<REACH_TRAFFIC, T>(a, sg.st); break;
+        case REACH_KS: rc = launch_onchip<REACH_KS, T>(a, sg.st); break;
+        case REACH_OSC: rc = launch_onchip<REACH_OSC, T>(a, sg.st); break;
+        default: rc = launch_onchip<REACH_LINEAR, T>(a, sg.st); break;
+        }
+    } else {
+        McStep s;
+        memset(&s, 0, sizeof s);
+        s.n = n;
+        s.m = base.m;
+        s.M = nblk * 32;
+        s.h = base.h;
+        s.seed = base.seed;
+        s.xlo = base.xlo;
+        s.xhi = base.xhi;
+        s.dlo = wl;
+        s.dhi = wh;
+        s.plo = a.plo;
+        s.phi = a.phi;
+        s.status = base.status;
+        void *bufA = nullptr, *bufB = nullptr;
+        if (base.N > 1) {
+            if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufA))) return rc;
+            if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufB))) return rc;
+        }
+        if (sys->kind == REACH_TRAFFIC) rc = launch_stream<REACH_TRAFFIC, T>(s, base.prm, base.N, bufA, bufB, sg.st);
+        else rc = launch_stream<REACH_KS, T>(s, base.prm, base.N, bufA, bufB, sg.st);
+    }
+    if (rc) return rc;
+    int64_t g = (n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    mc_reduce<<<(unsigned)g, 256, 0, sg.st>>>(a.plo, a.phi, nblk, n, dlo, dhi);
+    REACH_LAUNCHED("mc_reduce");
+    return REACH_OK;
+}
+
+extern "C" int reach_mc(const reach_system *sys, const double *x0_lo, const double *x0_hi, const double *w_lo,
+                        const double *w_hi, double t_final, double dt, int64_t m, uint64_t seed, int precision,
+                        double *lo, double *hi, void *stream) {
+    if (!sys || !x0_lo || !x0_hi || !lo || !hi) return REACH_EINVAL;
+    if (sys->nw > 0 && (!w_lo || !w_hi)) return REACH_EINVAL;
+    if (m < 1 || m >= (1LL << 32) || (precision != 32 && precision != 64)) return REACH_EINVAL;
+    int64_t N;
+    int rc = nsteps(t_final, dt, &N);
+    if (rc) return rc;
+    if ((rc = check_host_box(x0_lo, x0_hi, sys->n))) return rc;
+    if ((rc = check_host_box(w_lo, w_hi, sys->nw))) return rc;
+    const int64_t n = sys->n;
+    if (n >= (1LL << 32)) return REACH_EINVAL;
+
+    Staging sg((cudaStream_t)stream);
+    const double *dxlo, *dxhi, *dwlo = nullptr, *dwhi = nullptr;
+    double *dlo, *dhi;
+    if ((rc = sg.in(x0_lo, n, &dxlo)) || (rc = sg.in(x0_hi, n, &dxhi)) || (rc = sg.in(w_lo, sys->nw, &dwlo)) ||
+        (rc = sg.in(w_hi, sys->nw, &dwhi)) || (rc = sg.out(lo, n, &dlo)) || (rc = sg.out(hi, n, &dhi)) ||
+        (rc = sg.begin_status()))
+        return rc;
+    double wl = 0, wh = 0;
+    if (sys->kind == REACH_TRAFFIC) {
+        if (is_device_ptr(w_lo)) {
+            REACH_CUDA(cudaMemcpyAsync(&wl, w_lo, sizeof(double), cudaMemcpyDeviceToHost, sg.st));
+            REACH_CUDA(cudaMemcpyAsync(&wh, w_hi, sizeof(double), cudaMemcpyDeviceToHost, sg.st));
+            REACH_CUDA(cudaStreamSynchronize(sg.st));
+        } else {
+            wl = w_lo[0];
+            wh = w_hi[0];
+        }
+        if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;
+    }
+    McArgs a;
+    a.n = n;
+    a.nw = sys->nw;
+    a.m = m;
+    a.N = N;
+    a.h = dt;
+    a.seed = seed;
+    a.xlo = dxlo; a.xhi = dxhi; a.wlo = dwlo; a.whi = dwhi;
+    a.prm = sys->dprm;
+    a.status = sg.status;
+    a.plo = a.phi = nullptr;
+    rc = (precision == 64) ? mc_dispatch<double>(sys, sg, a, dlo, dhi, wl, wh)
+                           : mc_dispatch<float>(sys, sg, a, dlo, dhi, wl, wh);
+    if (rc) return rc;
+    return sg.finish();
+}

@@ -1,0 +1,254 @@
+// onchip.cuh -- whole-horizon RK4 of one MM / CGB problem by one thread group
+// with the stage vector in shared memory (small and medium n).
+//
+// The group's threads own components c = cbeg + gt, cbeg + gt + gs, ...; the
+// RK4 state z and the stage accumulator live in their registers, the stage
+// input y (both halves) in shared memory, and all N steps run without leaving
+// the SM: two group barriers per stage (all k computed from y, then y
+// rewritten), no global traffic between the first load and the final store.
+// The same device code serves one problem per block (reach_mm / reach_cgb on
+// small systems) and many problems per block in the batched persistent kernel.
+#pragma once
+
+#include "common.cuh"
+
+namespace reach {
+
+constexpr int QMAX = 16;   // components per thread
+
+struct OnItem {
+    int64_t n, nw;
+    int kind, method;
+    const double *xlo, *xhi, *wlo, *whi;
+    double *lo, *hi;
+    const double *prm;     // device parameters of the system (linear: A, n x n)
+    int64_t N;
+    double h;
+    int *status;
+};
+
+// group barrier: a warp syncs itself, a larger group uses a named barrier
+struct GroupSync {
+    int bar, nthreads;
+    __device__ __forceinline__ void operator()() const {
+        if (nthreads <= 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+    }
+};
+
+// ---- per-component right-hand sides.  yA / yB: the two halves of the
+// embedding (MM: x, xh) or of the center/radius system (CGB: c, r); wA / wB:
+// the inputs (MM: w_lo, w_hi; CGB: center, half-width of the input box).
+
+__device__ __forceinline__ double tr_flux_out(const double *y, int64_t i, int64_t n, double cap,
+                                              double v, double w, double wxbar) {
+    return (i == n - 1) ? fmin(cap, v * y[i]) : fmin(cap, fmin(v * y[i], fma(-w, y[i + 1], wxbar)));
+}
+
+template <int SYS, int METHOD>
+__device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double *__restrict__ yA,
+                                             const double *__restrict__ yB, const double *wA,
+                                             const double *wB, const double *prm, const double (&q)[8]) {
+    const bool upper = c >= n;
+    const int64_t i = upper ? c - n : c;
+    if constexpr (SYS == REACH_TRAFFIC) {
+        // q: cap, v, w, wxbar
+        if (METHOD == MM || !upper) {
+            const double *y = upper ? yB : yA;
+            double d = upper ? wB[0] : wA[0];
+            double fin = (i == 0) ? d : tr_flux_out(y, i - 1, n, q[0], q[1], q[2], q[3]);
+            return fin - tr_flux_out(y, i, n, q[0], q[1], q[2], q[3]);
+        } else {
+            double left = (i > 0) ? yB[i - 1] : 0.0;
+            double right = (i < n - 1) ? yB[i + 1] : 0.0;
+            double v = fma(q[1], left, q[2] * right);
+            return (i == 0) ? v + wB[0] : v;
+        }
+    } else if constexpr (SYS == REACH_KS) {
+        // q: a0, a1, a2, k
+        const int64_t im1 = i == 0 ? n - 1 : i - 1, ip1 = i == n - 1 ? 0 : i + 1;
+        const int64_t im2 = i < 2 ? i + n - 2 : i - 2, ip2 = i >= n - 2 ? i + 2 - n : i + 2;
+        const double a0 = q[0], a1 = q[1], a2 = q[2], k = q[3];
+        if constexpr (METHOD == MM) {
+            const double *Y = upper ? yB : yA, *O = upper ? yA : yB;   // own / other half
+            const bool s1 = a1 >= 0.0, s2 = a2 >= 0.0;
+            double l1 = (s1 ? Y[im1] : O[im1]) + (s1 ? Y[ip1] : O[ip1]);
+            double l2 = (s2 ? Y[im2] : O[im2]) + (s2 ? Y[ip2] : O[ip2]);
+            double lin = fma(a2, l2, fma(a1, l1, a0 * Y[i]));
+            double da = Y[ip1] - O[im1], db = O[ip1] - Y[im1];
+            double qq = -k * Y[i];
+            double ea = qq * da, eb = qq * db;
+            return lin + ((da <= db) ? fmin(ea, eb) : fmax(ea, eb));
+        } else {
+            double dc = yA[ip1] - yA[im1];
+            if (!upper) {
+                double lin = fma(a2, yA[im2] + yA[ip2], fma(a1, yA[im1] + yA[ip1], a0 * yA[i]));
+                return fma(-k * yA[i], dc, lin);
+            }
+            double sr = yB[ip1] + yB[im1];
+            double cii = fmax(fma(-k, dc - sr, a0), fma(-k, dc + sr, a0));
+            double t = k * yA[i], u = fabs(k * yB[i]);
+            double cip = fabs(a1 - t) + u, cim = fabs(a1 + t) + u;
+            return fma(fabs(a2), yB[im2] + yB[ip2], fma(cip, yB[ip1], fma(cim, yB[im1], cii * yB[i])));
+        }
+    } else if constexpr (SYS == REACH_OSC) {
+        // q: ka, kb, kc, ka + 2 kc, 3 kb, |kc|;  state [x_1..x_m | v_1..v_m]
+        const int64_t m = n >> 1;
+        if constexpr (METHOD == MM) {
+            const double *Y = upper ? yB : yA, *O = upper ? yA : yB;
+            if (i < m) return Y[m + i];
+            const int64_t j = i - m;
+            double z = O[j];   // x_j enters the v_j row through the hatted argument
+            double xl = (j > 0) ? Y[j - 1] : 0.0, xr = (j < m - 1) ? Y[j + 1] : 0.0;
+            double w = upper ? wB[j] : wA[j];
+            double t = fma(q[1] * z, z, q[0]);                 // ka + kb z^2
+            double r = fma(q[2], fma(-2.0, z, xl + xr), w);    // kc (xl - 2z + xr) + w
+            return fma(-t, z, r);
+        } else {
+            if (!upper) {
+                if (i < m) return yA[m + i];
+                const int64_t j = i - m;
+                double z = yA[j];
+                double xl = (j > 0) ? yA[j - 1] : 0.0, xr = (j < m - 1) ? yA[j + 1] : 0.0;
+                double t = fma(q[1] * z, z, q[0]);
+                double r = fma(q[2], fma(-2.0, z, xl + xr), wA[j]);
+                return fma(-t, z, r);
+            }
+            if (i < m) return yB[m + i];
+            const int64_t j = i - m;
+            double ax = fabs(yA[j]) + yB[j];
+            double cxx = fma(q[4] * ax, ax, q[3]);   // ka + 2kc + 3 kb (|c| + r)^2
+            double rl = (j > 0) ? yB[j - 1] : 0.0, rr = (j < m - 1) ? yB[j + 1] : 0.0;
+            return fma(cxx, yB[j], fma(q[5], rl + rr, wB[j]));
+        }
+    } else {   // REACH_LINEAR, prm = A row-major
+        const double *Arow = prm + i * n;
+        double acc = 0.0;
+        if constexpr (METHOD == MM) {
+            const double *Y = upper ? yB : yA, *O = upper ? yA : yB;
+            for (int64_t j = 0; j < n; ++j) {
+                double a = __ldg(Arow + j);
+                double v = (j == i || a >= 0.0) ? Y[j] : O[j];
+                acc = fma(a, v, acc);
+            }
+            return acc + (upper ? wB[i] : wA[i]);
+        } else {
+            if (!upper) {
+                for (int64_t j = 0; j < n; ++j) acc = fma(__ldg(Arow + j), yA[j], acc);
+                return acc + wA[i];
+            }
+            for (int64_t j = 0; j < n; ++j) {
+                double a = __ldg(Arow + j);
+                acc = fma(j == i ? a : fabs(a), yB[j], acc);
+            }
+            return acc + wB[i];
+        }
+    }
+}
+
+template <int SYS>
+__device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) q[t] = 0.0;
+    if constexpr (SYS == REACH_TRAFFIC) {
+        q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2]; q[3] = prm[2] * prm[3];
+    } else if constexpr (SYS == REACH_KS) {
+        q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2]; q[3] = prm[3];
+    } else if constexpr (SYS == REACH_OSC) {
+        q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2];
+        q[3] = prm[0] + 2.0 * prm[2]; q[4] = 3.0 * prm[1]; q[5] = fabs(prm[2]);
+    }
+}
+
+// Integrate one problem.  yA, yB: n doubles each of shared memory (may live in
+// different blocks of a cluster); wA, wB: nw doubles each; kb: cend - cbeg
+// doubles holding this group's stage derivatives.  The calling
+// threads own components [cbeg, cend) with stride gs starting at cbeg + gt.
+template <int SYS, int METHOD, class Sync>
+__device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA, double *wB,
+                           double *kb, int64_t cbeg, int64_t cend, int gt, int gs, const Sync &sync) {
+    const int64_t n = it.n;
+    double q[8];
+    load_consts<SYS>(it.prm, q);
+    int flags = 0;
+
+    // inputs: MM takes (w_lo, w_hi), CGB (center, half-width)
+    if (cbeg == 0) {
+        for (int64_t k = gt; k < it.nw; k += gs) {
+            double lo = it.wlo[k], hi = it.whi[k];
+            if (!(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+            wA[k] = (METHOD == CGB) ? 0.5 * (lo + hi) : lo;
+        }
+    }
+    if (cend == 2 * n) {
+        for (int64_t k = gt; k < it.nw; k += gs) {
+            double lo = it.wlo[k], hi = it.whi[k];
+            wB[k] = (METHOD == CGB) ? 0.5 * (hi - lo) : hi;
+        }
+    }
+
+    double z[QMAX], acc[QMAX];
+#pragma unroll
+    for (int s = 0; s < QMAX; ++s) {
+        int64_t c = cbeg + gt + (int64_t)s * gs;
+        z[s] = 0.0;
+        acc[s] = 0.0;
+        if (c < cend) {
+            int64_t i = c < n ? c : c - n;
+            double lo = it.xlo[i], hi = it.xhi[i];
+            if (c < n && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+            double v;
+            if (METHOD == CGB) v = (c < n) ? 0.5 * (lo + hi) : 0.5 * (hi - lo);
+            else v = (c < n) ? lo : hi;
+            z[s] = v;
+            (c < n ? yA[c] : yB[c - n]) = v;
+        }
+    }
+    sync();
+
+    const double h = it.h, hh = 0.5 * it.h, h6 = it.h / 6.0;
+    for (int64_t step = 0; step < it.N; ++step) {
+#pragma unroll 1
+        for (int stage = 0; stage < 4; ++stage) {
+#pragma unroll
+            for (int s = 0; s < QMAX; ++s) {
+                int64_t c = cbeg + gt + (int64_t)s * gs;
+                if (c < cend) kb[c - cbeg] = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
+            }
+            sync();
+            const double cst = (stage == 2) ? h : hh;
+#pragma unroll
+            for (int s = 0; s < QMAX; ++s) {
+                int64_t c = cbeg + gt + (int64_t)s * gs;
+                if (c < cend) {
+                    double y, k = kb[c - cbeg];
+                    if (stage == 0) acc[s] = k;
+                    else if (stage < 3) acc[s] = fma(2.0, k, acc[s]);
+                    else acc[s] += k;
+                    if (stage < 3) y = fma(cst, k, z[s]);
+                    else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
+                    (c < n ? yA[c] : yB[c - n]) = y;
+                }
+            }
+            sync();
+        }
+    }
+
+    // y holds the final state of both halves
+    for (int64_t c = cbeg + gt; c < cend; c += gs) {
+        if (c >= n) continue;
+        double a = yA[c], b = yB[c];
+        double lo = a, hi = b;
+        if (METHOD == CGB) {
+            if (b < 0.0) flags |= ST_NEGRADIUS;
+            lo = a - b;
+            hi = a + b;
+        }
+        if (!isfinite(lo) || !isfinite(hi)) flags |= ST_NONFINITE;
+        it.lo[c] = lo;
+        it.hi[c] = hi;
+    }
+    if (flags) atomicOr(it.status, flags);
+}
+
+}  // namespace reach

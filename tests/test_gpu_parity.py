@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small and ragged sizes are compared element by element on both kernels (the
+on-chip whole-horizon kernel and the streaming stencil kernel, forced through
+REACH_OPT_KERNEL), with several steps per launch; the full-size workloads of
+the benchmark are compared on sampled cells, each recomputed by the oracle on a
+window wider than its RK4 domain of dependence (4 R cells per step and side),
+which makes the window's own boundary irrelevant to that cell.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2001_10635_b300 as R
+import workloads as W
+from reachtest import TOL32, TOL64, assert_close, cuda_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(autouse=True)
+def _reset_options():
+    yield
+    R.reach_set_option(R.OPT_KERNEL, 0)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+    R.reach_set_option(R.OPT_BLOCK, 0)
+
+
+def gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=None, A=None, **kw):
+    with R.System(kind, n, params=params, A=A) as s:
+        if method == "mm":
+            return R.reach_mm(s, lo, hi, wlo, whi, t_final=T, dt=dt)
+        if method == "cgb":
+            return R.reach_cgb(s, lo, hi, wlo, whi, t_final=T, dt=dt)
+        return R.reach_mc(s, lo, hi, wlo, whi, t_final=T, dt=dt, **kw)
+
+
+def problem(kind, n, seed=0):
+    """(lo, hi, wlo, whi, T, dt, params, A) of a small test problem."""
+    g = np.random.default_rng(seed)
+    if kind == "traffic":
+        c = g.uniform(60, 200, n)
+        return c - 4, c + 4, np.array([35.0]), np.array([45.0]), 1.0, 0.01, None, None
+    if kind == "ks":
+        u = W.ks_profile(n) + g.uniform(-0.01, 0.01, n)
+        return u - 1e-3, u + 1e-3, None, None, 0.01, 1e-4, None, None
+    if kind == "osc":
+        m = n // 2
+        q = W.osc_query(m, seed=seed, half_width=1e-3, t_final=1.0)
+        return q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], 1.0, 0.005, None, None
+    A = W.linear_general(n, seed=seed, scale=0.5)
+    lo, hi = W.random_box(n, seed=seed + 1)
+    plo, phi = W.random_box(n, seed=seed + 2, centre=(-0.1, 0.1), width=(0.0, 0.05))
+    return lo, hi, plo, phi, 1.0, 0.01, None, A
+
+
+SMALL = [("traffic", 1), ("traffic", 2), ("traffic", 16), ("traffic", 37), ("ks", 5), ("ks", 64),
+         ("ks", 200), ("osc", 2), ("osc", 8), ("osc", 302), ("linear", 1), ("linear", 7), ("linear", 64)]
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("kind,n", SMALL, ids=[f"{k}{n}" for k, n in SMALL])
+def test_onchip_matches_oracle(method, kind, n):
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=n)
+    olo, ohi = O.reach(method, kind, lo, hi, wlo, whi, t_final=T, dt=dt, params=prm, A=A)
+    glo, ghi = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm, A=A)
+    assert_close(glo, olo, TOL64, f"{method} {kind} lo")
+    assert_close(ghi, ohi, TOL64, f"{method} {kind} hi")
+
+
+STREAM = [("traffic", 300, 1), ("traffic", 1000, 3), ("traffic", 4097, 1), ("traffic", 4097, 2),
+          ("ks", 256, 1), ("ks", 777, 2), ("ks", 3001, 1)]
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("kind,n,S", STREAM, ids=[f"{k}{n}S{s}" for k, n, s in STREAM])
+def test_streaming_kernel_matches_oracle(method, kind, n, S):
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=n)
+    T = 0.37 if kind == "traffic" else 0.005   # 37 / 50 steps: ragged against S
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    olo, ohi = O.reach(method, kind, lo, hi, wlo, whi, t_final=T, dt=dt, params=prm)
+    glo, ghi = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm)
+    assert_close(glo, olo, TOL64, f"{method} {kind} lo")
+    assert_close(ghi, ohi, TOL64, f"{method} {kind} hi")
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_large_onchip_traffic_matches_oracle(method):
+    lo, hi, wlo, whi, T, dt, prm, A = problem("traffic", 4000, seed=3)
+    R.reach_set_option(R.OPT_KERNEL, 2)
+    olo, ohi = O.reach(method, "traffic", lo, hi, wlo, whi, t_final=0.2, dt=dt)
+    glo, ghi = gpu_box(method, "traffic", 4000, lo, hi, wlo, whi, 0.2, dt)
+    assert_close(glo, olo, TOL64, "lo")
+    assert_close(ghi, ohi, TOL64, "hi")
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    lo, hi, wlo, whi, T, dt, _, _ = problem("traffic", 5000, seed=9)
+    with R.System("traffic", 5000) as s:
+        a = R.reach_mm(s, lo, hi, wlo, whi, t_final=0.5, dt=dt)
+        d = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in (lo, hi, wlo, whi)]
+        b = R.reach_mm(s, *d, t_final=0.5, dt=dt)
+        torch.cuda.synchronize()
+    assert np.array_equal(a[0], b[0].cpu().numpy()) and np.array_equal(a[1], b[1].cpu().numpy())
+
+
+# ------------------------------------------------------------------ traffic, n = 16 (BASELINE config 0)
+def test_traffic16_all_methods():
+    wl = W.traffic_small(16)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    kw = dict(t_final=wl["t_final"], dt=wl["dt"])
+    boxes = {}
+    for method in ("mm", "cgb"):
+        o = O.reach(method, "traffic", *args, **kw)
+        g = gpu_box(method, "traffic", 16, *args, wl["t_final"], wl["dt"])
+        assert_close(g[0], o[0], TOL64, method)
+        assert_close(g[1], o[1], TOL64, method)
+        boxes[method] = g
+    for prec, tol in ((64, TOL64), (32, TOL32)):
+        o = O.reach("mc", "traffic", *args, **kw, m=1000, seed=0, prec=prec)
+        g = gpu_box("mc", "traffic", 16, *args, wl["t_final"], wl["dt"], m=1000, seed=0, precision=prec)
+        assert_close(g[0], o[0], tol, f"mc{prec} lo")
+        assert_close(g[1], o[1], tol, f"mc{prec} hi")
+        if prec == 64:   # every sample inside the MM and CGB boxes, exactly
+            for b in boxes.values():
+                assert (g[0] >= b[0]).all() and (g[1] <= b[1]).all()
+
+
+# ------------------------------------------------------------------ Monte Carlo
+MC = [("traffic", 5, 33, 64), ("traffic", 40, 70, 32), ("ks", 64, 70, 64), ("ks", 64, 70, 32),
+      ("osc", 8, 100, 64), ("osc", 40, 45, 32), ("linear", 5, 33, 64), ("linear", 12, 1, 32)]
+
+
+@pytest.mark.parametrize("kind,n,m,prec", MC, ids=[f"{k}{n}m{m}p{p}" for k, n, m, p in MC])
+def test_mc_onchip_matches_oracle(kind, n, m, prec):
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=7)
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, A=A, m=m, seed=11, prec=prec)
+    g = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, A=A, m=m, seed=11, precision=prec)
+    tol = TOL64 if prec == 64 else TOL32
+    assert_close(g[0], o[0], tol, "lo")
+    assert_close(g[1], o[1], tol, "hi")
+
+
+MCS = [("traffic", 700, 70, 64), ("traffic", 300, 33, 32), ("ks", 600, 40, 64), ("ks", 513, 65, 32)]
+
+
+@pytest.mark.parametrize("kind,n,m,prec", MCS, ids=[f"{k}{n}m{m}p{p}" for k, n, m, p in MCS])
+def test_mc_streaming_matches_oracle(kind, n, m, prec):
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=5)
+    T = 0.13 if kind == "traffic" else 0.003
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, m=m, seed=3, prec=prec)
+    g = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=3, precision=prec)
+    tol = TOL64 if prec == 64 else TOL32
+    assert_close(g[0], o[0], tol, "lo")
+    assert_close(g[1], o[1], tol, "hi")
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("method", ["mm", "cgb", "mc"])
+def test_zero_horizon_returns_the_box(method):
+    lo, hi, wlo, whi, T, dt, _, _ = problem("traffic", 50)
+    kw = dict(m=5) if method == "mc" else {}
+    g = gpu_box(method, "traffic", 50, lo, hi, wlo, whi, 0.0, dt, **kw)
+    if method == "mc":
+        assert (g[0] >= lo).all() and (g[1] <= hi).all()
+    else:
+        assert np.array_equal(g[0], lo) and np.array_equal(g[1], hi)
+
+
+@pytest.mark.parametrize("kind", ["traffic", "ks", "osc", "linear"])
+def test_zero_width_box_is_one_trajectory(kind):
+    n = 6 if kind != "ks" else 16
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=1)
+    x = 0.5 * (lo + hi)
+    w = None if wlo is None else 0.5 * (wlo + whi)
+    traj = O.flow(kind, x, w, t_final=T, dt=dt, A=A)
+    for method in ("mm", "cgb"):
+        g = gpu_box(method, kind, n, x, x, w, w, T, dt, A=A)
+        assert_close(g[0], traj, TOL64, method)
+        assert_close(g[1], traj, TOL64, method)
+    g = gpu_box("mc", kind, n, x, x, w, w, T, dt, A=A, m=40)
+    assert_close(g[0], traj, TOL64, "mc")
+    assert np.array_equal(g[0], g[1])
+
+
+def test_invalid_arguments_are_rejected():
+    lo, hi, wlo, whi, T, dt, _, _ = problem("traffic", 20)
+    with R.System("traffic", 20) as s:
+        bad = [dict(t_final=1.0, dt=0.0), dict(t_final=1.0, dt=0.3), dict(t_final=-1.0, dt=0.1),
+               dict(t_final=float("nan"), dt=0.1)]
+        for kw in bad:
+            with pytest.raises(R.ReachError) as e:
+                R.reach_mm(s, lo, hi, wlo, whi, **kw)
+            assert e.value.code == -1
+        with pytest.raises(R.ReachError):
+            R.reach_mm(s, hi, lo, wlo, whi, t_final=T, dt=dt)   # lo > hi
+        with pytest.raises(R.ReachError):
+            R.reach_cgb(s, lo, hi, whi, wlo, t_final=T, dt=dt)  # input lo > hi
+        nan = lo.copy()
+        nan[3] = np.nan
+        with pytest.raises(R.ReachError):
+            R.reach_mm(s, nan, hi, wlo, whi, t_final=T, dt=dt)
+        for kw in (dict(m=0), dict(m=5, precision=16)):
+            with pytest.raises(R.ReachError):
+                R.reach_mc(s, lo, hi, wlo, whi, t_final=T, dt=dt, **kw)
+    for args in [("osc", 5), ("ks", 3), ("traffic", 0)]:
+        with pytest.raises(R.ReachError):
+            R.System(*args)
+
+
+def test_device_side_input_check():
+    import torch
+    lo, hi, wlo, whi, T, dt, _, _ = problem("traffic", 3000)
+    d = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in (hi, lo, wlo, whi)]   # swapped
+    with R.System("traffic", 3000) as s:
+        for f in (R.reach_mm, R.reach_cgb):
+            with pytest.raises(R.ReachError) as e:
+                f(s, *d, t_final=T, dt=dt)
+            assert e.value.code == -1
+
+
+def test_nonfinite_result_is_reported():
+    n = 16
+    lo, hi = np.full(n, -10.0), np.full(n, 10.0)
+    with pytest.raises(O.OracleError):
+        O.reach("mm", "ks", lo, hi, t_final=2.0, dt=1e-3)
+    with R.System("ks", n) as s:
+        with pytest.raises(R.ReachError) as e:
+            R.reach_mm(s, lo, hi, t_final=2.0, dt=1e-3)
+    assert e.value.code == -4
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled
+def _window(i, n, radius_cells):
+    a = max(0, i - radius_cells)
+    b = min(n, i + radius_cells + 1)
+    return a, b
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_traffic_full_size_sampled_cells(method):
+    wl = W.traffic_large(1 << 26, seed=0)
+    n, T, dt = 1 << 26, wl["t_final"], wl["dt"]
+    N = O.nsteps(T, dt)
+    g = gpu_box(method, "traffic", n, wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], T, dt)
+    assert np.isfinite(g[0]).all() and np.isfinite(g[1]).all() and (g[0] <= g[1]).all()
+    cells = [0, 1, 5, 4 * N, 12345678, n // 2 + 17, n - 4 * N - 3, n - 2, n - 1]
+    for i in cells:
+        a, b = _window(i, n, 4 * N + 2)
+        olo, ohi = O.reach(method, "traffic", wl["x_lo"][a:b], wl["x_hi"][a:b], wl["w_lo"], wl["w_hi"],
+                           t_final=T, dt=dt)
+        assert_close(g[0][i:i + 1], olo[i - a:i - a + 1], TOL64, f"cell {i} lo")
+        assert_close(g[1][i:i + 1], ohi[i - a:i - a + 1], TOL64, f"cell {i} hi")
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_ks_full_size_sampled_cells(method):
+    n = 1 << 20
+    wl = W.ks_grid(n)
+    T, dt = wl["t_final"], wl["dt"]
+    N = O.nsteps(T, dt)
+    g = gpu_box(method, "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt)
+    assert np.isfinite(g[0]).all() and (g[0] <= g[1]).all()
+    L = 16 * N + 8   # periodic window: the wrap travels 8N cells at most in N steps
+    for i in [0, 7, n // 3, n - 1]:
+        idx = (i - L // 2 + np.arange(L)) % n
+        olo, ohi = O.reach(method, "ks", wl["x_lo"][idx], wl["x_hi"][idx], t_final=T, dt=dt,
+                           params=wl["params"])
+        assert_close(g[0][i:i + 1], olo[L // 2:L // 2 + 1], TOL64, f"cell {i} lo")
+        assert_close(g[1][i:i + 1], ohi[L // 2:L // 2 + 1], TOL64, f"cell {i} hi")
+
+
+def test_ks_full_size_mc32_inside_mm():
+    n = 1 << 20
+    wl = W.ks_grid(n)
+    T, dt = wl["t_final"], wl["dt"]
+    mm = gpu_box("mm", "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt)
+    mc = gpu_box("mc", "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt, m=1024, seed=0, precision=32)
+    assert np.isfinite(mc[0]).all() and (mc[0] <= mc[1]).all()
+    # FP32 trajectories are inside the FP64 MM box up to FP32 rounding of the state
+    slack = 1e-5 * np.abs(mm[1]).max()
+    assert (mc[0] >= mm[0] - slack).all() and (mc[1] <= mm[1] + slack).all()
+    assert (mc[1] - mc[0]).min() > 0
