@@ -152,6 +152,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--cells", type=int, default=N_CELLS,
+                    help="chain length (default 2^26; smaller values are for profiler captures only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -173,14 +176,15 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = W.traffic_large(N_CELLS, seed=0)
+    n = args.cells
+    wl = W.traffic_large(n, seed=0)
     dev = torch.device("cuda", local)
     host = {k: np.ascontiguousarray(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
     d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
-    lo = torch.empty(N_CELLS, dtype=torch.float64, device=dev)
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
     hi = torch.empty_like(lo)
     stream = torch.cuda.current_stream(dev)
-    sysm = R.System("traffic", N_CELLS)
+    sysm = R.System("traffic", n)
     R.reach_set_option(R.OPT_KERNEL, 0)
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
 
@@ -218,18 +222,18 @@ def main():
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    comp_steps = 2 * 2 * N_CELLS * NSTEPS * args.steps * world
+    comp_steps = 2 * 2 * n * NSTEPS * args.steps * world
     value = comp_steps / (ms * 1e-3)
 
     # end to end through the public API with host buffers
-    hlo = np.empty(N_CELLS)
-    hhi = np.empty(N_CELLS)
-    for _ in range(1):
+    hlo = np.empty(n)
+    hhi = np.empty(n)
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 2))
+    if e2e_steps:
         R.reach_mm(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
                    lo=hlo, hi=hhi)
     barrier()
     te = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
         R.reach_mm(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
                    lo=hlo, hi=hhi)
@@ -241,13 +245,13 @@ def main():
         tt = torch.tensor([e2e_sec], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_sec = float(tt.item())
-    e2e_value = 2 * 2 * N_CELLS * NSTEPS * e2e_steps * world / e2e_sec
-    h2d = 2 * (2 * N_CELLS + 2) * 8
-    d2h = 2 * 2 * N_CELLS * 8
+    e2e_value = 2 * 2 * n * NSTEPS * e2e_steps * world / e2e_sec if e2e_steps else None
+    h2d = 2 * (2 * n + 2) * 8
+    d2h = 2 * 2 * n * 8
 
     # dominant kernel: the streaming RK4 kernel, 200 launches per call
     per_launch_ms = {m: statistics.median(v) / NSTEPS for m, v in method_ms.items()}
-    ops = {m: FP64_OPS[m] * 2 * N_CELLS for m in method_ms}          # per launch
+    ops = {m: FP64_OPS[m] * 2 * n for m in method_ms}          # per launch
     achieved = {m: ops[m] / (per_launch_ms[m] * 1e-3) for m in method_ms}
     mm_achieved = achieved["mm"]
     peaks = load_peaks()
@@ -258,8 +262,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "traffic chain n=2^26, MM + CGB, dt=0.01, T=2 (200 RK4 steps each)",
-                   "n": N_CELLS, "rk4_steps": NSTEPS, "methods": ["mm", "cgb"],
+        "config": {"workload": f"traffic chain n={n}, MM + CGB, dt=0.01, T=2 (200 RK4 steps each)",
+                   "n": n, "rk4_steps": NSTEPS, "methods": ["mm", "cgb"],
                    "l2": "inputs larger than L2 (2 x 512 MiB state per call)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -273,7 +277,7 @@ def main():
         "clocks": clk,
         "gpu_launches": int(launches),
     }
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {CPU_SAMPLE_CELLS} cells, MM + CGB, 200 steps ({sec:.1f} s)"}

@@ -47,6 +47,9 @@ int64_t opt_block();
 // kernels
 int64_t onchip_smem_bytes(int64_t n, int64_t nw);
 int onchip_max_smem();
+// raise a kernel's dynamic shared-memory limit to what the device allows
+// beside the kernel's own static shared memory
+int allow_max_dynamic_smem(const void *fn);
 int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st);
 int onchip_launch_batch(int kind, const void *items, const void *slots, const void *bins, int nbins,
                         int *counter, int grid, size_t smem, cudaStream_t st);

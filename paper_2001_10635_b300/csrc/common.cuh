@@ -56,6 +56,25 @@ int cuda_fail(cudaError_t e, const char *where);
         if (e__ != cudaSuccess) return ::reach::cuda_fail(e__, where); \
     } while (0)
 
+// Order-preserving integer key of a double: for non-NaN a, b,
+// a < b  <=>  key(a) < key(b) as signed 64-bit integers.  Minimum, maximum and
+// comparisons of doubles through these keys run on the integer pipe; the
+// FP64 pipe of this GPU retires two operations per SM per clock and is kept
+// for arithmetic.
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kmin(double a, double b) { return dkey(b) < dkey(a) ? b : a; }
+__device__ __forceinline__ double kmax(double a, double b) { return dkey(b) > dkey(a) ? b : a; }
+__device__ __forceinline__ bool kle(double a, double b) { return dkey(a) <= dkey(b); }
+__device__ __forceinline__ double kabs(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool kfinite(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the paper's
 // definition: 10 rounds of (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
 // lo(M0 c0)) with the key bumped by the Weyl constants between rounds.

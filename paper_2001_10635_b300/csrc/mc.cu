@@ -22,6 +22,10 @@ constexpr int MC_WARPS = 16;            // warps per block
 constexpr int MC_THREADS = 32 * MC_WARPS;
 constexpr int MC_Q = 8;                 // component rows per thread (on-chip)
 
+// minimum on the integer pipe for doubles (the FP64 pipe is the scarce one)
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return kmin(a, b); }
+
 // ------------------------------------------------------------------ plain f
 // Y: rows of 32 samples (row c at Y + 32 c), P: input rows.  `g` is the
 // global component of row c; rows c +- R exist in Y (halo or wrapped).
@@ -33,9 +37,8 @@ struct Plain<REACH_TRAFFIC, T> {
     static constexpr int R = 1;
     // flux out of global cell g given its row value y and right neighbour yr
     static __device__ __forceinline__ T flux(const T *q, T y, T yr, int64_t g, int64_t n, T d) {
-        T f = fmin(q[0], fmin(q[1] * y, fma(-q[2], yr, q[3])));
-        T fl = fmin(q[0], q[1] * y);
-        f = (g == n - 1) ? fl : f;
+        T cong = (g == n - 1) ? q[0] : fma(-q[2], yr, q[3]);
+        T f = tmin(q[0], tmin(q[1] * y, cong));
         f = (g == -1) ? d : f;
         f = (g < -1 || g >= n) ? T(0) : f;
         return f;
@@ -331,8 +334,8 @@ static int launch_onchip(const McArgs &a, cudaStream_t st) {
     size_t smem = (size_t)(a.n + a.nw) * 32 * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        REACH_CUDA(cudaFuncSetAttribute(mc_onchip<SYS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        onchip_max_smem()));
+        int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T>);
+        if (rc) return rc;
         attr = true;
     }
     mc_onchip<SYS, T><<<(unsigned)nblk, MC_THREADS, smem, st>>>(a);
@@ -351,8 +354,8 @@ static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, voi
     size_t smem = (size_t)rows * 32 * sizeof(T) * 2;
     static bool attr = false;
     if (!attr) {
-        REACH_CUDA(cudaFuncSetAttribute(mc_stream<SYS, T, MC_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        onchip_max_smem()));
+        int rc = allow_max_dynamic_smem((const void *)mc_stream<SYS, T, MC_TC>);
+        if (rc) return rc;
         attr = true;
     }
     int64_t ntile = (a.n + a.TC - 1) / a.TC;

@@ -1,6 +1,6 @@
 // onchip.cu -- kernels built on onchip_run: one problem per block, and the
 // batched persistent kernel that runs many uneven problems in one launch.
-#include "onchip.cuh"
+#include "api_internal.cuh"
 
 namespace reach {
 
@@ -17,6 +17,14 @@ __global__ void __launch_bounds__(512) onchip_single(OnItem it) {
 // shared memory of one problem: y (2n), inputs (2 nw), stage derivatives (2n)
 int64_t onchip_smem_bytes(int64_t n, int64_t nw) { return (4 * n + 2 * nw) * (int64_t)sizeof(double); }
 
+int allow_max_dynamic_smem(const void *fn) {
+    cudaFuncAttributes fa;
+    REACH_CUDA(cudaFuncGetAttributes(&fa, fn));
+    int cap = onchip_max_smem() - (int)fa.sharedSizeBytes;
+    REACH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    return REACH_OK;
+}
+
 int onchip_max_smem() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -29,8 +37,8 @@ static int launch_single_t(const OnItem &it, int threads, cudaStream_t st) {
     int64_t smem = onchip_smem_bytes(it.n, it.nw);
     static bool attr_set = false;
     if (!attr_set) {
-        REACH_CUDA(cudaFuncSetAttribute(onchip_single<SYS, METHOD>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, onchip_max_smem()));
+        int rc = allow_max_dynamic_smem((const void *)onchip_single<SYS, METHOD>);
+        if (rc) return rc;
         attr_set = true;
     }
     onchip_single<SYS, METHOD><<<1, threads, (size_t)smem, st>>>(it);
@@ -105,8 +113,8 @@ static int launch_batch_t(const OnItem *items, const Slot *slots, const Bin *bin
                           int grid, size_t smem, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        REACH_CUDA(cudaFuncSetAttribute(onchip_batch<SYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        onchip_max_smem()));
+        int rc = allow_max_dynamic_smem((const void *)onchip_batch<SYS>);
+        if (rc) return rc;
         attr_set = true;
     }
     onchip_batch<SYS><<<grid, BATCH_THREADS, smem, st>>>(items, slots, bins, nbins, counter);

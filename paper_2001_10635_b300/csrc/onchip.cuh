@@ -42,7 +42,8 @@ struct GroupSync {
 
 __device__ __forceinline__ double tr_flux_out(const double *y, int64_t i, int64_t n, double cap,
                                               double v, double w, double wxbar) {
-    return (i == n - 1) ? fmin(cap, v * y[i]) : fmin(cap, fmin(v * y[i], fma(-w, y[i + 1], wxbar)));
+    double cong = (i == n - 1) ? cap : fma(-w, y[i + 1], wxbar);
+    return kmin(cap, kmin(v * y[i], cong));
 }
 
 template <int SYS, int METHOD>
@@ -78,7 +79,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             double da = Y[ip1] - O[im1], db = O[ip1] - Y[im1];
             double qq = -k * Y[i];
             double ea = qq * da, eb = qq * db;
-            return lin + ((da <= db) ? fmin(ea, eb) : fmax(ea, eb));
+            return lin + (kle(da, db) ? kmin(ea, eb) : kmax(ea, eb));
         } else {
             double dc = yA[ip1] - yA[im1];
             if (!upper) {
@@ -86,10 +87,10 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                 return fma(-k * yA[i], dc, lin);
             }
             double sr = yB[ip1] + yB[im1];
-            double cii = fmax(fma(-k, dc - sr, a0), fma(-k, dc + sr, a0));
-            double t = k * yA[i], u = fabs(k * yB[i]);
-            double cip = fabs(a1 - t) + u, cim = fabs(a1 + t) + u;
-            return fma(fabs(a2), yB[im2] + yB[ip2], fma(cip, yB[ip1], fma(cim, yB[im1], cii * yB[i])));
+            double cii = kmax(fma(-k, dc - sr, a0), fma(-k, dc + sr, a0));
+            double t = k * yA[i], u = kabs(k * yB[i]);
+            double cip = kabs(a1 - t) + u, cim = kabs(a1 + t) + u;
+            return fma(kabs(a2), yB[im2] + yB[ip2], fma(cip, yB[ip1], fma(cim, yB[im1], cii * yB[i])));
         }
     } else if constexpr (SYS == REACH_OSC) {
         // q: ka, kb, kc, ka + 2 kc, 3 kb, |kc|;  state [x_1..x_m | v_1..v_m]
@@ -116,7 +117,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             }
             if (i < m) return yB[m + i];
             const int64_t j = i - m;
-            double ax = fabs(yA[j]) + yB[j];
+            double ax = kabs(yA[j]) + yB[j];
             double cxx = fma(q[4] * ax, ax, q[3]);   // ka + 2kc + 3 kb (|c| + r)^2
             double rl = (j > 0) ? yB[j - 1] : 0.0, rr = (j < m - 1) ? yB[j + 1] : 0.0;
             return fma(cxx, yB[j], fma(q[5], rl + rr, wB[j]));
@@ -128,7 +129,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             const double *Y = upper ? yB : yA, *O = upper ? yA : yB;
             for (int64_t j = 0; j < n; ++j) {
                 double a = __ldg(Arow + j);
-                double v = (j == i || a >= 0.0) ? Y[j] : O[j];
+                double v = (j == i || __double_as_longlong(a) >= 0) ? Y[j] : O[j];
                 acc = fma(a, v, acc);
             }
             return acc + (upper ? wB[i] : wA[i]);
@@ -139,7 +140,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             }
             for (int64_t j = 0; j < n; ++j) {
                 double a = __ldg(Arow + j);
-                acc = fma(j == i ? a : fabs(a), yB[j], acc);
+                acc = fma(j == i ? a : kabs(a), yB[j], acc);
             }
             return acc + wB[i];
         }
@@ -156,8 +157,37 @@ __device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
         q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2]; q[3] = prm[3];
     } else if constexpr (SYS == REACH_OSC) {
         q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2];
-        q[3] = prm[0] + 2.0 * prm[2]; q[4] = 3.0 * prm[1]; q[5] = fabs(prm[2]);
+        q[3] = prm[0] + 2.0 * prm[2]; q[4] = 3.0 * prm[1]; q[5] = kabs(prm[2]);
     }
+}
+
+// one RK4 stage of the group: all derivatives from y, then y rewritten
+template <int SYS, int METHOD, int STAGE, class Sync>
+__device__ __forceinline__ void onchip_stage(const OnItem &it, double *yA, double *yB, const double *wA,
+                                             const double *wB, double *kb, int64_t cbeg, int64_t cend, int gt,
+                                             int gs, const Sync &sync, const double (&q)[8], double (&z)[QMAX],
+                                             double (&acc)[QMAX]) {
+    const int64_t n = it.n;
+#pragma unroll
+    for (int s = 0; s < QMAX; ++s) {
+        int64_t c = cbeg + gt + (int64_t)s * gs;
+        if (c < cend) kb[c - cbeg] = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
+    }
+    sync();
+    const double h = it.h;
+#pragma unroll
+    for (int s = 0; s < QMAX; ++s) {
+        int64_t c = cbeg + gt + (int64_t)s * gs;
+        if (c < cend) {
+            double y, k = kb[c - cbeg];
+            if (STAGE == 0) { acc[s] = k; y = fma(0.5 * h, k, z[s]); }
+            if (STAGE == 1) { acc[s] = fma(2.0, k, acc[s]); y = fma(0.5 * h, k, z[s]); }
+            if (STAGE == 2) { acc[s] = fma(2.0, k, acc[s]); y = fma(h, k, z[s]); }
+            if (STAGE == 3) { acc[s] += k; z[s] = fma(h / 6.0, acc[s], z[s]); y = z[s]; }
+            (c < n ? yA[c] : yB[c - n]) = y;
+        }
+    }
+    sync();
 }
 
 // Integrate one problem.  yA, yB: n doubles each of shared memory (may live in
@@ -206,32 +236,11 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA,
     }
     sync();
 
-    const double h = it.h, hh = 0.5 * it.h, h6 = it.h / 6.0;
     for (int64_t step = 0; step < it.N; ++step) {
-#pragma unroll 1
-        for (int stage = 0; stage < 4; ++stage) {
-#pragma unroll
-            for (int s = 0; s < QMAX; ++s) {
-                int64_t c = cbeg + gt + (int64_t)s * gs;
-                if (c < cend) kb[c - cbeg] = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
-            }
-            sync();
-            const double cst = (stage == 2) ? h : hh;
-#pragma unroll
-            for (int s = 0; s < QMAX; ++s) {
-                int64_t c = cbeg + gt + (int64_t)s * gs;
-                if (c < cend) {
-                    double y, k = kb[c - cbeg];
-                    if (stage == 0) acc[s] = k;
-                    else if (stage < 3) acc[s] = fma(2.0, k, acc[s]);
-                    else acc[s] += k;
-                    if (stage < 3) y = fma(cst, k, z[s]);
-                    else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
-                    (c < n ? yA[c] : yB[c - n]) = y;
-                }
-            }
-            sync();
-        }
+        onchip_stage<SYS, METHOD, 0>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 1>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 2>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 3>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
     }
 
     // y holds the final state of both halves
@@ -240,11 +249,11 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA,
         double a = yA[c], b = yB[c];
         double lo = a, hi = b;
         if (METHOD == CGB) {
-            if (b < 0.0) flags |= ST_NEGRADIUS;
+            if (dkey(b) < 0) flags |= ST_NEGRADIUS;
             lo = a - b;
             hi = a + b;
         }
-        if (!isfinite(lo) || !isfinite(hi)) flags |= ST_NONFINITE;
+        if (!kfinite(lo) || !kfinite(hi)) flags |= ST_NONFINITE;
         it.lo[c] = lo;
         it.hi[c] = hi;
     }
