@@ -146,6 +146,30 @@ REACH_API int reach_mc(const reach_system *sys, const double *x0_lo, const doubl
    eps, delta outside (0, 1). */
 REACH_API int64_t reach_mc_samples(int64_t n, double eps, double delta);
 
+/* reach_mm for callers that cannot let a library allocate device memory
+   (the paper has no counterpart): a process whose device memory is held by
+   another allocator, such as a framework's caching pool that reserves nearly
+   all of HBM, or a latency-critical loop that must not enter the driver's
+   allocator, which can lock and synchronise.  It runs the same streaming RK4
+   kernel as reach_mm for REACH_TRAFFIC and REACH_KS systems, and it allocates
+   nothing: the kernel's ping-pong state buffer and the status word live in a
+   fixed device buffer of the library (16 MiB + 256 B, held on every GPU that
+   loads the library until the process exits).
+     - n <= REACH_NOALLOC_MAX_N, else REACH_EINVAL; other kinds: REACH_EINVAL.
+     - x0_lo, x0_hi, lo, hi must be device pointers (REACH_EINVAL otherwise);
+       w_lo, w_hi (traffic inflow) may be host or device.
+     - The first call on each device looks up the buffer's device address
+       (cudaGetSymbolAddress); make that first call before any stream capture.
+     - All calls share the buffer: calls whose work overlaps on the GPU (on
+       different streams, or from several threads) race and give wrong
+       results.  Each call clears the status word before use.
+   Otherwise as reach_mm: same arguments, results, status codes, and the call
+   returns after its results are complete. */
+#define REACH_NOALLOC_MAX_N 1048576
+REACH_API int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, const double *x0_hi,
+                               const double *w_lo, const double *w_hi, double t_final, double dt,
+                               double *lo, double *hi, void *stream);
+
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
 #define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming stencil: RK4 steps fused per launch, 1..8 */
