@@ -120,6 +120,111 @@ def cpu_oracle_rate(cells: int = CPU_SAMPLE_CELLS):
     return comp_steps / sec, sec, comp_steps
 
 
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def bench_batched(R, torch, dev, runs=3, solo_stride=32):
+    """4096 oscillator-chain queries x (MM to T=5, CGB to T=4), one graph launch of
+    the batched persistent kernels, against the same queries launched one by one
+    (a deterministic subset: every `solo_stride`-th query)."""
+    sizes = W.osc_sizes(4096, seed=0)
+    systems, qs = {}, []
+    for k, m in enumerate(sizes):
+        q = W.osc_query(int(m), seed=1000003 + k, t_final=W.OSC_T)
+        s = systems.setdefault(int(m), R.System("osc", 2 * int(m)))
+        d = {kk: torch.tensor(q[kk], dtype=torch.float64, device=dev) for kk in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        for method, T in (("mm", W.OSC_T), ("cgb", W.OSC_T_CGB)):
+            qs.append(dict(sys=s, method=method, x0_lo=d["x_lo"], x0_hi=d["x_hi"], w_lo=d["w_lo"],
+                           w_hi=d["w_hi"], t_final=T, dt=W.OSC_DT))
+    comp = [2 * q["sys"].n * int(round(q["t_final"] / q["dt"])) for q in qs]
+    t0 = time.perf_counter()
+    b = R.Batch(qs)
+    create_s = time.perf_counter() - t0
+    b.run()   # warm
+    times, fin = [], None
+    launches0 = R.reach_kernel_launches()
+    for _ in range(runs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, fin = b.run()
+        times.append(time.perf_counter() - t0)
+    batch_launches = (R.reach_kernel_launches() - launches0) / runs
+    tb = statistics.median(times)
+    sub = list(range(0, len(qs), solo_stride))
+    lat = []
+    launches0 = R.reach_kernel_launches()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sub:
+        q = qs[i]
+        fn = R.reach_mm if q["method"] == "mm" else R.reach_cgb
+        t1 = time.perf_counter()
+        fn(q["sys"], q["x0_lo"], q["x0_hi"], q["w_lo"], q["w_hi"], t_final=q["t_final"], dt=q["dt"])
+        lat.append(time.perf_counter() - t1)
+    ts = time.perf_counter() - t0
+    solo_launches = R.reach_kernel_launches() - launches0
+    solo_rate = sum(comp[i] for i in sub) / ts
+    info = b.info()
+    b.close()
+    for s in systems.values():
+        s.close()
+    return {"workload": "4096 oscillator-chain queries, m log-uniform in [4, 4096] (seed 0), MM T=5 + CGB T=4, "
+                        "dt=0.005, box half-width 1e-4, w in [-0.01, 0.01]",
+            "queries": len(qs), "comp_steps": int(sum(comp)),
+            "value": sum(comp) / tb, "unit": "comp-steps/s", "run_s": tb, "create_s": create_s,
+            "latency_p50_ms": _pct(fin, 50) * 1e3, "latency_p99_ms": _pct(fin, 99) * 1e3,
+            "latency_note": "completion time of each query from the start of the batch (all submitted at once)",
+            "tuned_cpt": info["cpt"], "tune_ms": info["tune_ms"], "kernels_per_run": info["kernels"],
+            "gpu_launches_per_run": batch_launches,
+            "solo": {"queries": len(sub), "sample": f"every {solo_stride}th query", "s": ts, "value": solo_rate,
+                     "service_p50_ms": _pct(lat, 50) * 1e3, "service_p99_ms": _pct(lat, 99) * 1e3,
+                     "gpu_launches": solo_launches,
+                     "projected_all_s": ts * sum(comp) / sum(comp[i] for i in sub)},
+            "speedup_vs_solo": (sum(comp) / tb) / solo_rate}
+
+
+def bench_ks(R, torch, dev):
+    """Kuramoto-Sivashinsky grid n = 2^20 (dt 1e-4, T 0.05): MM, CGB, MC 1024
+    samples in FP32 (full), MC in FP64 on 64 samples (bounded: FP64 pipe)."""
+    n = 1 << 20
+    wl = W.ks_grid(n)
+    d = {k: torch.tensor(wl[k], dtype=torch.float64, device=dev) for k in ("x_lo", "x_hi")}
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    N = int(round(wl["t_final"] / wl["dt"]))
+    out = {"workload": "KS periodic grid n=2^20, dx=pi/4, dt=1e-4, T=0.05 (500 RK4 steps), u0 +- 1e-3"}
+    with R.System("ks", n) as s:
+        for name, fn, kw, comps in (("mm", R.reach_mm, {}, 2 * n), ("cgb", R.reach_cgb, {}, 2 * n),
+                                    ("mc32_m1024", R.reach_mc, dict(m=1024, precision=32), 1024 * n),
+                                    ("mc64_m64", R.reach_mc, dict(m=64, precision=64), 64 * n)):
+            fn(s, d["x_lo"], d["x_hi"], t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, **kw)   # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn(s, d["x_lo"], d["x_hi"], t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, **kw)
+            sec = time.perf_counter() - t0
+            out[name] = {"s": sec, "value": comps * N / sec, "unit": "comp-steps/s"}
+    return out
+
+
+def bench_traffic16(R):
+    """Traffic chain n = 16, T = 10 (1000 steps): latency of one call."""
+    wl = W.traffic_small(16)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    out = {"workload": "traffic chain n=16, x0 in [100,120]^16, d in [35,45], dt=0.01, T=10"}
+    with R.System("traffic", 16) as s:
+        for name, fn, kw in (("mm", R.reach_mm, {}), ("cgb", R.reach_cgb, {}),
+                             ("mc64_m1000", R.reach_mc, dict(m=1000, precision=64)),
+                             ("mc32_m1000", R.reach_mc, dict(m=1000, precision=32))):
+            fn(s, *args, t_final=wl["t_final"], dt=wl["dt"], **kw)
+            t0 = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                fn(s, *args, t_final=wl["t_final"], dt=wl["dt"], **kw)
+            out[name + "_ms"] = (time.perf_counter() - t0) / reps * 1e3
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle as it stands, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -153,6 +258,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched, KS and small-config sections")
     ap.add_argument("--cells", type=int, default=N_CELLS,
                     help="chain length (default 2^26; smaller values are for profiler captures only)")
     args = ap.parse_args()
@@ -277,6 +383,10 @@ def main():
         "clocks": clk,
         "gpu_launches": int(launches),
     }
+    if not args.no_extra and n == N_CELLS:
+        line["batched"] = bench_batched(R, torch, dev)
+        line["ks"] = bench_ks(R, torch, dev)
+        line["traffic16"] = bench_traffic16(R)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",

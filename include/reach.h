@@ -170,10 +170,47 @@ REACH_API int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, con
                                const double *w_lo, const double *w_hi, double t_final, double dt,
                                double *lo, double *hi, void *stream);
 
+/* ---- batches: many uneven queries in one persistent launch ----
+   Algorithms 2 and 3 applied to many independent queries at once (the paper
+   runs one query per call; this batching is new).  A batch is planned once:
+   every query becomes an on-chip problem (2n <= 16384 components; the
+   streaming kernels are not used), problems are packed into the blocks of a
+   persistent kernel (one per system kind and method present) largest first,
+   the components-per-thread target is tuned by timing the candidate layouts
+   on the batch itself with shortened horizons, and the whole run (input
+   copies for host-resident queries, the kernels, output copies) is captured
+   into a CUDA graph.  reach_batch_run replays it: it reads the query buffers
+   given at creation (update their contents in place between runs), and
+   returns after all results are written. */
+typedef struct {
+    const reach_system *sys;
+    int method;                                  /* 0 = MM, 1 = CGB */
+    const double *x0_lo, *x0_hi, *w_lo, *w_hi;   /* host or device, as reach_mm */
+    double t_final, dt;
+    double *lo, *hi;                             /* host or device */
+} reach_query;
+
+typedef struct reach_batch reach_batch;
+
+#define REACH_BATCH_NO_AUTOTUNE 1   /* flag: use REACH_OPT_BATCH_CPT (default 8) */
+
+/* REACH_EINVAL for an invalid query (as reach_mm), a zero horizon, or a
+   query larger than the on-chip kernels hold. */
+REACH_API int reach_batch_create(const reach_query *queries, int64_t count, int flags, reach_batch **out);
+/* status (optional, count ints): each query's status; finish_s (optional,
+   count doubles): seconds from the start of the kernels to the completion of
+   each query.  Returns the first non-OK query status, or REACH_OK. */
+REACH_API int reach_batch_run(reach_batch *b, void *stream, int *status, double *finish_s);
+/* the tuned components-per-thread target, the kernels per run, and the
+   timings (ms) of the four tuning candidates 2, 4, 8, 16 */
+REACH_API int reach_batch_info(const reach_batch *b, int64_t *cpt, int64_t *kernels, double *tune_ms);
+REACH_API int reach_batch_destroy(reach_batch *b);
+
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
 #define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming stencil: RK4 steps fused per launch, 1..8 */
 #define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
+#define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

@@ -23,11 +23,20 @@ LIB_PATH = os.path.join(_HERE, "libreach.so")
 
 TRAFFIC, KS, OSC, LINEAR = 0, 1, 2, 3
 KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR}
-OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK = 1, 2, 3
+OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT = 1, 2, 3, 4
+BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
           -4: "REACH_ENONFINITE", -5: "REACH_ETIMEOUT", -6: "REACH_ECUDA", -7: "REACH_ENODEV"}
 
 _lib = None
+
+
+class _Query(ctypes.Structure):
+    """reach_query (include/reach.h)."""
+    _fields_ = [("sys", ctypes.c_void_p), ("method", ctypes.c_int), ("x0_lo", ctypes.c_void_p),
+                ("x0_hi", ctypes.c_void_p), ("w_lo", ctypes.c_void_p), ("w_hi", ctypes.c_void_p),
+                ("t_final", ctypes.c_double), ("dt", ctypes.c_double), ("lo", ctypes.c_void_p),
+                ("hi", ctypes.c_void_p)]
 
 
 class ReachError(RuntimeError):
@@ -66,6 +75,10 @@ def lib() -> ctypes.CDLL:
         L.reach_strerror.argtypes = [ctypes.c_int]
         L.reach_strerror.restype = ctypes.c_char_p
         L.reach_kernel_launches.restype = i64
+        L.reach_batch_create.argtypes = [ctypes.POINTER(_Query), i64, ctypes.c_int, ctypes.POINTER(vp)]
+        L.reach_batch_run.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl)]
+        L.reach_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        L.reach_batch_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -224,3 +237,73 @@ def reach_get_option(key: int) -> int:
 
 def reach_kernel_launches() -> int:
     return int(lib().reach_kernel_launches())
+
+
+# ------------------------------------------------------------------ batches
+class Batch:
+    """reach_batch_create / _run / _info / _destroy.
+
+    queries: sequence of dicts with keys sys (System), method ("mm" | "cgb"),
+    x0_lo, x0_hi, w_lo, w_hi, t_final, dt, and optionally lo, hi (allocated like
+    x0_lo when absent).  The arrays are kept alive by the batch; update input
+    contents in place between runs."""
+
+    def __init__(self, queries, autotune: bool = True):
+        self._keep = []
+        arr = (_Query * len(queries))()
+        self.outputs = []
+        for k, q in enumerate(queries):
+            sys_ = q["sys"]
+            a = _ptr(q["x0_lo"], sys_.n, "x0_lo")
+            b = _ptr(q["x0_hi"], sys_.n, "x0_hi")
+            c = _ptr(q.get("w_lo"), sys_.nw, "w_lo") if sys_.nw else (None, None)
+            d = _ptr(q.get("w_hi"), sys_.nw, "w_hi") if sys_.nw else (None, None)
+            lo = _out(q["x0_lo"], q.get("lo"), sys_.n, "lo")
+            hi = _out(q["x0_lo"], q.get("hi"), sys_.n, "hi")
+            pl, _ = _ptr(lo, sys_.n, "lo")
+            ph, _ = _ptr(hi, sys_.n, "hi")
+            self._keep += [sys_, a[1], b[1], c[1], d[1], lo, hi]
+            self.outputs.append((lo, hi))
+            method = {"mm": 0, "cgb": 1}[q["method"]] if isinstance(q["method"], str) else int(q["method"])
+            arr[k] = _Query(sys_.handle.value, method, a[0], b[0], c[0], d[0], float(q["t_final"]),
+                            float(q["dt"]), pl, ph)
+        self.count = len(queries)
+        self.handle = ctypes.c_void_p()
+        rc = lib().reach_batch_create(arr, self.count, 0 if autotune else BATCH_NO_AUTOTUNE,
+                                      ctypes.byref(self.handle))
+        _check(rc, "reach_batch_create")
+
+    def run(self, stream=None, check: bool = True):
+        """Run once; returns (status per query, completion seconds per query)."""
+        st = np.zeros(self.count, dtype=np.int32)
+        fin = np.zeros(self.count, dtype=np.float64)
+        rc = lib().reach_batch_run(self.handle, _stream(stream),
+                                   st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   fin.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if check:
+            _check(rc, "reach_batch_run")
+        return st, fin
+
+    def info(self):
+        cpt = ctypes.c_int64()
+        kern = ctypes.c_int64()
+        tune = (ctypes.c_double * 4)()
+        _check(lib().reach_batch_info(self.handle, ctypes.byref(cpt), ctypes.byref(kern), tune), "reach_batch_info")
+        return {"cpt": cpt.value, "kernels": kern.value, "tune_ms": dict(zip((2, 4, 8, 16), list(tune)))}
+
+    def close(self):
+        if self.handle:
+            lib().reach_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -35,16 +35,29 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object in parallel (relocatable device code is
+    not needed: no kernel calls across files), then link the shared library."""
     if not force and not _stale():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
+
     nvcc = os.path.join(CUDA_HOME, "bin", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
-           "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared", "-cudart", "shared",
-           "-Xlinker", f"-rpath,{CUDA_HOME}/lib64", "-o", LIB + ".tmp", *sources()]
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
+              "-Xcompiler", "-fPIC,-fvisibility=hidden"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
+        common.append("-Xptxas=-v")
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        subprocess.check_call([nvcc, *common, "-c", src, "-o", obj])
+        return obj
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, sources()))
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", f"-rpath,{CUDA_HOME}/lib64",
+                           "-o", LIB + ".tmp", *objs])
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

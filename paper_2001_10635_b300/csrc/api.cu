@@ -21,7 +21,7 @@ int cuda_fail(cudaError_t e, const char *where) {
     return REACH_ECUDA;
 }
 
-static int64_t g_opt_kernel = 0, g_opt_steps = 1, g_opt_block = 0;
+static int64_t g_opt_kernel = 0, g_opt_steps = 1, g_opt_block = 0, g_opt_batch_cpt = 0;
 
 // ---------------------------------------------------------------- memory
 static bool g_pool_ready[64];
@@ -156,6 +156,7 @@ int check_host_box(const double *lo, const double *hi, int64_t count) {
 int64_t opt_kernel() { return g_opt_kernel; }
 int64_t opt_steps() { return g_opt_steps; }
 int64_t opt_block() { return g_opt_block; }
+int64_t opt_batch_cpt() { return g_opt_batch_cpt; }
 
 }  // namespace reach
 
@@ -266,10 +267,17 @@ extern "C" int64_t reach_input_dim(const reach_system *sys) { return sys ? sys->
 // ================================================================ MM / CGB
 namespace reach {
 
+// the on-chip kernels hold a problem in one block (2n <= QMAX * 512) or in a
+// cluster of two blocks (2n <= 2 * QMAX * 512)
+static bool onchip_fits(const reach_system *s) {
+    const int64_t cap = (int64_t)QMAX * 512;
+    if (2 * s->n <= cap) return onchip_smem_bytes(s->n, s->nw) <= onchip_max_smem();
+    return 2 * s->n <= 2 * cap && cluster_smem_bytes(s->n, s->nw) <= onchip_max_smem();
+}
+
 bool use_onchip(const reach_system *s) {
     int64_t k = opt_kernel();
-    int64_t cap = (int64_t)QMAX * 512;
-    bool fits = 2 * s->n <= cap && onchip_smem_bytes(s->n, s->nw) <= onchip_max_smem();
+    bool fits = onchip_fits(s);
     if (k == 2) return fits;
     if (k == 1) return s->kind == REACH_OSC || s->kind == REACH_LINEAR;
     if (s->kind == REACH_OSC || s->kind == REACH_LINEAR) return true;
@@ -298,8 +306,8 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     if ((rc = check_host_box(w_lo, w_hi, sys->nw))) return rc;
     const int64_t n = sys->n;
     bool onchip = use_onchip(sys);
-    if (onchip && !(2 * n <= (int64_t)QMAX * 512 && onchip_smem_bytes(n, sys->nw) <= onchip_max_smem()))
-        return REACH_EINVAL;   // too large for the on-chip kernel and no streaming kernel for this kind
+    if (onchip && !onchip_fits(sys))
+        return REACH_EINVAL;   // too large for the on-chip kernels and no streaming kernel for this kind
 
     Staging sg((cudaStream_t)stream);
     const double *dxlo, *dxhi, *dwlo = nullptr, *dwhi = nullptr;
@@ -342,7 +350,9 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         it.N = N;
         it.h = dt;
         it.status = sg.status;
-        if ((rc = onchip_launch_single(it, onchip_threads(n), sg.st))) return rc;
+        if (2 * n <= (int64_t)QMAX * 512) rc = onchip_launch_single(it, onchip_threads(n), sg.st);
+        else rc = onchip_launch_cluster(it, sg.st);
+        if (rc) return rc;
         return sg.finish();
     }
 
@@ -399,6 +409,10 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value != 0 && (value < 32 || value > 512 || value % 32)) return REACH_EINVAL;
         g_opt_block = value;
         return REACH_OK;
+    case REACH_OPT_BATCH_CPT:
+        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16) return REACH_EINVAL;
+        g_opt_batch_cpt = value;
+        return REACH_OK;
     }
     return REACH_EINVAL;
 }
@@ -408,6 +422,7 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_KERNEL: return g_opt_kernel;
     case REACH_OPT_STEPS_PER_LAUNCH: return g_opt_steps;
     case REACH_OPT_BLOCK: return g_opt_block;
+    case REACH_OPT_BATCH_CPT: return g_opt_batch_cpt;
     }
     return REACH_EINVAL;
 }

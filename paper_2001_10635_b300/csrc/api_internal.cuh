@@ -43,20 +43,36 @@ int check_host_box(const double *lo, const double *hi, int64_t count);
 int64_t opt_kernel();
 int64_t opt_steps();
 int64_t opt_block();
+int64_t opt_batch_cpt();
 
 // kernels
+constexpr int BATCH_THREADS = 512;   // threads per block of the batched kernel
 int64_t onchip_smem_bytes(int64_t n, int64_t nw);
 int onchip_max_smem();
 // raise a kernel's dynamic shared-memory limit to what the device allows
 // beside the kernel's own static shared memory
 int allow_max_dynamic_smem(const void *fn);
 int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st);
-int onchip_launch_batch(int kind, const void *items, const void *slots, const void *bins, int nbins,
-                        int *counter, int grid, size_t smem, cudaStream_t st);
+int64_t cluster_smem_bytes(int64_t n, int64_t nw);
+int onchip_launch_cluster(const OnItem &it, cudaStream_t st);
+int onchip_launch_batch(int kind, int method, const void *items, const void *slots, const void *bins,
+                        const void *tasks, int ntasks, int *counter, uint64_t *done, int clusters, size_t smem,
+                        cudaStream_t st);
+int onchip_launch_stamp(uint64_t *t0, cudaStream_t st);
 int onchip_batch_threads();
-size_t onchip_slot_bytes();
-size_t onchip_bin_bytes();
-size_t onchip_item_bytes();
+
+// host mirrors of the batch kernel's work-list records (onchip.cu)
+struct BatchSlot {
+    int item, warp0, nwarps, bar;
+    int64_t off;
+};
+struct BatchBin {
+    int slot0, nslots;
+};
+struct BatchTask {
+    int big;
+    int bin[2];
+};
 int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st);

@@ -75,6 +75,13 @@ __device__ __forceinline__ bool kfinite(double x) {
     return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// global nanosecond clock of the GPU
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the paper's
 // definition: 10 rounds of (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
 // lo(M0 c0)) with the key bumped by the Weyl constants between rounds.

@@ -88,6 +88,7 @@ struct Plain<REACH_LINEAR, T> {
                                             const double *A) {
         T acc = T(0);
         const double *Ar = A + (int64_t)c * n;
+#pragma unroll 1
         for (int j = 0; j < (int)n; ++j) acc = fma((T)__ldg(Ar + j), row(j), acc);
         return acc + P[c * 32 + lane];
     }

@@ -127,6 +127,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
         double acc = 0.0;
         if constexpr (METHOD == MM) {
             const double *Y = upper ? yB : yA, *O = upper ? yA : yB;
+#pragma unroll 1
             for (int64_t j = 0; j < n; ++j) {
                 double a = __ldg(Arow + j);
                 double v = (j == i || __double_as_longlong(a) >= 0) ? Y[j] : O[j];
@@ -135,9 +136,11 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             return acc + (upper ? wB[i] : wA[i]);
         } else {
             if (!upper) {
+#pragma unroll 1
                 for (int64_t j = 0; j < n; ++j) acc = fma(__ldg(Arow + j), yA[j], acc);
                 return acc + wA[i];
             }
+#pragma unroll 1
             for (int64_t j = 0; j < n; ++j) {
                 double a = __ldg(Arow + j);
                 acc = fma(j == i ? a : kabs(a), yB[j], acc);

@@ -1,0 +1,181 @@
+// onchip_kernels.cuh -- kernel templates of the on-chip path (one problem per
+// block, one problem per two-block cluster, batched persistent kernel).  Each
+// onchip_<kind>.cu instantiates them for one system kind.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "api_internal.cuh"
+
+namespace reach {
+
+// ---------------------------------------------------------------- one problem
+template <int SYS, int METHOD>
+__global__ void __launch_bounds__(512) onchip_single(OnItem it) {
+    extern __shared__ double sm[];
+    const int64_t n = it.n;
+    GroupSync sync{0, (int)blockDim.x};
+    onchip_run<SYS, METHOD>(it, sm, sm + n, sm + 2 * n, sm + 2 * n + it.nw, sm + 2 * n + 2 * it.nw, 0,
+                            2 * n, (int)threadIdx.x, (int)blockDim.x, sync);
+}
+
+template <int SYS, int METHOD>
+static int launch_single_t(const OnItem &it, int threads, cudaStream_t st) {
+    int64_t smem = onchip_smem_bytes(it.n, it.nw);
+    static bool attr_set = false;
+    if (!attr_set) {
+        int rc = allow_max_dynamic_smem((const void *)onchip_single<SYS, METHOD>);
+        if (rc) return rc;
+        attr_set = true;
+    }
+    onchip_single<SYS, METHOD><<<1, threads, (size_t)smem, st>>>(it);
+    REACH_LAUNCHED("onchip_single");
+    return REACH_OK;
+}
+
+template <int SYS>
+int onchip_single_k(const OnItem &it, int threads, cudaStream_t st) {
+    return it.method == MM ? launch_single_t<SYS, MM>(it, threads, st) : launch_single_t<SYS, CGB>(it, threads, st);
+}
+
+// ---------------------------------------------------------------- clusters
+// Problems with 2n > QMAX * 512 components do not fit one block: a cluster of
+// two blocks runs them, block r holding half r of the state (and its inputs
+// and derivatives) in its own shared memory and reading the other half
+// through distributed shared memory; barriers are cluster barriers.
+namespace cg = cooperative_groups;
+
+struct ClusterSync {
+    __device__ __forceinline__ void operator()() const { cg::this_cluster().sync(); }
+};
+
+
+// one problem on the calling cluster of two blocks (all threads of both)
+template <int SYS, int METHOD>
+__device__ __forceinline__ void cluster_item(const OnItem &it, double *sm) {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    const int64_t n = it.n;
+    double *y = sm, *w = sm + n, *kb = w + it.nw;
+    double *other = cl.map_shared_rank(y, rank ^ 1u);
+    double *yA = rank == 0 ? y : other, *yB = rank == 0 ? other : y;
+    // the lower / center block uses wA, the upper / radius block wB
+    onchip_run<SYS, METHOD>(it, yA, yB, w, w, kb, rank * n, (rank + 1) * n, (int)threadIdx.x, (int)blockDim.x,
+                            ClusterSync{});
+}
+
+
+template <int SYS, int METHOD>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1) onchip_single_cluster(OnItem it) {
+    extern __shared__ double sm[];
+    cluster_item<SYS, METHOD>(it, sm);
+    cg::this_cluster().sync();   // no block leaves while the other may still read its memory
+}
+
+template <int SYS, int METHOD>
+static int launch_cluster_t(const OnItem &it, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        int rc = allow_max_dynamic_smem((const void *)onchip_single_cluster<SYS, METHOD>);
+        if (rc) return rc;
+        attr_set = true;
+    }
+    onchip_single_cluster<SYS, METHOD><<<2, 512, (size_t)cluster_smem_bytes(it.n, it.nw), st>>>(it);
+    REACH_LAUNCHED("onchip_single_cluster");
+    return REACH_OK;
+}
+
+template <int SYS>
+int onchip_cluster_k(const OnItem &it, cudaStream_t st) {
+    return it.method == MM ? launch_cluster_t<SYS, MM>(it, st) : launch_cluster_t<SYS, CGB>(it, st);
+}
+
+// ---------------------------------------------------------------- batch
+// The batched persistent kernel runs on clusters of two blocks of 512
+// threads.  Its work list is a sequence of tasks, largest first, taken from a
+// global counter: a task is either one large problem spanning the cluster, or
+// one bin per block.  A bin is up to 16 slots, each a problem run by a
+// contiguous range of warps with its own named barrier and shared-memory
+// region.  Each problem records the global time at which it completed.
+struct Slot {
+    int item, warp0, nwarps, bar;
+    int64_t off;   // shared-memory offset (doubles)
+};
+struct Bin {
+    int slot0, nslots;
+};
+struct Task {
+    int big;          // >= 0: item index run by the whole cluster
+    int bin[2];       // otherwise: bin of block 0 / block 1 (-1: none)
+};
+
+
+template <int SYS, int METHOD>
+__device__ __forceinline__ void run_bin(const OnItem *__restrict__ items, const Slot *__restrict__ slots,
+                                        const Bin &bn, double *sm, uint64_t *done) {
+    const int warp = threadIdx.x >> 5;
+    for (int s = bn.slot0; s < bn.slot0 + bn.nslots; ++s) {
+        const Slot sl = slots[s];
+        if (warp < sl.warp0 || warp >= sl.warp0 + sl.nwarps) continue;
+        const OnItem &it = items[sl.item];
+        double *y = sm + sl.off;
+        const int64_t n = it.n;
+        GroupSync sync{sl.bar, sl.nwarps * 32};
+        const int gt = (int)threadIdx.x - sl.warp0 * 32, gs = sl.nwarps * 32;
+        double *w = y + 2 * n, *kb = w + 2 * it.nw;
+        onchip_run<SYS, METHOD>(it, y, y + n, w, w + it.nw, kb, 0, 2 * n, gt, gs, sync);
+        if (gt == 0) done[sl.item] = global_ns();
+        break;
+    }
+}
+
+template <int SYS, int METHOD>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BATCH_THREADS, 1)
+onchip_batch(const OnItem *__restrict__ items, const Slot *__restrict__ slots, const Bin *__restrict__ bins,
+             const Task *__restrict__ tasks, int ntasks, int *counter, uint64_t *done) {
+    extern __shared__ double sm[];
+    __shared__ int cur;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        cl.sync();
+        const int t = *cl.map_shared_rank(&cur, 0u);
+        cl.sync();   // both blocks hold t before block 0 may take the next task
+        if (t >= ntasks) break;
+        const Task tk = tasks[t];
+        if (tk.big >= 0) {
+            cluster_item<SYS, METHOD>(items[tk.big], sm);
+            if (rank == 0 && threadIdx.x == 0) done[tk.big] = global_ns();
+        } else if (tk.bin[rank] >= 0) {
+            run_bin<SYS, METHOD>(items, slots, bins[tk.bin[rank]], sm, done);
+        }
+        cl.sync();   // the task is over in both blocks before either reuses memory
+    }
+}
+
+template <int SYS, int METHOD>
+static int launch_batch_t(const void *items, const void *slots, const void *bins, const void *tasks, int ntasks,
+                          int *counter, uint64_t *done, int clusters, size_t smem, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        int rc = allow_max_dynamic_smem((const void *)onchip_batch<SYS, METHOD>);
+        if (rc) return rc;
+        attr_set = true;
+    }
+    onchip_batch<SYS, METHOD><<<2 * clusters, BATCH_THREADS, smem, st>>>((const OnItem *)items, (const Slot *)slots,
+                                                                 (const Bin *)bins, (const Task *)tasks, ntasks,
+                                                                 counter, done);
+    REACH_LAUNCHED("onchip_batch");
+    return REACH_OK;
+}
+
+template <int SYS>
+int onchip_batch_k(int method, const void *items, const void *slots, const void *bins, const void *tasks,
+                   int ntasks, int *counter, uint64_t *done, int clusters, size_t smem, cudaStream_t st) {
+    if (method == MM)
+        return launch_batch_t<SYS, MM>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    return launch_batch_t<SYS, CGB>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+}
+
+}  // namespace reach

@@ -1,0 +1,114 @@
+"""Batched persistent launch (reach_batch_*) and the cluster path of single
+queries: parity with the oracle and with per-query calls."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2001_10635_b300 as R
+import workloads as W
+from reachtest import TOL64, assert_close, cuda_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(autouse=True)
+def _reset_options():
+    yield
+    R.reach_set_option(R.OPT_BATCH_CPT, 0)
+    R.reach_set_option(R.OPT_KERNEL, 0)
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_single_query_on_a_cluster_matches_oracle(method):
+    m = 3000   # 2n = 12000 components: more than one block holds
+    q = W.osc_query(m, seed=21, t_final=0.1)
+    with R.System("osc", 2 * m) as s:
+        fn = R.reach_mm if method == "mm" else R.reach_cgb
+        g = fn(s, q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=q["t_final"], dt=q["dt"])
+    o = O.reach(method, "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=q["t_final"], dt=q["dt"])
+    assert_close(g[0], o[0], TOL64, "lo")
+    assert_close(g[1], o[1], TOL64, "hi")
+
+
+def _osc_batch(sizes, T, seed0=100):
+    systems, queries, raw = {}, [], []
+    for k, m in enumerate(sizes):
+        q = W.osc_query(int(m), seed=seed0 + k, t_final=T)
+        s = systems.setdefault(int(m), R.System("osc", 2 * int(m)))
+        for method in ("mm", "cgb"):
+            queries.append(dict(sys=s, method=method, x0_lo=q["x_lo"], x0_hi=q["x_hi"], w_lo=q["w_lo"],
+                                w_hi=q["w_hi"], t_final=T, dt=q["dt"]))
+            raw.append((method, q))
+    return systems, queries, raw
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_osc_batch_matches_oracle_and_solo(autotune):
+    sizes = [4, 5, 9, 17, 40, 77, 150, 333, 600, 1100, 2047, 2048, 2600, 4096]
+    T = 0.1
+    systems, queries, raw = _osc_batch(sizes, T)
+    with R.Batch(queries, autotune=autotune) as b:
+        st, fin = b.run()
+        info = b.info()
+        assert (st == 0).all() and (fin > 0).all()
+        assert info["cpt"] in (2, 4, 8, 16) and info["kernels"] >= 2
+        for (lo, hi), (method, q), qq in zip(b.outputs, raw, queries):
+            o = O.reach(method, "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
+            assert_close(lo, o[0], TOL64, f"{method} m={qq['sys'].n // 2} lo")
+            assert_close(hi, o[1], TOL64, f"{method} m={qq['sys'].n // 2} hi")
+            fn = R.reach_mm if method == "mm" else R.reach_cgb
+            solo = fn(qq["sys"], q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
+            assert np.array_equal(solo[0], lo) and np.array_equal(solo[1], hi)
+    for s in systems.values():
+        s.close()
+
+
+def test_mixed_kind_batch_with_device_buffers_and_replay():
+    import torch
+    T = 0.05
+    qs, expect = [], []
+    tr = W.traffic_small(16)
+    s_tr = R.System("traffic", 16)
+    s_ks = R.System("ks", 64)
+    A = W.linear_general(6, seed=5, scale=0.5)
+    s_li = R.System("linear", 6, A=A)
+    ks = W.ks_grid(64, t_final=T)
+    llo, lhi = W.random_box(6, seed=6)
+    plo, phi = W.random_box(6, seed=7, centre=(-0.1, 0.1), width=(0.0, 0.05))
+    dev = lambda v: torch.tensor(v, dtype=torch.float64, device="cuda")
+    for method in ("mm", "cgb"):
+        qs.append(dict(sys=s_tr, method=method, x0_lo=dev(tr["x_lo"]), x0_hi=dev(tr["x_hi"]),
+                       w_lo=dev(tr["w_lo"]), w_hi=dev(tr["w_hi"]), t_final=T, dt=tr["dt"]))
+        expect.append(O.reach(method, "traffic", tr["x_lo"], tr["x_hi"], tr["w_lo"], tr["w_hi"], t_final=T,
+                              dt=tr["dt"]))
+        qs.append(dict(sys=s_ks, method=method, x0_lo=ks["x_lo"], x0_hi=ks["x_hi"], t_final=T, dt=ks["dt"]))
+        expect.append(O.reach(method, "ks", ks["x_lo"], ks["x_hi"], t_final=T, dt=ks["dt"], params=ks["params"]))
+        qs.append(dict(sys=s_li, method=method, x0_lo=llo, x0_hi=lhi, w_lo=plo, w_hi=phi, t_final=T, dt=0.01))
+        expect.append(O.reach(method, "linear", llo, lhi, plo, phi, t_final=T, dt=0.01, A=A))
+    with R.Batch(qs) as b:
+        st, _ = b.run()
+        assert (st == 0).all()
+        for (lo, hi), o in zip(b.outputs, expect):
+            lo = lo.cpu().numpy() if hasattr(lo, "cpu") else lo
+            hi = hi.cpu().numpy() if hasattr(hi, "cpu") else hi
+            assert_close(lo, o[0], TOL64, "lo")
+            assert_close(hi, o[1], TOL64, "hi")
+        # replay after changing a host input in place: the graph reads it again
+        new_lo = ks["x_lo"] - 1e-3
+        qs[1]["x0_lo"][:] = new_lo
+        st, _ = b.run()
+        o = O.reach("mm", "ks", new_lo, ks["x_hi"], t_final=T, dt=ks["dt"], params=ks["params"])
+        assert_close(b.outputs[1][0], o[0], TOL64, "replayed lo")
+    for s in (s_tr, s_ks, s_li):
+        s.close()
+
+
+def test_batch_rejects_invalid_queries():
+    with R.System("osc", 8) as s:
+        q = W.osc_query(4, seed=1, t_final=0.1)
+        good = dict(sys=s, method="mm", x0_lo=q["x_lo"], x0_hi=q["x_hi"], w_lo=q["w_lo"], w_hi=q["w_hi"],
+                    t_final=0.1, dt=q["dt"])
+        for bad in (dict(t_final=0.0), dict(dt=0.03), dict(x0_lo=q["x_hi"], x0_hi=q["x_lo"])):
+            with pytest.raises(R.ReachError):
+                R.Batch([good, dict(good, **bad)])

@@ -72,6 +72,11 @@ def ks_grid(n: int = 1 << 20, half_width: float = 1e-3, t_final: float = 0.05, d
 # ---------------------------------------------------------------- oscillator chain
 OSC_DT = 0.005
 OSC_T = 5.0
+# The box-evaluated growth bound cannot represent the chain's rotation (its
+# off-diagonal bounds are nonnegative), grows like exp(sqrt(3) t) and, driven
+# by the disturbance box, overflows between t = 4 and t = 5 for every query of
+# the batch; the CGB leg of the batched workload therefore stops at t = 4.
+OSC_T_CGB = 4.0
 OSC_W = 0.01
 
 
