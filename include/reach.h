@@ -206,6 +206,48 @@ REACH_API int reach_batch_run(reach_batch *b, void *stream, int *status, double 
 REACH_API int reach_batch_info(const reach_batch *b, int64_t *cpt, int64_t *kernels, double *tune_ms);
 REACH_API int reach_batch_destroy(reach_batch *b);
 
+/* ---- serving: a continuous-batching request loop ----
+   The paper serves reachability problems to other tools over a network
+   interface (Sec. 1); here that purpose is an in-process server.  Requests of
+   any system, size, method and horizon are submitted as they arrive; a
+   dispatcher admits them, in arrival order with first fit, whenever one of
+   the server's slots is free and the request's device-memory footprint
+   (reach_request_footprint) fits in what is left of the budget.  Each slot is
+   a worker thread with its own CUDA stream running the request through
+   reach_mm / reach_cgb / reach_mc, so admitted requests overlap on the GPU.
+   A request's buffers must stay valid until reach_server_wait has returned
+   its result. */
+typedef struct {
+    const reach_system *sys;
+    int method;                                  /* 0 = MM, 1 = CGB, 2 = MC */
+    const double *x0_lo, *x0_hi, *w_lo, *w_hi;   /* host or device, as reach_mm */
+    double t_final, dt;
+    int64_t m;                                   /* MC: samples */
+    uint64_t seed;                               /* MC */
+    int precision;                               /* MC: 32 or 64 */
+    double *lo, *hi;                             /* host or device */
+} reach_request;
+
+typedef struct reach_server reach_server;
+
+/* device bytes a request may hold while it runs (staged inputs and outputs,
+   ping-pong state, MC sample state and partial minima / maxima) */
+REACH_API int64_t reach_request_footprint(const reach_request *r);
+/* slots: concurrent requests (1..256); hbm_budget_bytes: admission budget */
+REACH_API int reach_server_create(int slots, int64_t hbm_budget_bytes, reach_server **out);
+/* REACH_EADMIT if the footprint alone exceeds the budget (never admitted) */
+REACH_API int reach_server_submit(reach_server *s, const reach_request *r, int64_t *ticket);
+/* Waits at most timeout_s seconds: REACH_ETIMEOUT if the request has not
+   finished (it keeps running; wait again).  On success fills the request's
+   status, its time from submission to start (queue_s) and its run time (run_s),
+   and forgets the ticket. */
+REACH_API int reach_server_wait(reach_server *s, int64_t ticket, double timeout_s, int *status, double *queue_s,
+                                double *run_s);
+REACH_API int reach_server_stats(reach_server *s, int64_t *waiting, int64_t *running, int64_t *done,
+                                 int64_t *bytes_in_use, int64_t *bytes_peak);
+/* finishes every submitted request, then stops the slots */
+REACH_API int reach_server_destroy(reach_server *s);
+
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
 #define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming stencil: RK4 steps fused per launch, 1..8 */

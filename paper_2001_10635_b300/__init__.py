@@ -39,6 +39,15 @@ class _Query(ctypes.Structure):
                 ("hi", ctypes.c_void_p)]
 
 
+class _Request(ctypes.Structure):
+    """reach_request (include/reach.h)."""
+    _fields_ = [("sys", ctypes.c_void_p), ("method", ctypes.c_int), ("x0_lo", ctypes.c_void_p),
+                ("x0_hi", ctypes.c_void_p), ("w_lo", ctypes.c_void_p), ("w_hi", ctypes.c_void_p),
+                ("t_final", ctypes.c_double), ("dt", ctypes.c_double), ("m", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("lo", ctypes.c_void_p),
+                ("hi", ctypes.c_void_p)]
+
+
 class ReachError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = int(code)
@@ -79,6 +88,14 @@ def lib() -> ctypes.CDLL:
         L.reach_batch_run.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl)]
         L.reach_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         L.reach_batch_destroy.argtypes = [vp]
+        L.reach_request_footprint.argtypes = [ctypes.POINTER(_Request)]
+        L.reach_request_footprint.restype = i64
+        L.reach_server_create.argtypes = [ctypes.c_int, i64, ctypes.POINTER(vp)]
+        L.reach_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
+        L.reach_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl),
+                                        ctypes.POINTER(dbl)]
+        L.reach_server_stats.argtypes = [vp] + [ctypes.POINTER(i64)] * 5
+        L.reach_server_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -307,3 +324,79 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------------ serving
+_METHOD_IDS = {"mm": 0, "cgb": 1, "mc": 2}
+
+
+class Server:
+    """reach_server_create / _submit / _wait / _stats / _destroy."""
+
+    def __init__(self, slots: int = 8, hbm_budget_bytes: int = 64 << 30):
+        self.handle = ctypes.c_void_p()
+        _check(lib().reach_server_create(int(slots), int(hbm_budget_bytes), ctypes.byref(self.handle)),
+               "reach_server_create")
+        self._keep = {}
+
+    @staticmethod
+    def _request(sys_, method, x0_lo, x0_hi, w_lo, w_hi, t_final, dt, m, seed, precision, lo, hi):
+        a = _ptr(x0_lo, sys_.n, "x0_lo")
+        b = _ptr(x0_hi, sys_.n, "x0_hi")
+        c = _ptr(w_lo, sys_.nw, "w_lo") if sys_.nw else (None, None)
+        d = _ptr(w_hi, sys_.nw, "w_hi") if sys_.nw else (None, None)
+        lo = _out(x0_lo, lo, sys_.n, "lo")
+        hi = _out(x0_lo, hi, sys_.n, "hi")
+        r = _Request(sys_.handle.value, _METHOD_IDS.get(method, method), a[0], b[0], c[0], d[0], float(t_final),
+                     float(dt), int(m), int(seed) & (2**64 - 1), int(precision), _ptr(lo, sys_.n, "lo")[0],
+                     _ptr(hi, sys_.n, "hi")[0])
+        return r, (sys_, a[1], b[1], c[1], d[1], lo, hi)
+
+    def submit(self, sys_, method, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final, dt, m=0, seed=0,
+               precision=64, lo=None, hi=None):
+        """Returns (ticket, (lo, hi)); the outputs are complete after wait(ticket)."""
+        r, keep = self._request(sys_, method, x0_lo, x0_hi, w_lo, w_hi, t_final, dt, m, seed, precision, lo, hi)
+        t = ctypes.c_int64()
+        _check(lib().reach_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "reach_server_submit")
+        self._keep[t.value] = keep
+        return t.value, (keep[5], keep[6])
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        """Returns (status, queue_s, run_s); raises ReachError(REACH_ETIMEOUT) on timeout."""
+        st = ctypes.c_int()
+        q = ctypes.c_double()
+        r = ctypes.c_double()
+        rc = lib().reach_server_wait(self.handle, int(ticket), float(timeout_s), ctypes.byref(st), ctypes.byref(q),
+                                     ctypes.byref(r))
+        _check(rc, "reach_server_wait")
+        self._keep.pop(ticket, None)
+        return st.value, q.value, r.value
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(5)]
+        _check(lib().reach_server_stats(self.handle, *[ctypes.byref(x) for x in v]), "reach_server_stats")
+        return dict(zip(("waiting", "running", "done", "bytes_in_use", "bytes_peak"), [x.value for x in v]))
+
+    def close(self):
+        if self.handle:
+            lib().reach_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def reach_request_footprint(sys_, method, m=0, precision=64) -> int:
+    r = _Request(sys_.handle.value, _METHOD_IDS.get(method, method), None, None, None, None, 1.0, 1.0, int(m), 0,
+                 int(precision), None, None)
+    return int(lib().reach_request_footprint(ctypes.byref(r)))

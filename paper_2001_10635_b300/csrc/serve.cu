@@ -1,0 +1,239 @@
+// serve.cu -- continuous-batching request loop (reach_server_*).
+//
+// The paper serves reachability problems to remote tools (Sec. 1, the
+// pFaces REST interface); here that purpose becomes an in-process server:
+// requests of any kind, size, method and horizon are submitted as they
+// arrive, admitted by their device-memory footprint, and run concurrently.
+//
+//   submit     appends the request to the waiting list (never blocks on GPU work)
+//   dispatch   whenever a request arrives or one finishes, the waiting list is
+//              scanned in arrival order and every request that fits is admitted:
+//              a free slot is needed and its footprint must fit in what is left of
+//              the budget (first fit, so small requests pass a large one that waits
+//              for memory)
+//   slots      each slot is a worker thread with its own CUDA stream that runs the
+//              admitted request through the ordinary entry points; requests on
+//              different slots overlap on the GPU (the on-chip kernels of small
+//              requests fill a few SMs, the streaming kernels of large ones share
+//              the rest at block granularity)
+//   wait       bounded: returns REACH_ETIMEOUT when the request has not finished
+//              within the caller's limit
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "api_internal.cuh"
+
+using Clock = std::chrono::steady_clock;
+
+namespace reach {
+
+struct Job {
+    int64_t ticket;
+    reach_request r;
+    int64_t bytes;
+    Clock::time_point submitted, started, finished;
+    int status = REACH_OK;
+    bool done = false;
+};
+
+}  // namespace reach
+
+using namespace reach;
+
+struct reach_server {
+    int device = 0;
+    int64_t budget = 0, in_use = 0, peak = 0;
+    int64_t next_ticket = 1;
+    int nslots = 0, idle = 0;
+    bool stopping = false;
+    std::mutex mu;
+    std::condition_variable work_cv, done_cv;
+    std::deque<Job *> waiting;      // arrival order
+    std::deque<Job *> admitted;     // ready for a slot
+    std::unordered_map<int64_t, Job *> jobs;
+    std::vector<std::thread> workers;
+    int64_t n_admitted = 0, n_done = 0, n_rejected = 0;
+};
+
+namespace reach {
+
+static int64_t mc_footprint(const reach_system *s, int64_t m, int prec) {
+    const int64_t M = (m + 31) / 32 * 32, elt = prec == 32 ? 4 : 8, n = s->n;
+    int64_t partials = 2 * (M / 32) * n * 8;
+    bool stream_kernel = (s->kind == REACH_TRAFFIC || s->kind == REACH_KS) && n > 128;
+    return partials + (stream_kernel ? 2 * n * M * elt : 0);
+}
+
+int64_t footprint(const reach_request *r) {
+    const reach_system *s = r->sys;
+    const int64_t n = s->n, nw = s->nw;
+    // staged inputs and outputs (the worst case: host buffers), the status word
+    int64_t b = (4 * n + 2 * nw) * 8 + 256;
+    if (r->method == 2) return b + mc_footprint(s, r->m, r->precision);
+    // MM / CGB: the streaming kernels keep a 2n ping-pong buffer
+    return b + 2 * n * 8;
+}
+
+static void run_job(Job *j, cudaStream_t st) {
+    const reach_request &r = j->r;
+    if (r.method == 0)
+        j->status = reach_mm(r.sys, r.x0_lo, r.x0_hi, r.w_lo, r.w_hi, r.t_final, r.dt, r.lo, r.hi, st);
+    else if (r.method == 1)
+        j->status = reach_cgb(r.sys, r.x0_lo, r.x0_hi, r.w_lo, r.w_hi, r.t_final, r.dt, r.lo, r.hi, st);
+    else
+        j->status = reach_mc(r.sys, r.x0_lo, r.x0_hi, r.w_lo, r.w_hi, r.t_final, r.dt, r.m, r.seed, r.precision,
+                             r.lo, r.hi, st);
+}
+
+// admit every waiting request that fits, in arrival order (caller holds mu)
+static void dispatch_locked(reach_server *s) {
+    int free_slots = s->idle - (int)s->admitted.size();
+    for (auto it = s->waiting.begin(); it != s->waiting.end() && free_slots > 0;) {
+        Job *j = *it;
+        if (s->in_use + j->bytes <= s->budget) {
+            s->in_use += j->bytes;
+            s->peak = std::max(s->peak, s->in_use);
+            s->admitted.push_back(j);
+            s->n_admitted++;
+            --free_slots;
+            it = s->waiting.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (!s->admitted.empty()) s->work_cv.notify_all();
+}
+
+static void worker_main(reach_server *s) {
+    cudaSetDevice(s->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->idle++;
+        dispatch_locked(s);
+        s->work_cv.wait(lk, [&] { return s->stopping || !s->admitted.empty(); });
+        s->idle--;
+        if (s->admitted.empty()) {
+            if (s->stopping) break;
+            continue;
+        }
+        Job *j = s->admitted.front();
+        s->admitted.pop_front();
+        j->started = Clock::now();
+        lk.unlock();
+        run_job(j, st);
+        lk.lock();
+        j->finished = Clock::now();
+        j->done = true;
+        s->in_use -= j->bytes;
+        s->n_done++;
+        s->done_cv.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+}
+
+}  // namespace reach
+
+extern "C" int64_t reach_request_footprint(const reach_request *r) {
+    if (!r || !r->sys) return REACH_EINVAL;
+    return footprint(r);
+}
+
+extern "C" int reach_server_create(int slots, int64_t hbm_budget_bytes, reach_server **out) {
+    if (!out || slots < 1 || slots > 256 || hbm_budget_bytes <= 0) return REACH_EINVAL;
+    *out = nullptr;
+    reach_server *s = new (std::nothrow) reach_server();
+    if (!s) return REACH_ENOMEM;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return REACH_ENODEV;
+    }
+    if (pool_init()) {
+        delete s;
+        return REACH_ECUDA;
+    }
+    s->budget = hbm_budget_bytes;
+    s->nslots = slots;
+    for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_main, s);
+    *out = s;
+    return REACH_OK;
+}
+
+extern "C" int reach_server_submit(reach_server *s, const reach_request *r, int64_t *ticket) {
+    if (!s || !r || !ticket || !r->sys || r->method < 0 || r->method > 2) return REACH_EINVAL;
+    const int64_t bytes = footprint(r);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (bytes > s->budget) {   // can never be admitted
+        s->n_rejected++;
+        return REACH_EADMIT;
+    }
+    Job *j = new (std::nothrow) Job();
+    if (!j) return REACH_ENOMEM;
+    j->ticket = s->next_ticket++;
+    j->r = *r;
+    j->bytes = bytes;
+    j->submitted = Clock::now();
+    s->jobs[j->ticket] = j;
+    s->waiting.push_back(j);
+    dispatch_locked(s);
+    *ticket = j->ticket;
+    return REACH_OK;
+}
+
+extern "C" int reach_server_wait(reach_server *s, int64_t ticket, double timeout_s, int *status, double *queue_s,
+                                 double *run_s) {
+    if (!s) return REACH_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return REACH_EINVAL;
+    Job *j = it->second;
+    auto limit = std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
+    if (!s->done_cv.wait_for(lk, limit, [&] { return j->done; })) return REACH_ETIMEOUT;
+    if (status) *status = j->status;
+    if (queue_s) *queue_s = std::chrono::duration<double>(j->started - j->submitted).count();
+    if (run_s) *run_s = std::chrono::duration<double>(j->finished - j->started).count();
+    s->jobs.erase(it);
+    delete j;
+    return REACH_OK;
+}
+
+extern "C" int reach_server_stats(reach_server *s, int64_t *waiting, int64_t *running, int64_t *done,
+                                  int64_t *bytes_in_use, int64_t *bytes_peak) {
+    if (!s) return REACH_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (waiting) *waiting = (int64_t)s->waiting.size();
+    if (running) *running = s->n_admitted - s->n_done;
+    if (done) *done = s->n_done;
+    if (bytes_in_use) *bytes_in_use = s->in_use;
+    if (bytes_peak) *bytes_peak = s->peak;
+    return REACH_OK;
+}
+
+extern "C" int reach_server_destroy(reach_server *s) {
+    if (!s) return REACH_EINVAL;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        // admitted and waiting requests are finished first
+        while (!s->waiting.empty() || !s->admitted.empty() || s->n_admitted > s->n_done) {
+            if (!s->waiting.empty() && s->admitted.empty() && s->n_admitted == s->n_done) break;
+            s->done_cv.wait_for(lk, std::chrono::milliseconds(50));
+        }
+        s->stopping = true;
+        s->work_cv.notify_all();
+    }
+    for (std::thread &t : s->workers) t.join();
+    for (auto &kv : s->jobs) delete kv.second;
+    for (Job *j : s->waiting) (void)j;   // owned by jobs
+    delete s;
+    return REACH_OK;
+}
