@@ -55,7 +55,7 @@ int allow_max_dynamic_smem(const void *fn);
 int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st);
 int64_t cluster_smem_bytes(int64_t n, int64_t nw);
 int onchip_launch_cluster(const OnItem &it, cudaStream_t st);
-int onchip_launch_batch(int kind, int method, const void *items, const void *slots, const void *bins,
+int onchip_launch_batch(int kind, int method, int q, const void *items, const void *slots, const void *bins,
                         const void *tasks, int ntasks, int *counter, uint64_t *done, int clusters, size_t smem,
                         cudaStream_t st);
 int onchip_launch_stamp(uint64_t *t0, cudaStream_t st);

@@ -66,6 +66,7 @@ struct reach_batch {
     cudaStream_t cap = nullptr;
     int nkernels = 0;
     int cpt = 0;
+    int plan_cpt = 16;   // the layout currently planned (tuning tries several)
     double tune_ms[4] = {0, 0, 0, 0};
 };
 
@@ -85,10 +86,10 @@ static int plan_group(reach_batch *b, Group &g, int cpt, int64_t n_override, std
         const int64_t comps = 2 * it.n;
         const int64_t N = n_override > 0 ? std::min<int64_t>(n_override, it.N) : it.N;
         const int64_t sm1 = onchip_smem_bytes(it.n, it.nw);
-        if (comps <= ITEM_MAX_BLOCK && sm1 <= smem_cap) {
-            int64_t w = ceil_div(comps, 32LL * cpt);
-            w = std::max(w, ceil_div(comps, 32LL * QMAX));
-            w = std::min<int64_t>(std::max<int64_t>(w, 1), BIN_WARPS);
+        // a bin slot holds at most cpt components per thread (the kernel is
+        // instantiated for that loop length) and at most one block of warps
+        if (comps <= (int64_t)BIN_WARPS * 32 * cpt && sm1 <= smem_cap) {
+            const int64_t w = std::max<int64_t>(1, ceil_div(comps, 32LL * cpt));
             small.push_back({qi, (int)w, sm1, ceil_div(comps, 32 * w) * N});
         } else if (comps <= 2 * ITEM_MAX_BLOCK && cluster_smem_bytes(it.n, it.nw) <= smem_cap) {
             big.push_back({qi, cluster_smem_bytes(it.n, it.nw), ceil_div(it.n, 512) * N});
@@ -186,6 +187,7 @@ static void free_groups(reach_batch *b) {
 
 static int plan_all(reach_batch *b, int cpt, int64_t n_override) {
     free_groups(b);
+    b->plan_cpt = cpt;
     std::vector<char> keep;
     for (Group &g : b->groups) {
         int rc = plan_group(b, g, cpt, n_override, keep);
@@ -207,7 +209,7 @@ static int enqueue(reach_batch *b, cudaStream_t st, bool with_copies) {
     if ((rc = onchip_launch_stamp(b->d_done + b->count, st))) return rc;
     for (size_t k = 0; k < b->groups.size(); ++k) {
         Group &g = b->groups[k];
-        if ((rc = onchip_launch_batch(g.kind, g.method, g.d_items, g.d_slots, g.d_bins, g.d_tasks, g.ntasks,
+        if ((rc = onchip_launch_batch(g.kind, g.method, b->plan_cpt, g.d_items, g.d_slots, g.d_bins, g.d_tasks, g.ntasks,
                                       b->d_counters + k, b->d_done, g.clusters, g.smem, st)))
             return rc;
     }

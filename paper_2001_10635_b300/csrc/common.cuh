@@ -75,6 +75,19 @@ __device__ __forceinline__ bool kfinite(double x) {
     return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// periodic index of g on a grid of n points without integer division (which
+// this GPU emulates partly on the FP64 pipe): one conditional wrap covers the
+// rows a tile can reach when n is at least the tile, a bounded loop the rest
+__device__ __forceinline__ int64_t wrap_index(int64_t g, int64_t n) {
+    g = g < 0 ? g + n : g;
+    g = g >= n ? g - n : g;
+    if (g < 0 || g >= n) {
+        while (g < 0) g += n;
+        while (g >= n) g -= n;
+    }
+    return g;
+}
+
 // global nanosecond clock of the GPU
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;

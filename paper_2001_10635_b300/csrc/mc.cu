@@ -12,6 +12,7 @@
 //               launch and the min/max into the last.
 // Per-block partial minima / maxima are combined by mc_reduce (no atomics, so
 // the result does not depend on scheduling).
+#include <algorithm>
 #include <cmath>
 
 #include "api_internal.cuh"
@@ -22,9 +23,14 @@ constexpr int MC_WARPS = 16;            // warps per block
 constexpr int MC_THREADS = 32 * MC_WARPS;
 constexpr int MC_Q = 8;                 // component rows per thread (on-chip)
 
-// minimum on the integer pipe for doubles (the FP64 pipe is the scarce one)
+// Precision-explicit helpers: a float trajectory must stay on the FP32 pipe
+// (an overload that promotes to double would run the stage arithmetic and two
+// conversions per operation on the FP64 pipe); minima of doubles use the
+// integer pipe.
 __device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double tmin(double a, double b) { return kmin(a, b); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 
 // ------------------------------------------------------------------ plain f
 // Y: rows of 32 samples (row c at Y + 32 c), P: input rows.  `g` is the
@@ -37,7 +43,7 @@ struct Plain<REACH_TRAFFIC, T> {
     static constexpr int R = 1;
     // flux out of global cell g given its row value y and right neighbour yr
     static __device__ __forceinline__ T flux(const T *q, T y, T yr, int64_t g, int64_t n, T d) {
-        T cong = (g == n - 1) ? q[0] : fma(-q[2], yr, q[3]);
+        T cong = (g == n - 1) ? q[0] : tfma(-q[2], yr, q[3]);
         T f = tmin(q[0], tmin(q[1] * y, cong));
         f = (g == -1) ? d : f;
         f = (g < -1 || g >= n) ? T(0) : f;
@@ -58,8 +64,8 @@ struct Plain<REACH_KS, T> {
     template <class Row>
     static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
         T um2 = row(c - 2), um1 = row(c - 1), u = row(c), up1 = row(c + 1), up2 = row(c + 2);
-        T lin = fma(q[2], um2 + up2, fma(q[1], um1 + up1, q[0] * u));
-        return fma(-q[3] * u, up1 - um1, lin);
+        T lin = tfma(q[2], um2 + up2, tfma(q[1], um1 + up1, q[0] * u));
+        return tfma(-q[3] * u, up1 - um1, lin);
     }
 };
 
@@ -74,9 +80,9 @@ struct Plain<REACH_OSC, T> {
         const int j = c - m;
         T z = row(j);
         T xl = (j > 0) ? row(j - 1) : T(0), xr = (j < m - 1) ? row(j + 1) : T(0);
-        T t = fma(q[1] * z, z, q[0]);
-        T r = fma(q[2], fma(T(-2), z, xl + xr), P[j * 32 + lane]);
-        return fma(-t, z, r);
+        T t = tfma(q[1] * z, z, q[0]);
+        T r = tfma(q[2], tfma(T(-2), z, xl + xr), P[j * 32 + lane]);
+        return tfma(-t, z, r);
     }
 };
 
@@ -89,7 +95,7 @@ struct Plain<REACH_LINEAR, T> {
         T acc = T(0);
         const double *Ar = A + (int64_t)c * n;
 #pragma unroll 1
-        for (int j = 0; j < (int)n; ++j) acc = fma((T)__ldg(Ar + j), row(j), acc);
+        for (int j = 0; j < (int)n; ++j) acc = tfma((T)__ldg(Ar + j), row(j), acc);
         return acc + P[c * 32 + lane];
     }
 };
@@ -107,18 +113,26 @@ __device__ __forceinline__ void mc_consts(const double *prm, T (&q)[4]) {
 template <class T>
 __device__ __forceinline__ T as_run(double v) { return (T)v; }
 
-// warp min / max over the valid lanes of one component row; lane 0 writes
+// warp min / max over the valid lanes of one component row, in the
+// trajectory's own precision (no FP64 work for binary32 samples); lane 0
+// writes the pair as binary64
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return kmax(a, b); }
+__device__ __forceinline__ bool tfinite(float v) { return isfinite(v); }
+__device__ __forceinline__ bool tfinite(double v) { return kfinite(v); }
+
 template <class T>
 __device__ __forceinline__ void warp_minmax(T v, bool valid, double *plo, double *phi, int *status) {
-    double a = valid ? (double)v : INFINITY, b = valid ? (double)v : -INFINITY;
-    bool bad = valid && !isfinite((double)v);
+    const T inf = (T)INFINITY;
+    T a = valid ? v : inf, b = valid ? v : -inf;
+    const bool bad = valid && !tfinite(v);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        a = tmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = tmax(b, __shfl_xor_sync(0xffffffffu, b, o));
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
-    if ((threadIdx.x & 31) == 0) { *plo = a; *phi = b; }
+    if ((threadIdx.x & 31) == 0) { *plo = (double)a; *phi = (double)b; }
 }
 
 struct McArgs {
@@ -190,10 +204,10 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
                 if (c < n) {
                     T y;
                     if (stage == 0) acc[s] = kk[s];
-                    else if (stage < 3) acc[s] = fma(T(2), kk[s], acc[s]);
+                    else if (stage < 3) acc[s] = tfma(T(2), kk[s], acc[s]);
                     else acc[s] += kk[s];
-                    if (stage < 3) y = fma(cst, kk[s], z[s]);
-                    else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
+                    if (stage < 3) y = tfma(cst, kk[s], z[s]);
+                    else { z[s] = tfma(h6, acc[s], z[s]); y = z[s]; }
                     Y[c * 32 + lane] = y;
                 }
             }
@@ -209,10 +223,20 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
 }
 
 // ------------------------------------------------------------------ streaming
+// Large stencil systems.  State in HBM, sample-fastest (x[i * M + j]); one
+// launch advances S RK4 steps.  A block covers 32 samples (lane = sample) and
+// WPB * MC_B consecutive components (rows); each warp owns MC_B rows in
+// registers, so the stencil along the rows is register-local and only R edge
+// rows per warp cross warps, through a small double-buffered shared-memory
+// exchange (one barrier per stage).  The 4 R S halo rows at each end of the
+// block are recomputed; the first launch draws the samples, the last one
+// reduces them.
 struct McStep {
     int64_t n, M, m;          // M: padded sample count (row stride)
-    int TC, H;                // owned rows per tile, halo rows per side
-    double h;
+    int TC, H;                // owned rows per block, halo rows per side (4 R S)
+    unsigned ntile;           // ceil(n / TC), computed on the host
+    int S;                    // RK4 steps in this launch (0: only sample, t_final = 0)
+    double h, hh, h6;         // h, h/2, h/6 (computed on the host)
     uint64_t seed;
     const double *xlo, *xhi;  // first launch: the initial box
     double dlo, dhi;          // traffic inflow box
@@ -220,96 +244,130 @@ struct McStep {
     void *out;
     double *plo, *phi;        // last launch: partials [sample block][n]
     int first, last;
-    int step;                 // 1: advance one RK4 step, 0: only sample (t_final = 0)
     int *status;
 };
 
-template <int SYS, class T, int TCMAX>
-__global__ void __launch_bounds__(MC_THREADS) mc_stream(McStep a, const double *__restrict__ prm) {
-    extern __shared__ unsigned char smraw[];
-    constexpr int R = Plain<SYS, T>::R;
-    const int rows = a.TC + 2 * a.H;
-    T *Y = (T *)smraw;                                    // [rows][32]
-    T *K = Y + rows * 32;                                 // [rows][32]
-    __shared__ T Pd[32];
+constexpr int MC_B = 16;   // rows per warp
+
+// traffic flux out of global cell g from its value y and its right neighbour yr
+template <class T>
+__device__ __forceinline__ T tr_flux(const T (&q)[4], T y, T yr, int64_t g, int64_t n, T d) {
+    T cong = (g == n - 1) ? q[0] : tfma(-q[2], yr, q[3]);
+    T f = tmin(q[0], tmin(q[1] * y, cong));
+    f = (g == -1) ? d : f;
+    return (g < -1 || g >= n) ? T(0) : f;
+}
+
+template <int SYS, class T, int WPB>
+__global__ void __launch_bounds__(32 * WPB, (sizeof(T) == 4 && SYS == REACH_KS) ? 2 : 1)
+mc_stream(McStep a, const double *__restrict__ prm) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    constexpr int B = MC_B;
+    __shared__ T edge[2][WPB][2 * R][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t ntile = (a.n + a.TC - 1) / a.TC;
-    const int64_t nsb = a.M / 32;
-    const int64_t tile = blockIdx.x % ntile, sb = blockIdx.x / ntile;
-    if (sb >= nsb) return;
+    const int64_t n = a.n;
+    const int64_t tile = blockIdx.x % a.ntile, sb = blockIdx.x / a.ntile;   // 32-bit division
     const int64_t j = sb * 32 + lane;
     const bool valid = j < a.m;
-    const int64_t n = a.n;
-    const int64_t i0 = tile * a.TC - a.H;   // global component of row 0
+    const int64_t own0 = tile * a.TC;
+    const int64_t row0 = own0 - a.H + (int64_t)warp * B;   // global row of this warp's first row
     T q[4];
     mc_consts<SYS, T>(prm, q);
     int flags = 0;
-    if (warp == 0) {
-        double d = (SYS == REACH_TRAFFIC) ? box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j, 0u, 1u)) : 0.0;
-        Pd[lane] = as_run<T>(d);
-    }
-    for (int c = warp; c < rows; c += MC_WARPS) {
-        int64_t g = i0 + c;
-        int64_t gi = g;
+    T d = T(0);
+    if (SYS == REACH_TRAFFIC) d = as_run<T>(box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j, 0u, 1u)));
+    // Row offsets advance by additions: a 64-bit integer multiply per row would
+    // occupy this GPU's FP64 pipe, which an FP32 trajectory does not otherwise use.
+    const int64_t nM = a.n * a.M;
+    const int64_t wr0 = (SYS == REACH_KS) ? wrap_index(row0, n) : row0;
+    int64_t off = wr0 * a.M + j;   // the one multiply per thread
+    int64_t gi = wr0;              // wrapped row index
+    T z[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const int64_t g = row0 + r;
         bool in = true;
-        if (SYS == REACH_KS) gi = ((g % n) + n) % n;
-        else in = g >= 0 && g < n;
+        if (SYS == REACH_KS) {
+            if (off >= nM) { off -= nM; gi -= n; }
+        } else {
+            in = g >= 0 && g < n;
+        }
         T v = T(0);
         if (in) {
             if (a.first) {
                 double lo = a.xlo[gi], hi = a.xhi[gi];
-                if (lane == 0 && c >= a.H && c < a.H + a.TC && !(lo <= hi && isfinite(lo) && isfinite(hi)))
-                    flags |= ST_BADINPUT;
+                const bool owned = g >= own0 && g < own0 + a.TC;
+                if (lane == 0 && owned && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
                 v = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)gi, 0u)));
             } else {
-                v = ((const T *)a.in)[gi * a.M + j];
+                v = ((const T *)a.in)[off];
             }
         }
-        Y[c * 32 + lane] = v;
+        z[r] = v;
+        off += a.M;
+        ++gi;
     }
-    __syncthreads();
-    // z and acc for this thread's rows
-    constexpr int QS = (TCMAX + 2 * 4 * R + MC_WARPS - 1) / MC_WARPS;
-    T z[QS], acc[QS];
+    const T h = (T)a.h, hh = (T)a.hh, h6 = (T)a.h6;
+    int buf = 0;
+    for (int s = 0; s < a.S; ++s) {
+        // e[R + r] is the stage input of row r; e[0..R) and e[R+B..) hold the
+        // neighbouring warps' edge rows
+        T e[B + 2 * R], acc[B];
 #pragma unroll
-    for (int s = 0; s < QS; ++s) {
-        int c = warp + s * MC_WARPS;
-        z[s] = (c < rows) ? Y[c * 32 + lane] : T(0);
-        acc[s] = T(0);
-    }
-    auto row = [&](int c) -> T { return (c >= 0 && c < rows) ? Y[c * 32 + lane] : T(0); };
-    const T h = (T)a.h, hh = (T)(0.5 * a.h), h6 = (T)(a.h / 6.0);
-#pragma unroll 1
-    for (int stage = 0; stage < 4 * a.step; ++stage) {
+        for (int r = 0; r < B; ++r) e[R + r] = z[r];
 #pragma unroll
-        for (int s = 0; s < QS; ++s) {
-            int c = warp + s * MC_WARPS;
-            if (c < rows) K[c * 32 + lane] = Plain<SYS, T>::rhs(q, row, c, i0 + c, n, Pd, lane);
-        }
-        __syncthreads();
-        const T cst = (stage == 2) ? h : hh;
+        for (int stage = 0; stage < 4; ++stage) {
 #pragma unroll
-        for (int s = 0; s < QS; ++s) {
-            int c = warp + s * MC_WARPS;
-            if (c < rows) {
-                T k = K[c * 32 + lane], y;
-                if (stage == 0) acc[s] = k;
-                else if (stage < 3) acc[s] = fma(T(2), k, acc[s]);
-                else acc[s] += k;
-                if (stage < 3) y = fma(cst, k, z[s]);
-                else { z[s] = fma(h6, acc[s], z[s]); y = z[s]; }
-                Y[c * 32 + lane] = y;
+            for (int q2 = 0; q2 < R; ++q2) {
+                edge[buf][warp][q2][lane] = e[R + q2];
+                edge[buf][warp][R + q2][lane] = e[B + q2];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q2 = 0; q2 < R; ++q2) {
+                e[q2] = warp > 0 ? edge[buf][warp - 1][R + q2][lane] : T(0);
+                e[B + R + q2] = warp < WPB - 1 ? edge[buf][warp + 1][q2][lane] : T(0);
+            }
+            buf ^= 1;
+            // derivative of row r, then the update of row r - R, whose stage
+            // input row r was the last to read; only R + 1 derivatives are live
+            T kring[R + 1];
+            T fprev = T(0);
+            if constexpr (SYS != REACH_KS) fprev = tr_flux<T>(q, e[0], e[1], row0 - 1, n, d);   // flux into row 0
+#pragma unroll
+            for (int r = 0; r < B + R; ++r) {
+                if (r < B) {
+                    T kr;
+                    if constexpr (SYS == REACH_KS) {
+                        T um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                        T lin = tfma(q[2], um2 + up2, tfma(q[1], um1 + up1, q[0] * u));
+                        kr = tfma(-q[3] * u, up1 - um1, lin);
+                    } else {
+                        T fout = tr_flux<T>(q, e[r + 1], e[r + 2], row0 + r, n, d);
+                        kr = fprev - fout;
+                        fprev = fout;
+                    }
+                    kring[r % (R + 1)] = kr;
+                }
+                if (r >= R) {
+                    const int u = r - R;
+                    const T k = kring[u % (R + 1)];
+                    if (stage == 0) { acc[u] = k; e[R + u] = tfma(hh, k, z[u]); }
+                    if (stage == 1) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(hh, k, z[u]); }
+                    if (stage == 2) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(h, k, z[u]); }
+                    if (stage == 3) { acc[u] += k; z[u] = tfma(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                }
             }
         }
-        __syncthreads();
     }
+    int64_t oo = row0 * a.M + j;                 // store offset of row 0 (owned rows are in range)
+    double *plo = a.plo + sb * n + row0, *phi = a.phi + sb * n + row0;
 #pragma unroll
-    for (int s = 0; s < QS; ++s) {
-        int c = warp + s * MC_WARPS;
-        int64_t g = i0 + c;
-        if (c < a.H || c >= a.H + a.TC || g >= n) continue;
-        if (a.last) warp_minmax<T>(z[s], valid, a.plo + sb * n + g, a.phi + sb * n + g, a.status);
-        else ((T *)a.out)[g * a.M + j] = z[s];
+    for (int r = 0; r < B; ++r, oo += a.M) {
+        const int64_t g = row0 + r;
+        if (g < own0 || g >= own0 + a.TC || g >= n) continue;   // warp-uniform
+        if (a.last) warp_minmax<T>(z[r], valid, plo + r, phi + r, a.status);
+        else ((T *)a.out)[oo] = z[r];
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -344,34 +402,35 @@ static int launch_onchip(const McArgs &a, cudaStream_t st) {
     return REACH_OK;
 }
 
-constexpr int MC_TC = 256;
+// warps per block of the streaming kernel: binary64 keeps 2x the registers
+template <class T>
+constexpr int mc_wpb() { return sizeof(T) == 4 ? 16 : 8; }
 
 template <int SYS, class T>
 static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
-    constexpr int R = Plain<SYS, T>::R;
-    a.TC = MC_TC;
-    a.H = 4 * R;
-    int rows = a.TC + 2 * a.H;
-    size_t smem = (size_t)rows * 32 * sizeof(T) * 2;
-    static bool attr = false;
-    if (!attr) {
-        int rc = allow_max_dynamic_smem((const void *)mc_stream<SYS, T, MC_TC>);
-        if (rc) return rc;
-        attr = true;
-    }
-    int64_t ntile = (a.n + a.TC - 1) / a.TC;
-    int64_t grid = ntile * (a.M / 32);
-    if (grid > 0x7fffffffLL) return REACH_EINVAL;
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    constexpr int WPB = mc_wpb<T>();
+    int S = (int)opt_steps();
+    while (S > 1 && 2 * 4 * R * S >= WPB * MC_B / 2) --S;   // keep the halo below half the block
+    const int64_t L = N > 0 ? (N + S - 1) / S : 1;
     void *buf[2] = {bufA, bufB};
-    const int64_t L = N > 0 ? N : 1;
-    for (int64_t s = 0; s < L; ++s) {
-        a.first = (s == 0);
-        a.last = (s == L - 1);
-        a.step = N > 0;
-        a.in = buf[s % 2];
-        a.out = buf[(s + 1) % 2];
-        mc_stream<SYS, T, MC_TC><<<(unsigned)grid, MC_THREADS, smem, st>>>(a, prm);
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = N > 0 ? (int)std::min<int64_t>(S, N - done) : 0;
+        a.S = s;
+        a.H = 4 * R * s;
+        a.TC = WPB * MC_B - 2 * a.H;
+        a.first = (q == 0);
+        a.last = (q == L - 1);
+        a.in = buf[q % 2];
+        a.out = buf[(q + 1) % 2];
+        const int64_t ntile = (a.n + a.TC - 1) / a.TC;
+        const int64_t grid = ntile * (a.M / 32);
+        if (grid > 0x7fffffffLL) return REACH_EINVAL;
+        a.ntile = (unsigned)ntile;
+        mc_stream<SYS, T, WPB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a, prm);
         REACH_LAUNCHED("mc_stream");
+        done += s;
     }
     return REACH_OK;
 }
@@ -418,6 +477,8 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         s.m = base.m;
         s.M = nblk * 32;
         s.h = base.h;
+        s.hh = 0.5 * base.h;
+        s.h6 = base.h / 6.0;
         s.seed = base.seed;
         s.xlo = base.xlo;
         s.xhi = base.xhi;
@@ -427,7 +488,7 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         s.phi = a.phi;
         s.status = base.status;
         void *bufA = nullptr, *bufB = nullptr;
-        if (base.N > 1) {
+        if (base.N > opt_steps() || base.N > 1) {
             if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufA))) return rc;
             if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufB))) return rc;
         }

@@ -38,8 +38,8 @@ int onchip_batch_threads() { return BATCH_THREADS; }
 template <int SYS> int onchip_single_k(const OnItem &, int, cudaStream_t);
 template <int SYS> int onchip_cluster_k(const OnItem &, cudaStream_t);
 template <int SYS>
-int onchip_batch_k(int, const void *, const void *, const void *, const void *, int, int *, uint64_t *, int, size_t,
-                   cudaStream_t);
+int onchip_batch_k(int, int, const void *, const void *, const void *, const void *, int, int *, uint64_t *, int,
+                   size_t, cudaStream_t);
 
 int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st) {
     switch (it.kind) {
@@ -61,14 +61,14 @@ int onchip_launch_cluster(const OnItem &it, cudaStream_t st) {
     return REACH_EINVAL;
 }
 
-int onchip_launch_batch(int kind, int method, const void *items, const void *slots, const void *bins,
+int onchip_launch_batch(int kind, int method, int q, const void *items, const void *slots, const void *bins,
                         const void *tasks, int ntasks, int *counter, uint64_t *done, int clusters, size_t smem,
                         cudaStream_t st) {
     switch (kind) {
-    case REACH_TRAFFIC: return onchip_batch_k<REACH_TRAFFIC>(method, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
-    case REACH_KS: return onchip_batch_k<REACH_KS>(method, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
-    case REACH_OSC: return onchip_batch_k<REACH_OSC>(method, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
-    case REACH_LINEAR: return onchip_batch_k<REACH_LINEAR>(method, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    case REACH_TRAFFIC: return onchip_batch_k<REACH_TRAFFIC>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    case REACH_KS: return onchip_batch_k<REACH_KS>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    case REACH_OSC: return onchip_batch_k<REACH_OSC>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    case REACH_LINEAR: return onchip_batch_k<REACH_LINEAR>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
     }
     return REACH_EINVAL;
 }

@@ -165,21 +165,21 @@ __device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
 }
 
 // one RK4 stage of the group: all derivatives from y, then y rewritten
-template <int SYS, int METHOD, int STAGE, class Sync>
+template <int SYS, int METHOD, int STAGE, int Q, class Sync>
 __device__ __forceinline__ void onchip_stage(const OnItem &it, double *yA, double *yB, const double *wA,
                                              const double *wB, double *kb, int64_t cbeg, int64_t cend, int gt,
-                                             int gs, const Sync &sync, const double (&q)[8], double (&z)[QMAX],
-                                             double (&acc)[QMAX]) {
+                                             int gs, const Sync &sync, const double (&q)[8], double (&z)[Q],
+                                             double (&acc)[Q]) {
     const int64_t n = it.n;
 #pragma unroll
-    for (int s = 0; s < QMAX; ++s) {
+    for (int s = 0; s < Q; ++s) {
         int64_t c = cbeg + gt + (int64_t)s * gs;
         if (c < cend) kb[c - cbeg] = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
     }
     sync();
     const double h = it.h;
 #pragma unroll
-    for (int s = 0; s < QMAX; ++s) {
+    for (int s = 0; s < Q; ++s) {
         int64_t c = cbeg + gt + (int64_t)s * gs;
         if (c < cend) {
             double y, k = kb[c - cbeg];
@@ -196,8 +196,11 @@ __device__ __forceinline__ void onchip_stage(const OnItem &it, double *yA, doubl
 // Integrate one problem.  yA, yB: n doubles each of shared memory (may live in
 // different blocks of a cluster); wA, wB: nw doubles each; kb: cend - cbeg
 // doubles holding this group's stage derivatives.  The calling
-// threads own components [cbeg, cend) with stride gs starting at cbeg + gt.
-template <int SYS, int METHOD, class Sync>
+// threads own components [cbeg, cend) with stride gs starting at cbeg + gt,
+// at most Q each (Q is a template parameter so that small problems run a
+// small loop: the code of a 16-slot loop does not fit a lone warp's
+// instruction cache).
+template <int SYS, int METHOD, int Q, class Sync>
 __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA, double *wB,
                            double *kb, int64_t cbeg, int64_t cend, int gt, int gs, const Sync &sync) {
     const int64_t n = it.n;
@@ -220,9 +223,9 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA,
         }
     }
 
-    double z[QMAX], acc[QMAX];
+    double z[Q], acc[Q];
 #pragma unroll
-    for (int s = 0; s < QMAX; ++s) {
+    for (int s = 0; s < Q; ++s) {
         int64_t c = cbeg + gt + (int64_t)s * gs;
         z[s] = 0.0;
         acc[s] = 0.0;
@@ -240,10 +243,10 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA,
     sync();
 
     for (int64_t step = 0; step < it.N; ++step) {
-        onchip_stage<SYS, METHOD, 0>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 1>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 2>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 3>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 0, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 1, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 2, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 3, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
     }
 
     // y holds the final state of both halves

@@ -10,27 +10,38 @@
 namespace reach {
 
 // ---------------------------------------------------------------- one problem
-template <int SYS, int METHOD>
+template <int SYS, int METHOD, int Q>
 __global__ void __launch_bounds__(512) onchip_single(OnItem it) {
     extern __shared__ double sm[];
     const int64_t n = it.n;
     GroupSync sync{0, (int)blockDim.x};
-    onchip_run<SYS, METHOD>(it, sm, sm + n, sm + 2 * n, sm + 2 * n + it.nw, sm + 2 * n + 2 * it.nw, 0,
+    onchip_run<SYS, METHOD, Q>(it, sm, sm + n, sm + 2 * n, sm + 2 * n + it.nw, sm + 2 * n + 2 * it.nw, 0,
                             2 * n, (int)threadIdx.x, (int)blockDim.x, sync);
 }
 
-template <int SYS, int METHOD>
-static int launch_single_t(const OnItem &it, int threads, cudaStream_t st) {
+template <int SYS, int METHOD, int Q>
+static int launch_single_q(const OnItem &it, int threads, cudaStream_t st) {
     int64_t smem = onchip_smem_bytes(it.n, it.nw);
     static bool attr_set = false;
     if (!attr_set) {
-        int rc = allow_max_dynamic_smem((const void *)onchip_single<SYS, METHOD>);
+        int rc = allow_max_dynamic_smem((const void *)onchip_single<SYS, METHOD, Q>);
         if (rc) return rc;
         attr_set = true;
     }
-    onchip_single<SYS, METHOD><<<1, threads, (size_t)smem, st>>>(it);
+    onchip_single<SYS, METHOD, Q><<<1, threads, (size_t)smem, st>>>(it);
     REACH_LAUNCHED("onchip_single");
     return REACH_OK;
+}
+
+// the smallest components-per-thread loop that covers 2n components
+template <int SYS, int METHOD>
+static int launch_single_t(const OnItem &it, int threads, cudaStream_t st) {
+    const int64_t per = (2 * it.n + threads - 1) / threads;
+    if (per <= 1) return launch_single_q<SYS, METHOD, 1>(it, threads, st);
+    if (per <= 2) return launch_single_q<SYS, METHOD, 2>(it, threads, st);
+    if (per <= 4) return launch_single_q<SYS, METHOD, 4>(it, threads, st);
+    if (per <= 8) return launch_single_q<SYS, METHOD, 8>(it, threads, st);
+    return launch_single_q<SYS, METHOD, QMAX>(it, threads, st);
 }
 
 template <int SYS>
@@ -60,7 +71,7 @@ __device__ __forceinline__ void cluster_item(const OnItem &it, double *sm) {
     double *other = cl.map_shared_rank(y, rank ^ 1u);
     double *yA = rank == 0 ? y : other, *yB = rank == 0 ? other : y;
     // the lower / center block uses wA, the upper / radius block wB
-    onchip_run<SYS, METHOD>(it, yA, yB, w, w, kb, rank * n, (rank + 1) * n, (int)threadIdx.x, (int)blockDim.x,
+    onchip_run<SYS, METHOD, QMAX>(it, yA, yB, w, w, kb, rank * n, (rank + 1) * n, (int)threadIdx.x, (int)blockDim.x,
                             ClusterSync{});
 }
 
@@ -110,7 +121,7 @@ struct Task {
 };
 
 
-template <int SYS, int METHOD>
+template <int SYS, int METHOD, int Q>
 __device__ __forceinline__ void run_bin(const OnItem *__restrict__ items, const Slot *__restrict__ slots,
                                         const Bin &bn, double *sm, uint64_t *done) {
     const int warp = threadIdx.x >> 5;
@@ -123,13 +134,13 @@ __device__ __forceinline__ void run_bin(const OnItem *__restrict__ items, const 
         GroupSync sync{sl.bar, sl.nwarps * 32};
         const int gt = (int)threadIdx.x - sl.warp0 * 32, gs = sl.nwarps * 32;
         double *w = y + 2 * n, *kb = w + 2 * it.nw;
-        onchip_run<SYS, METHOD>(it, y, y + n, w, w + it.nw, kb, 0, 2 * n, gt, gs, sync);
+        onchip_run<SYS, METHOD, Q>(it, y, y + n, w, w + it.nw, kb, 0, 2 * n, gt, gs, sync);
         if (gt == 0) done[sl.item] = global_ns();
         break;
     }
 }
 
-template <int SYS, int METHOD>
+template <int SYS, int METHOD, int Q>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BATCH_THREADS, 1)
 onchip_batch(const OnItem *__restrict__ items, const Slot *__restrict__ slots, const Bin *__restrict__ bins,
              const Task *__restrict__ tasks, int ntasks, int *counter, uint64_t *done) {
@@ -148,34 +159,44 @@ onchip_batch(const OnItem *__restrict__ items, const Slot *__restrict__ slots, c
             cluster_item<SYS, METHOD>(items[tk.big], sm);
             if (rank == 0 && threadIdx.x == 0) done[tk.big] = global_ns();
         } else if (tk.bin[rank] >= 0) {
-            run_bin<SYS, METHOD>(items, slots, bins[tk.bin[rank]], sm, done);
+            run_bin<SYS, METHOD, Q>(items, slots, bins[tk.bin[rank]], sm, done);
         }
         cl.sync();   // the task is over in both blocks before either reuses memory
     }
 }
 
-template <int SYS, int METHOD>
+template <int SYS, int METHOD, int Q>
 static int launch_batch_t(const void *items, const void *slots, const void *bins, const void *tasks, int ntasks,
                           int *counter, uint64_t *done, int clusters, size_t smem, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        int rc = allow_max_dynamic_smem((const void *)onchip_batch<SYS, METHOD>);
+        int rc = allow_max_dynamic_smem((const void *)onchip_batch<SYS, METHOD, Q>);
         if (rc) return rc;
         attr_set = true;
     }
-    onchip_batch<SYS, METHOD><<<2 * clusters, BATCH_THREADS, smem, st>>>((const OnItem *)items, (const Slot *)slots,
+    onchip_batch<SYS, METHOD, Q><<<2 * clusters, BATCH_THREADS, smem, st>>>((const OnItem *)items, (const Slot *)slots,
                                                                  (const Bin *)bins, (const Task *)tasks, ntasks,
                                                                  counter, done);
     REACH_LAUNCHED("onchip_batch");
     return REACH_OK;
 }
 
+// Q: the batch's components-per-thread target (the autotuned layout), which
+// bounds the components each thread of a bin slot holds
 template <int SYS>
-int onchip_batch_k(int method, const void *items, const void *slots, const void *bins, const void *tasks,
+int onchip_batch_k(int method, int q, const void *items, const void *slots, const void *bins, const void *tasks,
                    int ntasks, int *counter, uint64_t *done, int clusters, size_t smem, cudaStream_t st) {
-    if (method == MM)
-        return launch_batch_t<SYS, MM>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
-    return launch_batch_t<SYS, CGB>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+#define REACH_BQ(Q)                                                                                             \
+    if (q <= Q)                                                                                                 \
+        return method == MM                                                                                     \
+                   ? launch_batch_t<SYS, MM, Q>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st) \
+                   : launch_batch_t<SYS, CGB, Q>(items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    REACH_BQ(2)
+    REACH_BQ(4)
+    REACH_BQ(8)
+    REACH_BQ(QMAX)
+#undef REACH_BQ
+    return REACH_EINVAL;
 }
 
 }  // namespace reach

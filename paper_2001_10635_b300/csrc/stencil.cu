@@ -36,6 +36,7 @@ struct StepArgs {
     double *outA, *outB;
     int64_t n;
     int64_t W;                 // owned cells per tile = TILE - 2H
+    int64_t ntiles;            // ceil(n / W), computed on the host
     int H;                     // halo cells per side = 4 R S
     int S;                     // RK4 steps in this launch
     double h;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
-    const int64_t ntiles = (a.n + a.W - 1) / a.W;
+    const int64_t ntiles = a.ntiles;
     int flags = 0;
     for (int64_t t = warp; t < 2 * ntiles; t += nwarps) {
         if (t < ntiles) traffic_tile<METHOD, 0>(a, p, t, lane, flags);
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_ks_rk4(StepArgs 
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
     const int64_t n = a.n;
-    const int64_t ntiles = (n + a.W - 1) / a.W;
+    const int64_t ntiles = a.ntiles;
     int flags = 0;
 
     for (int64_t t = warp; t < ntiles; t += nwarps) {
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_ks_rk4(StepArgs 
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
             const int64_t g = g0 + j;
-            const int64_t idx = ((g % n) + n) % n;   // periodic grid
+            const int64_t idx = wrap_index(g, n);   // periodic grid
             double va = __ldg(a.inA + idx), vb = __ldg(a.inB + idx);
             if (a.first) {
                 const bool owned = g >= own0 && g < own0 + a.W && g < n && g >= 0;
@@ -339,6 +340,7 @@ static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, dou
         a.n = n;
         a.H = 4 * R * s;
         a.W = TILE - 2 * a.H;
+        a.ntiles = (n + a.W - 1) / a.W;
         a.S = s;
         a.h = h;
         a.first = (q == 0);

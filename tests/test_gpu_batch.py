@@ -112,3 +112,20 @@ def test_batch_rejects_invalid_queries():
         for bad in (dict(t_final=0.0), dict(dt=0.03), dict(x0_lo=q["x_hi"], x0_hi=q["x_lo"])):
             with pytest.raises(R.ReachError):
                 R.Batch([good, dict(good, **bad)])
+
+
+@pytest.mark.parametrize("cpt", [2, 4, 8, 16])
+def test_every_batch_layout_matches_solo(cpt):
+    sizes = [4, 31, 64, 200, 513, 1024, 3000]
+    T = 0.05
+    R.reach_set_option(R.OPT_BATCH_CPT, cpt)
+    systems, queries, raw = _osc_batch(sizes, T, seed0=300)
+    with R.Batch(queries) as b:
+        st, _ = b.run()
+        assert (st == 0).all() and b.info()["cpt"] == cpt
+        for (lo, hi), (method, q), qq in zip(b.outputs, raw, queries):
+            fn = R.reach_mm if method == "mm" else R.reach_cgb
+            solo = fn(qq["sys"], q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
+            assert np.array_equal(solo[0], lo) and np.array_equal(solo[1], hi)
+    for s in systems.values():
+        s.close()
