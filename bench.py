@@ -11,7 +11,7 @@ traffic cell-transmission chain with n = 2^26 cells, x0 box centres
   e2e    the same through the public API with host (numpy) buffers: the
          library's host->device copies and the result readback are inside
          the timed region
-  roofline  the dominant kernel (stencil_rk4): FP64-pipe operations per
+  roofline  the dominant kernel (stencil_traffic_rk4): FP64-pipe operations per
          launch / its average launch time, against the FP64 issue rate of
          148 SMs x 2 ops/clk x 2.032 GHz
   cpu_baseline / --impl reference  the FP64 oracle on one host core, on the
@@ -42,11 +42,13 @@ N_CELLS = 1 << 26
 T_FINAL, DT = 2.0, 0.01
 NSTEPS = 200
 # FP64 pipe operations per component-step of the fused kernel (add, mul and
-# fma each count one): traffic MM 19 (per cell-stage: v x, w (xbar - x'),
-# flux difference, stage input, accumulator; minus the first accumulator and
-# the last stage input, plus the final update); traffic CGB: center 19,
-# radius 15 (v r_l + w r_r is 2 per stage)
-FP64_OPS = {"mm": 19.0, "cgb": 17.0}
+# fma each count one).  Per cell and stage the traffic flux costs w (xbar - x')
+# (v x with v = 0.5 is an exponent shift on the integer pipe), then the flux
+# difference, the stage input and the accumulator: 4 per stage, minus the first
+# accumulator and the last stage input, plus the final update = 15.  The CGB
+# center costs the same; its radius v r_l + w r_r + stage input + accumulator
+# is also 15.
+FP64_OPS = {"mm": 15.0, "cgb": 15.0}
 SM_COUNT, FP64_PER_SM_CLK, SM_MAX_MHZ = 148, 2, 2032.0
 FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
 CPU_SAMPLE_CELLS = 1 << 20
@@ -483,7 +485,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": mm_achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
                      "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": None,
-                     "kernel": "stencil_rk4<traffic, MM>",
+                     "kernel": "stencil_traffic_rk4<MM>",
                      "per_launch_ms": per_launch_ms, "fp64_ops_per_comp_step": FP64_OPS,
                      "cgb_frac": achieved["cgb"] / FP64_PEAK_OPS,
                      "peak_source": "148 SMs x 2 FP64 ops/clk x 2032 MHz (recipe nominal FP64 1.25 TFLOP/s)",

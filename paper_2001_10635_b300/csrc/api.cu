@@ -153,6 +153,25 @@ int check_host_box(const double *lo, const double *hi, int64_t count) {
     return REACH_OK;
 }
 
+TrafficK make_traffic_k(const double *prm, double wl, double wh) {
+    TrafficK p;
+    p.cap = prm[0];
+    p.v = prm[1];
+    p.w = prm[2];
+    p.xbar = prm[3];
+    p.wxbar = p.w * p.xbar;
+    int e = 0;
+    const double m = std::frexp(p.v, &e);   // v = m 2^e, m in [0.5, 1)
+    p.v_pow2 = (p.v > 0.0 && m == 0.5) ? 1 : 0;
+    p.v_exp = e - 1;
+    p.v_add = p.v_exp >= 0 ? ((long long)p.v_exp << 52) : -((long long)(-p.v_exp) << 52);
+    p.d_lo = wl;
+    p.d_hi = wh;
+    p.d_c = 0.5 * (wl + wh);
+    p.d_r = 0.5 * (wh - wl);
+    return p;
+}
+
 int64_t opt_kernel() { return g_opt_kernel; }
 int64_t opt_steps() { return g_opt_steps; }
 int64_t opt_block() { return g_opt_block; }
@@ -361,12 +380,7 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     sB = sA + n;
     int S = (int)opt_steps();
     if (sys->kind == REACH_TRAFFIC) {
-        TrafficK p;
-        p.cap = sys->prm[0]; p.v = sys->prm[1]; p.w = sys->prm[2]; p.xbar = sys->prm[3];
-        p.wxbar = p.w * p.xbar;
-        p.d_lo = wl_host; p.d_hi = wh_host;
-        p.d_c = 0.5 * (wl_host + wh_host);
-        p.d_r = 0.5 * (wh_host - wl_host);
+        TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
         rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
     } else {
         KsK p;

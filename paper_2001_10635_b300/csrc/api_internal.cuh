@@ -45,6 +45,9 @@ int64_t opt_steps();
 int64_t opt_block();
 int64_t opt_batch_cpt();
 
+// traffic parameters as the streaming kernel sees them (inputs d in [wl, wh])
+TrafficK make_traffic_k(const double *prm, double wl, double wh);
+
 // kernels
 constexpr int BATCH_THREADS = 512;   // threads per block of the batched kernel
 int64_t onchip_smem_bytes(int64_t n, int64_t nw);

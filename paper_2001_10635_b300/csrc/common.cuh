@@ -16,6 +16,9 @@ enum Method : int { MM = 0, CGB = 1 };
 struct TrafficK {
     double cap, v, w, xbar;
     double wxbar;        // w * xbar
+    int v_pow2;          // v is 2^e exactly (e = v_exp), so v * x is an exponent shift
+    int v_exp;
+    long long v_add;     // e << 52, the shift as an addend to the bit pattern
     double d_lo, d_hi;   // MM inputs (p, ph)
     double d_c, d_r;     // CGB input center and half-width
 };
@@ -28,6 +31,17 @@ struct KsK {
 struct OscK {
     double ka, kb, kc;
 };
+
+// v * y as an exponent shift when v = 2^e: exact whenever y and the result are
+// normal numbers (then the product is a power-of-two scaling); scale_ok says
+// whether that holds for y
+__device__ __forceinline__ bool scale_ok(double y, int e) {
+    const int ef = (int)((__double_as_longlong(y) >> 52) & 0x7ff);
+    return ef != 0 && ef != 0x7ff && ef + e >= 1 && ef + e <= 0x7fe;
+}
+__device__ __forceinline__ double scale_pow2(double y, long long add) {
+    return __longlong_as_double(__double_as_longlong(y) + add);
+}
 
 // bit flags written by kernels into a per-call status word
 enum : int {

@@ -81,12 +81,7 @@ extern "C" int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, co
             wh = w_hi[0];
         }
         if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;
-        TrafficK p;
-        p.cap = sys->prm[0]; p.v = sys->prm[1]; p.w = sys->prm[2]; p.xbar = sys->prm[3];
-        p.wxbar = p.w * p.xbar;
-        p.d_lo = wl; p.d_hi = wh;
-        p.d_c = 0.5 * (wl + wh);
-        p.d_r = 0.5 * (wh - wl);
+        TrafficK p = make_traffic_k(sys->prm, wl, wh);
         rc = stencil_traffic(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, (int)opt_steps(), status, st);
     } else {
         KsK p;

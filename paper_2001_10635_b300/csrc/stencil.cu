@@ -74,17 +74,36 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
 // k[j] = f_{g-1} - f_g: flux out of cell g is min(cap, v y_g, w (xbar - y_{g+1}))
 // (min(cap, v y_g) for the last cell), the inflow of cell 0 is d, and cells
 // outside [0, n) carry no flux.
+template <bool POW2>
 __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                             int64_t n, double d, double (&k)[KC]) {
     double e[KC + 2];
     exchange<1>(y, e);
+    double vy[KC];
+    bool shifted = false;
+    if (POW2) {
+        // v = 2^e: free-flow flux by exponent shift on the integer pipe when
+        // every lane's values allow it (a warp-uniform choice)
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < KC; ++j) ok = ok && scale_ok(e[1 + j], p.v_exp);
+        if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+            for (int j = 0; j < KC; ++j) vy[j] = scale_pow2(e[1 + j], p.v_add);
+            shifted = true;
+        }
+    }
+    if (!shifted) {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) vy[j] = p.v * e[1 + j];
+    }
     double f[KC];
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int64_t g = g0 + j;
         double cong = fma(-p.w, e[2 + j], p.wxbar);
         cong = (g == n - 1) ? p.cap : cong;          // no congestion term at the outlet
-        double fj = kmin(p.cap, kmin(p.v * e[1 + j], cong));
+        double fj = kmin(p.cap, kmin(vy[j], cong));
         fj = (g == -1) ? d : fj;
         f[j] = (g < -1 || g >= n) ? 0.0 : fj;
     }
@@ -110,15 +129,15 @@ __device__ __forceinline__ void traffic_growth(const TrafficK &p, const double (
 }
 
 // one traffic half per warp: HALF 0 = x / c, HALF 1 = xh / r
-template <int METHOD, int HALF>
+template <int METHOD, int HALF, bool POW2>
 __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                                  int64_t n, double (&k)[KC]) {
-    if (METHOD == MM) traffic_rhs(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
-    else if (HALF == 0) traffic_rhs(p, y, g0, n, p.d_c, k);
+    if (METHOD == MM) traffic_rhs<POW2>(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
+    else if (HALF == 0) traffic_rhs<POW2>(p, y, g0, n, p.d_c, k);
     else traffic_growth(p, y, g0, n, k);
 }
 
-template <int METHOD, int HALF>
+template <int METHOD, int HALF, bool POW2>
 __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &p, int64_t t, int lane,
                                              int &flags) {
     const int64_t n = a.n;
@@ -143,13 +162,13 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
         double y[KC], acc[KC], k[KC];
 #pragma unroll
         for (int j = 0; j < KC; ++j) y[j] = z[j];
-        traffic_rhs_half<METHOD, HALF>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
         rk4_update<0>(z, y, acc, k, a.h);
-        traffic_rhs_half<METHOD, HALF>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
         rk4_update<1>(z, y, acc, k, a.h);
-        traffic_rhs_half<METHOD, HALF>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
         rk4_update<2>(z, y, acc, k, a.h);
-        traffic_rhs_half<METHOD, HALF>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
         rk4_update<3>(z, y, acc, k, a.h);
     }
     double *out = HALF ? a.outB : a.outA;
@@ -163,7 +182,7 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
     }
 }
 
-template <int METHOD>
+template <int METHOD, bool POW2>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(StepArgs a, TrafficK p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -171,8 +190,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
     const int64_t ntiles = a.ntiles;
     int flags = 0;
     for (int64_t t = warp; t < 2 * ntiles; t += nwarps) {
-        if (t < ntiles) traffic_tile<METHOD, 0>(a, p, t, lane, flags);
-        else traffic_tile<METHOD, 1>(a, p, t - ntiles, lane, flags);
+        if (t < ntiles) traffic_tile<METHOD, 0, POW2>(a, p, t, lane, flags);
+        else traffic_tile<METHOD, 1, POW2>(a, p, t - ntiles, lane, flags);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -363,8 +382,11 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
     int rc = run_steps(1, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
         const int64_t ntiles = (n + a.W - 1) / a.W;
         const unsigned grid = grid_for(2 * ntiles);
-        if (method == MM) stencil_traffic_rk4<MM><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-        else stencil_traffic_rk4<CGB><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+        const bool pw = p.v_pow2 != 0;
+        if (method == MM && pw) stencil_traffic_rk4<MM, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+        else if (method == MM) stencil_traffic_rk4<MM, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+        else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+        else stencil_traffic_rk4<CGB, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
         REACH_LAUNCHED("stencil_traffic_rk4");
         return REACH_OK;
     });

@@ -287,3 +287,17 @@ def test_ks_full_size_mc32_inside_mm():
     slack = 1e-5 * np.abs(mm[1]).max()
     assert (mc[0] >= mm[0] - slack).all() and (mc[1] <= mm[1] + slack).all()
     assert (mc[1] - mc[0]).min() > 0
+
+
+@pytest.mark.parametrize("v", [0.45, 0.25, 0.5])
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_streaming_traffic_parameters(method, v):
+    # v = 0.5 and 0.25 take the exponent-shift path for v x, 0.45 the multiply
+    prm = (38.0, v, 0.2, 300.0)
+    n = 3001
+    lo, hi, wlo, whi, T, dt, _, _ = problem("traffic", n, seed=17)
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    o = O.reach(method, "traffic", lo, hi, wlo, whi, t_final=0.3, dt=dt, params=prm)
+    g = gpu_box(method, "traffic", n, lo, hi, wlo, whi, 0.3, dt, params=prm)
+    assert_close(g[0], o[0], TOL64, "lo")
+    assert_close(g[1], o[1], TOL64, "hi")
