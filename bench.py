@@ -54,6 +54,23 @@ FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
 CPU_SAMPLE_CELLS = 1 << 20
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (timings: the job takes as long as
+    its slowest replica).  One process per GPU; dist may be None (one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -206,6 +223,38 @@ def bench_ks(R, torch, dev):
             fn(s, d["x_lo"], d["x_hi"], t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, **kw)
             sec = time.perf_counter() - t0
             out[name] = {"s": sec, "value": comps * N / sec, "unit": "comp-steps/s"}
+    return out
+
+
+def bench_temporal_blocking(R, torch, dev):
+    """RK4 steps per launch S (halo 4 R S recomputed) on traffic MM (FP64,
+    n = 2^24) and on KS MC32 (n = 2^20, 256 samples): the FP64 kernels are bound
+    by the FP64 pipe, so recomputation costs more than the HBM traffic it saves."""
+    out = {}
+    n = 1 << 24
+    wl = W.traffic_large(n, seed=0, t_final=0.24)
+    d = {k: torch.tensor(wl[k], dtype=torch.float64, device=dev) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+    ks = W.ks_grid(1 << 20, t_final=0.012)
+    kd = {k: torch.tensor(ks[k], dtype=torch.float64, device=dev) for k in ("x_lo", "x_hi")}
+    with R.System("traffic", n) as s, R.System("ks", 1 << 20) as sk:
+        for S in (1, 2, 4):
+            R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+            R.reach_mm(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=0.24, dt=0.01)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            R.reach_mm(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=0.24, dt=0.01)
+            sec = time.perf_counter() - t0
+            out[f"traffic_mm_S{S}"] = 2 * n * 24 / sec
+            if S <= 2:
+                kw = dict(t_final=0.012, dt=1e-4, m=256, seed=0, precision=32)
+                R.reach_mc(sk, kd["x_lo"], kd["x_hi"], **kw)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                R.reach_mc(sk, kd["x_lo"], kd["x_hi"], **kw)
+                sec = time.perf_counter() - t0
+                out[f"ks_mc32_S{S}"] = 256 * (1 << 20) * 120 / sec
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+    out["unit"] = "comp-steps/s"
     return out
 
 
@@ -433,13 +482,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = R.reach_kernel_launches() - launches0
-    ms = t0.elapsed_time(t1)
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    comp_steps = 2 * 2 * n * NSTEPS * args.steps * world
-    value = comp_steps / (ms * 1e-3)
+    ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
+    value = job_rate(2 * 2 * n * NSTEPS * args.steps, world, ms * 1e-3)
 
     # end to end through the public API with host buffers
     hlo = np.empty(n)
@@ -456,12 +500,8 @@ def main():
         R.reach_cgb(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,
                     lo=hlo, hi=hhi)
     barrier()
-    e2e_sec = time.perf_counter() - te
-    if dist is not None:
-        tt = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_sec = float(tt.item())
-    e2e_value = 2 * 2 * n * NSTEPS * e2e_steps * world / e2e_sec if e2e_steps else None
+    e2e_sec = max_over_ranks(time.perf_counter() - te, dist, dev)
+    e2e_value = job_rate(2 * 2 * n * NSTEPS * e2e_steps, world, e2e_sec) if e2e_steps else None
     h2d = 2 * (2 * n + 2) * 8
     d2h = 2 * 2 * n * 8
 
@@ -497,6 +537,7 @@ def main():
         line["batched"] = bench_batched(R, torch, dev)
         line["ks"] = bench_ks(R, torch, dev)
         line["traffic16"] = bench_traffic16(R)
+        line["temporal_blocking"] = bench_temporal_blocking(R, torch, dev)
         line["serving"] = bench_serving(R)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()

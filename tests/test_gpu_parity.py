@@ -301,3 +301,16 @@ def test_streaming_traffic_parameters(method, v):
     g = gpu_box(method, "traffic", n, lo, hi, wlo, whi, 0.3, dt, params=prm)
     assert_close(g[0], o[0], TOL64, "lo")
     assert_close(g[1], o[1], TOL64, "hi")
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_ks_rotation_is_tiling_invariant(method):
+    # periodic grid: rotating the input by a shift that is not a multiple of the
+    # tile must rotate the output (halo and wrap handling across tiles)
+    n, k = 5003, 777
+    lo, hi, _, _, _, dt, _, _ = problem("ks", n, seed=31)
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    a = gpu_box(method, "ks", n, lo, hi, None, None, 0.004, dt)
+    b = gpu_box(method, "ks", n, np.roll(lo, k), np.roll(hi, k), None, None, 0.004, dt)
+    assert_close(b[0], np.roll(a[0], k), TOL64, "lo")
+    assert_close(b[1], np.roll(a[1], k), TOL64, "hi")
