@@ -52,6 +52,10 @@ FP64_OPS = {"mm": 15.0, "cgb": 15.0}
 SM_COUNT, FP64_PER_SM_CLK, SM_MAX_MHZ = 148, 2, 2032.0
 FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
 CPU_SAMPLE_CELLS = 1 << 20
+# DRAM bytes (read + write) of one stencil_traffic_rk4<MM> launch, ncu capture on
+# 2^24 cells (profiles/stencil_traffic_rk4_mm_traffic_n16M.md); the traffic of a
+# launch is proportional to the cells, so it is scaled to the run's n
+NCU_DRAM_BYTES_PER_CELL_LAUNCH = (268.564224e6 + 224.05632e6) / (1 << 24)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -253,7 +257,7 @@ def bench_temporal_blocking(R, torch, dev):
                 R.reach_mc(sk, kd["x_lo"], kd["x_hi"], **kw)
                 sec = time.perf_counter() - t0
                 out[f"ks_mc32_S{S}"] = 256 * (1 << 20) * 120 / sec
-    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
     out["unit"] = "comp-steps/s"
     return out
 
@@ -451,7 +455,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sysm = R.System("traffic", n)
     R.reach_set_option(R.OPT_KERNEL, 0)
-    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
 
     method_ms = {"mm": [], "cgb": []}
 
@@ -524,7 +528,9 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": mm_achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
-                     "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": None,
+                     "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": NCU_DRAM_BYTES_PER_CELL_LAUNCH * n,
+                     "traffic_note": "ncu dram__bytes_read+write of one MM launch on 2^24 cells, scaled to n "
+                                     "(algorithmic: 16 B x 2n)",
                      "kernel": "stencil_traffic_rk4<MM>",
                      "per_launch_ms": per_launch_ms, "fp64_ops_per_comp_step": FP64_OPS,
                      "cgb_frac": achieved["cgb"] / FP64_PEAK_OPS,

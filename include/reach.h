@@ -141,6 +141,16 @@ REACH_API int reach_mc(const reach_system *sys, const double *x0_lo, const doubl
              int64_t m, uint64_t seed, int precision,
              double *lo, double *hi, void *stream);
 
+/* The reach pipe (Sec. 5.5): the MM (method 0) or CGB (method 1) box after
+   every `every` RK4 steps.  pipe_lo / pipe_hi receive N/every rows of n values
+   (row q = the box after (q+1) every steps, row-major); N must be a multiple
+   of every.  Each segment starts from the previous box: exact continuation
+   for MM, and for CGB a restart from its center and radius, equal to one
+   continuous integration up to one rounding of c and r per segment. */
+REACH_API int reach_pipe(const reach_system *sys, int method, const double *x0_lo, const double *x0_hi,
+                         const double *w_lo, const double *w_hi, double t_final, double dt, int64_t every,
+                         double *pipe_lo, double *pipe_hi, void *stream);
+
 /* Sample count for an (eps, delta) guarantee (Sec. 2.1):
    m = ceil((2n/eps) ln(2n/delta)).  Returns REACH_EINVAL for n < 1 or
    eps, delta outside (0, 1). */
@@ -250,7 +260,7 @@ REACH_API int reach_server_destroy(reach_server *s);
 
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
-#define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming stencil: RK4 steps fused per launch, 1..8 */
+#define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming kernels: RK4 steps per launch, 1..8; 0 = auto (FP64 1, FP32 MC 2) */
 #define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
 #define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
 REACH_API int reach_set_option(int key, int64_t value);

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
         L.reach_mm.argtypes = box + [vp, vp, vp]
         L.reach_cgb.argtypes = box + [vp, vp, vp]
         L.reach_mc.argtypes = box + [i64, ctypes.c_uint64, ctypes.c_int, vp, vp, vp]
+        L.reach_pipe.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, dbl, dbl, i64, vp, vp, vp]
         L.reach_mc_samples.argtypes = [i64, dbl, dbl]
         L.reach_mc_samples.restype = i64
         L.reach_set_option.argtypes = [ctypes.c_int, i64]
@@ -238,6 +239,27 @@ def reach_mc(sys: System, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final: float,
                         int(seed) & (2**64 - 1), int(precision), pl, ph, _stream(stream))
     _check(rc, "reach_mc")
     return lo, hi
+
+
+def reach_pipe(sys: System, method: str, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final: float, dt: float,
+               every: int, stream=None):
+    """The reach pipe (Sec. 5.5): boxes after every `every` steps, as two
+    (rows, n) arrays (numpy for host inputs, CUDA tensors for device inputs)."""
+    a, b, c, d = _box_args(sys, x0_lo, x0_hi, w_lo, w_hi)
+    rows = int(round(t_final / dt)) // int(every)
+    if _is_torch(x0_lo):
+        import torch
+        plo = torch.empty((rows, sys.n), dtype=torch.float64, device=x0_lo.device)
+        phi = torch.empty_like(plo)
+        pl, ph = plo.data_ptr(), phi.data_ptr()
+    else:
+        plo = np.empty((rows, sys.n))
+        phi = np.empty((rows, sys.n))
+        pl, ph = plo.ctypes.data, phi.ctypes.data
+    rc = lib().reach_pipe(sys.handle, {"mm": 0, "cgb": 1}[method], a[0], b[0], c[0], d[0], float(t_final),
+                          float(dt), int(every), pl, ph, _stream(stream))
+    _check(rc, "reach_pipe")
+    return plo, phi
 
 
 def reach_mc_samples(n: int, eps: float, delta: float) -> int:

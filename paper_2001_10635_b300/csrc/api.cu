@@ -21,7 +21,7 @@ int cuda_fail(cudaError_t e, const char *where) {
     return REACH_ECUDA;
 }
 
-static int64_t g_opt_kernel = 0, g_opt_steps = 1, g_opt_block = 0, g_opt_batch_cpt = 0;
+static int64_t g_opt_kernel = 0, g_opt_steps = 0, g_opt_block = 0, g_opt_batch_cpt = 0;
 
 // ---------------------------------------------------------------- memory
 static bool g_pool_ready[64];
@@ -378,7 +378,9 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     double *sA, *sB;
     if ((rc = sg.scratch(2 * n * sizeof(double), (void **)&sA))) return rc;
     sB = sA + n;
-    int S = (int)opt_steps();
+    // FP64 stencil kernels are bound by the FP64 pipe: recomputing a wider halo
+    // costs more than the HBM traffic it saves, so one step per launch
+    int S = opt_steps() > 0 ? (int)opt_steps() : 1;
     if (sys->kind == REACH_TRAFFIC) {
         TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
         rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
@@ -416,7 +418,7 @@ extern "C" int reach_set_option(int key, int64_t value) {
         g_opt_kernel = value;
         return REACH_OK;
     case REACH_OPT_STEPS_PER_LAUNCH:
-        if (value < 1 || value > 8) return REACH_EINVAL;
+        if (value < 0 || value > 8) return REACH_EINVAL;
         g_opt_steps = value;
         return REACH_OK;
     case REACH_OPT_BLOCK:
@@ -456,3 +458,39 @@ extern "C" const char *reach_strerror(int code) {
 }
 
 extern "C" int64_t reach_kernel_launches(void) { return g_launches.load(); }
+
+// ================================================================ reach pipe
+// Boxes after every `every` steps (the reach pipe of Sec. 5.5).  Each segment
+// integrates `every` steps from the previous box into the next pipe row on the
+// device.  The MM state is the box, so segments continue the integration
+// exactly; a CGB segment restarts from c = (lo + hi)/2, r = (hi - lo)/2 of the
+// previous row, which recovers the center and radius up to one rounding.
+extern "C" int reach_pipe(const reach_system *sys, int method, const double *x0_lo, const double *x0_hi,
+                          const double *w_lo, const double *w_hi, double t_final, double dt, int64_t every,
+                          double *pipe_lo, double *pipe_hi, void *stream) {
+    if (!sys || !x0_lo || !x0_hi || !pipe_lo || !pipe_hi || (method != MM && method != CGB) || every < 1)
+        return REACH_EINVAL;
+    if (sys->nw > 0 && (!w_lo || !w_hi)) return REACH_EINVAL;
+    int64_t N;
+    int rc = nsteps(t_final, dt, &N);
+    if (rc) return rc;
+    if (N % every) return REACH_EINVAL;
+    if ((rc = check_host_box(x0_lo, x0_hi, sys->n))) return rc;
+    if ((rc = check_host_box(w_lo, w_hi, sys->nw))) return rc;
+    const int64_t n = sys->n, rows = N / every;
+    if (rows == 0) return REACH_OK;
+    Staging sg((cudaStream_t)stream);
+    const double *dxlo, *dxhi, *dwlo = nullptr, *dwhi = nullptr;
+    double *plo, *phi;
+    if ((rc = sg.in(x0_lo, n, &dxlo)) || (rc = sg.in(x0_hi, n, &dxhi)) || (rc = sg.in(w_lo, sys->nw, &dwlo)) ||
+        (rc = sg.in(w_hi, sys->nw, &dwhi)) || (rc = sg.out(pipe_lo, rows * n, &plo)) ||
+        (rc = sg.out(pipe_hi, rows * n, &phi)))
+        return rc;
+    const double T = dt * (double)every;
+    for (int64_t q = 0; q < rows && !rc; ++q) {
+        const double *alo = q ? plo + (q - 1) * n : dxlo, *ahi = q ? phi + (q - 1) * n : dxhi;
+        rc = reach_box(method, sys, alo, ahi, dwlo, dwhi, T, dt, plo + q * n, phi + q * n, stream);
+    }
+    if (rc) return rc;
+    return sg.finish();
+}

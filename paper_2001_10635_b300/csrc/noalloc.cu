@@ -82,11 +82,11 @@ extern "C" int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, co
         }
         if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;
         TrafficK p = make_traffic_k(sys->prm, wl, wh);
-        rc = stencil_traffic(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, (int)opt_steps(), status, st);
+        rc = stencil_traffic(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, opt_steps() > 0 ? (int)opt_steps() : 1, status, st);
     } else {
         KsK p;
         p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
-        rc = stencil_ks(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, (int)opt_steps(), status, st);
+        rc = stencil_ks(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, opt_steps() > 0 ? (int)opt_steps() : 1, status, st);
     }
     if (rc) return rc;
     int host_status = 0;

@@ -25,7 +25,7 @@ pytestmark = [pytest.mark.gpu,
 def _reset_options():
     yield
     R.reach_set_option(R.OPT_KERNEL, 0)
-    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
     R.reach_set_option(R.OPT_BLOCK, 0)
 
 
@@ -314,3 +314,35 @@ def test_ks_rotation_is_tiling_invariant(method):
     b = gpu_box(method, "ks", n, np.roll(lo, k), np.roll(hi, k), None, None, 0.004, dt)
     assert_close(b[0], np.roll(a[0], k), TOL64, "lo")
     assert_close(b[1], np.roll(a[1], k), TOL64, "hi")
+
+
+PIPE = [("traffic", 16, 1.0, 10), ("traffic", 3000, 0.5, 5), ("ks", 300, 0.004, 8), ("osc", 20, 0.5, 25),
+        ("linear", 6, 0.5, 10)]
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("kind,n,T,every", PIPE, ids=[f"{p[0]}{p[1]}" for p in PIPE])
+def test_reach_pipe_matches_oracle(method, kind, n, T, every):
+    lo, hi, wlo, whi, _, dt, prm, A = problem(kind, n, seed=41)
+    opl, oph = O.reach_pipe(method, kind, lo, hi, wlo, whi, t_final=T, dt=dt, every=every, A=A)
+    with R.System(kind, n, A=A) as s:
+        gpl, gph = R.reach_pipe(s, method, lo, hi, wlo, whi, t_final=T, dt=dt, every=every)
+    assert gpl.shape == opl.shape
+    for q in range(opl.shape[0]):
+        assert_close(gpl[q], opl[q], TOL64, f"row {q} lo")
+        assert_close(gph[q], oph[q], TOL64, f"row {q} hi")
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+@pytest.mark.parametrize("kind,prec", [("ks", 32), ("traffic", 32), ("ks", 64)])
+def test_mc_streaming_steps_per_launch(kind, prec, S):
+    n, m = 1500, 40
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=9)
+    T = 0.07 if kind == "traffic" else 0.0007   # 7 steps: ragged against S
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, m=m, seed=2, prec=prec)
+    g = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=2, precision=prec)
+    tol = TOL64 if prec == 64 else TOL32
+    assert_close(g[0], o[0], tol, "lo")
+    assert_close(g[1], o[1], tol, "hi")
