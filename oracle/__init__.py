@@ -25,15 +25,17 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _LIB_OVERRIDE = os.environ.get("REACH_ORACLE_LIB")
 
 MM, CGB, MC = 0, 1, 2
-TRAFFIC, KS, OSC, LINEAR = 0, 1, 2, 3
+TRAFFIC, KS, OSC, LINEAR, HEAT = 0, 1, 2, 3, 4
 METHODS = {"mm": MM, "cgb": CGB, "mc": MC}
-KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR}
+KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT}
 
 # default parameters (BASELINE workloads): traffic (c, v, w, xbar); KS (dx, g_nl,
 # g_2, g_4); oscillator (ka, kb, kc)
 TRAFFIC_PRM = (40.0, 0.5, 1.0 / 6.0, 320.0)
 KS_PRM = (math.pi / 4.0, 1.0, 1.0, 1.0)
 OSC_PRM = (1.0, 0.1, 0.5)
+# heat: (alpha, l, open face); l is set from n by default_params
+HEAT_ALPHA = 8e-6
 
 
 def build(force: bool = False) -> str:
@@ -107,7 +109,9 @@ def _vec(a, n=None):
     return a
 
 
-def default_params(kind: str):
+def default_params(kind: str, n: int = 0):
+    if kind == "heat":
+        return (HEAT_ALPHA, float(round(n ** (1.0 / 3.0))), 1.0)
     return {"traffic": TRAFFIC_PRM, "ks": KS_PRM, "osc": OSC_PRM, "linear": ()}[kind]
 
 
@@ -116,7 +120,7 @@ def input_dim(kind: str, n: int) -> int:
 
 
 def _prep(kind, n, params, A, w_lo, w_hi):
-    prm = _vec(default_params(kind) if params is None else params)
+    prm = _vec(default_params(kind, n) if params is None else params)
     if prm.size == 0:
         prm = np.zeros(1)
     Aa = None

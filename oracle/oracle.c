@@ -38,6 +38,13 @@
  *     dx_i/dt = f_{i-1} - f_i (beta = T = 1).
  *  R7 (Sec. 2.1, MM).  The paper leaves the decomposition function to its
  *     references; each system below documents the one used.
+ *  R8 (Sec. 5.4).  Heat diffusion in the unit cube on an l x l x l grid,
+ *     spacing dx = 1/l, first-order differences: du_i/dt = alpha/dx^2 times the
+ *     sum over the six neighbours of (u_nb - u_i).  Five faces are insulated (a
+ *     missing neighbour contributes nothing); the face z = 0 exchanges heat with
+ *     an environment at temperature zero (a missing neighbour at z = -1 counts
+ *     as u_nb = 0).  The paper does not give alpha, the heated region or the
+ *     initial box; they are inputs here.
  *
  * Random numbers of the MC method come from Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3", SC'11),
@@ -51,7 +58,7 @@
 #include <string.h>
 
 enum { ORC_MM = 0, ORC_CGB = 1, ORC_MC = 2 };
-enum { ORC_TRAFFIC = 0, ORC_KS = 1, ORC_OSC = 2, ORC_LINEAR = 3 };
+enum { ORC_TRAFFIC = 0, ORC_KS = 1, ORC_OSC = 2, ORC_LINEAR = 3, ORC_HEAT = 4 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ENONFINITE = -4 };
 
 /* ---------------------------------------------------------------------- */
@@ -72,6 +79,10 @@ typedef struct {
     double ka, kb, kc;
     /* linear: dx/dt = A x + p, A row-major n x n */
     const double *A;
+    /* heat: grid side l, alpha / dx^2, whether the face z = 0 is open */
+    int64_t l;
+    double kh;
+    int open;
 } orc_sys;
 
 static int64_t input_dim(int kind, int64_t n)
@@ -81,6 +92,7 @@ static int64_t input_dim(int kind, int64_t n)
     case ORC_KS: return 0;
     case ORC_OSC: return n / 2;
     case ORC_LINEAR: return n;
+    case ORC_HEAT: return 0;
     }
     return -1;
 }
@@ -118,6 +130,16 @@ static int make_sys(orc_sys *s, int kind, const double *prm, const double *A, in
         if (!A) return ORC_EINVAL;
         s->A = A;
         break;
+    case ORC_HEAT: {
+        /* prm: alpha, l, open (1: the face z = 0 exchanges with zero temperature) */
+        double alpha = prm[0], dx;
+        s->l = (int64_t)prm[1];
+        s->open = prm[2] != 0.0;
+        if (s->l < 1 || s->l * s->l * s->l != n) return ORC_EINVAL;
+        dx = 1.0 / (double)s->l;
+        s->kh = alpha / (dx * dx);
+        break;
+    }
     default:
         return ORC_EINVAL;
     }
@@ -187,9 +209,31 @@ static void f_linear(const orc_sys *s, const double *x, const double *p, double 
     }
 }
 
+/* heat diffusion (reading R8): kh times the sum of (u_nb - u_i) over the
+   neighbours that exist, the ghost below z = 0 at zero when the face is open */
+static void f_heat(const orc_sys *s, const double *u, double *du)
+{
+    int64_t l = s->l;
+    for (int64_t z = 0; z < l; ++z)
+        for (int64_t y = 0; y < l; ++y)
+            for (int64_t x = 0; x < l; ++x) {
+                int64_t i = x + l * (y + l * z);
+                double acc = 0.0;
+                if (x > 0) acc += u[i - 1] - u[i];
+                if (x < l - 1) acc += u[i + 1] - u[i];
+                if (y > 0) acc += u[i - l] - u[i];
+                if (y < l - 1) acc += u[i + l] - u[i];
+                if (z > 0) acc += u[i - l * l] - u[i];
+                else if (s->open) acc += 0.0 - u[i];
+                if (z < l - 1) acc += u[i + l * l] - u[i];
+                du[i] = s->kh * acc;
+            }
+}
+
 static void f_sys(const orc_sys *s, const double *x, const double *p, double *dx)
 {
     switch (s->kind) {
+    case ORC_HEAT: f_heat(s, x, dx); break;
     case ORC_TRAFFIC: f_traffic(s, x, p, dx); break;
     case ORC_KS: f_ks(s, x, dx); break;
     case ORC_OSC: f_osc(s, x, p, dx); break;
@@ -274,6 +318,9 @@ static void d_sys(const orc_sys *s, const double *x, const double *p,
                   const double *xh, const double *ph, double *dx)
 {
     switch (s->kind) {
+    /* heat is linear with nonnegative off-diagonal coefficients (cooperative):
+       d(x, p, xh, ph) = f(x) */
+    case ORC_HEAT: f_heat(s, x, dx); break;
     case ORC_TRAFFIC: d_traffic(s, x, p, xh, ph, dx); break;
     case ORC_KS: d_ks(s, x, xh, dx); break;
     case ORC_OSC: d_osc(s, x, p, xh, ph, dx); break;
@@ -357,6 +404,8 @@ static void g_sys(const orc_sys *s, const double *c, const double *r,
                   const double *hp, double *dr)
 {
     switch (s->kind) {
+    /* heat: J = A is Metzler and constant, so C = A and g(r) = A r */
+    case ORC_HEAT: (void)c; (void)hp; f_heat(s, r, dr); break;
     case ORC_TRAFFIC: g_traffic(s, c, r, hp, dr); break;
     case ORC_KS: g_ks(s, c, r, dr); break;
     case ORC_OSC: g_osc(s, c, r, hp, dr); break;

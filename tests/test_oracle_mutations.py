@@ -53,6 +53,9 @@ MUTATIONS = [
     ("philox multiplier", "0xD2511F53u", "0xD2511F55u"),
     ("philox key schedule", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;"),
     ("uniform uses 52 bits", "(bits >> 11) * 0x1.0p-53", "(bits >> 12) * 0x1.0p-52"),
+    ("heat open face ignored", "else if (s->open) acc += 0.0 - u[i];", "else if (s->open) acc += 0.0;"),
+    ("heat y neighbour index", "if (y < l - 1) acc += u[i + l] - u[i];", "if (y < l - 1) acc += u[i + 1] - u[i];"),
+    ("heat coefficient", "s->kh = alpha / (dx * dx);", "s->kh = alpha / dx;"),
 ]
 
 

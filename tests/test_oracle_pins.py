@@ -543,3 +543,62 @@ def test_pipe_rows_are_intermediate_boxes(method):
         lo, hi = O.reach(method, "traffic", *args, t_final=0.25 * (q + 1), dt=0.01)
         np.testing.assert_allclose(plo[q], lo, rtol=1e-14)
         np.testing.assert_allclose(phi[q], hi, rtol=1e-14)
+
+
+# ------------------------------------------------------------------ 3-D heat diffusion (Sec. 5.4, reading R8)
+def _heat_matrix(l, kh, open_face):
+    """Graph Laplacian of the l^3 grid assembled from the PDE's stencil: each
+    present neighbour contributes kh (u_nb - u_i); below z = 0 an open face
+    contributes kh (0 - u_i)."""
+    n = l ** 3
+    A = np.zeros((n, n))
+    idx = lambda x, y, z: x + l * (y + l * z)
+    for z in range(l):
+        for y in range(l):
+            for x in range(l):
+                i = idx(x, y, z)
+                for dxx, dyy, dzz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    X, Y, Z = x + dxx, y + dyy, z + dzz
+                    if 0 <= X < l and 0 <= Y < l and 0 <= Z < l:
+                        A[i, idx(X, Y, Z)] += kh
+                        A[i, i] -= kh
+                    elif Z < 0 and open_face:
+                        A[i, i] -= kh
+    return A
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("open_face", [0.0, 1.0])
+def test_heat_equals_the_assembled_linear_system(method, open_face):
+    l, alpha = 3, 0.02
+    kh = alpha * l * l
+    lo, hi = W.random_box(l ** 3, seed=81, centre=(0.0, 1.0), width=(0.0, 0.1))
+    a = O.reach(method, "heat", lo, hi, t_final=1.0, dt=0.01, params=(alpha, l, open_face))
+    A = _heat_matrix(l, kh, open_face)
+    z = np.zeros(l ** 3)
+    b = O.reach(method, "linear", lo, hi, z, z, t_final=1.0, dt=0.01, A=A)
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [(1, 0, 0), (0, 2, 1), (3, 1, 2)])
+def test_heat_neumann_cosine_modes(k):
+    # with every face insulated, cos(pi k (x + 1/2) / l) in each direction is an
+    # eigenvector of the discrete operator with eigenvalue -2 kh sum(1 - cos(pi k / l))
+    l, alpha = 6, 0.01
+    kh = alpha * l * l
+    c = [np.cos(np.pi * kk * (np.arange(l) + 0.5) / l) for kk in k]
+    u = np.einsum("z,y,x->zyx", c[2], c[1], c[0]).reshape(-1)
+    lam = -2.0 * kh * sum(1.0 - np.cos(np.pi * kk / l) for kk in k)
+    np.testing.assert_allclose(O.rhs("heat", u, params=(alpha, l, 0.0)), lam * u, atol=1e-12)
+
+
+def test_heat_is_conserved_in_a_closed_box_and_leaks_through_the_open_face():
+    l, alpha = 5, 0.01
+    kh = alpha * l * l
+    u0 = np.random.default_rng(8).random(l ** 3)
+    closed = O.flow("heat", u0, t_final=2.0, dt=0.01, params=(alpha, l, 0.0))
+    assert abs(closed.sum() - u0.sum()) < 1e-12 * u0.sum()
+    # open face: the total changes at -kh times the heat of the bottom layer
+    du = O.rhs("heat", u0, params=(alpha, l, 1.0))
+    assert du.sum() == pytest.approx(-kh * u0[: l * l].sum(), rel=1e-12)
