@@ -230,6 +230,51 @@ def bench_ks(R, torch, dev):
     return out
 
 
+# FP64 pipe operations per component-step of the heat stage kernels (RK4 in
+# nested form for the linear system): per stage five neighbour additions, the
+# fma with the neighbour count and the stage fma = 7, four stages = 28
+HEAT_FP64_OPS = 28.0
+
+
+def bench_heat(R, torch, dev, l=1000, steps=10):
+    """3-D heat diffusion on the paper's l = 1000 cube (10^9 cells, Sec. 5.4),
+    MM and CGB over `steps` RK4 steps, timed with CUDA events; the rate gives
+    the time of the paper's 1000-step run."""
+    n = l ** 3
+    need = 10 * 8 * n + (2 << 30)
+    if torch.cuda.mem_get_info(dev)[0] < need:
+        return {"skipped": f"needs {need / 2**30:.0f} GiB of device memory"}
+    dt = W.HEAT_DT
+    T = steps * dt
+    xlo, xhi = W.heat_cube_torch(l, dev)
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"heat cube l={l} (n=1e9), alpha=8e-6, open face z=0, (0.4,0.6)^3 in [0.9,1.1], "
+                       f"else [0,0.01], dt=0.02, {steps} RK4 steps per call",
+           "unit": "comp-steps/s"}
+    with R.System("heat", n) as s:
+        for name, fn in (("mm", R.reach_mm), ("cgb", R.reach_cgb)):
+            fn(s, xlo, xhi, t_final=T, dt=dt, lo=lo, hi=hi, stream=stream)   # warm
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(s, xlo, xhi, t_final=T, dt=dt, lo=lo, hi=hi, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            rate = 2 * n * steps / sec
+            ops = HEAT_FP64_OPS * 2 * n * steps / sec
+            out[name] = {"s": sec, "value": rate, "ms_per_rk4_step": sec / steps * 1e3,
+                         "fp64_frac": ops / FP64_PEAK_OPS,
+                         "minutes_for_1000_steps": sec / steps * 1000 / 60}
+    out["paper_minutes_for_1000_steps"] = 350.2
+    out["fp64_ops_per_comp_step"] = HEAT_FP64_OPS
+    del xlo, xhi, lo, hi
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_temporal_blocking(R, torch, dev):
     """RK4 steps per launch S (halo 4 R S recomputed) on traffic MM (FP64,
     n = 2^24) and on KS MC32 (n = 2^20, 256 samples): the FP64 kernels are bound
@@ -545,6 +590,7 @@ def main():
         line["traffic16"] = bench_traffic16(R)
         line["temporal_blocking"] = bench_temporal_blocking(R, torch, dev)
         line["serving"] = bench_serving(R)
+        line["heat3d"] = bench_heat(R, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",

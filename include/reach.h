@@ -77,13 +77,21 @@ typedef enum {
     REACH_OSC = 2,
     /* Dense linear test system dx/dt = A x + p, nw = n, n <= 256.
        Params: reach_linear_params. */
-    REACH_LINEAR = 3
+    REACH_LINEAR = 3,
+    /* Heat diffusion in the unit cube (Sec. 5.4) on an l x l x l grid
+       (n = l^3, index x + l (y + l z)), spacing 1/l, first-order differences:
+       du_i/dt = alpha l^2 sum over the six neighbours of (u_nb - u_i); missing
+       neighbours of five faces contribute nothing (insulated), and with
+       open_face set the face z = 0 sees an environment at temperature zero.
+       nw = 0.  Params: reach_heat_params. */
+    REACH_HEAT3D = 4
 } reach_kind;
 
 typedef struct { double cap, v, w, xbar; } reach_traffic_params;   /* 40, 0.5, 1/6, 320 */
 typedef struct { double dx, g_nl, g_2, g_4; } reach_ks_params;     /* pi/4, 1, 1, 1 */
 typedef struct { double ka, kb, kc; } reach_osc_params;            /* 1, 0.1, 0.5 */
 typedef struct { const double *A; } reach_linear_params;           /* n x n, row-major */
+typedef struct { double alpha; int64_t l; int open_face; } reach_heat_params; /* 8e-6, cbrt(n), 1 */
 
 typedef struct reach_system reach_system;   /* opaque; parameters live on the device */
 
@@ -92,7 +100,7 @@ typedef struct reach_system reach_system;   /* opaque; parameters live on the de
    above (REACH_LINEAR requires params).  The parameters, including A, are
    copied to the current device; the caller's buffers may be freed
    afterwards.  REACH_EINVAL for n < 1, odd n with REACH_OSC, n < 5 with
-   REACH_KS, n > 256 with REACH_LINEAR, a wrong params_bytes or non-finite
+   REACH_KS, n > 256 with REACH_LINEAR, n != l^3 with REACH_HEAT3D, a wrong params_bytes or non-finite
    params (traffic additionally needs v, w >= 0; KS dx > 0; osc kb >= 0). */
 REACH_API int reach_system_create(int kind, int64_t n, const void *params, size_t params_bytes,
                         reach_system **out);

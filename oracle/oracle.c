@@ -38,13 +38,13 @@
  *     dx_i/dt = f_{i-1} - f_i (beta = T = 1).
  *  R7 (Sec. 2.1, MM).  The paper leaves the decomposition function to its
  *     references; each system below documents the one used.
- *  R8 (Sec. 5.4).  Heat diffusion in the unit cube on an l x l x l grid,
- *     spacing dx = 1/l, first-order differences: du_i/dt = alpha/dx^2 times the
- *     sum over the six neighbours of (u_nb - u_i).  Five faces are insulated (a
- *     missing neighbour contributes nothing); the face z = 0 exchanges heat with
- *     an environment at temperature zero (a missing neighbour at z = -1 counts
- *     as u_nb = 0).  The paper does not give alpha, the heated region or the
- *     initial box; they are inputs here.
+ *  R12 (Sec. 5.4).  Heat diffusion in the unit cube on an l x l x l grid,
+ *      spacing dx = 1/l, first-order differences: du_i/dt = alpha/dx^2 times the
+ *      sum over the six neighbours of (u_nb - u_i).  Five faces are insulated (a
+ *      missing neighbour contributes nothing); the face z = 0 exchanges heat with
+ *      an environment at temperature zero (a missing neighbour at z = -1 counts
+ *      as u_nb = 0).  The paper does not give alpha, the heated region or the
+ *      initial box; they are inputs here.
  *
  * Random numbers of the MC method come from Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3", SC'11),
@@ -209,7 +209,7 @@ static void f_linear(const orc_sys *s, const double *x, const double *p, double 
     }
 }
 
-/* heat diffusion (reading R8): kh times the sum of (u_nb - u_i) over the
+/* heat diffusion (reading R12): kh times the sum of (u_nb - u_i) over the
    neighbours that exist, the ghost below z = 0 at zero when the face is open */
 static void f_heat(const orc_sys *s, const double *u, double *du)
 {

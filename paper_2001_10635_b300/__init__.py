@@ -21,14 +21,18 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libreach.so")
 
-TRAFFIC, KS, OSC, LINEAR = 0, 1, 2, 3
-KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR}
+TRAFFIC, KS, OSC, LINEAR, HEAT3D = 0, 1, 2, 3, 4
+KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D}
 OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT = 1, 2, 3, 4
 BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
           -4: "REACH_ENONFINITE", -5: "REACH_ETIMEOUT", -6: "REACH_ECUDA", -7: "REACH_ENODEV"}
 
 _lib = None
+
+
+class _HeatParams(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("l", ctypes.c_int64), ("open_face", ctypes.c_int)]
 
 
 class _Query(ctypes.Structure):
@@ -163,6 +167,11 @@ class System:
             self._A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(n, n))
             buf = (ctypes.c_void_p * 1)(self._A.ctypes.data)
             nbytes = ctypes.sizeof(ctypes.c_void_p)
+        elif self.kind == HEAT3D and params is not None:
+            alpha, l, open_face = params
+            buf = _HeatParams(float(alpha), int(l), int(bool(open_face)))
+            nbytes = ctypes.sizeof(buf)
+            buf = ctypes.pointer(buf)
         elif params is not None:
             vals = [float(v) for v in params]
             if len(vals) != self._PARAM_FIELDS[self.kind]:

@@ -247,6 +247,20 @@ extern "C" int reach_system_create(int kind, int64_t n, const void *params, size
         s.nw = n;
         break;
     }
+    case REACH_HEAT3D: {
+        reach_heat_params p{8e-6, (int64_t)std::llround(std::cbrt((double)n)), 1};
+        if (params) {
+            if (params_bytes != sizeof p) return REACH_EINVAL;
+            memcpy(&p, params, sizeof p);
+        }
+        if (p.l < 1 || p.l > 2097151 || p.l * p.l * p.l != n || !std::isfinite(p.alpha) || p.alpha < 0)
+            return REACH_EINVAL;
+        s.nw = 0;
+        host[0] = p.alpha * (double)p.l * (double)p.l;   // alpha / dx^2
+        host[1] = (double)p.l;
+        host[2] = p.open_face ? 1.0 : 0.0;
+        break;
+    }
     default:
         return REACH_EINVAL;
     }
@@ -300,6 +314,7 @@ bool use_onchip(const reach_system *s) {
     if (k == 2) return fits;
     if (k == 1) return s->kind == REACH_OSC || s->kind == REACH_LINEAR;
     if (s->kind == REACH_OSC || s->kind == REACH_LINEAR) return true;
+    if (s->kind == REACH_HEAT3D) return 2 * s->n <= 1024;
     return 2 * s->n <= 1024 || (s->kind == REACH_KS && s->n < 256);
 }
 
@@ -375,19 +390,28 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         return sg.finish();
     }
 
-    double *sA, *sB;
-    if ((rc = sg.scratch(2 * n * sizeof(double), (void **)&sA))) return rc;
-    sB = sA + n;
-    // FP64 stencil kernels are bound by the FP64 pipe: recomputing a wider halo
-    // costs more than the HBM traffic it saves, so one step per launch
-    int S = opt_steps() > 0 ? (int)opt_steps() : 1;
-    if (sys->kind == REACH_TRAFFIC) {
-        TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
-        rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+    if (sys->kind == REACH_HEAT3D) {
+        HeatK p;
+        p.kh = sys->prm[0];
+        p.l = (int64_t)sys->prm[1];
+        p.open = sys->prm[2] != 0.0;
+        rc = heat_run(method, p, n, dxlo, dxhi, dlo, dhi, dt, N, sg);
     } else {
-        KsK p;
-        p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
-        rc = stencil_ks(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+        // ping-pong partner of the output for the fused stencil kernels
+        double *sA, *sB;
+        if ((rc = sg.scratch(2 * n * sizeof(double), (void **)&sA))) return rc;
+        sB = sA + n;
+        // FP64 stencil kernels are bound by the FP64 pipe: recomputing a wider
+        // halo costs more than the HBM traffic it saves, so one step per launch
+        const int S = opt_steps() > 0 ? (int)opt_steps() : 1;
+        if (sys->kind == REACH_TRAFFIC) {
+            TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
+            rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+        } else {
+            KsK p;
+            p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
+            rc = stencil_ks(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+        }
     }
     if (rc) return rc;
     return sg.finish();

@@ -32,6 +32,12 @@ struct OscK {
     double ka, kb, kc;
 };
 
+struct HeatK {
+    double kh;           // alpha / dx^2 = alpha l^2
+    int64_t l;
+    int open;            // the face z = 0 sees an environment at zero
+};
+
 // v * y as an exponent shift when v = 2^e: exact whenever y and the result are
 // normal numbers (then the product is a power-of-two scaling); scale_ok says
 // whether that holds for y

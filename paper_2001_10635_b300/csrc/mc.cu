@@ -87,6 +87,25 @@ struct Plain<REACH_OSC, T> {
 };
 
 template <class T>
+struct Plain<REACH_HEAT3D, T> {
+    static constexpr int R = 0;
+    // whole grid on chip; q: kh, l, open face
+    template <class Row>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
+        const int l = (int)q[1], pl = l * l;
+        const int x = c % l, y = (c / l) % l, z = c / pl;
+        T s = (x > 0) ? row(c - 1) : T(0);
+        s += (x + 1 < l) ? row(c + 1) : T(0);
+        s += (y > 0) ? row(c - l) : T(0);
+        s += (y + 1 < l) ? row(c + l) : T(0);
+        s += (z > 0) ? row(c - pl) : T(0);
+        s += (z + 1 < l) ? row(c + pl) : T(0);
+        const int m = (x > 0) + (x + 1 < l) + (y > 0) + (y + 1 < l) + (z > 0 || q[2] != T(0)) + (z + 1 < l);
+        return q[0] * tfma(-(T)m, row(c), s);
+    }
+};
+
+template <class T>
 struct Plain<REACH_LINEAR, T> {
     static constexpr int R = 0;
     template <class Row>
@@ -105,7 +124,7 @@ __device__ __forceinline__ void mc_consts(const double *prm, T (&q)[4]) {
     q[0] = q[1] = q[2] = q[3] = T(0);
     if (SYS == REACH_TRAFFIC) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)(prm[2] * prm[3]); }
     if (SYS == REACH_KS) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)prm[3]; }
-    if (SYS == REACH_OSC) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; }
+    if (SYS == REACH_OSC || SYS == REACH_HEAT3D) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; }
 }
 
 // sample value rounded to the run precision (binary32 runs start from the
@@ -470,6 +489,7 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         case REACH_TRAFFIC: rc = launch_onchip<REACH_TRAFFIC, T>(a, sg.st); break;
         case REACH_KS: rc = launch_onchip<REACH_KS, T>(a, sg.st); break;
         case REACH_OSC: rc = launch_onchip<REACH_OSC, T>(a, sg.st); break;
+        case REACH_HEAT3D: rc = launch_onchip<REACH_HEAT3D, T>(a, sg.st); break;
         default: rc = launch_onchip<REACH_LINEAR, T>(a, sg.st); break;
         }
     } else {

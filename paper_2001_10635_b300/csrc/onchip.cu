@@ -47,6 +47,7 @@ int onchip_launch_single(const OnItem &it, int threads, cudaStream_t st) {
     case REACH_KS: return onchip_single_k<REACH_KS>(it, threads, st);
     case REACH_OSC: return onchip_single_k<REACH_OSC>(it, threads, st);
     case REACH_LINEAR: return onchip_single_k<REACH_LINEAR>(it, threads, st);
+    case REACH_HEAT3D: return onchip_single_k<REACH_HEAT3D>(it, threads, st);
     }
     return REACH_EINVAL;
 }
@@ -57,6 +58,7 @@ int onchip_launch_cluster(const OnItem &it, cudaStream_t st) {
     case REACH_KS: return onchip_cluster_k<REACH_KS>(it, st);
     case REACH_OSC: return onchip_cluster_k<REACH_OSC>(it, st);
     case REACH_LINEAR: return onchip_cluster_k<REACH_LINEAR>(it, st);
+    case REACH_HEAT3D: return onchip_cluster_k<REACH_HEAT3D>(it, st);
     }
     return REACH_EINVAL;
 }
@@ -69,6 +71,7 @@ int onchip_launch_batch(int kind, int method, int q, const void *items, const vo
     case REACH_KS: return onchip_batch_k<REACH_KS>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
     case REACH_OSC: return onchip_batch_k<REACH_OSC>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
     case REACH_LINEAR: return onchip_batch_k<REACH_LINEAR>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
+    case REACH_HEAT3D: return onchip_batch_k<REACH_HEAT3D>(method, q, items, slots, bins, tasks, ntasks, counter, done, clusters, smem, st);
     }
     return REACH_EINVAL;
 }

@@ -122,6 +122,20 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             double rl = (j > 0) ? yB[j - 1] : 0.0, rr = (j < m - 1) ? yB[j + 1] : 0.0;
             return fma(cxx, yB[j], fma(q[5], rl + rr, wB[j]));
         }
+    } else if constexpr (SYS == REACH_HEAT3D) {
+        // q: kh, l (integer bits), open face;  both halves (MM: corners, CGB:
+        // center and radius, C = A) evolve by the same Metzler operator
+        const double *Y = upper ? yB : yA;
+        const int l = (int)__double_as_longlong(q[1]), pl = l * l;
+        const int ii = (int)i, x = ii % l, y = (ii / l) % l, z = ii / pl;
+        double s = (x > 0) ? Y[i - 1] : 0.0;
+        s += (x + 1 < l) ? Y[i + 1] : 0.0;
+        s += (y > 0) ? Y[i - l] : 0.0;
+        s += (y + 1 < l) ? Y[i + l] : 0.0;
+        s += (z > 0) ? Y[i - pl] : 0.0;
+        s += (z + 1 < l) ? Y[i + pl] : 0.0;
+        const int m = (x > 0) + (x + 1 < l) + (y > 0) + (y + 1 < l) + (z > 0 || q[2] != 0.0) + (z + 1 < l);
+        return q[0] * fma(-(double)m, Y[i], s);
     } else {   // REACH_LINEAR, prm = A row-major
         const double *Arow = prm + i * n;
         double acc = 0.0;
@@ -161,6 +175,8 @@ __device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
     } else if constexpr (SYS == REACH_OSC) {
         q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2];
         q[3] = prm[0] + 2.0 * prm[2]; q[4] = 3.0 * prm[1]; q[5] = kabs(prm[2]);
+    } else if constexpr (SYS == REACH_HEAT3D) {
+        q[0] = prm[0]; q[1] = __longlong_as_double((long long)prm[1]); q[2] = prm[2];
     }
 }
 

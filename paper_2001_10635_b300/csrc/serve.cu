@@ -78,8 +78,9 @@ int64_t footprint(const reach_request *r) {
     // staged inputs and outputs (the worst case: host buffers), the status word
     int64_t b = (4 * n + 2 * nw) * 8 + 256;
     if (r->method == 2) return b + mc_footprint(s, r->m, r->precision);
-    // MM / CGB: the streaming kernels keep a 2n ping-pong buffer
-    return b + 2 * n * 8;
+    // MM / CGB: the stencil kernels keep a 2n ping-pong buffer; the heat
+    // stage kernels keep the state and two stage vectors (6n)
+    return b + (s->kind == REACH_HEAT3D ? 6 : 2) * n * 8;
 }
 
 static void run_job(Job *j, cudaStream_t st) {

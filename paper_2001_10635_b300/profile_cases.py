@@ -8,6 +8,7 @@ Cases:
   traffic_mm           traffic chain, n cells (default 2^24), T (default 0.02)
   traffic16_mm         traffic chain n = 16, T = 10 (on-chip kernel)
   osc_batch            the 4096-query oscillator batch (MM T=5, CGB T=4)
+  heat_mm, heat_cgb    heat cube of side l = --n (default 256), --t (default 0.1)
 """
 from __future__ import annotations
 
@@ -63,6 +64,13 @@ def main(argv=None):
         with R.System("traffic", 16) as s:
             for _ in range(2):
                 R.reach_mm(s, wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    elif a.case in ("heat_mm", "heat_cgb"):
+        l = a.n or 256
+        lo, hi = W.heat_cube_torch(l, dev)
+        with R.System("heat", l ** 3) as s:
+            f = R.reach_mm if a.case == "heat_mm" else R.reach_cgb
+            for _ in range(2):
+                f(s, lo, hi, t_final=a.t or 0.1, dt=W.HEAT_DT)
     elif a.case == "osc_batch":
         sizes = W.osc_sizes(4096, seed=0)
         systems, qs = {}, []

@@ -545,7 +545,7 @@ def test_pipe_rows_are_intermediate_boxes(method):
         np.testing.assert_allclose(phi[q], hi, rtol=1e-14)
 
 
-# ------------------------------------------------------------------ 3-D heat diffusion (Sec. 5.4, reading R8)
+# ------------------------------------------------------------------ 3-D heat diffusion (Sec. 5.4, reading R12)
 def _heat_matrix(l, kh, open_face):
     """Graph Laplacian of the l^3 grid assembled from the PDE's stencil: each
     present neighbour contributes kh (u_nb - u_i); below z = 0 an open face

@@ -17,6 +17,9 @@ Workloads (all synthetic; the paper prints no datasets or reachable boxes):
   velocities 0, half-width 1e-4, disturbance w in [-0.01, 0.01], dt = 0.005,
   T = 5.
 * linear test systems (Metzler, general, nilpotent).
+* 3-D heat diffusion (Sec. 5.4): unit cube on an l^3 grid, cells meeting
+  (0.4, 0.6)^3 in [0.9, 1.1], all others in [0, 0.01]; alpha = 8e-6, face
+  z = 0 open, dt = 0.02, T = 20.
 * a Poisson arrival trace mixing traffic and KS queries for the serving loop.
 """
 from __future__ import annotations
@@ -127,6 +130,44 @@ def random_box(n: int, seed: int, centre=(-1.0, 1.0), width=(0.0, 0.2)):
     c = g.uniform(*centre, n)
     h = g.uniform(*width, n)
     return c - h, c + h
+
+
+# ---------------------------------------------------------------- 3-D heat
+HEAT_DT = 0.02
+HEAT_T = 20.0
+HEAT_ALPHA = 8e-6
+
+
+def heat_hot_cells(l: int) -> np.ndarray:
+    """Boolean mask over one axis: cells [k/l, (k+1)/l] meeting (0.4, 0.6)."""
+    k = np.arange(l)
+    return (5 * k < 3 * l) & (5 * (k + 1) > 2 * l)
+
+
+def heat_cube(l: int, t_final: float = HEAT_T, dt: float = HEAT_DT, alpha: float = HEAT_ALPHA,
+              open_face: bool = True, hot=(0.9, 1.1), cold=(0.0, 0.01)):
+    """Unit cube on an l^3 grid, index i = z l^2 + y l + x: cells meeting the
+    heated region (0.4, 0.6)^3 start in `hot`, all others in `cold`."""
+    a = heat_hot_cells(l)
+    mask = (a[:, None, None] & a[None, :, None] & a[None, None, :]).reshape(-1)
+    x_lo = np.where(mask, hot[0], cold[0])
+    x_hi = np.where(mask, hot[1], cold[1])
+    return {"x_lo": x_lo, "x_hi": x_hi, "t_final": t_final, "dt": dt,
+            "params": (alpha, l, 1 if open_face else 0)}
+
+
+def heat_cube_torch(l: int, device, hot=(0.9, 1.1), cold=(0.0, 0.01)):
+    """The box of heat_cube built directly in device memory (for l^3 too large
+    to stage from the host)."""
+    import torch
+    a = torch.from_numpy(heat_hot_cells(l)).to(device)
+    lo = torch.full((l, l, l), cold[0], dtype=torch.float64, device=device)
+    hi = torch.full((l, l, l), cold[1], dtype=torch.float64, device=device)
+    idx = torch.nonzero(a).flatten()
+    s0, s1 = int(idx[0]), int(idx[-1]) + 1
+    lo[s0:s1, s0:s1, s0:s1] = hot[0]
+    hi[s0:s1, s0:s1, s0:s1] = hot[1]
+    return lo.reshape(-1), hi.reshape(-1)
 
 
 # ---------------------------------------------------------------- serving trace
