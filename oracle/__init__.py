@@ -25,9 +25,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _LIB_OVERRIDE = os.environ.get("REACH_ORACLE_LIB")
 
 MM, CGB, MC = 0, 1, 2
-TRAFFIC, KS, OSC, LINEAR, HEAT = 0, 1, 2, 3, 4
+TRAFFIC, KS, OSC, LINEAR, HEAT, QUAD = 0, 1, 2, 3, 4, 5
 METHODS = {"mm": MM, "cgb": CGB, "mc": MC}
-KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT}
+KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT, "quad": QUAD}
 
 # default parameters (BASELINE workloads): traffic (c, v, w, xbar); KS (dx, g_nl,
 # g_2, g_4); oscillator (ka, kb, kc)
@@ -36,6 +36,8 @@ KS_PRM = (math.pi / 4.0, 1.0, 1.0, 1.0)
 OSC_PRM = (1.0, 0.1, 0.5)
 # heat: (alpha, l, open face); l is set from n by default_params
 HEAT_ALPHA = 8e-6
+# quadrotor: (m, g, F, Jx, Jy, Jz), hover thrust F = m g
+QUAD_PRM = (1.4, 9.81, 1.4 * 9.81, 0.054, 0.054, 0.104)
 
 
 def build(force: bool = False) -> str:
@@ -112,7 +114,7 @@ def _vec(a, n=None):
 def default_params(kind: str, n: int = 0):
     if kind == "heat":
         return (HEAT_ALPHA, float(round(n ** (1.0 / 3.0))), 1.0)
-    return {"traffic": TRAFFIC_PRM, "ks": KS_PRM, "osc": OSC_PRM, "linear": ()}[kind]
+    return {"traffic": TRAFFIC_PRM, "ks": KS_PRM, "osc": OSC_PRM, "linear": (), "quad": QUAD_PRM}[kind]
 
 
 def input_dim(kind: str, n: int) -> int:

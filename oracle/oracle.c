@@ -45,6 +45,18 @@
  *      an environment at temperature zero (a missing neighbour at z = -1 counts
  *      as u_nb = 0).  The paper does not give alpha, the heated region or the
  *      initial box; they are inputs here.
+ *  R13 (Sec. 5.2).  Quadrotor swarm of K = n/12 independent agents.  Agent k
+ *      holds x[12k + 0..11] = (p_n, p_e, h, dp_n, dp_e, dh, phi, theta, psi,
+ *      dphi, dtheta, dpsi) and inputs p[3k + 0..2] = (tau_phi, tau_theta,
+ *      tau_psi); the thrust F is a parameter (hover: F = m g), so the system
+ *      is input-affine as CGB requires.  The paper gives no mass, inertia,
+ *      thrust or sets; they are inputs here.  MM decomposition: the three
+ *      translational accelerations are not monotone in the angles; each takes
+ *      the lower end of its natural interval extension over the hull of the
+ *      two angle triples when (phi, theta, psi) <= (phi^, theta^, psi^), the
+ *      upper end otherwise; every other row is increasing in its argument and
+ *      takes its own.  CGB: C bounds |J| over the current box by the natural
+ *      interval extension of each partial derivative (R3); C_ii = 0.
  *
  * Random numbers of the MC method come from Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3", SC'11),
@@ -58,7 +70,7 @@
 #include <string.h>
 
 enum { ORC_MM = 0, ORC_CGB = 1, ORC_MC = 2 };
-enum { ORC_TRAFFIC = 0, ORC_KS = 1, ORC_OSC = 2, ORC_LINEAR = 3, ORC_HEAT = 4 };
+enum { ORC_TRAFFIC = 0, ORC_KS = 1, ORC_OSC = 2, ORC_LINEAR = 3, ORC_HEAT = 4, ORC_QUAD = 5 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ENONFINITE = -4 };
 
 /* ---------------------------------------------------------------------- */
@@ -83,6 +95,8 @@ typedef struct {
     int64_t l;
     double kh;
     int open;
+    /* quadrotor swarm: mass, gravity, thrust, moments of inertia */
+    double qm, qg, qF, Jx, Jy, Jz;
 } orc_sys;
 
 static int64_t input_dim(int kind, int64_t n)
@@ -93,6 +107,7 @@ static int64_t input_dim(int kind, int64_t n)
     case ORC_OSC: return n / 2;
     case ORC_LINEAR: return n;
     case ORC_HEAT: return 0;
+    case ORC_QUAD: return n % 12 ? -1 : n / 12 * 3;
     }
     return -1;
 }
@@ -140,6 +155,13 @@ static int make_sys(orc_sys *s, int kind, const double *prm, const double *A, in
         s->kh = alpha / (dx * dx);
         break;
     }
+    case ORC_QUAD:
+        /* prm: m, g, F, Jx, Jy, Jz */
+        s->qm = prm[0]; s->qg = prm[1]; s->qF = prm[2];
+        s->Jx = prm[3]; s->Jy = prm[4]; s->Jz = prm[5];
+        if (!(s->qm > 0.0) || !(s->qF >= 0.0) || !(s->Jx > 0.0) || !(s->Jy > 0.0) || !(s->Jz > 0.0))
+            return ORC_EINVAL;
+        break;
     default:
         return ORC_EINVAL;
     }
@@ -230,9 +252,36 @@ static void f_heat(const orc_sys *s, const double *u, double *du)
             }
 }
 
+/* quadrotor swarm (Sec. 5.2, reading R13): the translational accelerations
+   of the paper's model, double integrators for position and angles, angular
+   accelerations tau / J */
+static void f_quad(const orc_sys *s, const double *x, const double *p, double *dx)
+{
+    double a = s->qF / s->qm;
+    for (int64_t k = 0; k < s->n / 12; ++k) {
+        const double *y = x + 12 * k, *tau = p + 3 * k;
+        double *dy = dx + 12 * k;
+        double sf = sin(y[6]), cf = cos(y[6]), st = sin(y[7]), ct = cos(y[7]);
+        double sp = sin(y[8]), cp = cos(y[8]);
+        dy[0] = y[3];
+        dy[1] = y[4];
+        dy[2] = y[5];
+        dy[3] = a * (-(cf * st * cp) - sf * sp);
+        dy[4] = a * (-(cf * st * sp) + sf * cp);
+        dy[5] = s->qg - a * (cf * ct);
+        dy[6] = y[9];
+        dy[7] = y[10];
+        dy[8] = y[11];
+        dy[9] = tau[0] / s->Jx;
+        dy[10] = tau[1] / s->Jy;
+        dy[11] = tau[2] / s->Jz;
+    }
+}
+
 static void f_sys(const orc_sys *s, const double *x, const double *p, double *dx)
 {
     switch (s->kind) {
+    case ORC_QUAD: f_quad(s, x, p, dx); break;
     case ORC_HEAT: f_heat(s, x, dx); break;
     case ORC_TRAFFIC: f_traffic(s, x, p, dx); break;
     case ORC_KS: f_ks(s, x, dx); break;
@@ -314,10 +363,93 @@ static void d_linear(const orc_sys *s, const double *x, const double *p,
     }
 }
 
+/* Natural interval extensions for the quadrotor (reading R13). */
+typedef struct { double lo, hi; } ival;
+
+#define ORC_PI 3.141592653589793
+#define ORC_HALF_PI 1.5707963267948966
+#define ORC_TWO_PI 6.283185307179586
+#define ORC_INV_TWO_PI 0.15915494309189535
+
+static ival iv_hull(double a, double b) { ival r = {min2(a, b), max2(a, b)}; return r; }
+static ival iv_add(ival a, ival b) { ival r = {a.lo + b.lo, a.hi + b.hi}; return r; }
+static ival iv_neg(ival a) { ival r = {-a.hi, -a.lo}; return r; }
+static ival iv_mul(ival a, ival b)
+{
+    double p1 = a.lo * b.lo, p2 = a.lo * b.hi, p3 = a.hi * b.lo, p4 = a.hi * b.hi;
+    ival r = {min2(min2(p1, p2), min2(p3, p4)), max2(max2(p1, p2), max2(p3, p4))};
+    return r;
+}
+static ival iv_scale(double c, ival a) { return iv_mul((ival){c, c}, a); }
+static double iv_mag(ival a) { return max2(fabs(a.lo), fabs(a.hi)); }
+
+/* does c + 2 pi k lie in [a, b] for some integer k */
+static int holds_point(double a, double b, double c)
+{
+    double k = ceil((a - c) * ORC_INV_TWO_PI);
+    return c + ORC_TWO_PI * k <= b;
+}
+
+/* range of sin over [a, b]: the endpoints, and +-1 where a maximum
+   (pi/2 + 2 pi k) or minimum (-pi/2 + 2 pi k) lies inside */
+static ival iv_sin(ival a)
+{
+    ival r = {-1.0, 1.0};
+    double s0, s1;
+    if (a.hi - a.lo >= ORC_TWO_PI) return r;
+    s0 = sin(a.lo); s1 = sin(a.hi);
+    r.lo = holds_point(a.lo, a.hi, -ORC_HALF_PI) ? -1.0 : min2(s0, s1);
+    r.hi = holds_point(a.lo, a.hi, ORC_HALF_PI) ? 1.0 : max2(s0, s1);
+    return r;
+}
+
+/* range of cos over [a, b]: maxima at 2 pi k, minima at pi + 2 pi k */
+static ival iv_cos(ival a)
+{
+    ival r = {-1.0, 1.0};
+    double c0, c1;
+    if (a.hi - a.lo >= ORC_TWO_PI) return r;
+    c0 = cos(a.lo); c1 = cos(a.hi);
+    r.lo = holds_point(a.lo, a.hi, ORC_PI) ? -1.0 : min2(c0, c1);
+    r.hi = holds_point(a.lo, a.hi, 0.0) ? 1.0 : max2(c0, c1);
+    return r;
+}
+
+static void d_quad(const orc_sys *s, const double *x, const double *p,
+                   const double *xh, const double *ph, double *dx)
+{
+    double a = s->qF / s->qm;
+    (void)ph;
+    for (int64_t k = 0; k < s->n / 12; ++k) {
+        const double *y = x + 12 * k, *yh = xh + 12 * k, *tau = p + 3 * k;
+        double *dy = dx + 12 * k;
+        int lower = y[6] <= yh[6] && y[7] <= yh[7] && y[8] <= yh[8];
+        ival F = iv_hull(y[6], yh[6]), T = iv_hull(y[7], yh[7]), P = iv_hull(y[8], yh[8]);
+        ival sf = iv_sin(F), cf = iv_cos(F), st = iv_sin(T), ct = iv_cos(T);
+        ival sp = iv_sin(P), cp = iv_cos(P);
+        ival an = iv_scale(a, iv_add(iv_neg(iv_mul(iv_mul(cf, st), cp)), iv_neg(iv_mul(sf, sp))));
+        ival ae = iv_scale(a, iv_add(iv_neg(iv_mul(iv_mul(cf, st), sp)), iv_mul(sf, cp)));
+        ival ah = iv_add((ival){s->qg, s->qg}, iv_neg(iv_scale(a, iv_mul(cf, ct))));
+        dy[0] = y[3];
+        dy[1] = y[4];
+        dy[2] = y[5];
+        dy[3] = lower ? an.lo : an.hi;
+        dy[4] = lower ? ae.lo : ae.hi;
+        dy[5] = lower ? ah.lo : ah.hi;
+        dy[6] = y[9];
+        dy[7] = y[10];
+        dy[8] = y[11];
+        dy[9] = tau[0] / s->Jx;
+        dy[10] = tau[1] / s->Jy;
+        dy[11] = tau[2] / s->Jz;
+    }
+}
+
 static void d_sys(const orc_sys *s, const double *x, const double *p,
                   const double *xh, const double *ph, double *dx)
 {
     switch (s->kind) {
+    case ORC_QUAD: d_quad(s, x, p, xh, ph, dx); break;
     /* heat is linear with nonnegative off-diagonal coefficients (cooperative):
        d(x, p, xh, ph) = f(x) */
     case ORC_HEAT: f_heat(s, x, dx); break;
@@ -400,10 +532,54 @@ static void g_linear(const orc_sys *s, const double *r, const double *hp, double
     }
 }
 
+/* Quadrotor (reading R13): the only state-dependent Jacobian entries are
+   those of the translational accelerations with respect to the angles; each
+   is bounded in magnitude over the box [c - r, c + r] by the natural
+   interval extension of the partial derivative.  Rows of positions and angles
+   have the entry 1 on their velocity; the angular accelerations depend on
+   the inputs only, [p] entering as half-width / J. */
+static void g_quad(const orc_sys *s, const double *c, const double *r,
+                   const double *hp, double *dr)
+{
+    double a = s->qF / s->qm;
+    for (int64_t k = 0; k < s->n / 12; ++k) {
+        const double *cc = c + 12 * k, *rr = r + 12 * k, *hw = hp + 3 * k;
+        double *d = dr + 12 * k;
+        ival F = {cc[6] - rr[6], cc[6] + rr[6]}, T = {cc[7] - rr[7], cc[7] + rr[7]};
+        ival P = {cc[8] - rr[8], cc[8] + rr[8]};
+        ival sf = iv_sin(F), cf = iv_cos(F), st = iv_sin(T), ct = iv_cos(T);
+        ival sp = iv_sin(P), cp = iv_cos(P);
+        /* d/dphi, d/dtheta, d/dpsi of a(-cf st cp - sf sp) */
+        double n_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), cp), iv_neg(iv_mul(cf, sp))));
+        double n_t = a * iv_mag(iv_mul(iv_mul(cf, ct), cp));
+        double n_p = a * iv_mag(iv_add(iv_mul(iv_mul(cf, st), sp), iv_neg(iv_mul(sf, cp))));
+        /* of a(-cf st sp + sf cp) */
+        double e_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), sp), iv_mul(cf, cp)));
+        double e_t = a * iv_mag(iv_mul(iv_mul(cf, ct), sp));
+        double e_p = a * iv_mag(iv_add(iv_neg(iv_mul(iv_mul(cf, st), cp)), iv_neg(iv_mul(sf, sp))));
+        /* of g - a cf ct */
+        double h_f = a * iv_mag(iv_mul(sf, ct));
+        double h_t = a * iv_mag(iv_mul(cf, st));
+        d[0] = rr[3];
+        d[1] = rr[4];
+        d[2] = rr[5];
+        d[3] = n_f * rr[6] + n_t * rr[7] + n_p * rr[8];
+        d[4] = e_f * rr[6] + e_t * rr[7] + e_p * rr[8];
+        d[5] = h_f * rr[6] + h_t * rr[7];
+        d[6] = rr[9];
+        d[7] = rr[10];
+        d[8] = rr[11];
+        d[9] = hw[0] / s->Jx;
+        d[10] = hw[1] / s->Jy;
+        d[11] = hw[2] / s->Jz;
+    }
+}
+
 static void g_sys(const orc_sys *s, const double *c, const double *r,
                   const double *hp, double *dr)
 {
     switch (s->kind) {
+    case ORC_QUAD: g_quad(s, c, r, hp, dr); break;
     /* heat: J = A is Metzler and constant, so C = A and g(r) = A r */
     case ORC_HEAT: (void)c; (void)hp; f_heat(s, r, dr); break;
     case ORC_TRAFFIC: g_traffic(s, c, r, hp, dr); break;

@@ -55,7 +55,19 @@ MUTATIONS = [
     ("uniform uses 52 bits", "(bits >> 11) * 0x1.0p-53", "(bits >> 12) * 0x1.0p-52"),
     ("heat open face ignored", "else if (s->open) acc += 0.0 - u[i];", "else if (s->open) acc += 0.0;"),
     ("heat y neighbour index", "if (y < l - 1) acc += u[i + l] - u[i];", "if (y < l - 1) acc += u[i + 1] - u[i];"),
-    ("heat coefficient", "s->kh = alpha / (dx * dx);", "s->kh = alpha / dx;"),
+    ("heat coefficient", "s->kh = alpha / (dx * dx);", "s->kh = alpha / dx;"),    ('quad north acceleration sign', 'dy[3] = a * (-(cf * st * cp) - sf * sp);', 'dy[3] = a * (-(cf * st * cp) + sf * sp);'),
+    ('quad east acceleration uses cos psi', 'dy[4] = a * (-(cf * st * sp) + sf * cp);', 'dy[4] = a * (-(cf * st * cp) + sf * cp);'),
+    ('quad vertical acceleration drops cos theta', 'dy[5] = s->qg - a * (cf * ct);', 'dy[5] = s->qg - a * cf;'),
+    ('quad inertia swapped', '        dy[10] = tau[1] / s->Jy;\n        dy[11] = tau[2] / s->Jz;\n    }\n}\n\nstatic void f_sys', '        dy[10] = tau[1] / s->Jx;\n        dy[11] = tau[2] / s->Jz;\n    }\n}\n\nstatic void f_sys'),
+    ('quad agent input stride', 'const double *y = x + 12 * k, *tau = p + 3 * k;', 'const double *y = x + 12 * k, *tau = p + 2 * k;'),
+    ('quad interval sin misses its maximum', 'r.hi = holds_point(a.lo, a.hi, ORC_HALF_PI) ? 1.0 : max2(s0, s1);', 'r.hi = max2(s0, s1);'),
+    ('quad interval cos minimum point', 'r.lo = holds_point(a.lo, a.hi, ORC_PI) ? -1.0 : min2(c0, c1);', 'r.lo = holds_point(a.lo, a.hi, ORC_HALF_PI) ? -1.0 : min2(c0, c1);'),
+    ('quad interval product drops a corner', 'ival r = {min2(min2(p1, p2), min2(p3, p4)), max2(max2(p1, p2), max2(p3, p4))};', 'ival r = {min2(p1, p4), max2(p1, p4)};'),
+    ('quad decomposition orientation', 'dy[3] = lower ? an.lo : an.hi;', 'dy[3] = lower ? an.hi : an.lo;'),
+    ('quad growth drops the psi column', 'd[3] = n_f * rr[6] + n_t * rr[7] + n_p * rr[8];', 'd[3] = n_f * rr[6] + n_t * rr[7];'),
+    ('quad growth derivative sign', 'double n_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), cp), iv_neg(iv_mul(cf, sp))));', 'double n_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), cp), iv_mul(cf, sp)));'),
+    ('quad growth input not scaled by inertia', 'd[9] = hw[0] / s->Jx;', 'd[9] = hw[0];'),
+    ('quad growth box from the center only', 'ival F = {cc[6] - rr[6], cc[6] + rr[6]}', 'ival F = {cc[6], cc[6]}'),
 ]
 
 

@@ -602,3 +602,236 @@ def test_heat_is_conserved_in_a_closed_box_and_leaks_through_the_open_face():
     # open face: the total changes at -kh times the heat of the bottom layer
     du = O.rhs("heat", u0, params=(alpha, l, 1.0))
     assert du.sum() == pytest.approx(-kh * u0[: l * l].sum(), rel=1e-12)
+
+
+# ------------------------------------------------------------------ quadrotor swarm (Sec. 5.2, reading R13)
+QM, QG = 1.4, 9.81
+QPRM = (QM, QG, QM * QG, 0.054, 0.061, 0.104)   # Jx != Jy so that a swapped inertia shows
+
+
+def _agent(pos=(0, 0, 0), vel=(0, 0, 0), ang=(0, 0, 0), rate=(0, 0, 0)):
+    return np.array([*pos, *vel, *ang, *rate], dtype=float)
+
+
+def test_quad_hover_is_an_equilibrium():
+    x = _agent(pos=(1.0, -2.0, 3.0))
+    d = O.rhs("quad", x, np.zeros(3), params=QPRM)
+    np.testing.assert_allclose(d, 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("ang,unit", [
+    # (phi, theta, psi) -> (ddp_n / a, ddp_e / a, (ddh - g) / a) with a = F/m,
+    # worked out by hand from the paper's equations
+    ((math.pi / 2, 0.0, 0.0), (0.0, 1.0, 0.0)),
+    ((0.0, math.pi / 2, 0.0), (-1.0, 0.0, 0.0)),
+    ((0.0, math.pi / 2, math.pi / 2), (0.0, -1.0, 0.0)),
+    ((math.pi / 2, 0.0, math.pi / 2), (-1.0, 0.0, 0.0)),
+    ((math.pi, 0.0, 0.0), (0.0, 0.0, 1.0)),
+    ((0.0, 0.0, 1.0), (0.0, 0.0, -1.0)),
+])
+def test_quad_accelerations_at_right_angles(ang, unit):
+    a = QPRM[2] / QM
+    d = O.rhs("quad", _agent(ang=ang), np.zeros(3), params=QPRM)
+    np.testing.assert_allclose(d[3:6], (a * unit[0], a * unit[1], QG + a * unit[2]), atol=1e-12)
+
+
+def test_quad_thrust_direction_has_unit_length():
+    # (ddp_n, ddp_e, g - ddh) / a is the third column of a rotation matrix
+    g = np.random.default_rng(11)
+    a = QPRM[2] / QM
+    for _ in range(200):
+        x = _agent(ang=g.uniform(-4, 4, 3))
+        d = O.rhs("quad", x, np.zeros(3), params=QPRM)
+        v = np.array([d[3], d[4], QG - d[5]]) / a
+        assert abs(np.linalg.norm(v) - 1.0) < 1e-13
+
+
+def test_quad_passive_rows_and_inputs():
+    g = np.random.default_rng(12)
+    x = g.uniform(-1, 1, 24)
+    tau = g.uniform(-1, 1, 6)
+    d = O.rhs("quad", x, tau, params=QPRM)
+    for k in range(2):
+        y, dy, t = x[12 * k:12 * k + 12], d[12 * k:12 * k + 12], tau[3 * k:3 * k + 3]
+        np.testing.assert_array_equal(dy[0:3], y[3:6])
+        np.testing.assert_array_equal(dy[6:9], y[9:12])
+        np.testing.assert_allclose(dy[9:12], t / np.array(QPRM[3:6]), rtol=1e-15)
+
+
+def test_quad_flow_at_constant_attitude_is_a_parabola():
+    # no torque and no angular rate: the acceleration is constant, so RK4 is exact
+    ang = (0.3, -0.2, 1.1)
+    x0 = _agent(pos=(1.0, 2.0, -3.0), vel=(0.5, -0.25, 0.1), ang=ang)
+    acc = O.rhs("quad", x0, np.zeros(3), params=QPRM)[3:6]
+    T = 1.5
+    x = O.flow("quad", x0, np.zeros(3), t_final=T, dt=0.05, params=QPRM)
+    np.testing.assert_allclose(x[0:3], x0[0:3] + x0[3:6] * T + 0.5 * acc * T * T, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(x[3:6], x0[3:6] + acc * T, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(x[6:9], ang, rtol=0, atol=0)
+
+
+def test_quad_flow_of_the_angles_under_constant_torque():
+    tau = np.array([0.01, -0.02, 0.03])
+    x0 = _agent(ang=(0.0, 0.0, 0.2), rate=(0.0, 0.0, 0.0))
+    T = 1.0
+    x = O.flow("quad", x0, tau, t_final=T, dt=0.01, params=QPRM)
+    J = np.array(QPRM[3:6])
+    np.testing.assert_allclose(x[9:12], tau / J * T, rtol=1e-13)
+    np.testing.assert_allclose(x[6:9], x0[6:9] + 0.5 * tau / J * T * T, rtol=1e-12)
+
+
+def test_quad_agents_are_independent():
+    g = np.random.default_rng(13)
+    K = 4
+    c = g.uniform(-0.5, 0.5, 12 * K)
+    lo, hi = c - 0.01, c + 0.01
+    wl = g.uniform(-0.02, 0.0, 3 * K)
+    wh = wl + 0.02
+    for method in ("mm", "cgb"):
+        a = O.reach(method, "quad", lo, hi, wl, wh, t_final=0.5, dt=0.01, params=QPRM)
+        for k in range(K):
+            s, t = slice(12 * k, 12 * k + 12), slice(3 * k, 3 * k + 3)
+            b = O.reach(method, "quad", lo[s], hi[s], wl[t], wh[t], t_final=0.5, dt=0.01, params=QPRM)
+            np.testing.assert_array_equal(a[0][s], b[0])
+            np.testing.assert_array_equal(a[1][s], b[1])
+
+
+def test_quad_decomposition_at_a_point_is_f():
+    g = np.random.default_rng(14)
+    for _ in range(50):
+        x = g.uniform(-4, 4, 12)
+        p = g.uniform(-1, 1, 3)
+        np.testing.assert_array_equal(O.decomp("quad", x, p, x, p, params=QPRM),
+                                      O.rhs("quad", x, p, params=QPRM))
+
+
+def _single_angle_range(j, lo, hi, fixed):
+    """Exact range of the acceleration rows over an interval of angle j (the
+    other angles fixed): sampling with the endpoints and every multiple of
+    pi/2 inside (where sine and cosine have their extrema)."""
+    crit = [k * math.pi / 2 for k in range(math.ceil(lo / (math.pi / 2)), math.floor(hi / (math.pi / 2)) + 1)]
+    t = np.concatenate([np.linspace(lo, hi, 401), [lo, hi], crit])
+    vals = []
+    for v in t:
+        ang = list(fixed)
+        ang[j] = v
+        vals.append(O.rhs("quad", _agent(ang=ang), np.zeros(3), params=QPRM)[3:6])
+    vals = np.array(vals)
+    return vals.min(axis=0), vals.max(axis=0)
+
+
+@pytest.mark.parametrize("j,fixed", [(0, (0.0, 0.0, 0.0)), (1, (0.0, 0.0, 0.0)), (2, (0.0, 0.7, 0.0)),
+                                     (0, (0.0, 0.0, 0.9))])
+def test_quad_decomposition_is_tight_when_one_angle_varies(j, fixed):
+    # with one angle varying, each acceleration has that angle in one factor (or
+    # none), so the interval extension is the exact range: this pins the
+    # extremum logic of the interval sine and cosine, including wide intervals
+    g = np.random.default_rng(15 + j)
+    intervals = [(-0.3, 0.2), (1.2, 1.9), (-1.9, -1.2), (2.9, 3.4), (-7.0, 0.5), (0.1, 6.5), (-3.5, -2.9)]
+    intervals += [tuple(sorted(g.uniform(-7, 7, 2))) for _ in range(6)]
+    for lo_a, hi_a in intervals:
+        x = _agent(ang=fixed)
+        xh = x.copy()
+        x[6 + j], xh[6 + j] = lo_a, hi_a
+        dlo = O.decomp("quad", x, np.zeros(3), xh, np.zeros(3), params=QPRM)
+        dhi = O.decomp("quad", xh, np.zeros(3), x, np.zeros(3), params=QPRM)
+        rmin, rmax = _single_angle_range(j, lo_a, hi_a, fixed)
+        np.testing.assert_allclose(dlo[3:6], rmin, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(dhi[3:6], rmax, rtol=1e-12, atol=1e-12)
+
+
+def test_quad_decomposition_bounds_f_on_the_box_and_is_monotone():
+    g = np.random.default_rng(16)
+    for _ in range(20):
+        c = g.uniform(-3, 3, 12)
+        h = g.uniform(0, 0.6, 12)
+        lo, hi = c - h, c + h
+        p = np.zeros(3)
+        dlo = O.decomp("quad", lo, p, hi, p, params=QPRM)
+        dhi = O.decomp("quad", hi, p, lo, p, params=QPRM)
+        for _ in range(100):
+            f = O.rhs("quad", g.uniform(lo, hi), p, params=QPRM)
+            assert np.all(dlo[3:6] <= f[3:6] + 1e-12) and np.all(f[3:6] <= dhi[3:6] + 1e-12)
+        # shrinking the box (raising x, lowering xh) can only raise d(x, xh)
+        lo2 = lo + g.uniform(0, 1, 12) * h
+        hi2 = hi - g.uniform(0, 1, 12) * h
+        d2 = O.decomp("quad", lo2, p, hi2, p, params=QPRM)
+        assert np.all(d2[3:6] >= dlo[3:6] - 1e-12)
+
+
+def _fd_jacobian(x, eps=1e-6):
+    J = np.empty((12, 12))
+    for j in range(12):
+        e = np.zeros(12)
+        e[j] = eps
+        J[:, j] = (O.rhs("quad", x + e, np.zeros(3), params=QPRM) -
+                   O.rhs("quad", x - e, np.zeros(3), params=QPRM)) / (2 * eps)
+    return J
+
+
+def test_quad_growth_bounds_the_jacobian():
+    # a box with one angle of nonzero radius isolates one column of C in the
+    # acceleration rows: C_ij r_j >= |J_ij(y)| r_j at every y in the box
+    g = np.random.default_rng(17)
+    for _ in range(12):
+        c = _agent(ang=g.uniform(-3, 3, 3))
+        for j in range(3):
+            r = np.zeros(12)
+            r[6 + j] = g.uniform(0.01, 0.5)
+            dr = O.growth("quad", c, r, np.zeros(3), params=QPRM)
+            Cj = dr[3:6] / r[6 + j]
+            best = np.zeros(3)
+            for t in np.linspace(-1, 1, 41):
+                y = c.copy()
+                y[6 + j] += t * r[6 + j]
+                Jy = np.abs(_fd_jacobian(y)[3:6, 6 + j])
+                assert np.all(Jy <= Cj + 1e-6)
+                best = np.maximum(best, Jy)
+            # the natural extension overestimates where the angle occurs twice
+            # (dependency), by at most the enclosure widths: O(a r_j)
+            assert np.all(Cj <= best + 2.0 * QPRM[2] / QM * r[6 + j] + 1e-6)
+
+
+def test_quad_growth_structure():
+    g = np.random.default_rng(18)
+    c = g.uniform(-1, 1, 12)
+    r = g.uniform(0, 0.1, 12)
+    hp = g.uniform(0, 0.01, 3)
+    dr = O.growth("quad", c, r, hp, params=QPRM)
+    np.testing.assert_array_equal(dr[0:3], r[3:6])
+    np.testing.assert_array_equal(dr[6:9], r[9:12])
+    np.testing.assert_allclose(dr[9:12], hp / np.array(QPRM[3:6]), rtol=1e-15)
+    np.testing.assert_array_equal(O.growth("quad", c, np.zeros(12), np.zeros(3), params=QPRM), 0.0)
+    # at a point the angular entries equal |J| exactly (the interval extension of
+    # a point is the point)
+    J = _fd_jacobian(c)
+    r1 = np.zeros(12)
+    r1[6:9] = 1e-9
+    dr1 = O.growth("quad", c, r1, np.zeros(3), params=QPRM)
+    np.testing.assert_allclose(dr1[3:6] / 1e-9, np.abs(J[3:6, 6:9]).sum(axis=1), rtol=1e-5)
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_quad_boxes_contain_sampled_trajectories(method):
+    g = np.random.default_rng(19)
+    K = 3
+    c = np.concatenate([_agent(pos=g.uniform(-5, 5, 3), vel=g.uniform(-1, 1, 3),
+                               ang=(*g.uniform(-0.3, 0.3, 2), g.uniform(-3, 3)), rate=g.uniform(-0.1, 0.1, 3))
+                        for _ in range(K)])
+    h = np.tile(np.array([0.05] * 3 + [0.01] * 3 + [0.02] * 3 + [0.01] * 3), K)
+    wl = np.tile([-0.005, -0.005, -0.002], K)
+    wh = -wl
+    lo, hi = O.reach(method, "quad", c - h, c + h, wl, wh, t_final=1.0, dt=0.01, params=QPRM)
+    _, _, finals = O.reach("mc", "quad", c - h, c + h, wl, wh, t_final=1.0, dt=0.01, params=QPRM,
+                           m=64, seed=5, return_finals=True)
+    assert np.all(finals >= lo - 1e-9) and np.all(finals <= hi + 1e-9)
+
+
+def test_quad_point_box_is_the_trajectory():
+    x0 = _agent(pos=(1, 2, 3), vel=(0.1, 0.2, 0.3), ang=(0.2, -0.1, 2.0), rate=(0.05, -0.02, 0.1))
+    tau = np.array([0.003, -0.001, 0.002])
+    traj = O.flow("quad", x0, tau, t_final=1.0, dt=0.01, params=QPRM)
+    for method in ("mm", "cgb"):
+        lo, hi = O.reach(method, "quad", x0, x0, tau, tau, t_final=1.0, dt=0.01, params=QPRM)
+        np.testing.assert_allclose(lo, traj, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(hi, traj, rtol=1e-13, atol=1e-13)

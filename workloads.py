@@ -17,6 +17,8 @@ Workloads (all synthetic; the paper prints no datasets or reachable boxes):
   velocities 0, half-width 1e-4, disturbance w in [-0.01, 0.01], dt = 0.005,
   T = 5.
 * linear test systems (Metzler, general, nilpotent).
+* quadrotor swarm (Sec. 5.2): K agents of 12 states, hover thrust, torque
+  inputs, dt = 0.01, T = 2 (see quad_swarm).
 * 3-D heat diffusion (Sec. 5.4): unit cube on an l^3 grid, cells meeting
   (0.4, 0.6)^3 in [0.9, 1.1], all others in [0, 0.01]; alpha = 8e-6, face
   z = 0 open, dt = 0.02, T = 20.
@@ -168,6 +170,32 @@ def heat_cube_torch(l: int, device, hot=(0.9, 1.1), cold=(0.0, 0.01)):
     lo[s0:s1, s0:s1, s0:s1] = hot[0]
     hi[s0:s1, s0:s1, s0:s1] = hot[1]
     return lo.reshape(-1), hi.reshape(-1)
+
+
+# ---------------------------------------------------------------- quadrotor swarm
+QUAD_DT = 0.01
+QUAD_T = 2.0
+QUAD_PRM = (1.4, 9.81, 1.4 * 9.81, 0.054, 0.054, 0.104)   # m, g, F (hover), Jx, Jy, Jz
+QUAD_HALF = (0.05,) * 3 + (0.01,) * 3 + (0.01,) * 3 + (0.005,) * 3
+QUAD_TAU = (0.005, 0.005, 0.002)
+
+
+def quad_swarm(K: int, seed: int = 0, t_final: float = QUAD_T, dt: float = QUAD_DT):
+    """K independent quadrotors, 12 states each (p_n, p_e, h, velocities,
+    phi, theta, psi, angular rates): box centres positions U[-10, 10], velocities
+    U[-1, 1], roll / pitch U[-0.2, 0.2], yaw U[-pi, pi], rates U[-0.05, 0.05];
+    half-widths QUAD_HALF; torques in [-QUAD_TAU, QUAD_TAU]."""
+    g = _rng(seed)
+    c = np.empty((K, 12))
+    c[:, 0:3] = g.uniform(-10.0, 10.0, (K, 3))
+    c[:, 3:6] = g.uniform(-1.0, 1.0, (K, 3))
+    c[:, 6:8] = g.uniform(-0.2, 0.2, (K, 2))
+    c[:, 8] = g.uniform(-math.pi, math.pi, K)
+    c[:, 9:12] = g.uniform(-0.05, 0.05, (K, 3))
+    h = np.asarray(QUAD_HALF)
+    tau = np.tile(np.asarray(QUAD_TAU), K)
+    return {"x_lo": (c - h).reshape(-1), "x_hi": (c + h).reshape(-1), "w_lo": -tau, "w_hi": tau.copy(),
+            "t_final": t_final, "dt": dt, "params": QUAD_PRM}
 
 
 # ---------------------------------------------------------------- serving trace
