@@ -275,6 +275,40 @@ def bench_heat(R, torch, dev, l=1000, steps=10):
     return out
 
 
+def bench_quad(R, torch, dev, K=10_000_000):
+    """Quadrotor swarm (Sec. 5.2) at the largest size the paper reports on a
+    GPU: n = 1.2e8 states (10^7 agents), hover thrust, torque inputs, dt = 0.01,
+    T = 2 (200 RK4 steps); MM, CGB and MC with 32 FP32 samples."""
+    n = 12 * K
+    wl = W.quad_swarm(K, seed=0)
+    d = {k: torch.from_numpy(wl[k]).to(dev) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    stream = torch.cuda.current_stream(dev)
+    N = int(round(wl["t_final"] / wl["dt"]))
+    out = {"workload": f"quadrotor swarm K={K} (n={n}), hover thrust, torques +-(5e-3, 5e-3, 2e-3), "
+                       f"dt=0.01, T=2 ({N} RK4 steps), one launch per call",
+           "unit": "comp-steps/s"}
+    args = (d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"])
+    with R.System("quad", n) as s:
+        for name, fn, kw, comps in (("mm", R.reach_mm, {}, 2 * n), ("cgb", R.reach_cgb, {}, 2 * n),
+                                    ("mc32_m32", R.reach_mc, dict(m=32, seed=0, precision=32), 32 * n)):
+            fn(s, *args, t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, stream=stream, **kw)   # warm
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(s, *args, t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, stream=stream, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            out[name] = {"s": sec, "value": comps * N / sec}
+    out["paper_gpu_seconds_for_this_n"] = 46.0
+    out["paper_note"] = "p3.2xlarge (V100), CGB, n = 1.2e8; the paper does not state its horizon"
+    del d, lo, hi
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_temporal_blocking(R, torch, dev):
     """RK4 steps per launch S (halo 4 R S recomputed) on traffic MM (FP64,
     n = 2^24) and on KS MC32 (n = 2^20, 256 samples): the FP64 kernels are bound
@@ -591,6 +625,7 @@ def main():
         line["temporal_blocking"] = bench_temporal_blocking(R, torch, dev)
         line["serving"] = bench_serving(R)
         line["heat3d"] = bench_heat(R, torch, dev)
+        line["quad"] = bench_quad(R, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",

@@ -84,7 +84,20 @@ typedef enum {
        neighbours of five faces contribute nothing (insulated), and with
        open_face set the face z = 0 sees an environment at temperature zero.
        nw = 0.  Params: reach_heat_params. */
-    REACH_HEAT3D = 4
+    REACH_HEAT3D = 4,
+    /* Quadrotor swarm (Sec. 5.2): K = n / 12 independent agents; agent k holds
+       x[12k + 0..11] = (p_n, p_e, h, dp_n, dp_e, dh, phi, theta, psi, dphi,
+       dtheta, dpsi) and inputs p[3k + 0..2] = (tau_phi, tau_theta, tau_psi):
+         ddp_n = F/m (-cos phi sin theta cos psi - sin phi sin psi)
+         ddp_e = F/m (-cos phi sin theta sin psi + sin phi cos psi)
+         ddh   = g - F/m cos phi cos theta
+         ddphi = tau_phi / Jx, ddtheta = tau_theta / Jy, ddpsi = tau_psi / Jz,
+       with the thrust F a parameter (so the system is input-affine).  MM uses
+       the natural interval extension of the accelerations over the angle box;
+       CGB bounds |J| over the current box the same way.  nw = 3 K.
+       Params: reach_quad_params.  Not accepted by reach_batch_create (one
+       call already runs every agent in one launch). */
+    REACH_QUAD = 5
 } reach_kind;
 
 typedef struct { double cap, v, w, xbar; } reach_traffic_params;   /* 40, 0.5, 1/6, 320 */
@@ -92,6 +105,7 @@ typedef struct { double dx, g_nl, g_2, g_4; } reach_ks_params;     /* pi/4, 1, 1
 typedef struct { double ka, kb, kc; } reach_osc_params;            /* 1, 0.1, 0.5 */
 typedef struct { const double *A; } reach_linear_params;           /* n x n, row-major */
 typedef struct { double alpha; int64_t l; int open_face; } reach_heat_params; /* 8e-6, cbrt(n), 1 */
+typedef struct { double m, g, F, Jx, Jy, Jz; } reach_quad_params; /* 1.4, 9.81, m g, 0.054, 0.054, 0.104 */
 
 typedef struct reach_system reach_system;   /* opaque; parameters live on the device */
 
@@ -100,8 +114,9 @@ typedef struct reach_system reach_system;   /* opaque; parameters live on the de
    above (REACH_LINEAR requires params).  The parameters, including A, are
    copied to the current device; the caller's buffers may be freed
    afterwards.  REACH_EINVAL for n < 1, odd n with REACH_OSC, n < 5 with
-   REACH_KS, n > 256 with REACH_LINEAR, n != l^3 with REACH_HEAT3D, a wrong params_bytes or non-finite
-   params (traffic additionally needs v, w >= 0; KS dx > 0; osc kb >= 0). */
+   REACH_KS, n > 256 with REACH_LINEAR, n != l^3 with REACH_HEAT3D, n not a multiple of 12 with
+   REACH_QUAD, a wrong params_bytes or non-finite params (traffic additionally needs v, w >= 0; KS
+   dx > 0; osc kb >= 0; quad m, Jx, Jy, Jz > 0 and F >= 0). */
 REACH_API int reach_system_create(int kind, int64_t n, const void *params, size_t params_bytes,
                         reach_system **out);
 REACH_API int reach_system_destroy(reach_system *sys);

@@ -21,8 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libreach.so")
 
-TRAFFIC, KS, OSC, LINEAR, HEAT3D = 0, 1, 2, 3, 4
-KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D}
+TRAFFIC, KS, OSC, LINEAR, HEAT3D, QUAD = 0, 1, 2, 3, 4, 5
+KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D, "quad": QUAD}
 OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT = 1, 2, 3, 4
 BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
@@ -157,7 +157,7 @@ def _stream(stream):
 class System:
     """reach_system_create / reach_system_destroy."""
 
-    _PARAM_FIELDS = {TRAFFIC: 4, KS: 4, OSC: 3}
+    _PARAM_FIELDS = {TRAFFIC: 4, KS: 4, OSC: 3, QUAD: 6}
 
     def __init__(self, kind, n: int, params=None, A=None):
         self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)

@@ -261,6 +261,20 @@ extern "C" int reach_system_create(int kind, int64_t n, const void *params, size
         host[2] = p.open_face ? 1.0 : 0.0;
         break;
     }
+    case REACH_QUAD: {
+        reach_quad_params p{1.4, 9.81, 1.4 * 9.81, 0.054, 0.054, 0.104};
+        if (params) {
+            if (params_bytes != sizeof p) return REACH_EINVAL;
+            memcpy(&p, params, sizeof p);
+        }
+        if (n % 12 || !(p.m > 0) || !(p.F >= 0) || !(p.Jx > 0) || !(p.Jy > 0) || !(p.Jz > 0) ||
+            !std::isfinite(p.m) || !std::isfinite(p.g) || !std::isfinite(p.F) || !std::isfinite(p.Jx) ||
+            !std::isfinite(p.Jy) || !std::isfinite(p.Jz))
+            return REACH_EINVAL;
+        s.nw = n / 12 * 3;
+        host[0] = p.F / p.m; host[1] = p.g; host[2] = p.Jx; host[3] = p.Jy; host[4] = p.Jz;
+        break;
+    }
     default:
         return REACH_EINVAL;
     }
@@ -309,6 +323,7 @@ static bool onchip_fits(const reach_system *s) {
 }
 
 bool use_onchip(const reach_system *s) {
+    if (s->kind == REACH_QUAD) return false;   // one thread per agent at every size
     int64_t k = opt_kernel();
     bool fits = onchip_fits(s);
     if (k == 2) return fits;
@@ -390,7 +405,11 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         return sg.finish();
     }
 
-    if (sys->kind == REACH_HEAT3D) {
+    if (sys->kind == REACH_QUAD) {
+        QuadK p;
+        p.a = sys->prm[0]; p.g = sys->prm[1]; p.Jx = sys->prm[2]; p.Jy = sys->prm[3]; p.Jz = sys->prm[4];
+        rc = quad_run(method, p, n, dxlo, dxhi, dwlo, dwhi, dlo, dhi, dt, N, sg.status, sg.st);
+    } else if (sys->kind == REACH_HEAT3D) {
         HeatK p;
         p.kh = sys->prm[0];
         p.l = (int64_t)sys->prm[1];

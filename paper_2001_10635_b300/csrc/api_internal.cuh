@@ -3,6 +3,7 @@
 
 #include "common.cuh"
 #include "onchip.cuh"
+#include "quad.cuh"
 
 struct reach_system {
     int kind;
@@ -79,6 +80,8 @@ struct BatchTask {
 int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st);
+int quad_run(int method, const QuadK &p, int64_t n, const double *xlo, const double *xhi, const double *wlo,
+             const double *whi, double *lo, double *hi, double h, int64_t N, int *status, cudaStream_t st);
 int heat_run(int method, const HeatK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
              double *hi, double h, int64_t N, Staging &sg);
 int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "api_internal.cuh"
+#include "quad.cuh"
 
 namespace reach {
 
@@ -405,6 +406,66 @@ __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, in
     }
 }
 
+// ------------------------------------------------------------------ quadrotor swarm
+// Lane = sample of one agent: a warp integrates 32 samples of agent k (blockIdx.x
+// * 4 + warp) over the whole horizon in registers (the agents are independent)
+// and reduces each of its 12 components over the samples; blockIdx.y is the
+// 32-sample chunk, so the partials have the [chunk][n] layout of mc_reduce.
+template <class T>
+__global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (k >= a.n / 12) return;   // whole warps leave together
+    const int64_t j = (int64_t)blockIdx.y * 32 + lane;
+    const bool valid = j < a.m;
+    const double J[3] = {p.Jx, p.Jy, p.Jz};
+    QChain<T> c;
+    int flags = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int64_t i = 12 * k + 3 * r + d;
+            const double lo = a.xlo[i], hi = a.xhi[i];
+            if (!(kle(lo, hi) && kfinite(lo) && kfinite(hi))) flags |= ST_BADINPUT;
+            const T v = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)i, 0u)));
+            if (r == 0) c.p[d] = v;
+            else if (r == 1) c.v[d] = v;
+            else if (r == 2) c.q[d] = v;
+            else c.w[d] = v;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t i = 3 * k + d;
+        const double lo = a.wlo[i], hi = a.whi[i];
+        if (!(kle(lo, hi) && kfinite(lo) && kfinite(hi))) flags |= ST_BADINPUT;
+        const T tau = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)i, 1u)));
+        c.al[d] = tau / (T)J[d];
+    }
+    const T h = (T)a.h, fa = (T)p.a, fg = (T)p.g;
+    for (int64_t s = 0; s < a.N; ++s) {
+        QSums<T> m;
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            T q[3], acc[3];
+            stage_angles(c, st, h, q);
+            quad_acc_point<T>(q, fa, fg, acc);
+            add_stage(m, acc, st);
+        }
+        chain_update(c, m, h);
+    }
+    double *plo = a.plo + (int64_t)blockIdx.y * a.n + 12 * k, *phi = a.phi + (int64_t)blockIdx.y * a.n + 12 * k;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        warp_minmax<T>(c.p[d], valid, plo + d, phi + d, a.status);
+        warp_minmax<T>(c.v[d], valid, plo + 3 + d, phi + 3 + d, a.status);
+        warp_minmax<T>(c.q[d], valid, plo + 6 + d, phi + 6 + d, a.status);
+        warp_minmax<T>(c.w[d], valid, plo + 9 + d, phi + 9 + d, a.status);
+    }
+    if (flags && lane == 0) atomicOr(a.status, flags);
+}
+
 // ------------------------------------------------------------------ host
 template <int SYS, class T>
 static int launch_onchip(const McArgs &a, cudaStream_t st) {
@@ -477,6 +538,23 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
                        double wl, double wh) {
     const int64_t n = sys->n;
     int rc;
+    if (sys->kind == REACH_QUAD) {
+        const int64_t nblk = (base.m + 31) / 32;
+        if (nblk > 65535) return REACH_EINVAL;   // chunks run along the grid's y dimension
+        McArgs a = base;
+        if ((rc = sg.scratch(2 * nblk * n * sizeof(double), (void **)&a.plo))) return rc;
+        a.phi = a.plo + nblk * n;
+        QuadK p;
+        p.a = sys->prm[0]; p.g = sys->prm[1]; p.Jx = sys->prm[2]; p.Jy = sys->prm[3]; p.Jz = sys->prm[4];
+        const dim3 grid((unsigned)((n / 12 + 3) / 4), (unsigned)nblk);
+        mc_quad<T><<<grid, 128, 0, sg.st>>>(a, p);
+        REACH_LAUNCHED("mc_quad");
+        int64_t g = (n + 255) / 256;
+        if (g > 148 * 16) g = 148 * 16;
+        mc_reduce<<<(unsigned)g, 256, 0, sg.st>>>(a.plo, a.phi, nblk, n, dlo, dhi);
+        REACH_LAUNCHED("mc_reduce");
+        return REACH_OK;
+    }
     bool onchip = n <= mc_onchip_limit(sys->kind, sizeof(T) == 4 ? 32 : 64);
     if (opt_kernel() == 1 && (sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS) && n >= 16) onchip = false;
     if (!onchip && !(sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS)) return REACH_EINVAL;

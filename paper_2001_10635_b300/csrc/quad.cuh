@@ -1,0 +1,193 @@
+// quad.cuh -- device code of the quadrotor swarm (Sec. 5.2): K independent
+// agents of 12 states (p_n, p_e, h, dp_n, dp_e, dh, phi, theta, psi, dphi,
+// dtheta, dpsi), torque inputs (tau_phi, tau_theta, tau_psi) per agent, thrust
+// F a parameter.  Shared by the MM / CGB kernels (quad.cu) and the Monte Carlo
+// kernel (mc.cu).
+//
+// RK4 of one agent in chain form.  Every row except the three translational
+// accelerations is linear: dp = v, dq = w (angles q, rates w), dw = alpha =
+// tau / J, constant over a call.  Classic RK4 (Sec. 3.1) of this structure
+// needs the accelerations a_1..a_4 at the four stage angle triples
+//   q_1 = q,  q_2 = q + h/2 w,  q_3 = q + h/2 (w + h/2 alpha),  q_4 = q + h (w + h/2 alpha),
+// and then gives exactly (in exact arithmetic) the classic update
+//   v+ = v + h/6 (a_1 + 2 a_2 + 2 a_3 + a_4),  p+ = p + h v + h^2/6 (a_1 + a_2 + a_3),
+//   q+ = q + h w + h^2/2 alpha,  w+ = w + h alpha,
+// so a step evaluates the trigonometric part four times and carries no stage
+// vectors.  The CGB radius follows the same chain with C r_q in place of the
+// accelerations and [p] / J in place of alpha.
+#pragma once
+
+#include "common.cuh"
+
+namespace reach {
+
+struct QuadK {
+    double a;            // F / m
+    double g;
+    double Jx, Jy, Jz;
+};
+
+constexpr double Q_PI = 3.141592653589793;
+constexpr double Q_HALF_PI = 1.5707963267948966;
+constexpr double Q_TWO_PI = 6.283185307179586;
+constexpr double Q_INV_TWO_PI = 0.15915494309189535;
+
+struct Iv {
+    double lo, hi;
+};
+
+__device__ __forceinline__ Iv iv_add(Iv a, Iv b) { return {a.lo + b.lo, a.hi + b.hi}; }
+__device__ __forceinline__ Iv iv_neg(Iv a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ Iv iv_mul(Iv a, Iv b) {
+    const double p1 = a.lo * b.lo, p2 = a.lo * b.hi, p3 = a.hi * b.lo, p4 = a.hi * b.hi;
+    return {kmin(kmin(p1, p2), kmin(p3, p4)), kmax(kmax(p1, p2), kmax(p3, p4))};
+}
+// c >= 0 (F / m)
+__device__ __forceinline__ Iv iv_scale(double c, Iv a) { return {c * a.lo, c * a.hi}; }
+__device__ __forceinline__ double iv_mag(Iv a) { return kmax(kabs(a.lo), kabs(a.hi)); }
+
+// does c + 2 pi k lie in [a, b] for an integer k; rounded products and sums
+// are kept separate (no contraction) so that the decision is the same as a
+// plain IEEE evaluation of the same expression
+__device__ __forceinline__ bool holds_point(double a, double b, double c) {
+    const double k = ceil(__dmul_rn(__dsub_rn(a, c), Q_INV_TWO_PI));
+    return __dadd_rn(c, __dmul_rn(Q_TWO_PI, k)) <= b;
+}
+
+// ranges of sin and cos over [lo, hi] (lo <= hi): the endpoint values, and
+// +-1 where an extremum lies inside
+__device__ __forceinline__ void iv_sincos(double lo, double hi, Iv &S, Iv &C) {
+    if (hi - lo >= Q_TWO_PI) {
+        S = {-1.0, 1.0};
+        C = {-1.0, 1.0};
+        return;
+    }
+    double s0, c0, s1, c1;
+    sincos(lo, &s0, &c0);
+    sincos(hi, &s1, &c1);
+    S.lo = holds_point(lo, hi, -Q_HALF_PI) ? -1.0 : kmin(s0, s1);
+    S.hi = holds_point(lo, hi, Q_HALF_PI) ? 1.0 : kmax(s0, s1);
+    C.lo = holds_point(lo, hi, Q_PI) ? -1.0 : kmin(c0, c1);
+    C.hi = holds_point(lo, hi, 0.0) ? 1.0 : kmax(c0, c1);
+}
+
+// accelerations at one attitude (the plain system), in the run precision
+template <class T>
+__device__ __forceinline__ void quad_acc_point(const T (&q)[3], T a, T g, T (&acc)[3]) {
+    T sf, cf, st, ct, sp, cp;
+    if constexpr (sizeof(T) == 4) {
+        sincosf(q[0], &sf, &cf);
+        sincosf(q[1], &st, &ct);
+        sincosf(q[2], &sp, &cp);
+    } else {
+        sincos(q[0], &sf, &cf);
+        sincos(q[1], &st, &ct);
+        sincos(q[2], &sp, &cp);
+    }
+    const T cs = cf * st;
+    acc[0] = a * (-(cs * cp) - sf * sp);
+    acc[1] = a * (-(cs * sp) + sf * cp);
+    acc[2] = g - a * (cf * ct);
+}
+
+// MM: natural interval extension of the accelerations over the hull of the
+// two attitudes; the lower chain takes the lower ends, the upper chain the
+// upper ends
+__device__ __forceinline__ void quad_acc_mm(const double (&ql)[3], const double (&qh)[3], const QuadK &p,
+                                            double (&al)[3], double (&ah)[3]) {
+    Iv sf, cf, st, ct, sp, cp;
+    iv_sincos(kmin(ql[0], qh[0]), kmax(ql[0], qh[0]), sf, cf);
+    iv_sincos(kmin(ql[1], qh[1]), kmax(ql[1], qh[1]), st, ct);
+    iv_sincos(kmin(ql[2], qh[2]), kmax(ql[2], qh[2]), sp, cp);
+    const Iv cs = iv_mul(cf, st);
+    const Iv an = iv_scale(p.a, iv_add(iv_neg(iv_mul(cs, cp)), iv_neg(iv_mul(sf, sp))));
+    const Iv ae = iv_scale(p.a, iv_add(iv_neg(iv_mul(cs, sp)), iv_mul(sf, cp)));
+    const Iv ac = iv_scale(p.a, iv_mul(cf, ct));
+    al[0] = an.lo; ah[0] = an.hi;
+    al[1] = ae.lo; ah[1] = ae.hi;
+    al[2] = p.g - ac.hi; ah[2] = p.g - ac.lo;
+}
+
+// CGB: the center's accelerations, and C r over the angle rows of the radius,
+// C bounding |d acc / d angle| over the box [c - r, c + r]
+__device__ __forceinline__ void quad_acc_cgb(const double (&qc)[3], const double (&qr)[3], const QuadK &p,
+                                             double (&ac)[3], double (&ar)[3]) {
+    double qq[3] = {qc[0], qc[1], qc[2]};
+    quad_acc_point<double>(qq, p.a, p.g, ac);
+    Iv sf, cf, st, ct, sp, cp;
+    iv_sincos(qc[0] - qr[0], qc[0] + qr[0], sf, cf);
+    iv_sincos(qc[1] - qr[1], qc[1] + qr[1], st, ct);
+    iv_sincos(qc[2] - qr[2], qc[2] + qr[2], sp, cp);
+    const Iv sfst = iv_mul(sf, st), cs = iv_mul(cf, st), cc = iv_mul(cf, ct);
+    const double n_f = p.a * iv_mag(iv_add(iv_mul(sfst, cp), iv_neg(iv_mul(cf, sp))));
+    const double n_t = p.a * iv_mag(iv_mul(cc, cp));
+    const double n_p = p.a * iv_mag(iv_add(iv_mul(cs, sp), iv_neg(iv_mul(sf, cp))));
+    const double e_f = p.a * iv_mag(iv_add(iv_mul(sfst, sp), iv_mul(cf, cp)));
+    const double e_t = p.a * iv_mag(iv_mul(cc, sp));
+    const double e_p = p.a * iv_mag(iv_add(iv_neg(iv_mul(cs, cp)), iv_neg(iv_mul(sf, sp))));
+    const double h_f = p.a * iv_mag(iv_mul(sf, ct));
+    const double h_t = p.a * iv_mag(cs);
+    ar[0] = fma(n_f, qr[0], fma(n_t, qr[1], n_p * qr[2]));
+    ar[1] = fma(e_f, qr[0], fma(e_t, qr[1], e_p * qr[2]));
+    ar[2] = fma(h_f, qr[0], h_t * qr[1]);
+}
+
+// one chain of an agent: positions, velocities, angles, rates, angular
+// acceleration (constant)
+template <class T>
+struct QChain {
+    T p[3], v[3], q[3], w[3], al[3];
+};
+
+// stage angle triple s (0..3) of a chain
+template <class T>
+__device__ __forceinline__ void stage_angles(const QChain<T> &c, int s, T h, T (&q)[3]) {
+    const T hh = T(0.5) * h;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (s == 0) q[j] = c.q[j];
+        else if (s == 1) q[j] = c.q[j] + hh * c.w[j];
+        else if (s == 2) q[j] = c.q[j] + hh * (c.w[j] + hh * c.al[j]);
+        else q[j] = c.q[j] + h * (c.w[j] + hh * c.al[j]);
+    }
+}
+
+// running sums of the stage accelerations: a_1 + 2 a_2 + 2 a_3 + a_4 for the
+// velocities and a_1 + a_2 + a_3 for the positions, so that a stage's
+// accelerations are dead once added
+template <class T>
+struct QSums {
+    T sv[3], sp[3];
+};
+
+template <class T>
+__device__ __forceinline__ void add_stage(QSums<T> &m, const T (&a)[3], int s) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (s == 0) {
+            m.sv[j] = a[j];
+            m.sp[j] = a[j];
+        } else if (s == 3) {
+            m.sv[j] = m.sv[j] + a[j];
+        } else {
+            m.sv[j] = m.sv[j] + T(2) * a[j];
+            m.sp[j] = m.sp[j] + a[j];
+        }
+    }
+}
+
+// the step update from the summed stage accelerations
+template <class T>
+__device__ __forceinline__ void chain_update(QChain<T> &c, const QSums<T> &m, T h) {
+    const T h6 = h / T(6), hh = T(0.5) * h;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T v0 = c.v[j];
+        c.v[j] = v0 + h6 * m.sv[j];
+        c.p[j] = c.p[j] + h * v0 + (h * h6) * m.sp[j];
+        c.q[j] = c.q[j] + h * c.w[j] + (h * hh) * c.al[j];
+        c.w[j] = c.w[j] + h * c.al[j];
+    }
+}
+
+}  // namespace reach

@@ -80,6 +80,7 @@ int64_t footprint(const reach_request *r) {
     if (r->method == 2) return b + mc_footprint(s, r->m, r->precision);
     // MM / CGB: the stencil kernels keep a 2n ping-pong buffer; the heat
     // stage kernels keep the state and two stage vectors (6n)
+    if (s->kind == REACH_QUAD) return b;   // registers only
     return b + (s->kind == REACH_HEAT3D ? 6 : 2) * n * 8;
 }
 

@@ -9,6 +9,7 @@ Cases:
   traffic16_mm         traffic chain n = 16, T = 10 (on-chip kernel)
   osc_batch            the 4096-query oscillator batch (MM T=5, CGB T=4)
   heat_mm, heat_cgb    heat cube of side l = --n (default 256), --t (default 0.1)
+  quad_mm, quad_cgb, quad_mc32   quadrotor swarm of --n agents (default 10^6), --t (default 0.1)
 """
 from __future__ import annotations
 
@@ -71,6 +72,20 @@ def main(argv=None):
             f = R.reach_mm if a.case == "heat_mm" else R.reach_cgb
             for _ in range(2):
                 f(s, lo, hi, t_final=a.t or 0.1, dt=W.HEAT_DT)
+    elif a.case.startswith("quad_"):
+        K = a.n or 1_000_000
+        wl = W.quad_swarm(K, seed=0, t_final=a.t or 0.1)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        args = (d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"])
+        kw = dict(t_final=wl["t_final"], dt=wl["dt"])
+        with R.System("quad", 12 * K) as s:
+            for _ in range(2):
+                if a.case == "quad_mm":
+                    R.reach_mm(s, *args, **kw)
+                elif a.case == "quad_cgb":
+                    R.reach_cgb(s, *args, **kw)
+                else:
+                    R.reach_mc(s, *args, **kw, m=a.m or 32, seed=0, precision=32)
     elif a.case == "osc_batch":
         sizes = W.osc_sizes(4096, seed=0)
         systems, qs = {}, []
