@@ -32,6 +32,8 @@ KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEA
 # default parameters (BASELINE workloads): traffic (c, v, w, xbar); KS (dx, g_nl,
 # g_2, g_4); oscillator (ka, kb, kc)
 TRAFFIC_PRM = (40.0, 0.5, 1.0 / 6.0, 320.0)
+# the same with the box-evaluated CGB contraction matrix (reading R14)
+TRAFFIC_LOCAL_PRM = TRAFFIC_PRM + (1.0,)
 KS_PRM = (math.pi / 4.0, 1.0, 1.0, 1.0)
 OSC_PRM = (1.0, 0.1, 0.5)
 # heat: (alpha, l, open face); l is set from n by default_params
@@ -123,6 +125,8 @@ def input_dim(kind: str, n: int) -> int:
 
 def _prep(kind, n, params, A, w_lo, w_hi):
     prm = _vec(default_params(kind, n) if params is None else params)
+    if kind == "traffic" and prm.size == 4:
+        prm = np.append(prm, 0.0)   # CGB with the bounds valid for every state
     if prm.size == 0:
         prm = np.zeros(1)
     Aa = None

@@ -45,6 +45,14 @@
  *      an environment at temperature zero (a missing neighbour at z = -1 counts
  *      as u_nb = 0).  The paper does not give alpha, the heated region or the
  *      initial box; they are inputs here.
+ *  R14 (Sec. 2.1, CGB; Sec. 5.1).  Optional box-evaluated contraction matrix
+ *      for the traffic chain (traffic parameter 5 nonzero): instead of the
+ *      bounds valid for every state (C_{i,i-1} = v, C_{i,i+1} = w, C_ii = 0),
+ *      C is taken over the current box [c - r, c + r] (as in R3): an
+ *      off-diagonal entry keeps v (w) only if the free-flow (congestion)
+ *      branch of the flux can be the minimum somewhere in the box, and the
+ *      diagonal gets -v (-w) where the free-flow branch of f_i (the
+ *      congestion branch of f_{i-1}) is strictly the minimum everywhere in it.
  *  R13 (Sec. 5.2).  Quadrotor swarm of K = n/12 independent agents.  Agent k
  *      holds x[12k + 0..11] = (p_n, p_e, h, dp_n, dp_e, dh, phi, theta, psi,
  *      dphi, dtheta, dpsi) and inputs p[3k + 0..2] = (tau_phi, tau_theta,
@@ -84,6 +92,7 @@ typedef struct {
     /* traffic (Sec. 5.1): capacity c, free-flow speed v, congestion wave
        speed w, jam density xbar */
     double cap, v, w, xbar;
+    int tr_local;       /* CGB with the box-evaluated C (reading R14) */
     /* KS grid: u_t = -g_nl u u_x - g_2 u_xx - g_4 u_xxxx, spacing dx */
     double dx, g_nl, g_2, g_4;
     double a0, a1, a2;  /* 5-point stencil of -g_2 u_xx - g_4 u_xxxx */
@@ -124,6 +133,7 @@ static int make_sys(orc_sys *s, int kind, const double *prm, const double *A, in
     switch (kind) {
     case ORC_TRAFFIC:
         s->cap = prm[0]; s->v = prm[1]; s->w = prm[2]; s->xbar = prm[3];
+        s->tr_local = prm[4] != 0.0;
         break;
     case ORC_KS: {
         double d2, d4;
@@ -481,6 +491,66 @@ static void g_traffic(const orc_sys *s, const double *c, const double *r,
     }
 }
 
+/* Reading R14: the traffic flux out of cell j is min(cap, v x_j, w (xbar -
+   x_{j+1})) (the last cell has no congestion term).  Over the box
+   [lo, hi] = [c - r, c + r], the free-flow branch v x_j can be the minimum
+   somewhere iff it can at x_j = lo_j, x_{j+1} = lo_{j+1}, and is strictly the
+   minimum everywhere iff it is at hi_j, hi_{j+1}; the congestion branch can
+   be the minimum iff it can at hi_j, hi_{j+1}, and is strictly everywhere
+   iff it is at lo_j, lo_{j+1}. */
+static int tr_ff_possible(const orc_sys *s, const double *lo, int64_t j)
+{
+    double f = s->v * lo[j];
+    if (!(f <= s->cap)) return 0;
+    return j == s->n - 1 || f <= s->w * (s->xbar - lo[j + 1]);
+}
+
+static int tr_ff_certain(const orc_sys *s, const double *hi, int64_t j)
+{
+    double f = s->v * hi[j];
+    if (!(f < s->cap)) return 0;
+    return j == s->n - 1 || f < s->w * (s->xbar - hi[j + 1]);
+}
+
+static int tr_cong_possible(const orc_sys *s, const double *hi, int64_t j)
+{
+    double q;
+    if (j == s->n - 1) return 0;
+    q = s->w * (s->xbar - hi[j + 1]);
+    return q <= s->cap && q <= s->v * hi[j];
+}
+
+static int tr_cong_certain(const orc_sys *s, const double *lo, int64_t j)
+{
+    double q;
+    if (j == s->n - 1) return 0;
+    q = s->w * (s->xbar - lo[j + 1]);
+    return q < s->cap && q < s->v * lo[j];
+}
+
+static void g_traffic_local(const orc_sys *s, const double *c, const double *r,
+                            const double *hp, double *dr)
+{
+    int64_t n = s->n;
+    double *lo = malloc(sizeof(double) * n), *hi = malloc(sizeof(double) * n);
+    if (!lo || !hi) { free(lo); free(hi); for (int64_t i = 0; i < n; ++i) dr[i] = NAN; return; }
+    for (int64_t i = 0; i < n; ++i) { lo[i] = c[i] - r[i]; hi[i] = c[i] + r[i]; }
+    for (int64_t i = 0; i < n; ++i) {
+        double cl = (i > 0 && tr_ff_possible(s, lo, i - 1)) ? s->v : 0.0;
+        double cr = tr_cong_possible(s, hi, i) ? s->w : 0.0;
+        double cd = 0.0;
+        double acc = 0.0;
+        if (tr_ff_certain(s, hi, i)) cd -= s->v;
+        if (i > 0 && tr_cong_certain(s, lo, i - 1)) cd -= s->w;
+        if (i > 0) acc += cl * r[i - 1];
+        acc += cd * r[i];
+        if (i < n - 1) acc += cr * r[i + 1];
+        dr[i] = acc + ((i == 0) ? hp[0] : 0.0);
+    }
+    free(lo);
+    free(hi);
+}
+
 static void g_ks(const orc_sys *s, const double *c, const double *r, double *dr)
 {
     /* J_ii = a0 - g_nl D_i,  J_{i,i+1} = a1 - g_nl u_i/(2dx),
@@ -582,7 +652,10 @@ static void g_sys(const orc_sys *s, const double *c, const double *r,
     case ORC_QUAD: g_quad(s, c, r, hp, dr); break;
     /* heat: J = A is Metzler and constant, so C = A and g(r) = A r */
     case ORC_HEAT: (void)c; (void)hp; f_heat(s, r, dr); break;
-    case ORC_TRAFFIC: g_traffic(s, c, r, hp, dr); break;
+    case ORC_TRAFFIC:
+        if (s->tr_local) g_traffic_local(s, c, r, hp, dr);
+        else g_traffic(s, c, r, hp, dr);
+        break;
     case ORC_KS: g_ks(s, c, r, dr); break;
     case ORC_OSC: g_osc(s, c, r, hp, dr); break;
     case ORC_LINEAR: g_linear(s, r, hp, dr); break;

@@ -68,6 +68,11 @@ MUTATIONS = [
     ('quad growth derivative sign', 'double n_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), cp), iv_neg(iv_mul(cf, sp))));', 'double n_f = a * iv_mag(iv_add(iv_mul(iv_mul(sf, st), cp), iv_mul(cf, sp)));'),
     ('quad growth input not scaled by inertia', 'd[9] = hw[0] / s->Jx;', 'd[9] = hw[0];'),
     ('quad growth box from the center only', 'ival F = {cc[6] - rr[6], cc[6] + rr[6]}', 'ival F = {cc[6], cc[6]}'),
+    ('traffic local: free flow certain ignores congestion', 'return j == s->n - 1 || f < s->w * (s->xbar - hi[j + 1]);', 'return 1;'),
+    ('traffic local: congestion possible ignores capacity', 'return q <= s->cap && q <= s->v * hi[j];', 'return q <= s->v * hi[j];'),
+    ('traffic local: congested-inflow diagonal dropped', 'if (i > 0 && tr_cong_certain(s, lo, i - 1)) cd -= s->w;', ''),
+    ('traffic local: free flow possible tested at the upper corner', 'double cl = (i > 0 && tr_ff_possible(s, lo, i - 1)) ? s->v : 0.0;', 'double cl = (i > 0 && tr_ff_possible(s, hi, i - 1)) ? s->v : 0.0;'),
+    ('traffic local: superdiagonal keeps w', 'double cr = tr_cong_possible(s, hi, i) ? s->w : 0.0;', 'double cr = s->w;'),
 ]
 
 

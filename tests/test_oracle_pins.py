@@ -835,3 +835,95 @@ def test_quad_point_box_is_the_trajectory():
         lo, hi = O.reach(method, "quad", x0, x0, tau, tau, t_final=1.0, dt=0.01, params=QPRM)
         np.testing.assert_allclose(lo, traj, rtol=1e-13, atol=1e-13)
         np.testing.assert_allclose(hi, traj, rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------------------ box-evaluated traffic C (reading R14)
+TLP = O.TRAFFIC_LOCAL_PRM
+
+
+def _traffic_fd_jacobian(x, eps=1e-5):
+    n = x.size
+    J = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = eps
+        J[:, j] = (O.rhs("traffic", x + e, [40.0], params=TLP) - O.rhs("traffic", x - e, [40.0], params=TLP)) / (2 * eps)
+    return J
+
+
+@pytest.mark.parametrize("regime", [(1.0, 60.0), (60.0, 250.0), (240.0, 320.0), (0.0, 320.0)])
+def test_traffic_local_growth_bounds_the_jacobian(regime):
+    # C r >= J_ii r_i + sum_{j != i} |J_ij| r_j at every point of the box
+    g = np.random.default_rng(int(regime[0]) + 5)
+    n = 10
+    for _ in range(8):
+        a = g.uniform(*regime, n)
+        b = g.uniform(*regime, n)
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        c, r = (lo + hi) / 2, (hi - lo) / 2
+        dr = O.growth("traffic", c, r, [0.0], params=TLP)
+        for _ in range(60):
+            y = g.uniform(lo, hi)
+            J = _traffic_fd_jacobian(y)
+            need = np.abs(J) @ r - np.abs(np.diag(J)) * r + np.diag(J) * r
+            # (a difference quotient across a kink lies between the one-sided slopes)
+            assert np.all(dr >= need - 1e-7 * (1.0 + r.sum()))
+
+
+def test_traffic_local_is_tighter_than_the_global_bound():
+    g = np.random.default_rng(6)
+    for _ in range(20):
+        c = g.uniform(0, 320, 12)
+        r = g.uniform(0, 30, 12)
+        loc = O.growth("traffic", c, r, [2.0], params=TLP)
+        glob = O.growth("traffic", c, r, [2.0], params=O.TRAFFIC_PRM)
+        assert np.all(loc <= glob + 1e-12)
+
+
+def test_traffic_local_free_flow_and_congested_boxes():
+    v, w = 0.5, 1.0 / 6.0
+    g = np.random.default_rng(7)
+    n = 8
+    # free flow everywhere in the box: C = v on the subdiagonal, -v on the diagonal
+    c = g.uniform(3, 8, n)
+    r = g.uniform(0.5, 2, n)
+    dr = O.growth("traffic", c, r, [1.5], params=TLP)
+    want = -v * r
+    want[1:] += v * r[:-1]
+    want[0] += 1.5
+    np.testing.assert_allclose(dr, want, rtol=1e-14, atol=1e-14)
+    # congested everywhere (the last cell flows at capacity): w on the
+    # superdiagonal, -w on the diagonal of every cell with a congested inflow
+    c = g.uniform(302, 308, n)
+    r = g.uniform(0.5, 2, n)
+    dr = O.growth("traffic", c, r, [1.5], params=TLP)
+    want = np.zeros(n)
+    want[:-1] += w * r[1:]
+    want[1:] -= w * r[1:]
+    want[0] += 1.5
+    np.testing.assert_allclose(dr, want, rtol=1e-14, atol=1e-14)
+
+
+def test_traffic_local_cgb_contains_sampled_trajectories():
+    wl = W.traffic_small(16)
+    lo, hi = O.reach("cgb", "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=2.0, dt=0.01,
+                     params=TLP)
+    glo, ghi = O.reach("cgb", "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=2.0, dt=0.01)
+    _, _, finals = O.reach("mc", "traffic", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=2.0,
+                           dt=0.01, m=200, seed=1, return_finals=True)
+    assert np.all(finals >= lo - 1e-9) and np.all(finals <= hi + 1e-9)
+    # and it is tighter than the global bound on this workload
+    assert np.all(hi - lo <= ghi - glo + 1e-9) and np.sum(hi - lo) < 0.9 * np.sum(ghi - glo)
+
+
+def test_traffic_local_capacity_box():
+    # with capacity 20, densities in [105, 145] flow at capacity everywhere
+    # (v x > 20 and w (xbar - x) > 20): every entry of C vanishes
+    prm = (20.0, 0.5, 1.0 / 6.0, 320.0, 1.0)
+    g = np.random.default_rng(8)
+    c = g.uniform(110, 140, 9)
+    r = g.uniform(0.5, 5, 9)
+    dr = O.growth("traffic", c, r, [0.75], params=prm)
+    want = np.zeros(9)
+    want[0] = 0.75
+    np.testing.assert_array_equal(dr, want)
