@@ -309,6 +309,35 @@ def bench_quad(R, torch, dev, K=10_000_000):
     return out
 
 
+def bench_traffic_local(R, torch, dev, d, n):
+    """Traffic CGB with the contraction matrix taken over the current box
+    (reading R14) on the headline workload: time and the summed width of the
+    final box against the global bound's."""
+    stream = torch.cuda.current_stream(dev)
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    out = {"workload": f"traffic chain n={n}, CGB with box-evaluated C, dt=0.01, T=2 (200 RK4 steps)",
+           "unit": "comp-steps/s"}
+    widths = {}
+    for name, prm in (("local", (40.0, 0.5, 1.0 / 6.0, 320.0, 1)), ("global", None)):
+        with R.System("traffic", n, params=prm) as s:
+            args = (d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"])
+            R.reach_cgb(s, *args, t_final=T_FINAL, dt=DT, lo=lo, hi=hi, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.reach_cgb(s, *args, t_final=T_FINAL, dt=DT, lo=lo, hi=hi, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            widths[name] = float((hi - lo).sum())
+            if name == "local":
+                out["value"] = 2 * n * NSTEPS / sec
+                out["s"] = sec
+    out["width_sum_local_over_global"] = widths["local"] / widths["global"]
+    return out
+
+
 def bench_temporal_blocking(R, torch, dev):
     """RK4 steps per launch S (halo 4 R S recomputed) on traffic MM (FP64,
     n = 2^24) and on KS MC32 (n = 2^20, 256 samples): the FP64 kernels are bound
@@ -626,6 +655,7 @@ def main():
         line["serving"] = bench_serving(R)
         line["heat3d"] = bench_heat(R, torch, dev)
         line["quad"] = bench_quad(R, torch, dev)
+        line["traffic_cgb_local"] = bench_traffic_local(R, torch, dev, d, n)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",

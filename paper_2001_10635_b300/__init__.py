@@ -31,6 +31,11 @@ STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADM
 _lib = None
 
 
+class _TrafficParams(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_double), ("v", ctypes.c_double), ("w", ctypes.c_double),
+                ("xbar", ctypes.c_double), ("cgb_local", ctypes.c_int)]
+
+
 class _HeatParams(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("l", ctypes.c_int64), ("open_face", ctypes.c_int)]
 
@@ -167,6 +172,10 @@ class System:
             self._A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(n, n))
             buf = (ctypes.c_void_p * 1)(self._A.ctypes.data)
             nbytes = ctypes.sizeof(ctypes.c_void_p)
+        elif self.kind == TRAFFIC and params is not None and len(params) == 5:
+            cap, v, w, xbar, local = params
+            buf = ctypes.pointer(_TrafficParams(float(cap), float(v), float(w), float(xbar), int(bool(local))))
+            nbytes = ctypes.sizeof(_TrafficParams)
         elif self.kind == HEAT3D and params is not None:
             alpha, l, open_face = params
             buf = _HeatParams(float(alpha), int(l), int(bool(open_face)))

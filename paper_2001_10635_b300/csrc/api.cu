@@ -2,6 +2,7 @@
 // checking, host/device staging, kernel dispatch and status reporting.
 #include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -169,6 +170,7 @@ TrafficK make_traffic_k(const double *prm, double wl, double wh) {
     p.d_hi = wh;
     p.d_c = 0.5 * (wl + wh);
     p.d_r = 0.5 * (wh - wl);
+    p.local = prm[4] != 0.0;
     return p;
 }
 
@@ -199,16 +201,19 @@ extern "C" int reach_system_create(int kind, int64_t n, const void *params, size
     double host[8] = {0};
     switch (kind) {
     case REACH_TRAFFIC: {
-        reach_traffic_params p{40.0, 0.5, 1.0 / 6.0, 320.0};
+        reach_traffic_params p{40.0, 0.5, 1.0 / 6.0, 320.0, 0};
         if (params) {
-            if (params_bytes != sizeof p) return REACH_EINVAL;
-            memcpy(&p, params, sizeof p);
+            // the struct without its last field (cgb_local) is accepted too
+            const size_t base = offsetof(reach_traffic_params, cgb_local);
+            if (params_bytes != sizeof p && params_bytes != base) return REACH_EINVAL;
+            memcpy(&p, params, params_bytes);
         }
         if (!std::isfinite(p.cap) || !std::isfinite(p.v) || !std::isfinite(p.w) || !std::isfinite(p.xbar) ||
             p.v < 0 || p.w < 0)
             return REACH_EINVAL;
         s.nw = 1;
         host[0] = p.cap; host[1] = p.v; host[2] = p.w; host[3] = p.xbar;
+        host[4] = p.cgb_local ? 1.0 : 0.0;
         break;
     }
     case REACH_KS: {

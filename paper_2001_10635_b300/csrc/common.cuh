@@ -21,6 +21,7 @@ struct TrafficK {
     long long v_add;     // e << 52, the shift as an addend to the bit pattern
     double d_lo, d_hi;   // MM inputs (p, ph)
     double d_c, d_r;     // CGB input center and half-width
+    int local;           // CGB with the box-evaluated contraction matrix
 };
 
 struct KsK {

@@ -53,7 +53,38 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
     const bool upper = c >= n;
     const int64_t i = upper ? c - n : c;
     if constexpr (SYS == REACH_TRAFFIC) {
-        // q: cap, v, w, wxbar
+        // q: cap, v, w, wxbar, box-evaluated C, xbar
+        if (METHOD == CGB && upper && q[4] != 0.0) {
+            // radius with C over the stage box [c - r, c + r] (reading R14)
+            auto lo = [&](int64_t j) { return __dsub_rn(yA[j], yB[j]); };
+            auto hi = [&](int64_t j) { return __dadd_rn(yA[j], yB[j]); };
+            auto cong = [&](double x) { return __dmul_rn(q[2], __dsub_rn(q[5], x)); };
+            auto ffp = [&](int64_t j) {
+                const double f = __dmul_rn(q[1], lo(j));
+                return dkey(f) <= dkey(q[0]) && (j == n - 1 || dkey(f) <= dkey(cong(lo(j + 1))));
+            };
+            auto ffc = [&](int64_t j) {
+                const double f = __dmul_rn(q[1], hi(j));
+                return dkey(f) < dkey(q[0]) && (j == n - 1 || dkey(f) < dkey(cong(hi(j + 1))));
+            };
+            auto cgp = [&](int64_t j) {
+                if (j == n - 1) return false;
+                const double c = cong(hi(j + 1));
+                return dkey(c) <= dkey(q[0]) && dkey(c) <= dkey(__dmul_rn(q[1], hi(j)));
+            };
+            auto cgc = [&](int64_t j) {
+                if (j == n - 1) return false;
+                const double c = cong(lo(j + 1));
+                return dkey(c) < dkey(q[0]) && dkey(c) < dkey(__dmul_rn(q[1], lo(j)));
+            };
+            const double cl = (i > 0 && ffp(i - 1)) ? q[1] : 0.0;
+            const double cr = cgp(i) ? q[2] : 0.0;
+            double cd = ffc(i) ? -q[1] : 0.0;
+            cd = (i > 0 && cgc(i - 1)) ? cd - q[2] : cd;
+            const double left = (i > 0) ? yB[i - 1] : 0.0, right = (i < n - 1) ? yB[i + 1] : 0.0;
+            const double v = fma(cl, left, fma(cr, right, cd * yB[i]));
+            return (i == 0) ? v + wB[0] : v;
+        }
         if (METHOD == MM || !upper) {
             const double *y = upper ? yB : yA;
             double d = upper ? wB[0] : wA[0];
@@ -170,6 +201,7 @@ __device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
     for (int t = 0; t < 8; ++t) q[t] = 0.0;
     if constexpr (SYS == REACH_TRAFFIC) {
         q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2]; q[3] = prm[2] * prm[3];
+        q[4] = prm[4]; q[5] = prm[3];
     } else if constexpr (SYS == REACH_KS) {
         q[0] = prm[0]; q[1] = prm[1]; q[2] = prm[2]; q[3] = prm[3];
     } else if constexpr (SYS == REACH_OSC) {

@@ -196,6 +196,123 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
     if (flags) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ traffic, box-evaluated C
+// CGB radius with the contraction matrix taken over the stage box [c - r, c + r]
+// (reading R14): C_{g,g-1} = v only if the free-flow branch of f_{g-1} can be
+// the minimum in the box, C_{g,g+1} = w only if the congestion branch of f_g
+// can, and C_gg = -v (-w) where the free-flow branch of f_g (congestion branch
+// of f_{g-1}) is strictly the minimum everywhere.  The tests use the plain
+// IEEE products w (xbar - x) and v x, so that they decide as a direct
+// evaluation of those expressions would.
+__device__ __forceinline__ bool klt(double a, double b) { return dkey(a) < dkey(b); }
+
+__device__ __forceinline__ void traffic_growth_local(const TrafficK &p, const double (&cc)[KC],
+                                                     const double (&rr)[KC], int64_t g0, int64_t n,
+                                                     double (&k)[KC]) {
+    double C[KC + 2], Rr[KC + 2];
+    exchange<1>(cc, C);
+    exchange<1>(rr, Rr);
+    double vlo[KC + 2], vhi[KC + 2], qlo[KC + 2], qhi[KC + 2];
+#pragma unroll
+    for (int m = 0; m < KC + 2; ++m) {
+        const double lo = __dsub_rn(C[m], Rr[m]), hi = __dadd_rn(C[m], Rr[m]);
+        vlo[m] = __dmul_rn(p.v, lo);
+        vhi[m] = __dmul_rn(p.v, hi);
+        qlo[m] = __dmul_rn(p.w, __dsub_rn(p.xbar, lo));   // congestion term of the cell to the left
+        qhi[m] = __dmul_rn(p.w, __dsub_rn(p.xbar, hi));
+    }
+    // branch tests of the flux out of cell g0 - 1 + m, m = 0..KC
+    bool ffp[KC + 1], ffc[KC + 1], cgp[KC + 1], cgc[KC + 1];
+#pragma unroll
+    for (int m = 0; m <= KC; ++m) {
+        const bool last = g0 - 1 + m == n - 1;
+        ffp[m] = kle(vlo[m], p.cap) && (last || kle(vlo[m], qlo[m + 1]));
+        ffc[m] = klt(vhi[m], p.cap) && (last || klt(vhi[m], qhi[m + 1]));
+        cgp[m] = !last && kle(qhi[m + 1], p.cap) && kle(qhi[m + 1], vhi[m]);
+        cgc[m] = !last && klt(qlo[m + 1], p.cap) && klt(qlo[m + 1], vlo[m]);
+    }
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        const int64_t g = g0 + j;
+        const double cl = (g > 0 && ffp[j]) ? p.v : 0.0;
+        const double cr = cgp[j + 1] ? p.w : 0.0;
+        double cd = ffc[j + 1] ? -p.v : 0.0;
+        cd = (g > 0 && cgc[j]) ? cd - p.w : cd;
+        const double left = (g > 0) ? Rr[j] : 0.0;
+        const double right = (g < n - 1) ? Rr[j + 2] : 0.0;
+        const double add = (g == 0) ? p.d_r : 0.0;
+        const double v = fma(cl, left, fma(cr, right, fma(cd, Rr[j + 1], add)));
+        k[j] = (g < 0 || g >= n) ? 0.0 : v;
+    }
+}
+
+// both halves per warp: the radius reads the center
+template <bool POW2>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4(StepArgs a, TrafficK p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t n = a.n;
+    int flags = 0;
+    for (int64_t t = warp; t < a.ntiles; t += nwarps) {
+        const int64_t own0 = t * a.W;
+        const int64_t g0 = own0 - a.H + (int64_t)lane * KC;
+        double zc[KC], zr[KC];
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            const bool in = g >= 0 && g < n;
+            double va = in ? __ldg(a.inA + g) : 0.0, vb = in ? __ldg(a.inB + g) : 0.0;
+            if (a.first) {
+                const bool owned = g >= own0 && g < own0 + a.W && in;
+                if (owned && !(kle(va, vb) && kfinite(va) && kfinite(vb))) flags |= ST_BADINPUT;
+                const double c = 0.5 * (va + vb), r = 0.5 * (vb - va);
+                va = c;
+                vb = r;
+            }
+            zc[j] = va;
+            zr[j] = vb;
+        }
+        for (int s = 0; s < a.S; ++s) {
+            double yc[KC], yr[KC], ac[KC], ar[KC], kc[KC], kr[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) { yc[j] = zc[j]; yr[j] = zr[j]; }
+            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            traffic_growth_local(p, yc, yr, g0, n, kr);
+            rk4_update<0>(zc, yc, ac, kc, a.h);
+            rk4_update<0>(zr, yr, ar, kr, a.h);
+            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            traffic_growth_local(p, yc, yr, g0, n, kr);
+            rk4_update<1>(zc, yc, ac, kc, a.h);
+            rk4_update<1>(zr, yr, ar, kr, a.h);
+            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            traffic_growth_local(p, yc, yr, g0, n, kr);
+            rk4_update<2>(zc, yc, ac, kc, a.h);
+            rk4_update<2>(zr, yr, ar, kr, a.h);
+            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            traffic_growth_local(p, yc, yr, g0, n, kr);
+            rk4_update<3>(zc, yc, ac, kc, a.h);
+            rk4_update<3>(zr, yr, ar, kr, a.h);
+        }
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            if (!(g >= own0 && g < own0 + a.W && g < n && g >= 0)) continue;
+            double oa = zc[j], ob = zr[j];
+            if (a.last) {
+                if (dkey(ob) < 0) flags |= ST_NEGRADIUS;
+                const double lo = oa - ob, hi = oa + ob;
+                oa = lo;
+                ob = hi;
+                if (!kfinite(oa) || !kfinite(ob)) flags |= ST_NONFINITE;
+            }
+            a.outA[g] = oa;
+            a.outB[g] = ob;
+        }
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
 // CGB output box from the final center and radius: lo = c - r, hi = c + r
 __global__ void cgb_box(double *c_lo, double *r_hi, int64_t n, int *status) {
     int flags = 0;
@@ -379,10 +496,17 @@ static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, dou
 int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st) {
+    const bool local = method == CGB && p.local;
     int rc = run_steps(1, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
         const int64_t ntiles = (n + a.W - 1) / a.W;
-        const unsigned grid = grid_for(2 * ntiles);
         const bool pw = p.v_pow2 != 0;
+        if (local) {
+            if (pw) stencil_traffic_cgbl_rk4<true><<<grid_for(ntiles), 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+            else stencil_traffic_cgbl_rk4<false><<<grid_for(ntiles), 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+            REACH_LAUNCHED("stencil_traffic_cgbl_rk4");
+            return REACH_OK;
+        }
+        const unsigned grid = grid_for(2 * ntiles);
         if (method == MM && pw) stencil_traffic_rk4<MM, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
         else if (method == MM) stencil_traffic_rk4<MM, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
         else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
@@ -390,7 +514,7 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
         REACH_LAUNCHED("stencil_traffic_rk4");
         return REACH_OK;
     });
-    if (rc || method != CGB) return rc;
+    if (rc || method != CGB || local) return rc;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
     cgb_box<<<(unsigned)blocks, 256, 0, st>>>(lo, hi, n, status);

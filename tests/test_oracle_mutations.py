@@ -40,7 +40,9 @@ MUTATIONS = [
      "else acc += posp(a) * x[j] + negp(a) * xh[j];", "else acc += negp(a) * x[j] + posp(a) * xh[j];"),
     ("traffic growth bound entries swapped", "if (i > 0) acc += s->v * r[i - 1];",
      "if (i > 0) acc += s->w * r[i - 1];"),
-    ("traffic growth bound without input", "dr[i] = acc + ((i == 0) ? hp[0] : 0.0);", "dr[i] = acc;"),
+    ("traffic growth bound without input",
+     "if (i < s->n - 1) acc += s->w * r[i + 1];\n        dr[i] = acc + ((i == 0) ? hp[0] : 0.0);",
+     "if (i < s->n - 1) acc += s->w * r[i + 1];\n        dr[i] = acc;"),
     ("ks growth diagonal uses the infimum", "double Cii = max2(s->a0 - k * dmin, s->a0 - k * dmax);",
      "double Cii = min2(s->a0 - k * dmin, s->a0 - k * dmax);"),
     ("osc growth bound drops the radius", "double amax = fabs(cx[i]) + rx[i];", "double amax = fabs(cx[i]);"),
