@@ -8,9 +8,9 @@ traffic cell-transmission chain with n = 2^26 cells, x0 box centres
 (MM and CGB integrate 2n components each).
 
   value  inputs resident in HBM (device tensors), CUDA events on the stream
-  e2e    the same through the public API with host (numpy) buffers: the
-         library's host->device copies and the result readback are inside
-         the timed region
+  e2e    the same through the public API with host buffers (page-locked,
+         passed as numpy arrays): the library's host->device copies and the
+         result readback are inside the timed region
   roofline  the dominant kernel (stencil_traffic_rk4): FP64-pipe operations per
          launch / its average launch time, against the FP64 issue rate of
          148 SMs x 2 ops/clk x 2.032 GHz
@@ -556,7 +556,14 @@ def main():
     n = args.cells
     wl = W.traffic_large(n, seed=0)
     dev = torch.device("cuda", local)
-    host = {k: np.ascontiguousarray(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+    def pinned(a):
+        # page-locked host buffer seen by the library as a plain host pointer
+        t = torch.empty(a.size, dtype=torch.float64, pin_memory=True)
+        v = t.numpy()
+        v[:] = a
+        return v
+
+    host = {k: pinned(np.ascontiguousarray(wl[k])) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
     d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     lo = torch.empty(n, dtype=torch.float64, device=dev)
     hi = torch.empty_like(lo)
@@ -598,8 +605,8 @@ def main():
     value = job_rate(2 * 2 * n * NSTEPS * args.steps, world, ms * 1e-3)
 
     # end to end through the public API with host buffers
-    hlo = np.empty(n)
-    hhi = np.empty(n)
+    hlo = pinned(np.zeros(n))
+    hhi = pinned(np.zeros(n))
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 2))
     if e2e_steps:
         R.reach_mm(sysm, host["x_lo"], host["x_hi"], host["w_lo"], host["w_hi"], t_final=T_FINAL, dt=DT,

@@ -356,7 +356,9 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     int64_t N;
     int rc = nsteps(t_final, dt, &N);
     if (rc) return rc;
-    if ((rc = check_host_box(x0_lo, x0_hi, sys->n))) return rc;
+    // with N > 0 the first launch of every kernel checks the box on the device
+    // (REACH_EINVAL through the status word), so a host box is not read twice
+    if (N == 0 && (rc = check_host_box(x0_lo, x0_hi, sys->n))) return rc;
     if ((rc = check_host_box(w_lo, w_hi, sys->nw))) return rc;
     const int64_t n = sys->n;
     bool onchip = use_onchip(sys);

@@ -612,7 +612,7 @@ extern "C" int reach_mc(const reach_system *sys, const double *x0_lo, const doub
     int64_t N;
     int rc = nsteps(t_final, dt, &N);
     if (rc) return rc;
-    if ((rc = check_host_box(x0_lo, x0_hi, sys->n))) return rc;
+    // the sampling kernels check the state box on the device
     if ((rc = check_host_box(w_lo, w_hi, sys->nw))) return rc;
     const int64_t n = sys->n;
     if (n >= (1LL << 32)) return REACH_EINVAL;

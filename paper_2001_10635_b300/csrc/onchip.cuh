@@ -212,45 +212,42 @@ __device__ __forceinline__ void load_consts(const double *prm, double (&q)[8]) {
     }
 }
 
-// one RK4 stage of the group: all derivatives from y, then y rewritten
+// One RK4 stage of the group.  The stage vector is double-buffered: the
+// derivatives are taken from (yA, yB) and the next stage input is written to
+// (oA, oB) at once, so a stage needs one barrier and no derivative buffer.
 template <int SYS, int METHOD, int STAGE, int Q, class Sync>
-__device__ __forceinline__ void onchip_stage(const OnItem &it, double *yA, double *yB, const double *wA,
-                                             const double *wB, double *kb, int64_t cbeg, int64_t cend, int gt,
-                                             int gs, const Sync &sync, const double (&q)[8], double (&z)[Q],
-                                             double (&acc)[Q]) {
+__device__ __forceinline__ void onchip_stage(const OnItem &it, const double *yA, const double *yB, double *oA,
+                                             double *oB, const double *wA, const double *wB, int64_t cbeg,
+                                             int64_t cend, int gt, int gs, const Sync &sync, const double (&q)[8],
+                                             double (&z)[Q], double (&acc)[Q]) {
     const int64_t n = it.n;
-#pragma unroll
-    for (int s = 0; s < Q; ++s) {
-        int64_t c = cbeg + gt + (int64_t)s * gs;
-        if (c < cend) kb[c - cbeg] = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
-    }
-    sync();
     const double h = it.h;
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
         int64_t c = cbeg + gt + (int64_t)s * gs;
         if (c < cend) {
-            double y, k = kb[c - cbeg];
+            const double k = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
+            double y;
             if (STAGE == 0) { acc[s] = k; y = fma(0.5 * h, k, z[s]); }
             if (STAGE == 1) { acc[s] = fma(2.0, k, acc[s]); y = fma(0.5 * h, k, z[s]); }
             if (STAGE == 2) { acc[s] = fma(2.0, k, acc[s]); y = fma(h, k, z[s]); }
             if (STAGE == 3) { acc[s] += k; z[s] = fma(h / 6.0, acc[s], z[s]); y = z[s]; }
-            (c < n ? yA[c] : yB[c - n]) = y;
+            (c < n ? oA[c] : oB[c - n]) = y;
         }
     }
     sync();
 }
 
-// Integrate one problem.  yA, yB: n doubles each of shared memory (may live in
-// different blocks of a cluster); wA, wB: nw doubles each; kb: cend - cbeg
-// doubles holding this group's stage derivatives.  The calling
-// threads own components [cbeg, cend) with stride gs starting at cbeg + gt,
-// at most Q each (Q is a template parameter so that small problems run a
-// small loop: the code of a 16-slot loop does not fit a lone warp's
-// instruction cache).
+// Integrate one problem.  (yA, yB) and (yA2, yB2): the two stage buffers, n
+// doubles per half (the halves may live in different blocks of a cluster);
+// wA, wB: nw doubles each.  The calling threads own components [cbeg, cend)
+// with stride gs starting at cbeg + gt, at most Q each (Q is a template
+// parameter so that small problems run a small loop: the code of a 16-slot
+// loop does not fit a lone warp's instruction cache).  The final state is in
+// (yA, yB).
 template <int SYS, int METHOD, int Q, class Sync>
-__device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA, double *wB,
-                           double *kb, int64_t cbeg, int64_t cend, int gt, int gs, const Sync &sync) {
+__device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *yA2, double *yB2, double *wA,
+                           double *wB, int64_t cbeg, int64_t cend, int gt, int gs, const Sync &sync) {
     const int64_t n = it.n;
     double q[8];
     load_consts<SYS>(it.prm, q);
@@ -291,10 +288,10 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *wA,
     sync();
 
     for (int64_t step = 0; step < it.N; ++step) {
-        onchip_stage<SYS, METHOD, 0, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 1, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 2, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
-        onchip_stage<SYS, METHOD, 3, Q>(it, yA, yB, wA, wB, kb, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 0, Q>(it, yA, yB, yA2, yB2, wA, wB, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 1, Q>(it, yA2, yB2, yA, yB, wA, wB, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 2, Q>(it, yA, yB, yA2, yB2, wA, wB, cbeg, cend, gt, gs, sync, q, z, acc);
+        onchip_stage<SYS, METHOD, 3, Q>(it, yA2, yB2, yA, yB, wA, wB, cbeg, cend, gt, gs, sync, q, z, acc);
     }
 
     // y holds the final state of both halves

@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(512) onchip_single(OnItem it) {
     extern __shared__ double sm[];
     const int64_t n = it.n;
     GroupSync sync{0, (int)blockDim.x};
-    onchip_run<SYS, METHOD, Q>(it, sm, sm + n, sm + 2 * n, sm + 2 * n + it.nw, sm + 2 * n + 2 * it.nw, 0,
-                            2 * n, (int)threadIdx.x, (int)blockDim.x, sync);
+    // [yA | yB | yA2 | yB2 | wA | wB]
+    onchip_run<SYS, METHOD, Q>(it, sm, sm + n, sm + 2 * n, sm + 3 * n, sm + 4 * n, sm + 4 * n + it.nw, 0, 2 * n,
+                               (int)threadIdx.x, (int)blockDim.x, sync);
 }
 
 template <int SYS, int METHOD, int Q>
@@ -67,12 +68,14 @@ __device__ __forceinline__ void cluster_item(const OnItem &it, double *sm) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
     const int64_t n = it.n;
-    double *y = sm, *w = sm + n, *kb = w + it.nw;
-    double *other = cl.map_shared_rank(y, rank ^ 1u);
+    // per block [y | y2 | w]: this block's half in both stage buffers
+    double *y = sm, *y2 = sm + n, *w = sm + 2 * n;
+    double *other = cl.map_shared_rank(y, rank ^ 1u), *other2 = cl.map_shared_rank(y2, rank ^ 1u);
     double *yA = rank == 0 ? y : other, *yB = rank == 0 ? other : y;
+    double *yA2 = rank == 0 ? y2 : other2, *yB2 = rank == 0 ? other2 : y2;
     // the lower / center block uses wA, the upper / radius block wB
-    onchip_run<SYS, METHOD, QMAX>(it, yA, yB, w, w, kb, rank * n, (rank + 1) * n, (int)threadIdx.x, (int)blockDim.x,
-                            ClusterSync{});
+    onchip_run<SYS, METHOD, QMAX>(it, yA, yB, yA2, yB2, w, w, rank * n, (rank + 1) * n, (int)threadIdx.x,
+                                  (int)blockDim.x, ClusterSync{});
 }
 
 
@@ -133,8 +136,9 @@ __device__ __forceinline__ void run_bin(const OnItem *__restrict__ items, const 
         const int64_t n = it.n;
         GroupSync sync{sl.bar, sl.nwarps * 32};
         const int gt = (int)threadIdx.x - sl.warp0 * 32, gs = sl.nwarps * 32;
-        double *w = y + 2 * n, *kb = w + 2 * it.nw;
-        onchip_run<SYS, METHOD, Q>(it, y, y + n, w, w + it.nw, kb, 0, 2 * n, gt, gs, sync);
+        // [yA | yB | wA | wB | yA2 | yB2]
+        double *w = y + 2 * n, *y2 = w + 2 * it.nw;
+        onchip_run<SYS, METHOD, Q>(it, y, y + n, y2, y2 + n, w, w + it.nw, 0, 2 * n, gt, gs, sync);
         if (gt == 0) done[sl.item] = global_ns();
         break;
     }
