@@ -34,6 +34,8 @@ KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEA
 TRAFFIC_PRM = (40.0, 0.5, 1.0 / 6.0, 320.0)
 # the same with the box-evaluated CGB contraction matrix (reading R14)
 TRAFFIC_LOCAL_PRM = TRAFFIC_PRM + (1.0,)
+# outward-rounded MM / CGB (reading R15)
+TRAFFIC_SOUND_PRM = TRAFFIC_PRM + (0.0, 1.0)
 KS_PRM = (math.pi / 4.0, 1.0, 1.0, 1.0)
 OSC_PRM = (1.0, 0.1, 0.5)
 # heat: (alpha, l, open face); l is set from n by default_params
@@ -88,6 +90,15 @@ def lib():
         L.orc_rhs.restype = ctypes.c_int
         L.orc_decomp.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, dp, dp, dp]
         L.orc_decomp.restype = ctypes.c_int
+        pd = ctypes.POINTER(ctypes.c_double)
+        L.orc_sound_op.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, pd]
+        L.orc_sound_op.restype = ctypes.c_int
+        L.orc_sound_mul_pos.argtypes = [ctypes.c_double] * 4 + [pd, pd]
+        L.orc_sound_mul_pos.restype = ctypes.c_int
+        L.orc_traffic_sound_rhs.argtypes = [dp, ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_traffic_sound_rhs.restype = ctypes.c_int
+        L.orc_traffic_sound_radius_rhs.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_double, dp]
+        L.orc_traffic_sound_radius_rhs.restype = ctypes.c_int
         L.orc_growth.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, dp, dp]
         L.orc_growth.restype = ctypes.c_int
         _lib = L
@@ -125,8 +136,9 @@ def input_dim(kind: str, n: int) -> int:
 
 def _prep(kind, n, params, A, w_lo, w_hi):
     prm = _vec(default_params(kind, n) if params is None else params)
-    if kind == "traffic" and prm.size == 4:
-        prm = np.append(prm, 0.0)   # CGB with the bounds valid for every state
+    if kind == "traffic" and prm.size < 6:
+        # defaults: CGB with the bounds valid for every state; round to nearest
+        prm = np.concatenate([prm, np.zeros(6 - prm.size)])
     if prm.size == 0:
         prm = np.zeros(1)
     Aa = None
@@ -195,6 +207,51 @@ def flow(kind: str, x0, w=None, *, t_final: float, dt: float, params=None, A=Non
     if rc != 0:
         raise OracleError(rc)
     return out
+
+
+def sound_op(op: str, a: float, b: float) -> float:
+    """One directed operation of reading R15: op in add_dn, add_up, mul_dn,
+    mul_up, div_dn, div_up."""
+    code = ["add_dn", "add_up", "mul_dn", "mul_up", "div_dn", "div_up"].index(op)
+    out = ctypes.c_double(0.0)
+    rc = lib().orc_sound_op(code, float(a), float(b), ctypes.byref(out))
+    if rc != 0:
+        raise OracleError(rc)
+    return out.value
+
+
+def sound_mul_pos(cl, cu, ql, qu):
+    """[ql, qu] times a constant in [cl, cu] (cl >= 0), rounded outward."""
+    rl, ru = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib().orc_sound_mul_pos(float(cl), float(cu), float(ql), float(qu), ctypes.byref(rl), ctypes.byref(ru))
+    if rc != 0:
+        raise OracleError(rc)
+    return rl.value, ru.value
+
+
+def traffic_sound_rhs(yl, yu, dl, du, params=None):
+    """Interval right-hand side of the traffic chain, rounded outward (R15)."""
+    yl = _vec(yl)
+    n = yl.size
+    yu = _vec(yu, n)
+    prm, _, _, _ = _prep("traffic", n, params, None, [dl], [du])
+    kl, ku = np.empty(n), np.empty(n)
+    rc = lib().orc_traffic_sound_rhs(_p(prm), n, _p(yl), _p(yu), float(dl), float(du), _p(kl), _p(ku))
+    if rc != 0:
+        raise OracleError(rc)
+    return kl, ku
+
+
+def traffic_sound_radius_rhs(r, hp, params=None):
+    """Upper bound of the traffic CGB radius right-hand side C r + [p] (R15)."""
+    r = _vec(r)
+    n = r.size
+    prm, _, _, _ = _prep("traffic", n, params, None, [0.0], [0.0])
+    dr = np.empty(n)
+    rc = lib().orc_traffic_sound_radius_rhs(_p(prm), n, _p(r), float(hp), _p(dr))
+    if rc != 0:
+        raise OracleError(rc)
+    return dr
 
 
 def nsteps(t_final: float, dt: float) -> int:

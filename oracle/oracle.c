@@ -53,6 +53,17 @@
  *      branch of the flux can be the minimum somewhere in the box, and the
  *      diagonal gets -v (-w) where the free-flow branch of f_i (the
  *      congestion branch of f_{i-1}) is strictly the minimum everywhere in it.
+ *  R15 (Sec. 2.1, Sec. 3.1; optional).  Outward-rounded MM and CGB for the
+ *      traffic chain (traffic parameter 6 nonzero): the computed box contains
+ *      the box the same method (R1, R2, R6) yields in exact real arithmetic
+ *      from the same binary64 inputs and step.  Each MM half and the CGB
+ *      center are carried as intervals of binary64 numbers that contain the
+ *      exact value, every operation rounded outward; the CGB radius has only
+ *      nonnegative coefficients, so each of its operations is rounded up.
+ *      Directed rounding is computed from round-to-nearest results and their
+ *      exact errors (TwoSum: Knuth, TAOCP vol. 2, 4.2.2; the product error by
+ *      one fused multiply-add), stepping to the adjacent binary64 number where
+ *      the error shows the rounded result on the wrong side.
  *  R13 (Sec. 5.2).  Quadrotor swarm of K = n/12 independent agents.  Agent k
  *      holds x[12k + 0..11] = (p_n, p_e, h, dp_n, dp_e, dh, phi, theta, psi,
  *      dphi, dtheta, dpsi) and inputs p[3k + 0..2] = (tau_phi, tau_theta,
@@ -93,6 +104,7 @@ typedef struct {
        speed w, jam density xbar */
     double cap, v, w, xbar;
     int tr_local;       /* CGB with the box-evaluated C (reading R14) */
+    int tr_sound;       /* outward-rounded MM / CGB (reading R15) */
     /* KS grid: u_t = -g_nl u u_x - g_2 u_xx - g_4 u_xxxx, spacing dx */
     double dx, g_nl, g_2, g_4;
     double a0, a1, a2;  /* 5-point stencil of -g_2 u_xx - g_4 u_xxxx */
@@ -134,6 +146,8 @@ static int make_sys(orc_sys *s, int kind, const double *prm, const double *A, in
     case ORC_TRAFFIC:
         s->cap = prm[0]; s->v = prm[1]; s->w = prm[2]; s->xbar = prm[3];
         s->tr_local = prm[4] != 0.0;
+        s->tr_sound = prm[5] != 0.0;
+        if (s->tr_local && s->tr_sound) return ORC_EINVAL;
         break;
     case ORC_KS: {
         double d2, d4;
@@ -923,6 +937,228 @@ static int reach_mc(const orc_sys *s, const double *xlo, const double *xhi,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Outward rounding (reading R15)                                           */
+/* ---------------------------------------------------------------------- */
+
+/* a + b rounded down / up: s = fl(a + b) and its exact error e (TwoSum) */
+static double add_dn(double a, double b)
+{
+    double s = a + b, bb = s - a, e = (a - (s - bb)) + (b - bb);
+    return e < 0.0 ? nextafter(s, -INFINITY) : s;
+}
+
+static double add_up(double a, double b)
+{
+    double s = a + b, bb = s - a, e = (a - (s - bb)) + (b - bb);
+    return e > 0.0 ? nextafter(s, INFINITY) : s;
+}
+
+/* a * b rounded down / up: the error of p = fl(a b) is fma(a, b, -p), exact */
+static double mul_dn(double a, double b)
+{
+    double p = a * b, e = fma(a, b, -p);
+    return e < 0.0 ? nextafter(p, -INFINITY) : p;
+}
+
+static double mul_up(double a, double b)
+{
+    double p = a * b, e = fma(a, b, -p);
+    return e > 0.0 ? nextafter(p, INFINITY) : p;
+}
+
+/* a / b (b > 0) rounded down / up: the remainder a - q b is fma(-q, b, a), exact */
+static double div_dn(double a, double b)
+{
+    double q = a / b, e = fma(-q, b, a);
+    return e < 0.0 ? nextafter(q, -INFINITY) : q;
+}
+
+static double div_up(double a, double b)
+{
+    double q = a / b, e = fma(-q, b, a);
+    return e > 0.0 ? nextafter(q, INFINITY) : q;
+}
+
+/* the interval [ql, qu] times c, for the constant c in [cl, cu], cl >= 0 */
+static void imul_pos(double cl, double cu, double ql, double qu, double *rl, double *ru)
+{
+    *rl = mul_dn(ql >= 0.0 ? cl : cu, ql);
+    *ru = mul_up(qu >= 0.0 ? cu : cl, qu);
+}
+
+/* interval traffic right-hand side: the flux of R6 with every operation
+   rounded outward, inflow [dl, du] */
+static void tr_flux_iv(const orc_sys *s, const double *yl, const double *yu, int64_t i,
+                       double *fl, double *fu)
+{
+    double vl = mul_dn(s->v, yl[i]), vu = mul_up(s->v, yu[i]);
+    if (i == s->n - 1) {
+        *fl = min2(s->cap, vl);
+        *fu = min2(s->cap, vu);
+        return;
+    }
+    /* w (xbar - y_{i+1}) is decreasing in y_{i+1} */
+    *fl = min2(s->cap, min2(vl, mul_dn(s->w, add_dn(s->xbar, -yu[i + 1]))));
+    *fu = min2(s->cap, min2(vu, mul_up(s->w, add_up(s->xbar, -yl[i + 1]))));
+}
+
+static void f_traffic_iv(const orc_sys *s, const double *yl, const double *yu, double dl, double du,
+                         double *kl, double *ku)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double inl = dl, inu = du, outl, outu;
+        if (i > 0) tr_flux_iv(s, yl, yu, i - 1, &inl, &inu);
+        tr_flux_iv(s, yl, yu, i, &outl, &outu);
+        kl[i] = add_dn(inl, -outu);
+        ku[i] = add_up(inu, -outl);
+    }
+}
+
+/* upper bound of the CGB radius right-hand side C r + [p] (all terms >= 0) */
+static void g_traffic_up(const orc_sys *s, const double *r, double hp, double *dr)
+{
+    for (int64_t i = 0; i < s->n; ++i) {
+        double acc = (i == 0) ? hp : 0.0;
+        if (i > 0) acc = add_up(acc, mul_up(s->v, r[i - 1]));
+        if (i < s->n - 1) acc = add_up(acc, mul_up(s->w, r[i + 1]));
+        dr[i] = acc;
+    }
+}
+
+/* N classic RK4 steps (R1) of the traffic chain on the interval state
+   [zl, zu] with inflow [dl, du], all rounded outward.  With zl == NULL only
+   the upper end is carried and the right-hand side is the radius bound
+   (every quantity nonnegative). */
+static int rk4_sound(const orc_sys *s, double *zl, double *zu, double dl, double du, double hp,
+                     double h, int64_t N)
+{
+    int64_t n = s->n;
+    const int radius = zl == NULL;
+    double hh = 0.5 * h, c6l = div_dn(h, 6.0), c6u = div_up(h, 6.0);
+    double *b = malloc(sizeof(double) * 6 * n);
+    double *yl, *yu, *kl, *ku, *al, *au;
+    if (!b) return ORC_ENOMEM;
+    yl = b; yu = b + n; kl = b + 2 * n; ku = b + 3 * n; al = b + 4 * n; au = b + 5 * n;
+    for (int64_t step = 0; step < N; ++step) {
+        for (int64_t i = 0; i < n; ++i) { yu[i] = zu[i]; if (!radius) yl[i] = zl[i]; }
+        for (int stage = 0; stage < 4; ++stage) {
+            /* stage weights 1, 2, 2, 1 and stage inputs y + h/2 k, y + h/2 k, y + h k */
+            double cs = (stage == 2) ? h : hh;
+            if (radius) g_traffic_up(s, yu, hp, ku);
+            else f_traffic_iv(s, yl, yu, dl, du, kl, ku);
+            for (int64_t i = 0; i < n; ++i) {
+                double tl = 0.0, tu;
+                if (radius) tu = ku[i];
+                else { tl = kl[i]; tu = ku[i]; }
+                if (stage == 0) { au[i] = tu; if (!radius) al[i] = tl; }
+                else if (stage == 3) { au[i] = add_up(au[i], tu); if (!radius) al[i] = add_dn(al[i], tl); }
+                else { au[i] = add_up(au[i], 2.0 * tu); if (!radius) al[i] = add_dn(al[i], 2.0 * tl); }
+                if (stage < 3) {
+                    yu[i] = add_up(zu[i], mul_up(cs, tu));
+                    if (!radius) yl[i] = add_dn(zl[i], mul_dn(cs, tl));
+                }
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            double ql, qu;
+            /* z + (h/6) acc with h/6 in [c6l, c6u] */
+            imul_pos(c6l, c6u, radius ? au[i] : al[i], au[i], &ql, &qu);
+            zu[i] = add_up(zu[i], qu);
+            if (!radius) zl[i] = add_dn(zl[i], ql);
+        }
+    }
+    free(b);
+    return ORC_OK;
+}
+
+/* The pieces of R15 one by one, for the pins: a directed operation (op 0..5:
+   add, mul, div, each down then up), the constant-interval product, and the
+   interval right-hand sides of the traffic chain and of its radius. */
+int orc_sound_op(int op, double a, double b, double *out)
+{
+    switch (op) {
+    case 0: *out = add_dn(a, b); return ORC_OK;
+    case 1: *out = add_up(a, b); return ORC_OK;
+    case 2: *out = mul_dn(a, b); return ORC_OK;
+    case 3: *out = mul_up(a, b); return ORC_OK;
+    case 4: if (!(b > 0.0)) return ORC_EINVAL; *out = div_dn(a, b); return ORC_OK;
+    case 5: if (!(b > 0.0)) return ORC_EINVAL; *out = div_up(a, b); return ORC_OK;
+    }
+    return ORC_EINVAL;
+}
+
+int orc_sound_mul_pos(double cl, double cu, double ql, double qu, double *rl, double *ru)
+{
+    if (!(cl >= 0.0) || !(cu >= cl)) return ORC_EINVAL;
+    imul_pos(cl, cu, ql, qu, rl, ru);
+    return ORC_OK;
+}
+
+int orc_traffic_sound_rhs(const double *prm, int64_t n, const double *yl, const double *yu,
+                          double dl, double du, double *kl, double *ku)
+{
+    orc_sys s;
+    int rc = make_sys(&s, ORC_TRAFFIC, prm, NULL, n);
+    if (rc) return rc;
+    f_traffic_iv(&s, yl, yu, dl, du, kl, ku);
+    return ORC_OK;
+}
+
+int orc_traffic_sound_radius_rhs(const double *prm, int64_t n, const double *r, double hp, double *dr)
+{
+    orc_sys s;
+    int rc = make_sys(&s, ORC_TRAFFIC, prm, NULL, n);
+    if (rc) return rc;
+    g_traffic_up(&s, r, hp, dr);
+    return ORC_OK;
+}
+
+static int reach_sound(int method, const orc_sys *s, const double *xlo, const double *xhi,
+                       const double *wlo, const double *whi, double h, int64_t N,
+                       double *lo, double *hi)
+{
+    int64_t n = s->n;
+    int rc = ORC_OK;
+    double *z = malloc(sizeof(double) * 3 * n);
+    if (!z) return ORC_ENOMEM;
+    if (method == ORC_MM) {
+        /* the two corner trajectories, each from a point */
+        double *l = z, *u = z + n, *t = z + 2 * n;
+        memcpy(l, xlo, sizeof(double) * n);
+        memcpy(u, xlo, sizeof(double) * n);
+        rc = rk4_sound(s, l, u, wlo[0], wlo[0], 0.0, h, N);
+        if (!rc) {
+            memcpy(lo, l, sizeof(double) * n);
+            memcpy(u, xhi, sizeof(double) * n);
+            memcpy(t, xhi, sizeof(double) * n);
+            rc = rk4_sound(s, t, u, whi[0], whi[0], 0.0, h, N);
+            if (!rc) memcpy(hi, u, sizeof(double) * n);
+        }
+    } else {
+        /* center [cl, cu] and radius upper bound ru */
+        double *cl = z, *cu = z + n, *ru = z + 2 * n;
+        double dcl = 0.5 * add_dn(wlo[0], whi[0]), dcu = 0.5 * add_up(wlo[0], whi[0]);
+        double hp = 0.5 * add_up(whi[0], -wlo[0]);
+        for (int64_t i = 0; i < n; ++i) {
+            cl[i] = 0.5 * add_dn(xlo[i], xhi[i]);
+            cu[i] = 0.5 * add_up(xlo[i], xhi[i]);
+            ru[i] = 0.5 * add_up(xhi[i], -xlo[i]);
+        }
+        rc = rk4_sound(s, cl, cu, dcl, dcu, 0.0, h, N);
+        if (!rc) rc = rk4_sound(s, NULL, ru, 0.0, 0.0, hp, h, N);
+        if (!rc) {
+            for (int64_t i = 0; i < n; ++i) {
+                lo[i] = add_dn(cl[i], -ru[i]);
+                hi[i] = add_up(cu[i], ru[i]);
+            }
+        }
+    }
+    if (!rc && (!all_finite(lo, n) || !all_finite(hi, n))) rc = ORC_ENONFINITE;
+    free(z);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Entry point                                                              */
 /* ---------------------------------------------------------------------- */
 int orc_reach(int method, int kind, const double *prm, const double *A, int64_t n,
@@ -938,6 +1174,8 @@ int orc_reach(int method, int kind, const double *prm, const double *A, int64_t 
     if ((rc = orc_nsteps(t_final, dt, &N))) return rc;
     if ((rc = check_box(x_lo, x_hi, n))) return rc;
     if ((rc = check_box(w_lo, w_hi, s.nw))) return rc;
+    if (s.kind == ORC_TRAFFIC && s.tr_sound && (method == ORC_MM || method == ORC_CGB))
+        return reach_sound(method, &s, x_lo, x_hi, w_lo, w_hi, dt, N, lo, hi);
     switch (method) {
     case ORC_MM: return reach_mm(&s, x_lo, x_hi, w_lo, w_hi, dt, N, N > 0 ? N : 1, NULL, NULL, lo, hi);
     case ORC_CGB: return reach_cgb(&s, x_lo, x_hi, w_lo, w_hi, dt, N, N > 0 ? N : 1, NULL, NULL, lo, hi);
@@ -962,6 +1200,7 @@ int orc_reach_pipe(int method, int kind, const double *prm, const double *A, int
     if (rc) return rc;
     if ((rc = orc_nsteps(t_final, dt, &N))) return rc;
     if (every < 1 || N % every) return ORC_EINVAL;
+    if (s.kind == ORC_TRAFFIC && s.tr_sound) return ORC_EINVAL;   /* R15 covers whole horizons only */
     if ((rc = check_box(x_lo, x_hi, n))) return rc;
     if ((rc = check_box(w_lo, w_hi, s.nw))) return rc;
     if (method == ORC_MM)

@@ -75,6 +75,12 @@ MUTATIONS = [
     ('traffic local: congested-inflow diagonal dropped', 'if (i > 0 && tr_cong_certain(s, lo, i - 1)) cd -= s->w;', ''),
     ('traffic local: free flow possible tested at the upper corner', 'double cl = (i > 0 && tr_ff_possible(s, lo, i - 1)) ? s->v : 0.0;', 'double cl = (i > 0 && tr_ff_possible(s, hi, i - 1)) ? s->v : 0.0;'),
     ('traffic local: superdiagonal keeps w', 'double cr = tr_cong_possible(s, hi, i) ? s->w : 0.0;', 'double cr = s->w;'),
+    ('sound: flux difference rounded up for the lower end', 'kl[i] = add_dn(inl, -outu);', 'kl[i] = add_up(inl, -outu);'),
+    ('sound: congestion term from the wrong end', '*fl = min2(s->cap, min2(vl, mul_dn(s->w, add_dn(s->xbar, -yu[i + 1]))));', '*fl = min2(s->cap, min2(vl, mul_dn(s->w, add_dn(s->xbar, -yl[i + 1]))));'),
+    ('sound: h/6 bound ignores the sign', '*rl = mul_dn(ql >= 0.0 ? cl : cu, ql);', '*rl = mul_dn(cl, ql);'),
+    ('sound: radius product rounded down', 'if (i > 0) acc = add_up(acc, mul_up(s->v, r[i - 1]));', 'if (i > 0) acc = add_up(acc, mul_dn(s->v, r[i - 1]));'),
+    ('sound: downward sum rounds to nearest', '    double s = a + b, bb = s - a, e = (a - (s - bb)) + (b - bb);\n    return e < 0.0 ? nextafter(s, -INFINITY) : s;', '    double s = a + b;\n    return s;'),
+    ('sound: center rounded to nearest', 'cl[i] = 0.5 * add_dn(xlo[i], xhi[i]);', 'cl[i] = 0.5 * (xlo[i] + xhi[i]);'),
 ]
 
 

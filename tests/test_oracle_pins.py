@@ -927,3 +927,169 @@ def test_traffic_local_capacity_box():
     want = np.zeros(9)
     want[0] = 0.75
     np.testing.assert_array_equal(dr, want)
+
+
+# ------------------------------------------------------------------ outward rounding (reading R15)
+from fractions import Fraction as Fr  # noqa: E402
+
+TSP = O.TRAFFIC_SOUND_PRM
+
+
+def _exact_traffic_rk4(x, d, h, N, prm, radius=False, hp=None):
+    """Classic RK4 (R1) of the traffic chain (R6), or of its CGB radius
+    dynamics C r + [p], in exact rational arithmetic."""
+    cap, v, w, xbar = (Fr(p) for p in prm[:4])
+    n = len(x)
+
+    def f(y):
+        if radius:
+            return [(v * y[i - 1] if i > 0 else 0) + (w * y[i + 1] if i < n - 1 else 0) + (hp if i == 0 else 0)
+                    for i in range(n)]
+        flux = [min(cap, v * y[i], w * (xbar - y[i + 1])) if i < n - 1 else min(cap, v * y[i]) for i in range(n)]
+        return [(d if i == 0 else flux[i - 1]) - flux[i] for i in range(n)]
+
+    z = list(x)
+    for _ in range(N):
+        k1 = f(z)
+        k2 = f([z[i] + h / 2 * k1[i] for i in range(n)])
+        k3 = f([z[i] + h / 2 * k2[i] for i in range(n)])
+        k4 = f([z[i] + h * k3[i] for i in range(n)])
+        z = [z[i] + h / 6 * (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]) for i in range(n)]
+    return z
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sound_boxes_contain_the_exact_arithmetic_result(seed):
+    g = np.random.default_rng(40 + seed)
+    n, N, dt = int(g.integers(3, 6)), int(g.integers(3, 7)), 0.05
+    c = g.uniform(5, 315, n)
+    hw = g.uniform(0, 8, n)
+    lo, hi = c - hw, c + hw
+    dl = float(g.uniform(20, 40))
+    dh = dl + float(g.uniform(0, 10))
+    T = N * dt
+    h = Fr(dt)
+    X0, X1 = [Fr(a) for a in lo], [Fr(a) for a in hi]
+    # MM: two corner trajectories
+    mlo, mhi = O.reach("mm", "traffic", lo, hi, [dl], [dh], t_final=T, dt=dt, params=TSP)
+    elo = _exact_traffic_rk4(X0, Fr(dl), h, N, TSP)
+    ehi = _exact_traffic_rk4(X1, Fr(dh), h, N, TSP)
+    assert all(Fr(mlo[i]) <= elo[i] for i in range(n))
+    assert all(Fr(mhi[i]) >= ehi[i] for i in range(n))
+    # CGB: center and radius in exact arithmetic
+    clo, chi = O.reach("cgb", "traffic", lo, hi, [dl], [dh], t_final=T, dt=dt, params=TSP)
+    cc = _exact_traffic_rk4([(a + b) / 2 for a, b in zip(X0, X1)], (Fr(dl) + Fr(dh)) / 2, h, N, TSP)
+    rr = _exact_traffic_rk4([(b - a) / 2 for a, b in zip(X0, X1)], None, h, N, TSP, radius=True,
+                            hp=(Fr(dh) - Fr(dl)) / 2)
+    assert all(Fr(clo[i]) <= cc[i] - rr[i] for i in range(n))
+    assert all(Fr(chi[i]) >= cc[i] + rr[i] for i in range(n))
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_sound_boxes_contain_the_nearest_rounded_boxes(method):
+    wl = W.traffic_small(16)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    a = O.reach(method, "traffic", *args, t_final=10.0, dt=0.01)
+    b = O.reach(method, "traffic", *args, t_final=10.0, dt=0.01, params=TSP)
+    assert np.all(b[0] <= a[0]) and np.all(b[1] >= a[1])
+    # the outward rounding costs a few ulps per step, nothing more
+    scale = np.abs(a[1]).max()
+    assert np.max(a[0] - b[0]) < 1e-11 * scale and np.max(b[1] - a[1]) < 1e-11 * scale
+    assert np.max(a[0] - b[0]) > 0 and np.max(b[1] - a[1]) > 0
+
+
+def _is_down(x, exact):
+    return Fr(x) <= exact < Fr(np.nextafter(x, np.inf))
+
+
+def _is_up(x, exact):
+    return Fr(np.nextafter(x, -np.inf)) < exact <= Fr(x)
+
+
+def test_sound_primitives_are_the_directed_roundings():
+    g = np.random.default_rng(50)
+    vals = np.concatenate([g.uniform(-1, 1, 60) * 10.0 ** g.integers(-8, 9, 60), [0.1, 1.0 / 3, 320.0, -40.0]])
+    for a in vals[:32]:
+        for b in vals[32:]:
+            A, B = Fr(a), Fr(b)
+            assert _is_down(O.sound_op("add_dn", a, b), A + B)
+            assert _is_up(O.sound_op("add_up", a, b), A + B)
+            assert _is_down(O.sound_op("mul_dn", a, b), A * B)
+            assert _is_up(O.sound_op("mul_up", a, b), A * B)
+            if b > 0:
+                assert _is_down(O.sound_op("div_dn", a, b), A / B)
+                assert _is_up(O.sound_op("div_up", a, b), A / B)
+
+
+def test_sound_constant_interval_product():
+    c = 0.01 / 6
+    cl, cu = O.sound_op("div_dn", 0.01, 6.0), O.sound_op("div_up", 0.01, 6.0)
+    assert Fr(cl) <= Fr(0.01) / 6 <= Fr(cu)
+    for ql, qu in [(-3.7, 2.9), (0.3, 5.1), (-8.2, -1.3)]:
+        rl, ru = O.sound_mul_pos(cl, cu, ql, qu)
+        lo_exact = min(Fr(cl) * Fr(ql), Fr(cu) * Fr(ql))
+        hi_exact = max(Fr(cl) * Fr(qu), Fr(cu) * Fr(qu))
+        assert _is_down(rl, lo_exact) and _is_up(ru, hi_exact)
+    del c
+
+
+@pytest.mark.parametrize("regime", [(1.0, 60.0), (90.0, 200.0), (250.0, 319.0), (0.0, 320.0)])
+def test_traffic_sound_rhs_encloses_the_exact_range(regime):
+    g = np.random.default_rng(int(regime[0]) + 51)
+    cap, v, w, xbar = (Fr(p) for p in TSP[:4])
+    n = 7
+    for _ in range(20):
+        a, b = g.uniform(*regime, n), g.uniform(*regime, n)
+        yl, yu = np.minimum(a, b), np.maximum(a, b)
+        if _ == 0:
+            yu = yl.copy()   # a point: the enclosure of one value
+        dl = float(g.uniform(20, 40))
+        du = dl + float(g.uniform(0, 5))
+        kl, ku = O.traffic_sound_rhs(yl, yu, dl, du, params=TSP)
+        L, U = [Fr(x) for x in yl], [Fr(x) for x in yu]
+        fmin = [min(cap, v * L[i], w * (xbar - U[i + 1])) if i < n - 1 else min(cap, v * L[i]) for i in range(n)]
+        fmax = [min(cap, v * U[i], w * (xbar - L[i + 1])) if i < n - 1 else min(cap, v * U[i]) for i in range(n)]
+        for i in range(n):
+            inl, inu = (Fr(dl), Fr(du)) if i == 0 else (fmin[i - 1], fmax[i - 1])
+            emin, emax = inl - fmax[i], inu - fmin[i]
+            assert Fr(kl[i]) <= emin and Fr(ku[i]) >= emax
+            # and no looser than a few roundings of the operands (fluxes up to
+            # cap, congestion terms up to w xbar)
+            tol = Fr(8 * np.spacing(64.0))
+            assert emin - Fr(kl[i]) <= tol and Fr(ku[i]) - emax <= tol
+
+
+@pytest.mark.parametrize("v", [0.5, 0.45])
+def test_traffic_sound_radius_rhs_is_an_upper_bound(v):
+    g = np.random.default_rng(52)
+    prm = (40.0, v, 1.0 / 6.0, 320.0, 0.0, 1.0)
+    v, w = Fr(prm[1]), Fr(prm[2])
+    for _ in range(30):
+        n = 6
+        r = g.uniform(0, 10, n) * 10.0 ** g.integers(-3, 3)
+        hp = float(g.uniform(0, 5))
+        dr = O.traffic_sound_radius_rhs(r, hp, params=prm)
+        R_ = [Fr(x) for x in r]
+        for i in range(n):
+            e = (Fr(hp) if i == 0 else 0) + (v * R_[i - 1] if i > 0 else 0) + (w * R_[i + 1] if i < n - 1 else 0)
+            assert Fr(dr[i]) >= e
+            assert Fr(dr[i]) - e <= Fr(4 * np.spacing(float(e) if e > 0 else 1.0))
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+def test_sound_zero_horizon_contains_the_box(method):
+    # with no step the exact method returns the initial box itself: the
+    # outward-rounded center and radius must reproduce it or contain it
+    g = np.random.default_rng(53)
+    for k in range(40):
+        if k % 2:
+            # hi - lo exact (Sterbenz) and lo + hi inexact half of the time: the
+            # center's rounding alone decides the containment
+            a, b = g.uniform(100, 120, 9), g.uniform(100, 120, 9)
+            lo, hi = np.minimum(a, b), np.maximum(a, b)
+        else:
+            c = g.uniform(0, 320, 9)
+            h = g.uniform(0, 10, 9) * 10.0 ** g.integers(-6, 1)
+            lo, hi = c - h, c + h
+        blo, bhi = O.reach(method, "traffic", lo, hi, [30.0], [40.0], t_final=0.0, dt=0.01, params=TSP)
+        assert np.all(blo <= lo) and np.all(bhi >= hi)
