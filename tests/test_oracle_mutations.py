@@ -84,18 +84,38 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_mutation(mut, tmp_path):
+def _run_mutation(mut, workdir):
+    """Build the mutated oracle and run the pins against it; True when they fail."""
     name, old, new = mut
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site not unique: {old!r}"
-    mutated = tmp_path / "oracle.c"
-    mutated.write_text(src.replace(old, new))
-    lib = tmp_path / "liboracle_mut.so"
+    os.makedirs(workdir, exist_ok=True)
+    mutated = os.path.join(workdir, "oracle.c")
+    with open(mutated, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(workdir, "liboracle_mut.so")
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
-                           "-o", str(lib), str(mutated), "-lm"])
-    env = dict(os.environ, REACH_ORACLE_LIB=str(lib))
+                           "-o", lib, mutated, "-lm"])
+    env = dict(os.environ, REACH_ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(HERE, "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+    return r.returncode != 0, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutation run once, concurrently (each is a compiler call and a
+    pytest subprocess, so threads only wait on them)."""
+    from concurrent.futures import ThreadPoolExecutor
+    base = tmp_path_factory.mktemp("mutations")
+    workers = max(1, min(len(MUTATIONS), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        futs = {m[0]: ex.submit(_run_mutation, m, str(base / f"m{k}")) for k, m in enumerate(MUTATIONS)}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("mut", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_mutation(mut, outcomes):
+    caught, log = outcomes[mut[0]]
+    assert caught, f"pins did not catch: {mut[0]}\n{log}"
