@@ -338,6 +338,37 @@ def bench_traffic_local(R, torch, dev, d, n):
     return out
 
 
+def bench_traffic_sound(R, torch, dev, d, n):
+    """Outward-rounded traffic MM and CGB (reading R15) on the headline
+    workload: time, and how far the outward box reaches beyond the
+    round-to-nearest one."""
+    stream = torch.cuda.current_stream(dev)
+    lo = torch.empty(n, dtype=torch.float64, device=dev)
+    hi = torch.empty_like(lo)
+    rlo = torch.empty_like(lo)
+    rhi = torch.empty_like(lo)
+    args = (d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"])
+    out = {"workload": f"traffic chain n={n}, outward-rounded MM and CGB, dt=0.01, T=2 (200 RK4 steps)",
+           "unit": "comp-steps/s"}
+    with R.System("traffic", n, params=(40.0, 0.5, 1.0 / 6.0, 320.0, 0, 1)) as s, R.System("traffic", n) as sr:
+        for name, fn in (("mm", R.reach_mm), ("cgb", R.reach_cgb)):
+            fn(s, *args, t_final=T_FINAL, dt=DT, lo=lo, hi=hi, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(s, *args, t_final=T_FINAL, dt=DT, lo=lo, hi=hi, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            fn(sr, *args, t_final=T_FINAL, dt=DT, lo=rlo, hi=rhi, stream=stream)
+            torch.cuda.synchronize()
+            scale = float(rhi.abs().max())
+            out[name] = {"s": sec, "value": 2 * n * NSTEPS / sec,
+                         "max_outward_excess_rel": max(float((rlo - lo).max()), float((hi - rhi).max())) / scale,
+                         "contains_nearest": bool((lo <= rlo).all() and (hi >= rhi).all())}
+    return out
+
+
 def bench_temporal_blocking(R, torch, dev):
     """RK4 steps per launch S (halo 4 R S recomputed) on traffic MM (FP64,
     n = 2^24) and on KS MC32 (n = 2^20, 256 samples): the FP64 kernels are bound
@@ -663,6 +694,7 @@ def main():
         line["heat3d"] = bench_heat(R, torch, dev)
         line["quad"] = bench_quad(R, torch, dev)
         line["traffic_cgb_local"] = bench_traffic_local(R, torch, dev, d, n)
+        line["traffic_sound"] = bench_traffic_sound(R, torch, dev, d, n)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",

@@ -103,9 +103,13 @@ typedef enum {
 /* cgb_local != 0: CGB takes the contraction matrix over the current box
    [c - r, c + r] (free-flow / congestion branches that can be, or are
    everywhere, the minimum of the flux) instead of the bounds valid for every
-   state; a struct without this last field (params_bytes = 4 doubles) is
-   accepted and means 0. */
-typedef struct { double cap, v, w, xbar; int cgb_local; } reach_traffic_params; /* 40, 0.5, 1/6, 320, 0 */
+   state.  sound != 0: MM and CGB round every operation outward, so that the
+   box contains the one the same method gives in exact real arithmetic from
+   the same binary64 inputs and step (the MM halves and the CGB center are
+   carried as intervals, the CGB radius rounded up); not with cgb_local, not
+   with reach_pipe, reach_mm_noalloc or batches, and MC ignores it.  A struct
+   of only the four doubles (params_bytes = 32) is accepted and means 0, 0. */
+typedef struct { double cap, v, w, xbar; int cgb_local; int sound; } reach_traffic_params; /* 40, 0.5, 1/6, 320, 0, 0 */
 typedef struct { double dx, g_nl, g_2, g_4; } reach_ks_params;     /* pi/4, 1, 1, 1 */
 typedef struct { double ka, kb, kc; } reach_osc_params;            /* 1, 0.1, 0.5 */
 typedef struct { const double *A; } reach_linear_params;           /* n x n, row-major */

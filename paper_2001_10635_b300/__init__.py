@@ -33,7 +33,7 @@ _lib = None
 
 class _TrafficParams(ctypes.Structure):
     _fields_ = [("cap", ctypes.c_double), ("v", ctypes.c_double), ("w", ctypes.c_double),
-                ("xbar", ctypes.c_double), ("cgb_local", ctypes.c_int)]
+                ("xbar", ctypes.c_double), ("cgb_local", ctypes.c_int), ("sound", ctypes.c_int)]
 
 
 class _HeatParams(ctypes.Structure):
@@ -172,9 +172,11 @@ class System:
             self._A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(n, n))
             buf = (ctypes.c_void_p * 1)(self._A.ctypes.data)
             nbytes = ctypes.sizeof(ctypes.c_void_p)
-        elif self.kind == TRAFFIC and params is not None and len(params) == 5:
-            cap, v, w, xbar, local = params
-            buf = ctypes.pointer(_TrafficParams(float(cap), float(v), float(w), float(xbar), int(bool(local))))
+        elif self.kind == TRAFFIC and params is not None and len(params) in (5, 6):
+            cap, v, w, xbar, local = params[:5]
+            sound = params[5] if len(params) == 6 else 0
+            buf = ctypes.pointer(_TrafficParams(float(cap), float(v), float(w), float(xbar), int(bool(local)),
+                                                int(bool(sound))))
             nbytes = ctypes.sizeof(_TrafficParams)
         elif self.kind == HEAT3D and params is not None:
             alpha, l, open_face = params

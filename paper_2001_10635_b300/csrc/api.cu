@@ -171,6 +171,9 @@ TrafficK make_traffic_k(const double *prm, double wl, double wh) {
     p.d_c = 0.5 * (wl + wh);
     p.d_r = 0.5 * (wh - wl);
     p.local = prm[4] != 0.0;
+    p.sound = prm[5] != 0.0;
+    // h / 6 rounded down and up (set per call by the caller when sound)
+    p.c6l = p.c6u = 0.0;
     return p;
 }
 
@@ -201,19 +204,21 @@ extern "C" int reach_system_create(int kind, int64_t n, const void *params, size
     double host[8] = {0};
     switch (kind) {
     case REACH_TRAFFIC: {
-        reach_traffic_params p{40.0, 0.5, 1.0 / 6.0, 320.0, 0};
+        reach_traffic_params p{40.0, 0.5, 1.0 / 6.0, 320.0, 0, 0};
         if (params) {
-            // the struct without its last field (cgb_local) is accepted too
+            // the four doubles alone are accepted too
             const size_t base = offsetof(reach_traffic_params, cgb_local);
             if (params_bytes != sizeof p && params_bytes != base) return REACH_EINVAL;
             memcpy(&p, params, params_bytes);
         }
+        if (p.cgb_local && p.sound) return REACH_EINVAL;
         if (!std::isfinite(p.cap) || !std::isfinite(p.v) || !std::isfinite(p.w) || !std::isfinite(p.xbar) ||
             p.v < 0 || p.w < 0)
             return REACH_EINVAL;
         s.nw = 1;
         host[0] = p.cap; host[1] = p.v; host[2] = p.w; host[3] = p.xbar;
         host[4] = p.cgb_local ? 1.0 : 0.0;
+        host[5] = p.sound ? 1.0 : 0.0;
         break;
     }
     case REACH_KS: {
@@ -329,6 +334,7 @@ static bool onchip_fits(const reach_system *s) {
 
 bool use_onchip(const reach_system *s) {
     if (s->kind == REACH_QUAD) return false;   // one thread per agent at every size
+    if (s->kind == REACH_TRAFFIC && s->prm[5] != 0.0) return false;   // outward rounding: streaming kernel only
     int64_t k = opt_kernel();
     bool fits = onchip_fits(s);
     if (k == 2) return fits;
@@ -432,7 +438,8 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         const int S = opt_steps() > 0 ? (int)opt_steps() : 1;
         if (sys->kind == REACH_TRAFFIC) {
             TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
-            rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+            if (p.sound) rc = stencil_traffic_sound(method, p, n, dxlo, dxhi, dlo, dhi, dt, N, S, sg);
+            else rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
         } else {
             KsK p;
             p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
@@ -520,6 +527,7 @@ extern "C" int reach_pipe(const reach_system *sys, int method, const double *x0_
                           double *pipe_lo, double *pipe_hi, void *stream) {
     if (!sys || !x0_lo || !x0_hi || !pipe_lo || !pipe_hi || (method != MM && method != CGB) || every < 1)
         return REACH_EINVAL;
+    if (sys->kind == REACH_TRAFFIC && sys->prm[5] != 0.0) return REACH_EINVAL;   // outward rounding: whole horizons
     if (sys->nw > 0 && (!w_lo || !w_hi)) return REACH_EINVAL;
     int64_t N;
     int rc = nsteps(t_final, dt, &N);

@@ -82,6 +82,8 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
                     int *status, cudaStream_t st);
 int quad_run(int method, const QuadK &p, int64_t n, const double *xlo, const double *xhi, const double *wlo,
              const double *whi, double *lo, double *hi, double h, int64_t N, int *status, cudaStream_t st);
+int stencil_traffic_sound(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+                          double *lo, double *hi, double h, int64_t N, int S, Staging &sg);
 int heat_run(int method, const HeatK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
              double *hi, double h, int64_t N, Staging &sg);
 int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,

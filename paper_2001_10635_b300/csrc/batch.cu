@@ -253,7 +253,7 @@ extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int
     b->N.resize(count);
     for (int64_t i = 0; i < count; ++i) {
         const reach_query &q = queries[i];
-        if (!q.sys || q.sys->kind == REACH_QUAD || (q.method != MM && q.method != CGB) || !q.x0_lo || !q.x0_hi || !q.lo || !q.hi ||
+        if (!q.sys || q.sys->kind == REACH_QUAD || (q.sys->kind == REACH_TRAFFIC && q.sys->prm[5] != 0.0) || (q.method != MM && q.method != CGB) || !q.x0_lo || !q.x0_hi || !q.lo || !q.hi ||
             (q.sys->nw > 0 && (!q.w_lo || !q.w_hi))) {
             destroy(b);
             return REACH_EINVAL;

@@ -22,6 +22,8 @@ struct TrafficK {
     double d_lo, d_hi;   // MM inputs (p, ph)
     double d_c, d_r;     // CGB input center and half-width
     int local;           // CGB with the box-evaluated contraction matrix
+    int sound;           // outward rounding
+    double c6l, c6u;     // h / 6 rounded down and up (outward rounding)
 };
 
 struct KsK {

@@ -49,6 +49,7 @@ extern "C" int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, co
                                 double *lo, double *hi, void *stream) {
     if (!sys || !x0_lo || !x0_hi || !lo || !hi) return REACH_EINVAL;
     if (sys->kind != REACH_TRAFFIC && sys->kind != REACH_KS) return REACH_EINVAL;
+    if (sys->kind == REACH_TRAFFIC && sys->prm[5] != 0.0) return REACH_EINVAL;   // no outward-rounded kernel here
     if (sys->n > REACH_NOALLOC_MAX_N) return REACH_EINVAL;   // larger than the fixed buffer
     if (sys->nw > 0 && (!w_lo || !w_hi)) return REACH_EINVAL;
     // no staging copies: the state vectors must already be on the device

@@ -81,6 +81,7 @@ int64_t footprint(const reach_request *r) {
     // MM / CGB: the stencil kernels keep a 2n ping-pong buffer; the heat
     // stage kernels keep the state and two stage vectors (6n)
     if (s->kind == REACH_QUAD) return b;   // registers only
+    if (s->kind == REACH_TRAFFIC && s->prm[5] != 0.0) return b + 8 * n * 8;   // interval halves, ping-pong
     return b + (s->kind == REACH_HEAT3D ? 6 : 2) * n * 8;
 }
 

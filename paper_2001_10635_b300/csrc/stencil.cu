@@ -23,6 +23,8 @@
 // which halves its registers.  The KS halves are coupled and stay together.
 #include <stdint.h>
 
+#include <cmath>
+
 #include "api_internal.cuh"
 
 namespace reach {
@@ -313,6 +315,168 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4
     if (flags) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ traffic, outward rounding
+// Every operation rounded outward (reading R15): a warp carries one half as an
+// interval [zl, zu] of binary64 numbers containing the exact-arithmetic value
+// (MM halves, CGB center) or, for the CGB radius, only its upper end (all its
+// terms are nonnegative).  The operations are the ones a plain evaluation
+// takes, each with its directed-rounding instruction: products and sums are
+// not fused, so that each result is the directed rounding of the exact one.
+struct SoundArgs {
+    const double *xlo, *xhi;
+    const double *inL[2], *inU[2];   // interval state per half (previous launch)
+    double *outL[2], *outU[2];
+    double *lo, *hi;                 // MM: written by the last launch
+    int64_t n, W, ntiles;
+    int H, S;
+    double h;
+    int first, last;
+    int *status;
+};
+
+// flux of R6 out of cell g, as an interval; y?n: the right neighbour
+__device__ __forceinline__ void flux_iv(const TrafficK &p, double yl, double yu, double yln, double yun, int64_t g,
+                                        int64_t n, double &fl, double &fu) {
+    const double vl = __dmul_rd(p.v, yl), vu = __dmul_ru(p.v, yu);
+    if (g == n - 1) {
+        fl = kmin(p.cap, vl);
+        fu = kmin(p.cap, vu);
+    } else {
+        fl = kmin(p.cap, kmin(vl, __dmul_rd(p.w, __dadd_rd(p.xbar, -yun))));
+        fu = kmin(p.cap, kmin(vu, __dmul_ru(p.w, __dadd_ru(p.xbar, -yln))));
+    }
+}
+
+template <int RADIUS>
+__device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[KC], const double (&yu)[KC],
+                                          int64_t g0, int64_t n, double dl, double du, double hp,
+                                          double (&kl)[KC], double (&ku)[KC]) {
+    double EU[KC + 2];
+    exchange<1>(yu, EU);
+    if (RADIUS) {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            double acc = (g == 0) ? hp : 0.0;
+            if (g > 0) acc = __dadd_ru(acc, __dmul_ru(p.v, EU[j]));
+            if (g < n - 1) acc = __dadd_ru(acc, __dmul_ru(p.w, EU[j + 2]));
+            ku[j] = (g < 0 || g >= n) ? 0.0 : acc;
+        }
+        return;
+    }
+    double EL[KC + 2];
+    exchange<1>(yl, EL);
+    // fluxes out of cells g0 - 1 .. g0 + KC - 1
+    double fl[KC + 1], fu[KC + 1];
+#pragma unroll
+    for (int m = 0; m <= KC; ++m) {
+        const int64_t g = g0 - 1 + m;
+        flux_iv(p, EL[m], EU[m], EL[m + 1], EU[m + 1], g, n, fl[m], fu[m]);
+        if (g == -1) { fl[m] = dl; fu[m] = du; }   // inflow of cell 0
+    }
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        const int64_t g = g0 + j;
+        const double a = __dadd_rd(fl[j], -fu[j + 1]), b = __dadd_ru(fu[j], -fl[j + 1]);
+        const bool in = g >= 0 && g < n;
+        kl[j] = in ? a : 0.0;
+        ku[j] = in ? b : 0.0;
+    }
+}
+
+template <int METHOD, int HALF>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_sound_rk4(SoundArgs a, TrafficK p) {
+    constexpr int RADIUS = (METHOD == CGB && HALF == 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t n = a.n;
+    int flags = 0;
+    // inflow of this half: MM the corner's own input, CGB the center's interval
+    double dl, du;
+    if (METHOD == MM) { dl = du = HALF ? p.d_hi : p.d_lo; }
+    else { dl = 0.5 * __dadd_rd(p.d_lo, p.d_hi); du = 0.5 * __dadd_ru(p.d_lo, p.d_hi); }
+    const double hp = 0.5 * __dadd_ru(p.d_hi, -p.d_lo);
+    const double hh = 0.5 * a.h;
+    for (int64_t t = warp; t < a.ntiles; t += nwarps) {
+        const int64_t own0 = t * a.W;
+        const int64_t g0 = own0 - a.H + (int64_t)lane * KC;
+        double zl[KC], zu[KC];
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            const bool in = g >= 0 && g < n;
+            if (a.first) {
+                const double lo = in ? __ldg(a.xlo + g) : 0.0, hi = in ? __ldg(a.xhi + g) : 0.0;
+                const bool owned = g >= own0 && g < own0 + a.W && in;
+                if (HALF == 0 && owned && !(kle(lo, hi) && kfinite(lo) && kfinite(hi))) flags |= ST_BADINPUT;
+                if (METHOD == MM) { zl[j] = zu[j] = HALF ? hi : lo; }
+                else if (HALF == 0) { zl[j] = 0.5 * __dadd_rd(lo, hi); zu[j] = 0.5 * __dadd_ru(lo, hi); }
+                else { zl[j] = 0.0; zu[j] = 0.5 * __dadd_ru(hi, -lo); }
+            } else {
+                zl[j] = (in && !RADIUS) ? __ldg(a.inL[HALF] + g) : 0.0;
+                zu[j] = in ? __ldg(a.inU[HALF] + g) : 0.0;
+            }
+        }
+        for (int s = 0; s < a.S; ++s) {
+            double yl[KC], yu[KC], al[KC], au[KC], kl[KC], ku[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) { yl[j] = zl[j]; yu[j] = zu[j]; }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                sound_rhs<RADIUS>(p, yl, yu, g0, n, dl, du, hp, kl, ku);
+                const double cs = (st == 2) ? a.h : hh;
+#pragma unroll
+                for (int j = 0; j < KC; ++j) {
+                    if (st == 0) { au[j] = ku[j]; al[j] = kl[j]; }
+                    else if (st == 3) { au[j] = __dadd_ru(au[j], ku[j]); al[j] = __dadd_rd(al[j], kl[j]); }
+                    else { au[j] = __dadd_ru(au[j], 2.0 * ku[j]); al[j] = __dadd_rd(al[j], 2.0 * kl[j]); }
+                    if (st < 3) {
+                        yu[j] = __dadd_ru(zu[j], __dmul_ru(cs, ku[j]));
+                        if (!RADIUS) yl[j] = __dadd_rd(zl[j], __dmul_rd(cs, kl[j]));
+                    }
+                }
+            }
+            // z + (h/6) acc with h/6 in [c6l, c6u]
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+                const double ql = RADIUS ? au[j] : al[j];
+                zu[j] = __dadd_ru(zu[j], __dmul_ru(dkey(au[j]) >= 0 ? p.c6u : p.c6l, au[j]));
+                if (!RADIUS) zl[j] = __dadd_rd(zl[j], __dmul_rd(dkey(ql) >= 0 ? p.c6l : p.c6u, ql));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            if (!(g >= own0 && g < own0 + a.W && g < n && g >= 0)) continue;
+            if (a.last && METHOD == MM) {
+                const double v = HALF ? zu[j] : zl[j];
+                if (!kfinite(v)) flags |= ST_NONFINITE;
+                (HALF ? a.hi : a.lo)[g] = v;
+            } else {
+                if (!RADIUS) a.outL[HALF][g] = zl[j];
+                a.outU[HALF][g] = zu[j];
+            }
+        }
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// CGB outward box: lo = (cl - ru) rounded down, hi = (cu + ru) rounded up
+__global__ void sound_cgb_box(const double *cl, const double *cu, const double *ru, double *lo, double *hi, int64_t n,
+                              int *status) {
+    int flags = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double r = ru[i];
+        if (dkey(r) < 0) flags |= ST_NEGRADIUS;
+        const double l = __dadd_rd(cl[i], -r), u = __dadd_ru(cu[i], r);
+        if (!kfinite(l) || !kfinite(u)) flags |= ST_NONFINITE;
+        lo[i] = l;
+        hi[i] = u;
+    }
+    if (flags) atomicOr(status, flags);
+}
+
 // CGB output box from the final center and radius: lo = c - r, hi = c + r
 __global__ void cgb_box(double *c_lo, double *r_hi, int64_t n, int *status) {
     int flags = 0;
@@ -519,6 +683,74 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
     if (blocks > 148 * 16) blocks = 148 * 16;
     cgb_box<<<(unsigned)blocks, 256, 0, st>>>(lo, hi, n, status);
     REACH_LAUNCHED("cgb_box");
+    return REACH_OK;
+}
+
+// h / 6 rounded down and up: q = fl(h / 6) and the exact remainder h - 6 q
+static void sixth_bounds(double h, double *dn, double *up) {
+    const double q = h / 6.0, e = std::fma(-q, 6.0, h);
+    *dn = e < 0.0 ? std::nextafter(q, -INFINITY) : q;
+    *up = e > 0.0 ? std::nextafter(q, INFINITY) : q;
+}
+
+int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const double *xlo, const double *xhi,
+                          double *lo, double *hi, double h, int64_t N, int S, Staging &sg) {
+    TrafficK p = p0;
+    sixth_bounds(h, &p.c6l, &p.c6u);
+    // two sets of interval state (lower and upper end per half)
+    double *buf;
+    int rc;
+    if ((rc = sg.scratch(8 * n * sizeof(double), (void **)&buf))) return rc;
+    double *setL[2][2], *setU[2][2];
+    for (int q = 0; q < 2; ++q)
+        for (int half = 0; half < 2; ++half) {
+            setL[q][half] = buf + (4 * q + 2 * half) * n;
+            setU[q][half] = buf + (4 * q + 2 * half + 1) * n;
+        }
+    const int64_t L = (N + S - 1) / S;
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = (int)((N - done) < S ? (N - done) : S);
+        SoundArgs a;
+        a.xlo = xlo;
+        a.xhi = xhi;
+        for (int half = 0; half < 2; ++half) {
+            a.inL[half] = setL[q % 2][half];
+            a.inU[half] = setU[q % 2][half];
+            a.outL[half] = setL[(q + 1) % 2][half];
+            a.outU[half] = setU[(q + 1) % 2][half];
+        }
+        a.lo = lo;
+        a.hi = hi;
+        a.n = n;
+        a.H = 4 * s;
+        a.W = TILE - 2 * a.H;
+        a.ntiles = (n + a.W - 1) / a.W;
+        a.S = s;
+        a.h = h;
+        a.first = q == 0;
+        a.last = q == L - 1;
+        a.status = sg.status;
+        const unsigned grid = grid_for(a.ntiles);
+        if (method == MM) {
+            stencil_traffic_sound_rk4<MM, 0><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<MM, 1><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+        } else {
+            stencil_traffic_sound_rk4<CGB, 0><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<CGB, 1><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+        }
+        REACH_LAUNCHED("stencil_traffic_sound_rk4");
+        REACH_LAUNCHED("stencil_traffic_sound_rk4");
+        done += s;
+    }
+    if (method == CGB) {
+        const int fin = (int)(L % 2);   // the set the last launch wrote
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        sound_cgb_box<<<(unsigned)blocks, 256, 0, sg.st>>>(setL[fin][0], setU[fin][0], setU[fin][1], lo, hi, n,
+                                                          sg.status);
+        REACH_LAUNCHED("sound_cgb_box");
+    }
     return REACH_OK;
 }
 
