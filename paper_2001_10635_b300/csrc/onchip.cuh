@@ -102,26 +102,29 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
         const int64_t im2 = i < 2 ? i + n - 2 : i - 2, ip2 = i >= n - 2 ? i + 2 - n : i + 2;
         const double a0 = q[0], a1 = q[1], a2 = q[2], k = q[3];
         if constexpr (METHOD == MM) {
+            // the product term of R7 is q d with q = -k u_i and d the difference
+            // at (own_{i+1}, other_{i-1}) when q >= 0, at (other_{i+1}, own_{i-1})
+            // otherwise (the stencil kernel's form)
             const double *Y = upper ? yB : yA, *O = upper ? yA : yB;   // own / other half
             const bool s1 = a1 >= 0.0, s2 = a2 >= 0.0;
             double l1 = (s1 ? Y[im1] : O[im1]) + (s1 ? Y[ip1] : O[ip1]);
             double l2 = (s2 ? Y[im2] : O[im2]) + (s2 ? Y[ip2] : O[ip2]);
-            double lin = fma(a2, l2, fma(a1, l1, a0 * Y[i]));
-            double da = Y[ip1] - O[im1], db = O[ip1] - Y[im1];
-            double qq = -k * Y[i];
-            double ea = qq * da, eb = qq * db;
-            return lin + (kle(da, db) ? kmin(ea, eb) : kmax(ea, eb));
+            const double da = Y[ip1] - O[im1], db = O[ip1] - Y[im1];
+            const bool qpos = (__double_as_longlong(k) ^ __double_as_longlong(Y[i])) < 0;
+            return fma(Y[i], fma(-k, qpos ? da : db, a0), fma(a1, l1, a2 * l2));
         } else {
             double dc = yA[ip1] - yA[im1];
+            const double t = k * yA[i];
             if (!upper) {
                 double lin = fma(a2, yA[im2] + yA[ip2], fma(a1, yA[im1] + yA[ip1], a0 * yA[i]));
-                return fma(-k * yA[i], dc, lin);
+                return fma(-t, dc, lin);
             }
-            double sr = yB[ip1] + yB[im1];
-            double cii = kmax(fma(-k, dc - sr, a0), fma(-k, dc + sr, a0));
-            double t = k * yA[i], u = kabs(k * yB[i]);
-            double cip = kabs(a1 - t) + u, cim = kabs(a1 + t) + u;
-            return fma(kabs(a2), yB[im2] + yB[ip2], fma(cip, yB[ip1], fma(cim, yB[im1], cii * yB[i])));
+            const double ak = kabs(k), sr = yB[ip1] + yB[im1];
+            const double cii = fma(ak, sr, fma(-k, dc, a0));
+            double acc = fma(kabs(a2), yB[im2] + yB[ip2], cii * yB[i]);
+            acc = fma(ak * yB[i], sr, acc);
+            acc = fma(kabs(a1 - t), yB[ip1], acc);
+            return fma(kabs(a1 + t), yB[im1], acc);
         }
     } else if constexpr (SYS == REACH_OSC) {
         // q: ka, kb, kc, ka + 2 kc, 3 kb, |kc|;  state [x_1..x_m | v_1..v_m]

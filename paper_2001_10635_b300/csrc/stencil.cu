@@ -492,15 +492,26 @@ __global__ void cgb_box(double *c_lo, double *r_hi, int64_t n, int *status) {
 }
 
 // ------------------------------------------------------------------ KS
-// MM embedding (oracle d_ks): linear stencil split by coefficient sign, the
-// product -g_nl u_i u_x bounded with u_i at its own argument over the interval
-// of u_x spanned by the neighbours.
+// MM embedding (the decomposition of R7): linear stencil split by coefficient
+// sign, the product -g_nl u_i u_x bounded with u_i at its own argument over
+// the interval of u_x spanned by the neighbours.  With q = -k u_i and the two
+// candidate differences dL (at x_{i+1}, xh_{i-1}) and dH (at xh_{i+1}, x_{i-1}),
+// the lower half takes min(q dL, q dH) when dL <= dH and the max otherwise;
+// in both cases that is q times dL when q >= 0 and dH when q < 0 (the upper
+// half likewise with the roles of dL and dH exchanged).  The sign of q is
+// read from the sign bits of k and u_i (u_i = 0 makes the term vanish either
+// way), and u_i (a0 - k d) + a1 l1 + a2 l2 takes four fused operations.
+__device__ __forceinline__ bool sign_differs(double a, double b) {
+    return (__double_as_longlong(a) ^ __double_as_longlong(b)) < 0;
+}
+
 __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], const double (&xh)[KC],
                                           double (&kx)[KC], double (&kxh)[KC]) {
     double X[KC + 4], XH[KC + 4];
     exchange<2>(x, X);
     exchange<2>(xh, XH);
     const bool s1 = p.a1 >= 0.0, s2 = p.a2 >= 0.0;
+    const double nk = -p.k;
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int c = j + 2;
@@ -508,39 +519,39 @@ __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], c
         double l2 = (s2 ? X[c - 2] : XH[c - 2]) + (s2 ? X[c + 2] : XH[c + 2]);
         double u1 = (s1 ? XH[c - 1] : X[c - 1]) + (s1 ? XH[c + 1] : X[c + 1]);
         double u2 = (s2 ? XH[c - 2] : X[c - 2]) + (s2 ? XH[c + 2] : X[c + 2]);
-        double linl = fma(p.a2, l2, fma(p.a1, l1, p.a0 * X[c]));
-        double linu = fma(p.a2, u2, fma(p.a1, u1, p.a0 * XH[c]));
-        double dL = X[c + 1] - XH[c - 1];   // 2dx * u_x at (x_{i+1}, xh_{i-1})
-        double dH = XH[c + 1] - X[c - 1];   // 2dx * u_x at (xh_{i+1}, x_{i-1})
-        double ql = -p.k * X[c], qu = -p.k * XH[c];
-        double ea = ql * dL, eb = ql * dH;
-        double fa = qu * dH, fb = qu * dL;
-        const bool lo_first = kle(dL, dH), hi_first = kle(dH, dL);
-        kx[j] = linl + (lo_first ? kmin(ea, eb) : kmax(ea, eb));
-        kxh[j] = linu + (hi_first ? kmin(fa, fb) : kmax(fa, fb));
+        const double dL = X[c + 1] - XH[c - 1];   // 2dx * u_x at (x_{i+1}, xh_{i-1})
+        const double dH = XH[c + 1] - X[c - 1];   // 2dx * u_x at (xh_{i+1}, x_{i-1})
+        // -k u >= 0 exactly when the signs of k and u differ
+        const double dl = sign_differs(p.k, X[c]) ? dL : dH;
+        const double dh = sign_differs(p.k, XH[c]) ? dH : dL;
+        kx[j] = fma(X[c], fma(nk, dl, p.a0), fma(p.a1, l1, p.a2 * l2));
+        kxh[j] = fma(XH[c], fma(nk, dh, p.a0), fma(p.a1, u1, p.a2 * u2));
     }
 }
 
 // CGB: center f(c) and radius C(c, r) r with C the supremum of the Jacobian
-// over the box [c - r, c + r]
+// over the box [c - r, c + r] (R3): C_ii = a0 - k dc + |k| (r_{i+1} + r_{i-1}),
+// C_{i,i+-1} = |a1 -+ k c_i| + |k| r_i, C_{i,i+-2} = |a2|
 __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC], const double (&rr)[KC],
                                            double (&kc)[KC], double (&kr)[KC]) {
     double C[KC + 4], Rr[KC + 4];
     exchange<2>(cc, C);
     exchange<2>(rr, Rr);
-    const double aa2 = kabs(p.a2);
+    const double aa2 = kabs(p.a2), ak = kabs(p.k), nk = -p.k;
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int c = j + 2;
-        double dc = C[c + 1] - C[c - 1];
-        double lin = fma(p.a2, C[c - 2] + C[c + 2], fma(p.a1, C[c - 1] + C[c + 1], p.a0 * C[c]));
-        kc[j] = fma(-p.k * C[c], dc, lin);
-        double sr = Rr[c + 1] + Rr[c - 1];
-        double cii = kmax(fma(-p.k, dc - sr, p.a0), fma(-p.k, dc + sr, p.a0));
-        double t = p.k * C[c], u = kabs(p.k * Rr[c]);
-        double cip = kabs(p.a1 - t) + u;   // sup |a1 - k u_i| over the box
-        double cim = kabs(p.a1 + t) + u;   // sup |a1 + k u_i|
-        kr[j] = fma(aa2, Rr[c - 2] + Rr[c + 2], fma(cip, Rr[c + 1], fma(cim, Rr[c - 1], cii * Rr[c])));
+        const double dc = C[c + 1] - C[c - 1];
+        const double t = p.k * C[c];
+        const double lin = fma(p.a2, C[c - 2] + C[c + 2], fma(p.a1, C[c - 1] + C[c + 1], p.a0 * C[c]));
+        kc[j] = fma(-t, dc, lin);
+        const double sr = Rr[c + 1] + Rr[c - 1];
+        const double cii = fma(ak, sr, fma(nk, dc, p.a0));
+        const double u = ak * Rr[c];
+        double acc = fma(aa2, Rr[c - 2] + Rr[c + 2], cii * Rr[c]);
+        acc = fma(u, sr, acc);
+        acc = fma(kabs(p.a1 - t), Rr[c + 1], acc);
+        kr[j] = fma(kabs(p.a1 + t), Rr[c - 1], acc);
     }
 }
 
