@@ -65,8 +65,8 @@ struct Plain<REACH_KS, T> {
     template <class Row>
     static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
         T um2 = row(c - 2), um1 = row(c - 1), u = row(c), up1 = row(c + 1), up2 = row(c + 2);
-        T lin = tfma(q[2], um2 + up2, tfma(q[1], um1 + up1, q[0] * u));
-        return tfma(-q[3] * u, up1 - um1, lin);
+        // u (a0 - k (u_{i+1} - u_{i-1})) + a1 (u_{i-1} + u_{i+1}) + a2 (u_{i-2} + u_{i+2})
+        return tfma(u, tfma(-q[3], up1 - um1, q[0]), tfma(q[1], um1 + up1, q[2] * (um2 + up2)));
     }
 };
 
@@ -360,8 +360,7 @@ mc_stream(McStep a, const double *__restrict__ prm) {
                     T kr;
                     if constexpr (SYS == REACH_KS) {
                         T um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
-                        T lin = tfma(q[2], um2 + up2, tfma(q[1], um1 + up1, q[0] * u));
-                        kr = tfma(-q[3] * u, up1 - um1, lin);
+                        kr = tfma(u, tfma(-q[3], up1 - um1, q[0]), tfma(q[1], um1 + up1, q[2] * (um2 + up2)));
                     } else {
                         T fout = tr_flux<T>(q, e[r + 1], e[r + 2], row0 + r, n, d);
                         kr = fprev - fout;
