@@ -4,7 +4,8 @@
 // chains (MM: lower and upper corner; CGB: center and radius) over the whole
 // horizon in registers: one launch per call, HBM touched only to read the box
 // and write the result.  The work is the trigonometric part of the
-// accelerations (FP64 sincos at each end of three angle intervals per stage),
+// accelerations (sines and cosines at each end of three angle intervals per
+// stage: a sincos per angle at the step start, the stages by angle addition),
 // which makes the kernel bound by the FP64 pipe.
 #include "api_internal.cuh"
 #include "quad.cuh"
@@ -51,16 +52,48 @@ __global__ void __launch_bounds__(128) quad_box(QuadArgs A) {
     }
     const double h = A.h;
     for (int64_t s = 0; s < A.N; ++s) {
+        // sines and cosines at the step start: MM the two chains' attitudes;
+        // CGB the center's and the two ends of the angle box
+        double sa[3], ca[3], sb[3], cb[3], sx[3], cx[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (METHOD == MM) {
+                sincos(c0.q[j], &sa[j], &ca[j]);
+                sincos(c1.q[j], &sb[j], &cb[j]);
+            } else {
+                sincos(c0.q[j], &sx[j], &cx[j]);
+                sincos(c0.q[j] - c1.q[j], &sa[j], &ca[j]);
+                sincos(c0.q[j] + c1.q[j], &sb[j], &cb[j]);
+            }
+        }
         QSums<double> m0, m1;
         // stages in a loop: the trigonometric code is large, and unrolling it
         // four times costs registers and instruction cache without adding ILP
 #pragma unroll 1
         for (int st = 0; st < 4; ++st) {
-            double q0[3], q1[3], a0[3], a1[3];
+            double q0[3], q1[3], d0[3], d1[3], a0[3], a1[3];
             stage_angles(c0, st, h, q0);
             stage_angles(c1, st, h, q1);
-            if (METHOD == MM) quad_acc_mm(q0, q1, A.p, a0, a1);
-            else quad_acc_cgb(q0, q1, A.p, a0, a1);
+            stage_deltas(c0, st, h, d0);
+            stage_deltas(c1, st, h, d1);
+            double s_a[3], c_a[3], s_b[3], c_b[3];
+            if (METHOD == MM) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    shifted_sincos(q0[j], d0[j], sa[j], ca[j], s_a[j], c_a[j]);
+                    shifted_sincos(q1[j], d1[j], sb[j], cb[j], s_b[j], c_b[j]);
+                }
+                quad_acc_mm(q0, q1, s_a, c_a, s_b, c_b, A.p, a0, a1);
+            } else {
+                double s_x[3], c_x[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    shifted_sincos(q0[j], d0[j], sx[j], cx[j], s_x[j], c_x[j]);
+                    shifted_sincos(q0[j] - q1[j], d0[j] - d1[j], sa[j], ca[j], s_a[j], c_a[j]);
+                    shifted_sincos(q0[j] + q1[j], d0[j] + d1[j], sb[j], cb[j], s_b[j], c_b[j]);
+                }
+                quad_acc_cgb(q0, q1, s_x, c_x, s_a, c_a, s_b, c_b, A.p, a0, a1);
+            }
             add_stage(m0, a0, st);
             add_stage(m1, a1, st);
         }

@@ -54,51 +54,87 @@ __device__ __forceinline__ bool holds_point(double a, double b, double c) {
     return __dadd_rn(c, __dmul_rn(Q_TWO_PI, k)) <= b;
 }
 
-// ranges of sin and cos over [lo, hi] (lo <= hi): the endpoint values, and
-// +-1 where an extremum lies inside
-__device__ __forceinline__ void iv_sincos(double lo, double hi, Iv &S, Iv &C) {
+// ranges of sin and cos over [lo, hi] (lo <= hi) from the endpoint values
+// (s0, c0 at lo; s1, c1 at hi), and +-1 where an extremum lies inside
+__device__ __forceinline__ void iv_sincos_at(double lo, double hi, double s0, double c0, double s1, double c1,
+                                             Iv &S, Iv &C) {
     if (hi - lo >= Q_TWO_PI) {
         S = {-1.0, 1.0};
         C = {-1.0, 1.0};
         return;
     }
-    double s0, c0, s1, c1;
-    sincos(lo, &s0, &c0);
-    sincos(hi, &s1, &c1);
     S.lo = holds_point(lo, hi, -Q_HALF_PI) ? -1.0 : kmin(s0, s1);
     S.hi = holds_point(lo, hi, Q_HALF_PI) ? 1.0 : kmax(s0, s1);
     C.lo = holds_point(lo, hi, Q_PI) ? -1.0 : kmin(c0, c1);
     C.hi = holds_point(lo, hi, 0.0) ? 1.0 : kmax(c0, c1);
 }
 
+// Sines and cosines at the stage angles.  The stage angle q_s = q + d_s lies
+// within a small d_s = O(h |w|) of the step-start angle, so its sine and
+// cosine follow from the step start's by the angle-addition formulas, with
+// sin d and cos d from their Maclaurin series through d^9 and d^10 (for
+// |d| <= 1/16 the first omitted terms are below 2e-21 and 1e-23, far under
+// the rounding of the result); a larger d falls back to sincos.
+constexpr double Q_SMALL = 0.0625;
+
+__device__ __forceinline__ void small_sincos(double d, double &s, double &c) {
+    const double d2 = d * d;
+    const double ps = fma(d2, fma(d2, fma(d2, 2.7557319223985893e-06, -0.0001984126984126984),
+                                  0.008333333333333333), -0.16666666666666666);
+    s = fma(d * d2, ps, d);
+    const double pc = fma(d2, fma(d2, fma(d2, fma(d2, -2.755731922398589e-07, 2.48015873015873e-05),
+                                          -0.001388888888888889), 0.041666666666666664), -0.5);
+    c = fma(d2, pc, 1.0);
+}
+
+// sin and cos of a + d from s0 = sin a, c0 = cos a (ang = a + d as rounded)
+__device__ __forceinline__ void shifted_sincos(double ang, double d, double s0, double c0, double &s, double &c) {
+    if (kabs(d) <= Q_SMALL) {
+        double sd, cd;
+        small_sincos(d, sd, cd);
+        s = fma(s0, cd, c0 * sd);
+        c = fma(c0, cd, -(s0 * sd));
+    } else {
+        sincos(ang, &s, &c);
+    }
+}
+
+// the plain accelerations from the sines and cosines of the attitude
+template <class T>
+__device__ __forceinline__ void quad_acc_trig(const T (&s)[3], const T (&c)[3], T a, T g, T (&acc)[3]) {
+    const T cs = c[0] * s[1];
+    acc[0] = a * (-(cs * c[2]) - s[0] * s[2]);
+    acc[1] = a * (-(cs * s[2]) + s[0] * c[2]);
+    acc[2] = g - a * (c[0] * c[1]);
+}
+
 // accelerations at one attitude (the plain system), in the run precision
 template <class T>
 __device__ __forceinline__ void quad_acc_point(const T (&q)[3], T a, T g, T (&acc)[3]) {
-    T sf, cf, st, ct, sp, cp;
-    if constexpr (sizeof(T) == 4) {
-        sincosf(q[0], &sf, &cf);
-        sincosf(q[1], &st, &ct);
-        sincosf(q[2], &sp, &cp);
-    } else {
-        sincos(q[0], &sf, &cf);
-        sincos(q[1], &st, &ct);
-        sincos(q[2], &sp, &cp);
+    T s[3], c[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if constexpr (sizeof(T) == 4) sincosf(q[j], &s[j], &c[j]);
+        else sincos(q[j], &s[j], &c[j]);
     }
-    const T cs = cf * st;
-    acc[0] = a * (-(cs * cp) - sf * sp);
-    acc[1] = a * (-(cs * sp) + sf * cp);
-    acc[2] = g - a * (cf * ct);
+    quad_acc_trig<T>(s, c, a, g, acc);
 }
 
 // MM: natural interval extension of the accelerations over the hull of the
-// two attitudes; the lower chain takes the lower ends, the upper chain the
-// upper ends
-__device__ __forceinline__ void quad_acc_mm(const double (&ql)[3], const double (&qh)[3], const QuadK &p,
-                                            double (&al)[3], double (&ah)[3]) {
-    Iv sf, cf, st, ct, sp, cp;
-    iv_sincos(kmin(ql[0], qh[0]), kmax(ql[0], qh[0]), sf, cf);
-    iv_sincos(kmin(ql[1], qh[1]), kmax(ql[1], qh[1]), st, ct);
-    iv_sincos(kmin(ql[2], qh[2]), kmax(ql[2], qh[2]), sp, cp);
+// two attitudes (ql, qh: the stage angles of the two chains; sl, cl, sh, ch:
+// their sines and cosines); the lower chain takes the lower ends, the upper
+// chain the upper ends
+__device__ __forceinline__ void quad_acc_mm(const double (&ql)[3], const double (&qh)[3], const double (&sl)[3],
+                                            const double (&cl)[3], const double (&sh)[3], const double (&ch)[3],
+                                            const QuadK &p, double (&al)[3], double (&ah)[3]) {
+    Iv S[3], C[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const bool ord = kle(ql[j], qh[j]);
+        if (ord) iv_sincos_at(ql[j], qh[j], sl[j], cl[j], sh[j], ch[j], S[j], C[j]);
+        else iv_sincos_at(qh[j], ql[j], sh[j], ch[j], sl[j], cl[j], S[j], C[j]);
+    }
+    const Iv &sf = S[0], &cf = C[0], &st = S[1], &ct = C[1], &sp = S[2], &cp = C[2];
     const Iv cs = iv_mul(cf, st);
     const Iv an = iv_scale(p.a, iv_add(iv_neg(iv_mul(cs, cp)), iv_neg(iv_mul(sf, sp))));
     const Iv ae = iv_scale(p.a, iv_add(iv_neg(iv_mul(cs, sp)), iv_mul(sf, cp)));
@@ -108,22 +144,26 @@ __device__ __forceinline__ void quad_acc_mm(const double (&ql)[3], const double 
     al[2] = p.g - ac.hi; ah[2] = p.g - ac.lo;
 }
 
-// CGB: the center's accelerations, and C r over the angle rows of the radius,
-// C bounding |d acc / d angle| over the box [c - r, c + r]
-__device__ __forceinline__ void quad_acc_cgb(const double (&qc)[3], const double (&qr)[3], const QuadK &p,
+// CGB: the center's accelerations (sc, cc: sines and cosines of the center's
+// attitude), and C r over the angle rows of the radius, C bounding
+// |d acc / d angle| over the box [c - r, c + r] (slo, clo, shi, chi: sines
+// and cosines at its ends)
+__device__ __forceinline__ void quad_acc_cgb(const double (&qc)[3], const double (&qr)[3], const double (&sc)[3],
+                                             const double (&cc)[3], const double (&slo)[3], const double (&clo)[3],
+                                             const double (&shi)[3], const double (&chi)[3], const QuadK &p,
                                              double (&ac)[3], double (&ar)[3]) {
-    double qq[3] = {qc[0], qc[1], qc[2]};
-    quad_acc_point<double>(qq, p.a, p.g, ac);
-    Iv sf, cf, st, ct, sp, cp;
-    iv_sincos(qc[0] - qr[0], qc[0] + qr[0], sf, cf);
-    iv_sincos(qc[1] - qr[1], qc[1] + qr[1], st, ct);
-    iv_sincos(qc[2] - qr[2], qc[2] + qr[2], sp, cp);
-    const Iv sfst = iv_mul(sf, st), cs = iv_mul(cf, st), cc = iv_mul(cf, ct);
+    quad_acc_trig<double>(sc, cc, p.a, p.g, ac);
+    Iv S[3], C[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        iv_sincos_at(qc[j] - qr[j], qc[j] + qr[j], slo[j], clo[j], shi[j], chi[j], S[j], C[j]);
+    const Iv &sf = S[0], &cf = C[0], &st = S[1], &ct = C[1], &sp = S[2], &cp = C[2];
+    const Iv sfst = iv_mul(sf, st), cs = iv_mul(cf, st), ccx = iv_mul(cf, ct);
     const double n_f = p.a * iv_mag(iv_add(iv_mul(sfst, cp), iv_neg(iv_mul(cf, sp))));
-    const double n_t = p.a * iv_mag(iv_mul(cc, cp));
+    const double n_t = p.a * iv_mag(iv_mul(ccx, cp));
     const double n_p = p.a * iv_mag(iv_add(iv_mul(cs, sp), iv_neg(iv_mul(sf, cp))));
     const double e_f = p.a * iv_mag(iv_add(iv_mul(sfst, sp), iv_mul(cf, cp)));
-    const double e_t = p.a * iv_mag(iv_mul(cc, sp));
+    const double e_t = p.a * iv_mag(iv_mul(ccx, sp));
     const double e_p = p.a * iv_mag(iv_add(iv_neg(iv_mul(cs, cp)), iv_neg(iv_mul(sf, sp))));
     const double h_f = p.a * iv_mag(iv_mul(sf, ct));
     const double h_t = p.a * iv_mag(cs);
@@ -149,6 +189,19 @@ __device__ __forceinline__ void stage_angles(const QChain<T> &c, int s, T h, T (
         else if (s == 1) q[j] = c.q[j] + hh * c.w[j];
         else if (s == 2) q[j] = c.q[j] + hh * (c.w[j] + hh * c.al[j]);
         else q[j] = c.q[j] + h * (c.w[j] + hh * c.al[j]);
+    }
+}
+
+// increment d_s of the stage angles over the step-start angles (d_0 = 0)
+template <class T>
+__device__ __forceinline__ void stage_deltas(const QChain<T> &c, int s, T h, T (&d)[3]) {
+    const T hh = T(0.5) * h;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (s == 0) d[j] = T(0);
+        else if (s == 1) d[j] = hh * c.w[j];
+        else if (s == 2) d[j] = hh * (c.w[j] + hh * c.al[j]);
+        else d[j] = h * (c.w[j] + hh * c.al[j]);
     }
 }
 
