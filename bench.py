@@ -527,23 +527,32 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
                             "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad}}
 
 
+def headline_config(n, world):
+    return {"workload": f"traffic chain n={n}, MM + CGB, dt=0.01, T=2 (200 RK4 steps each)",
+            "n": n, "rk4_steps": NSTEPS, "methods": ["mm", "cgb"],
+            "l2": "inputs larger than L2 (2 x 512 MiB state per call)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
-    """--impl reference: the oracle as it stands, timed on the host cores."""
+    """--impl reference: the oracle as it stands, timed on the host cores on a
+    bounded sample of the same workload (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     if rank != 0:
         return 0
-    rates = []
     for _ in range(max(args.warmup, 0)):
-        pass   # the oracle has no warm state; warm-up steps are not needed
+        cpu_oracle_rate()
+    rates = []
     for _ in range(args.steps):
         r, sec, cs = cpu_oracle_rate()
         rates.append(r)
     value = statistics.median(rates)
     sample = f"first {CPU_SAMPLE_CELLS} cells of the 2^26-cell chain, MM + CGB, 200 RK4 steps, per step"
     line = {"metric": "state-component RK4 updates/s", "value": value, "unit": "comp-steps/s",
-            "impl": "reference", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "traffic chain n=2^26, MM+CGB, dt=0.01, T=2 (bounded sample)"},
+            "config": headline_config(N_CELLS, world),
             "cpu_baseline": {"value": value, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "comp-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -668,10 +677,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"traffic chain n={n}, MM + CGB, dt=0.01, T=2 (200 RK4 steps each)",
-                   "n": n, "rk4_steps": NSTEPS, "methods": ["mm", "cgb"],
-                   "l2": "inputs larger than L2 (2 x 512 MiB state per call)",
-                   "parallelism": f"replicas x{world}"},
+        "config": headline_config(n, world),
         "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": mm_achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
                      "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": NCU_DRAM_BYTES_PER_CELL_LAUNCH * n,
