@@ -22,20 +22,22 @@ int cuda_fail(cudaError_t e, const char *where) {
     return REACH_ECUDA;
 }
 
-static int64_t g_opt_kernel = 0, g_opt_steps = 0, g_opt_block = 0, g_opt_batch_cpt = 0;
+// process-wide options; read by calls on any thread
+static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0};
 
 // ---------------------------------------------------------------- memory
-static bool g_pool_ready[64];
+static std::atomic<bool> g_pool_ready[64];
 
+// (setting the attribute twice from two threads is harmless)
 int pool_init() {
     int dev = 0;
     REACH_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !g_pool_ready[dev]) {
+    if (dev < 64 && !g_pool_ready[dev].load()) {
         cudaMemPool_t pool;
         REACH_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
         uint64_t thr = UINT64_MAX;   // keep freed blocks cached for the next call
         REACH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-        g_pool_ready[dev] = true;
+        g_pool_ready[dev].store(true);
     }
     return REACH_OK;
 }

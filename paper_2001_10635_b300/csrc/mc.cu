@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <atomic>
+
 #include "api_internal.cuh"
 #include "quad.cuh"
 
@@ -470,11 +472,11 @@ template <int SYS, class T>
 static int launch_onchip(const McArgs &a, cudaStream_t st) {
     int64_t nblk = (a.m + 31) / 32;
     size_t smem = (size_t)(a.n + a.nw) * 32 * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};   // idempotent: a second setter is harmless
+    if (!attr.load()) {
         int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T>);
         if (rc) return rc;
-        attr = true;
+        attr.store(true);
     }
     mc_onchip<SYS, T><<<(unsigned)nblk, MC_THREADS, smem, st>>>(a);
     REACH_LAUNCHED("mc_onchip");

@@ -5,6 +5,8 @@
 
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "api_internal.cuh"
 
 namespace reach {
@@ -23,11 +25,11 @@ __global__ void __launch_bounds__(512) onchip_single(OnItem it) {
 template <int SYS, int METHOD, int Q>
 static int launch_single_q(const OnItem &it, int threads, cudaStream_t st) {
     int64_t smem = onchip_smem_bytes(it.n, it.nw);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set{false};   // idempotent: a second setter is harmless
+    if (!attr_set.load()) {
         int rc = allow_max_dynamic_smem((const void *)onchip_single<SYS, METHOD, Q>);
         if (rc) return rc;
-        attr_set = true;
+        attr_set.store(true);
     }
     onchip_single<SYS, METHOD, Q><<<1, threads, (size_t)smem, st>>>(it);
     REACH_LAUNCHED("onchip_single");
@@ -88,11 +90,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1) onchip_singl
 
 template <int SYS, int METHOD>
 static int launch_cluster_t(const OnItem &it, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set{false};   // idempotent: a second setter is harmless
+    if (!attr_set.load()) {
         int rc = allow_max_dynamic_smem((const void *)onchip_single_cluster<SYS, METHOD>);
         if (rc) return rc;
-        attr_set = true;
+        attr_set.store(true);
     }
     onchip_single_cluster<SYS, METHOD><<<2, 512, (size_t)cluster_smem_bytes(it.n, it.nw), st>>>(it);
     REACH_LAUNCHED("onchip_single_cluster");
@@ -172,11 +174,11 @@ onchip_batch(const OnItem *__restrict__ items, const Slot *__restrict__ slots, c
 template <int SYS, int METHOD, int Q>
 static int launch_batch_t(const void *items, const void *slots, const void *bins, const void *tasks, int ntasks,
                           int *counter, uint64_t *done, int clusters, size_t smem, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set{false};   // idempotent: a second setter is harmless
+    if (!attr_set.load()) {
         int rc = allow_max_dynamic_smem((const void *)onchip_batch<SYS, METHOD, Q>);
         if (rc) return rc;
-        attr_set = true;
+        attr_set.store(true);
     }
     onchip_batch<SYS, METHOD, Q><<<2 * clusters, BATCH_THREADS, smem, st>>>((const OnItem *)items, (const Slot *)slots,
                                                                  (const Bin *)bins, (const Task *)tasks, ntasks,
