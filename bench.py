@@ -691,7 +691,9 @@ def main():
         "clocks": clk,
         "gpu_launches": int(launches),
     }
-    if not args.no_extra and n == N_CELLS:
+    # the extra sections describe single-GPU workloads: they run in the N = 1
+    # run only, so the scaling runs time the headline step and nothing else
+    if not args.no_extra and n == N_CELLS and world == 1:
         line["batched"] = bench_batched(R, torch, dev)
         line["ks"] = bench_ks(R, torch, dev)
         line["traffic16"] = bench_traffic16(R)
