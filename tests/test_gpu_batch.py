@@ -129,3 +129,31 @@ def test_every_batch_layout_matches_solo(cpt):
             assert np.array_equal(solo[0], lo) and np.array_equal(solo[1], hi)
     for s in systems.values():
         s.close()
+
+
+def test_full_osc_batch_sampled_queries_match_oracle():
+    """The benchmark's batch as it runs there: 4096 queries x (MM to T = 5,
+    CGB to T = 4), autotuned; sampled queries against the oracle."""
+    sizes = W.osc_sizes(4096, seed=0)
+    systems, queries, raw = {}, [], []
+    for k, m in enumerate(sizes):
+        q = W.osc_query(int(m), seed=1000003 + k, t_final=W.OSC_T)
+        s = systems.setdefault(int(m), R.System("osc", 2 * int(m)))
+        for method, T in (("mm", W.OSC_T), ("cgb", W.OSC_T_CGB)):
+            queries.append(dict(sys=s, method=method, x0_lo=q["x_lo"], x0_hi=q["x_hi"], w_lo=q["w_lo"],
+                                w_hi=q["w_hi"], t_final=T, dt=W.OSC_DT))
+            raw.append((method, T, q))
+    with R.Batch(queries) as b:
+        st, fin = b.run()
+        assert (st == 0).all() and (fin > 0).all()
+        big = int(np.argmax(sizes))
+        small = int(np.argmin(sizes))
+        picks = sorted({2 * big, 2 * big + 1, 2 * small, 2 * small + 1, 1, 2 * 1234, 2 * 4095 + 1, 2 * 777 + 1})
+        for i in picks:
+            method, T, q = raw[i]
+            lo, hi = b.outputs[i]
+            o = O.reach(method, "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=W.OSC_DT)
+            assert_close(lo, o[0], TOL64, f"query {i} {method} lo")
+            assert_close(hi, o[1], TOL64, f"query {i} {method} hi")
+    for s in systems.values():
+        s.close()
