@@ -346,3 +346,28 @@ def test_mc_streaming_steps_per_launch(kind, prec, S):
     tol = TOL64 if prec == 64 else TOL32
     assert_close(g[0], o[0], tol, "lo")
     assert_close(g[1], o[1], tol, "hi")
+
+
+BAD = [("traffic", 16, None), ("traffic", 3000, None), ("traffic", 3000, (40.0, 0.5, 1 / 6, 320.0, 1, 0)),
+       ("traffic", 3000, (40.0, 0.5, 1 / 6, 320.0, 0, 1)), ("ks", 64, None), ("ks", 3000, None), ("osc", 40, None),
+       ("heat", 27, (0.05, 3, 1)), ("heat", 4096, (1e-4, 16, 1)), ("quad", 120, None)]
+
+
+@pytest.mark.parametrize("kind,n,prm", BAD, ids=[f"{k}{n}{'p' if p else ''}{i}" for i, (k, n, p) in enumerate(BAD)])
+def test_every_kernel_rejects_an_inverted_box(kind, n, prm):
+    # one component with lo > hi, in host buffers: with at least one step the
+    # kernels check the box on the device and the call returns REACH_EINVAL
+    g = np.random.default_rng(n)
+    c = g.uniform(1, 2, n)
+    lo, hi = c - 0.01, c + 0.01
+    lo[n // 2], hi[n // 2] = hi[n // 2], lo[n // 2]
+    nw = {"traffic": 1, "ks": 0, "osc": n // 2, "heat": 0, "quad": n // 12 * 3}[kind]
+    wlo, whi = (np.full(nw, 35.0), np.full(nw, 45.0)) if nw else (None, None)
+    with R.System(kind, n, params=prm) as s:
+        methods = [R.reach_mm, R.reach_cgb]
+        if prm is None or kind != "traffic":
+            methods.append(lambda *a, **k: R.reach_mc(*a, **k, m=40, seed=1, precision=64))
+        for f in methods:
+            with pytest.raises(R.ReachError) as e:
+                f(s, lo, hi, wlo, whi, t_final=0.02, dt=0.01)
+            assert e.value.code == -1
