@@ -43,10 +43,31 @@ struct StepArgs {
     int S;                     // RK4 steps in this launch
     double h;
     int first, last;           // convert the input box / emit the output box
+    int vec;                   // every state pointer is 16-byte aligned: runs move as double2
     int *status;
 };
 
 // ------------------------------------------------------------------ helpers
+// A lane's KC consecutive cells start at an even cell (tile starts and halos
+// are even), so with 16-byte aligned arrays a run that lies inside [0, n)
+// moves as KC/2 double2 loads or stores.
+__device__ __forceinline__ void load_run(const double *src, int64_t g0, int64_t n, bool vec, double (&v)[KC]) {
+    if (vec && g0 >= 0 && g0 + KC <= n) {
+        const double2 *p = reinterpret_cast<const double2 *>(src + g0);
+#pragma unroll
+        for (int j = 0; j < KC / 2; ++j) {
+            const double2 t = __ldg(p + j);
+            v[2 * j] = t.x;
+            v[2 * j + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            v[j] = (g >= 0 && g < n) ? __ldg(src + g) : 0.0;
+        }
+    }
+}
 template <int R>
 __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC + 2 * R]) {
     // e[R + j] = y[j];  e[0..R-1] from lane-1, e[R+KC..] from lane+1
@@ -146,19 +167,20 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
     const int64_t own0 = t * a.W;
     const int64_t g0 = own0 - a.H + (int64_t)lane * KC;
     double z[KC];
+    if (a.first) {
+        double lo[KC], hi[KC];
+        load_run(a.inA, g0, n, a.vec, lo);
+        load_run(a.inB, g0, n, a.vec, hi);
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        const int64_t g = g0 + j;
-        const bool in = g >= 0 && g < n;
-        if (a.first) {
-            double lo = in ? __ldg(a.inA + g) : 0.0, hi = in ? __ldg(a.inB + g) : 0.0;
-            const bool owned = g >= own0 && g < own0 + a.W && in;
-            if (HALF == 0 && owned && !(kle(lo, hi) && kfinite(lo) && kfinite(hi))) flags |= ST_BADINPUT;
-            if (METHOD == MM) z[j] = HALF ? hi : lo;
-            else z[j] = HALF ? 0.5 * (hi - lo) : 0.5 * (lo + hi);
-        } else {
-            z[j] = in ? __ldg((HALF ? a.inB : a.inA) + g) : 0.0;
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            const bool owned = g >= own0 && g < own0 + a.W && g >= 0 && g < n;
+            if (HALF == 0 && owned && !(kle(lo[j], hi[j]) && kfinite(lo[j]) && kfinite(hi[j]))) flags |= ST_BADINPUT;
+            if (METHOD == MM) z[j] = HALF ? hi[j] : lo[j];
+            else z[j] = HALF ? 0.5 * (hi[j] - lo[j]) : 0.5 * (lo[j] + hi[j]);
         }
+    } else {
+        load_run(HALF ? a.inB : a.inA, g0, n, a.vec, z);
     }
     for (int s = 0; s < a.S; ++s) {
         double y[KC], acc[KC], k[KC];
@@ -174,12 +196,22 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
         rk4_update<3>(z, y, acc, k, a.h);
     }
     double *out = HALF ? a.outB : a.outA;
+    if (a.last && METHOD == MM) {
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        const int64_t g = g0 + j;
-        if (g >= own0 && g < own0 + a.W && g < n && g >= 0) {
-            if (a.last && METHOD == MM && !kfinite(z[j])) flags |= ST_NONFINITE;
-            out[g] = z[j];
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            if (g >= own0 && g < own0 + a.W && g < n && g >= 0 && !kfinite(z[j])) flags |= ST_NONFINITE;
+        }
+    }
+    if (a.vec && g0 >= own0 && g0 + KC <= own0 + a.W && g0 + KC <= n) {
+        double2 *p = reinterpret_cast<double2 *>(out + g0);
+#pragma unroll
+        for (int j = 0; j < KC / 2; ++j) p[j] = make_double2(z[2 * j], z[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            if (g >= own0 && g < own0 + a.W && g < n && g >= 0) out[g] = z[j];
         }
     }
 }
@@ -661,6 +693,10 @@ static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, dou
         a.outA = bufA[(L - 1 - q) % 2];
         a.outB = bufB[(L - 1 - q) % 2];
         a.status = status;
+        const double *ptrs[6] = {a.inA, a.inB, a.outA, a.outB, sA, sB};
+        a.vec = 1;
+        for (const double *ptr : ptrs)
+            if (reinterpret_cast<uintptr_t>(ptr) % 16) a.vec = 0;
         int rc = launch(a);
         if (rc) return rc;
         done += s;
