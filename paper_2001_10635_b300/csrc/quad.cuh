@@ -46,27 +46,43 @@ __device__ __forceinline__ Iv iv_mul(Iv a, Iv b) {
 __device__ __forceinline__ Iv iv_scale(double c, Iv a) { return {c * a.lo, c * a.hi}; }
 __device__ __forceinline__ double iv_mag(Iv a) { return kmax(kabs(a.lo), kabs(a.hi)); }
 
-// does c + 2 pi k lie in [a, b] for an integer k; rounded products and sums
-// are kept separate (no contraction) so that the decision is the same as a
-// plain IEEE evaluation of the same expression
-__device__ __forceinline__ bool holds_point(double a, double b, double c) {
-    const double k = ceil(__dmul_rn(__dsub_rn(a, c), Q_INV_TWO_PI));
-    return __dadd_rn(c, __dmul_rn(Q_TWO_PI, k)) <= b;
+constexpr double Q_THREE_HALF_PI = 4.71238898038469;
+
+// Does c + 2 pi k (c in [0, 2 pi)) lie in [a, b] for an integer k: with
+// r = a - 2 pi floor(a / 2 pi), where a falls in [0, 2 pi), the first such
+// point at or after a lies c - r beyond it (c + 2 pi - r when c < r).  r is
+// shared by the four extrema of an interval; products and sums are kept
+// separate (no contraction) so that each decision is the one a plain IEEE
+// evaluation of the same expressions takes.
+__device__ __forceinline__ double turn_position(double a) {
+    const double k = floor(__dmul_rn(a, Q_INV_TWO_PI));
+    return __dsub_rn(a, __dmul_rn(Q_TWO_PI, k));
+}
+
+template <int C_ID>
+__device__ __forceinline__ bool holds_point(double r, double w) {
+    constexpr double c = C_ID == 0 ? 0.0 : C_ID == 1 ? Q_HALF_PI : C_ID == 2 ? Q_PI : Q_THREE_HALF_PI;
+    constexpr double c2 = c + Q_TWO_PI;
+    const double d = (c >= r) ? __dsub_rn(c, r) : __dsub_rn(c2, r);
+    return d <= w;
 }
 
 // ranges of sin and cos over [lo, hi] (lo <= hi) from the endpoint values
-// (s0, c0 at lo; s1, c1 at hi), and +-1 where an extremum lies inside
+// (s0, c0 at lo; s1, c1 at hi), and +-1 where an extremum lies inside:
+// sin peaks at pi/2 and 3 pi/2, cos at 0 and pi
 __device__ __forceinline__ void iv_sincos_at(double lo, double hi, double s0, double c0, double s1, double c1,
                                              Iv &S, Iv &C) {
-    if (hi - lo >= Q_TWO_PI) {
+    const double w = hi - lo;
+    if (w >= Q_TWO_PI) {
         S = {-1.0, 1.0};
         C = {-1.0, 1.0};
         return;
     }
-    S.lo = holds_point(lo, hi, -Q_HALF_PI) ? -1.0 : kmin(s0, s1);
-    S.hi = holds_point(lo, hi, Q_HALF_PI) ? 1.0 : kmax(s0, s1);
-    C.lo = holds_point(lo, hi, Q_PI) ? -1.0 : kmin(c0, c1);
-    C.hi = holds_point(lo, hi, 0.0) ? 1.0 : kmax(c0, c1);
+    const double r = turn_position(lo);
+    S.lo = holds_point<3>(r, w) ? -1.0 : kmin(s0, s1);
+    S.hi = holds_point<1>(r, w) ? 1.0 : kmax(s0, s1);
+    C.lo = holds_point<2>(r, w) ? -1.0 : kmin(c0, c1);
+    C.hi = holds_point<0>(r, w) ? 1.0 : kmax(c0, c1);
 }
 
 // Sines and cosines at the stage angles.  The stage angle q_s = q + d_s lies
