@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
 // reduces them.
 struct McStep {
     int64_t n, M, m;          // M: padded sample count (row stride)
+    int64_t nM;               // n * M, the state size (computed on the host)
     int TC, H;                // owned rows per block, halo rows per side (4 R S)
     unsigned ntile;           // ceil(n / TC), computed on the host
     int S;                    // RK4 steps in this launch (0: only sample, t_final = 0)
@@ -298,11 +299,12 @@ mc_stream(McStep a, const double *__restrict__ prm) {
     int flags = 0;
     T d = T(0);
     if (SYS == REACH_TRAFFIC) d = as_run<T>(box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j, 0u, 1u)));
-    // Row offsets advance by additions: a 64-bit integer multiply per row would
-    // occupy this GPU's FP64 pipe, which an FP32 trajectory does not otherwise use.
-    const int64_t nM = a.n * a.M;
+    // Row offsets advance by additions, and the few products are 32 x 32 -> 64
+    // bit (n, M < 2^32): a 64-bit integer multiply would occupy this GPU's FP64
+    // pipe, which an FP32 trajectory does not otherwise use.
+    const int64_t nM = a.nM;
     const int64_t wr0 = (SYS == REACH_KS) ? wrap_index(row0, n) : row0;
-    int64_t off = wr0 * a.M + j;   // the one multiply per thread
+    int64_t off = (int64_t)(int32_t)wr0 * (int32_t)a.M + j;
     int64_t gi = wr0;              // wrapped row index
     T z[B];
 #pragma unroll
@@ -381,8 +383,9 @@ mc_stream(McStep a, const double *__restrict__ prm) {
             }
         }
     }
-    int64_t oo = row0 * a.M + j;                 // store offset of row 0 (owned rows are in range)
-    double *plo = a.plo + sb * n + row0, *phi = a.phi + sb * n + row0;
+    int64_t oo = (int64_t)(int32_t)row0 * (int32_t)a.M + j;   // store offset of row 0 (owned rows are in range)
+    const int64_t pb = (int64_t)((uint64_t)(uint32_t)sb * (uint32_t)n);
+    double *plo = a.plo + pb + row0, *phi = a.phi + pb + row0;
 #pragma unroll
     for (int r = 0; r < B; ++r, oo += a.M) {
         const int64_t g = row0 + r;
@@ -574,9 +577,12 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
     } else {
         McStep s;
         memset(&s, 0, sizeof s);
+        // the kernel forms row offsets by 32 x 32 -> 64-bit products
+        if (n > INT32_MAX - 64 || nblk * 32 > INT32_MAX) return REACH_EINVAL;
         s.n = n;
         s.m = base.m;
         s.M = nblk * 32;
+        s.nM = n * s.M;
         s.h = base.h;
         s.hh = 0.5 * base.h;
         s.h6 = base.h / 6.0;
