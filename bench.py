@@ -143,6 +143,50 @@ def cpu_oracle_rate(cells: int = CPU_SAMPLE_CELLS):
     return comp_steps / sec, sec, comp_steps
 
 
+def oracle_rates():
+    """The oracle (one host core) on bounded samples of the extra sections'
+    workloads, in each section's unit; each sample is a few seconds of CPU."""
+    import oracle as O
+    out = {}
+
+    def timed(label, comps, fn, sample):
+        t0 = time.perf_counter()
+        fn()
+        sec = time.perf_counter() - t0
+        out[label] = {"value": comps / sec, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+                      "sample": sample, "s": sec}
+
+    ks = W.ks_grid(1 << 14, t_final=0.005)
+    timed("ks_mm", 2 * (1 << 14) * 50,
+          lambda: O.reach("mm", "ks", ks["x_lo"], ks["x_hi"], t_final=0.005, dt=1e-4),
+          "KS grid n=2^14, MM, 50 steps")
+    hc = W.heat_cube(64, t_final=0.2)
+    timed("heat3d_mm", 2 * 64 ** 3 * 10,
+          lambda: O.reach("mm", "heat", hc["x_lo"], hc["x_hi"], t_final=0.2, dt=W.HEAT_DT),
+          "heat cube l=64 (the paper's alpha and region), MM, 10 steps")
+    qs = W.quad_swarm(2000, seed=0)
+    timed("quad_mm", 2 * 12 * 2000 * 200,
+          lambda: O.reach("mm", "quad", qs["x_lo"], qs["x_hi"], qs["w_lo"], qs["w_hi"], t_final=qs["t_final"],
+                          dt=qs["dt"]),
+          "quadrotor swarm K=2000, MM, 200 steps")
+    for label, prm, cells in (("traffic_cgb_local", O.TRAFFIC_LOCAL_PRM, 1 << 16),
+                              ("traffic_sound_mm", O.TRAFFIC_SOUND_PRM, 1 << 12)):
+        method = "cgb" if "cgb" in label else "mm"
+        tr = W.traffic_large(cells, seed=0)
+        timed(label, 2 * cells * 200,
+              lambda prm=prm, method=method, tr=tr: O.reach(method, "traffic", tr["x_lo"], tr["x_hi"], tr["w_lo"],
+                                                            tr["w_hi"], t_final=2.0, dt=0.01, params=prm),
+              f"traffic chain n={cells}, {method.upper()}, 200 steps")
+    sizes = W.osc_sizes(4096, seed=0)[:64]
+    def osc_subset():
+        for k, m in enumerate(sizes):
+            q = W.osc_query(int(m), seed=1000003 + k, t_final=W.OSC_T)
+            O.reach("mm", "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=W.OSC_T, dt=W.OSC_DT)
+    timed("batched_mm", sum(2 * 2 * int(m) * 1000 for m in sizes), osc_subset,
+          "the first 64 queries of the oscillator batch, MM, 1000 steps")
+    return out
+
+
 def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
@@ -704,6 +748,8 @@ def main():
         line["traffic_cgb_local"] = bench_traffic_local(R, torch, dev, d, n)
         line["traffic_sound"] = bench_traffic_sound(R, torch, dev, d, n)
     if rank == 0 and world == 1 and not args.no_cpu and n == N_CELLS:
+        if "batched" in line:
+            line["cpu_oracle_sections"] = oracle_rates()
         r, sec, cs = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {CPU_SAMPLE_CELLS} cells, MM + CGB, 200 steps ({sec:.1f} s)"}
