@@ -271,7 +271,18 @@ def bench_ks(R, torch, dev):
             fn(s, d["x_lo"], d["x_hi"], t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, **kw)
             sec = time.perf_counter() - t0
             out[name] = {"s": sec, "value": comps * N / sec, "unit": "comp-steps/s"}
+            if name in KS_FP64_OPS:
+                out[name]["fp64_frac"] = KS_FP64_OPS[name] * comps * N / sec / FP64_PEAK_OPS
+    out["fp64_ops_per_comp_step"] = KS_FP64_OPS
     return out
+
+
+# FP64 pipe operations per component-step of the KS stencil kernels: per stage
+# and component MM takes 7 (two pair sums, one difference shared by two, four
+# fused operations per half) plus the stage input and accumulator, CGB about
+# 9.5 (center 3.5, radius 6) plus those two; over four stages, minus the
+# first accumulator and the last stage input, plus the final update
+KS_FP64_OPS = {"mm": 35.0, "cgb": 45.0, "mc64_m64": 35.0}
 
 
 # FP64 pipe operations per component-step of the heat stage kernels (RK4 in
