@@ -51,6 +51,12 @@ def problem(kind, n, seed=0):
         m = n // 2
         q = W.osc_query(m, seed=seed, half_width=1e-3, t_final=1.0)
         return q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], 1.0, 0.005, None, None
+    if kind == "heat":
+        lo, hi = W.random_box(n, seed=seed, centre=(0.0, 1.0), width=(0.0, 0.1))
+        return lo, hi, None, None, 0.2, 0.02, None, None
+    if kind == "quad":
+        q = W.quad_swarm(n // 12, seed=seed, t_final=0.5)
+        return q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], 0.5, q["dt"], None, None
     A = W.linear_general(n, seed=seed, scale=0.5)
     lo, hi = W.random_box(n, seed=seed + 1)
     plo, phi = W.random_box(n, seed=seed + 2, centre=(-0.1, 0.1), width=(0.0, 0.05))
@@ -317,7 +323,7 @@ def test_ks_rotation_is_tiling_invariant(method):
 
 
 PIPE = [("traffic", 16, 1.0, 10), ("traffic", 3000, 0.5, 5), ("ks", 300, 0.004, 8), ("osc", 20, 0.5, 25),
-        ("linear", 6, 0.5, 10)]
+        ("linear", 6, 0.5, 10), ("heat", 4096, 0.2, 2), ("heat", 125, 0.2, 5), ("quad", 60, 0.5, 10)]
 
 
 @pytest.mark.parametrize("method", ["mm", "cgb"])
