@@ -373,6 +373,22 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     if (onchip && !onchip_fits(sys))
         return REACH_EINVAL;   // too large for the on-chip kernels and no streaming kernel for this kind
 
+    // the traffic streaming kernel with host buffers in and out: copies in
+    // chunks that overlap the first and last steps (the input checks run on
+    // the device as for every launch)
+    if (sys->kind == REACH_TRAFFIC && !onchip && N > 0 && sys->prm[4] == 0.0 && sys->prm[5] == 0.0 &&
+        n >= 2 * OVERLAP_CHUNKS * 256 && !is_device_ptr(x0_lo) && !is_device_ptr(x0_hi) && !is_device_ptr(lo) &&
+        !is_device_ptr(hi) && !is_device_ptr(w_lo)) {
+        const double wl = w_lo[0], wh = w_hi[0];
+        if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;
+        Staging sg((cudaStream_t)stream);
+        if ((rc = sg.begin_status())) return rc;
+        const TrafficK p = make_traffic_k(sys->prm, wl, wh);
+        const int S = opt_steps() > 0 ? (int)opt_steps() : 1;
+        if ((rc = stencil_traffic_overlap(method, p, n, x0_lo, x0_hi, lo, hi, dt, N, S, sg))) return rc;
+        return sg.finish();
+    }
+
     Staging sg((cudaStream_t)stream);
     const double *dxlo, *dxhi, *dwlo = nullptr, *dwhi = nullptr;
     double *dlo, *dhi;

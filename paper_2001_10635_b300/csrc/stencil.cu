@@ -39,6 +39,7 @@ struct StepArgs {
     int64_t n;
     int64_t W;                 // owned cells per tile = TILE - 2H
     int64_t ntiles;            // ceil(n / W), computed on the host
+    int64_t tile0, tcount;     // the tiles this launch covers (traffic: a range, for overlapped copies)
     int H;                     // halo cells per side = 4 R S
     int S;                     // RK4 steps in this launch
     double h;
@@ -221,11 +222,11 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
-    const int64_t ntiles = a.ntiles;
+    const int64_t cnt = a.tcount;
     int flags = 0;
-    for (int64_t t = warp; t < 2 * ntiles; t += nwarps) {
-        if (t < ntiles) traffic_tile<METHOD, 0, POW2>(a, p, t, lane, flags);
-        else traffic_tile<METHOD, 1, POW2>(a, p, t - ntiles, lane, flags);
+    for (int64_t t = warp; t < 2 * cnt; t += nwarps) {
+        if (t < cnt) traffic_tile<METHOD, 0, POW2>(a, p, a.tile0 + t, lane, flags);
+        else traffic_tile<METHOD, 1, POW2>(a, p, a.tile0 + t - cnt, lane, flags);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -684,6 +685,8 @@ static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, dou
         a.H = 4 * R * s;
         a.W = TILE - 2 * a.H;
         a.ntiles = (n + a.W - 1) / a.W;
+        a.tile0 = 0;
+        a.tcount = a.ntiles;
         a.S = s;
         a.h = h;
         a.first = (q == 0);
@@ -730,6 +733,210 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
     if (blocks > 148 * 16) blocks = 148 * 16;
     cgb_box<<<(unsigned)blocks, 256, 0, st>>>(lo, hi, n, status);
     REACH_LAUNCHED("cgb_box");
+    return REACH_OK;
+}
+
+// Host buffers in and out: the input box goes to the device in chunks on a
+// second stream, the first launch runs chunk by chunk behind those copies
+// (chunk c waits for c + 1, which holds its right halo), and the last launch
+// sends each chunk's result back while the next chunk computes, so the
+// copies overlap the first and last RK4 steps instead of preceding and
+// following the whole run.
+namespace {
+struct CopyLane {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[2 * OVERLAP_CHUNKS] = {};
+    int nev = 0;
+    ~CopyLane() {
+        for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+}  // namespace
+
+int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const double *hxlo, const double *hxhi,
+                            double *hlo, double *hhi, double h, int64_t N, int S, Staging &sg) {
+    constexpr int C = OVERLAP_CHUNKS;
+    double *buf;
+    int rc;
+    const int64_t np = (n + 1) & ~(int64_t)1;   // even stride: every vector starts on 16 bytes
+    if ((rc = sg.scratch(6 * np * sizeof(double), (void **)&buf))) return rc;
+    double *dxlo = buf, *dxhi = buf + np, *dlo = buf + 2 * np, *dhi = buf + 3 * np, *sA = buf + 4 * np,
+           *sB = buf + 5 * np;
+    CopyLane cl;
+    REACH_CUDA(cudaStreamCreateWithFlags(&cl.cs, cudaStreamNonBlocking));
+    for (int i = 0; i < 2 * C; ++i) {
+        REACH_CUDA(cudaEventCreateWithFlags(&cl.ev[i], cudaEventDisableTiming));
+        cl.nev = i + 1;
+    }
+    cudaEvent_t *ein = cl.ev, *eout = cl.ev + C;
+    const cudaStream_t st = sg.st;
+    // the copy stream starts after the work already queued on the call's stream
+    REACH_CUDA(cudaEventRecord(eout[0], st));
+    REACH_CUDA(cudaStreamWaitEvent(cl.cs, eout[0], 0));
+
+    const int64_t L = (N + S - 1) / S;
+    const bool pw = p.v_pow2 != 0;
+    auto launch = [&](const StepArgs &b) {
+        const unsigned grid = grid_for(2 * b.tcount);
+        if (method == MM && pw) stencil_traffic_rk4<MM, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
+        else if (method == MM) stencil_traffic_rk4<MM, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
+        else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
+        else stencil_traffic_rk4<CGB, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
+        REACH_LAUNCHED("stencil_traffic_rk4");
+    };
+    if (N % S == 0 && L >= 2 * C) {
+        // Wavefront at both ends: the first C launches and the last C launches
+        // run chunk by chunk, the launches between them whole.  Within an end,
+        // launch q's chunk c reads chunks c - 1 .. c + 1 of launch q - 1's
+        // output and is issued on diagonal q + c, earlier launches first within
+        // a diagonal, so chunk c + 1 of launch q - 1 (same diagonal, smaller q)
+        // precedes it; launch q + 1 overwrites chunk c of launch q's input on
+        // diagonal q + c + 1, after all of its readers (launch q, chunks
+        // c - 1 .. c + 1).  Everything is on one stream.  The input copies then
+        // overlap the first diagonals, and chunk c of the last launch completes
+        // early, its copy back overlapping the rest of the end.
+        StepArgs a;
+        a.n = n;
+        a.H = 4 * S;
+        a.W = TILE - 2 * a.H;
+        a.ntiles = (n + a.W - 1) / a.W;
+        a.S = S;
+        a.h = h;
+        a.status = sg.status;
+        a.vec = (reinterpret_cast<uintptr_t>(buf) % 16) == 0;   // one allocation, even strides
+        double *bufA[2] = {dlo, sA}, *bufB[2] = {dhi, sB};
+        auto tile_at = [&](int c) { return a.ntiles * c / C; };
+        auto args_for = [&](int64_t q) {
+            StepArgs b = a;
+            b.first = (q == 0);
+            b.last = (q == L - 1);
+            b.inA = (q == 0) ? dxlo : bufA[(L - q) % 2];
+            b.inB = (q == 0) ? dxhi : bufB[(L - q) % 2];
+            b.outA = bufA[(L - 1 - q) % 2];
+            b.outB = bufB[(L - 1 - q) % 2];
+            b.tile0 = 0;
+            b.tcount = a.ntiles;
+            return b;
+        };
+        for (int c = 0; c < C; ++c) {
+            const int64_t c0 = tile_at(c) * a.W, c1 = std::min<int64_t>(tile_at(c + 1) * a.W, n);
+            REACH_CUDA(cudaMemcpyAsync(dxlo + c0, hxlo + c0, (c1 - c0) * sizeof(double), cudaMemcpyHostToDevice,
+                                       cl.cs));
+            REACH_CUDA(cudaMemcpyAsync(dxhi + c0, hxhi + c0, (c1 - c0) * sizeof(double), cudaMemcpyHostToDevice,
+                                       cl.cs));
+            REACH_CUDA(cudaEventRecord(ein[c], cl.cs));
+        }
+        // launches [q0, q0 + C) in wavefront order
+        auto wavefront = [&](int64_t q0) -> int {
+            for (int64_t d = 0; d < 2 * C - 1; ++d) {
+                const int64_t qlo = d - (C - 1) > 0 ? d - (C - 1) : 0, qhi = d < C - 1 ? d : C - 1;
+                for (int64_t dq = qlo; dq <= qhi; ++dq) {
+                    const int64_t q = q0 + dq;
+                    const int c = (int)(d - dq);
+                    StepArgs b = args_for(q);
+                    b.tile0 = tile_at(c);
+                    b.tcount = tile_at(c + 1) - b.tile0;
+                    if (q == 0) REACH_CUDA(cudaStreamWaitEvent(st, ein[c + 1 < C ? c + 1 : C - 1], 0));
+                    launch(b);
+                    if (q == L - 1) {
+                        const int64_t c0 = b.tile0 * a.W, c1 = std::min<int64_t>((b.tile0 + b.tcount) * a.W, n);
+                        if (method == CGB) {
+                            int64_t blocks = (c1 - c0 + 255) / 256;
+                            if (blocks > 148 * 16) blocks = 148 * 16;
+                            cgb_box<<<(unsigned)blocks, 256, 0, st>>>(dlo + c0, dhi + c0, c1 - c0, sg.status);
+                            REACH_LAUNCHED("cgb_box");
+                        }
+                        REACH_CUDA(cudaEventRecord(eout[c], st));
+                        REACH_CUDA(cudaStreamWaitEvent(cl.cs, eout[c], 0));
+                        REACH_CUDA(cudaMemcpyAsync(hlo + c0, dlo + c0, (c1 - c0) * sizeof(double),
+                                                   cudaMemcpyDeviceToHost, cl.cs));
+                        REACH_CUDA(cudaMemcpyAsync(hhi + c0, dhi + c0, (c1 - c0) * sizeof(double),
+                                                   cudaMemcpyDeviceToHost, cl.cs));
+                    }
+                }
+            }
+            return REACH_OK;
+        };
+        if ((rc = wavefront(0))) return rc;
+        for (int64_t q = C; q < L - C; ++q) launch(args_for(q));
+        if ((rc = wavefront(L - C))) return rc;
+        REACH_CUDA(cudaEventRecord(eout[0], cl.cs));
+        REACH_CUDA(cudaStreamWaitEvent(st, eout[0], 0));
+        REACH_CUDA(cudaStreamSynchronize(cl.cs));
+        return REACH_OK;
+    }
+    // few launches, or launches of unequal length (N not a multiple of S): only
+    // the first and the last launch run chunk by chunk
+    double *bufA[2] = {dlo, sA}, *bufB[2] = {dhi, sB};
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = (int)((N - done) < S ? (N - done) : S);
+        StepArgs a;
+        a.n = n;
+        a.H = 4 * s;
+        a.W = TILE - 2 * a.H;
+        a.ntiles = (n + a.W - 1) / a.W;
+        a.tile0 = 0;
+        a.tcount = a.ntiles;
+        a.S = s;
+        a.h = h;
+        a.first = (q == 0);
+        a.last = (q == L - 1);
+        a.inA = (q == 0) ? dxlo : bufA[(L - q) % 2];
+        a.inB = (q == 0) ? dxhi : bufB[(L - q) % 2];
+        a.outA = bufA[(L - 1 - q) % 2];
+        a.outB = bufB[(L - 1 - q) % 2];
+        a.status = sg.status;
+        a.vec = (reinterpret_cast<uintptr_t>(buf) % 16) == 0;   // one allocation, even strides
+        if (!a.first && !a.last) {
+            launch(a);
+            done += s;
+            continue;
+        }
+        // chunk c: tiles [t0, t1), cells [t0 W, t1 W) of the output and of the input copy
+        auto tile_at = [&](int c) { return a.ntiles * c / C; };
+        if (a.first) {
+            for (int c = 0; c < C; ++c) {
+                const int64_t c0 = tile_at(c) * a.W, c1 = std::min<int64_t>(tile_at(c + 1) * a.W, n);
+                if (c1 > c0) {
+                    REACH_CUDA(cudaMemcpyAsync(dxlo + c0, hxlo + c0, (c1 - c0) * sizeof(double),
+                                               cudaMemcpyHostToDevice, cl.cs));
+                    REACH_CUDA(cudaMemcpyAsync(dxhi + c0, hxhi + c0, (c1 - c0) * sizeof(double),
+                                               cudaMemcpyHostToDevice, cl.cs));
+                }
+                REACH_CUDA(cudaEventRecord(ein[c], cl.cs));
+            }
+        }
+        for (int c = 0; c < C; ++c) {
+            StepArgs b = a;
+            b.tile0 = tile_at(c);
+            b.tcount = tile_at(c + 1) - b.tile0;
+            if (a.first) REACH_CUDA(cudaStreamWaitEvent(st, ein[c + 1 < C ? c + 1 : C - 1], 0));
+            if (b.tcount > 0) launch(b);
+            if (a.last) {
+                const int64_t c0 = b.tile0 * a.W, c1 = std::min<int64_t>((b.tile0 + b.tcount) * a.W, n);
+                if (c1 <= c0) continue;
+                if (method == CGB) {
+                    int64_t blocks = (c1 - c0 + 255) / 256;
+                    if (blocks > 148 * 16) blocks = 148 * 16;
+                    cgb_box<<<(unsigned)blocks, 256, 0, st>>>(dlo + c0, dhi + c0, c1 - c0, sg.status);
+                    REACH_LAUNCHED("cgb_box");
+                }
+                REACH_CUDA(cudaEventRecord(eout[c], st));
+                REACH_CUDA(cudaStreamWaitEvent(cl.cs, eout[c], 0));
+                REACH_CUDA(cudaMemcpyAsync(hlo + c0, dlo + c0, (c1 - c0) * sizeof(double), cudaMemcpyDeviceToHost,
+                                           cl.cs));
+                REACH_CUDA(cudaMemcpyAsync(hhi + c0, dhi + c0, (c1 - c0) * sizeof(double), cudaMemcpyDeviceToHost,
+                                           cl.cs));
+            }
+        }
+        done += s;
+    }
+    // the call's stream waits for the copies back, so the caller's stream order holds
+    REACH_CUDA(cudaEventRecord(eout[0], cl.cs));
+    REACH_CUDA(cudaStreamWaitEvent(st, eout[0], 0));
+    REACH_CUDA(cudaStreamSynchronize(cl.cs));
     return REACH_OK;
 }
 

@@ -377,3 +377,23 @@ def test_every_kernel_rejects_an_inverted_box(kind, n, prm):
             with pytest.raises(R.ReachError) as e:
                 f(s, lo, hi, wlo, whi, t_final=0.02, dt=0.01)
             assert e.value.code == -1
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("T,S", [(0.01, 1), (0.05, 1), (0.05, 3), (0.07, 2), (0.16, 1), (0.2, 1), (0.4, 2)])
+def test_host_buffer_overlap_path(method, T, S):
+    # host buffers in and out take the path that overlaps the copies with the
+    # first and last launches; it must give the oracle's box and, bit for bit,
+    # the box of the same call on device buffers
+    import torch
+    n = 20011
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    lo, hi, wlo, whi, _, dt, _, _ = problem("traffic", n, seed=77)
+    o = O.reach(method, "traffic", lo, hi, wlo, whi, t_final=T, dt=dt)
+    g = gpu_box(method, "traffic", n, lo, hi, wlo, whi, T, dt)
+    assert_close(g[0], o[0], TOL64, "lo")
+    assert_close(g[1], o[1], TOL64, "hi")
+    d = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in (lo, hi, wlo, whi)]
+    gd = gpu_box(method, "traffic", n, *d, T, dt)
+    np.testing.assert_array_equal(g[0], gd[0].cpu().numpy())
+    np.testing.assert_array_equal(g[1], gd[1].cpu().numpy())
