@@ -29,7 +29,7 @@ TRAFFIC, KS, OSC, LINEAR, HEAT, QUAD = 0, 1, 2, 3, 4, 5
 METHODS = {"mm": MM, "cgb": CGB, "mc": MC}
 KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT, "quad": QUAD}
 
-# default parameters (BASELINE workloads): traffic (c, v, w, xbar); KS (dx, g_nl,
+# default parameters of the benchmark workloads: traffic (c, v, w, xbar); KS (dx, g_nl,
 # g_2, g_4); oscillator (ka, kb, kc)
 TRAFFIC_PRM = (40.0, 0.5, 1.0 / 6.0, 320.0)
 # the same with the box-evaluated CGB contraction matrix (reading R14)

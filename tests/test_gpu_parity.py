@@ -115,7 +115,7 @@ def test_device_pointers_match_host_pointers():
     assert np.array_equal(a[0], b[0].cpu().numpy()) and np.array_equal(a[1], b[1].cpu().numpy())
 
 
-# ------------------------------------------------------------------ traffic, n = 16 (BASELINE config 0)
+# ------------------------------------------------------------------ traffic, n = 16 (the small chain)
 def test_traffic16_all_methods():
     wl = W.traffic_small(16)
     args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
