@@ -83,8 +83,9 @@ struct Plain<REACH_OSC, T> {
         const int j = c - m;
         T z = row(j);
         T xl = (j > 0) ? row(j - 1) : T(0), xr = (j < m - 1) ? row(j + 1) : T(0);
-        T t = tfma(q[1] * z, z, q[0]);
-        T r = tfma(q[2], tfma(T(-2), z, xl + xr), P[j * 32 + lane]);
+        // -(ka + 2kc + kb z^2) z + kc (xl + xr) + w
+        T t = tfma(q[1], z * z, q[3]);
+        T r = tfma(q[2], xl + xr, P[j * 32 + lane]);
         return tfma(-t, z, r);
     }
 };
@@ -128,6 +129,7 @@ __device__ __forceinline__ void mc_consts(const double *prm, T (&q)[4]) {
     if (SYS == REACH_TRAFFIC) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)(prm[2] * prm[3]); }
     if (SYS == REACH_KS) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; q[3] = (T)prm[3]; }
     if (SYS == REACH_OSC || SYS == REACH_HEAT3D) { q[0] = (T)prm[0]; q[1] = (T)prm[1]; q[2] = (T)prm[2]; }
+    if (SYS == REACH_OSC) q[3] = (T)(prm[0] + 2.0 * prm[2]);
 }
 
 // sample value rounded to the run precision (binary32 runs start from the

@@ -136,8 +136,9 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             double z = O[j];   // x_j enters the v_j row through the hatted argument
             double xl = (j > 0) ? Y[j - 1] : 0.0, xr = (j < m - 1) ? Y[j + 1] : 0.0;
             double w = upper ? wB[j] : wA[j];
-            double t = fma(q[1] * z, z, q[0]);                 // ka + kb z^2
-            double r = fma(q[2], fma(-2.0, z, xl + xr), w);    // kc (xl - 2z + xr) + w
+            // -(ka + kb z^2) z + kc (xl - 2z + xr) + w = -(ka + 2kc + kb z^2) z + kc (xl + xr) + w
+            double t = fma(q[1], z * z, q[3]);
+            double r = fma(q[2], xl + xr, w);
             return fma(-t, z, r);
         } else {
             if (!upper) {
@@ -145,8 +146,8 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                 const int64_t j = i - m;
                 double z = yA[j];
                 double xl = (j > 0) ? yA[j - 1] : 0.0, xr = (j < m - 1) ? yA[j + 1] : 0.0;
-                double t = fma(q[1] * z, z, q[0]);
-                double r = fma(q[2], fma(-2.0, z, xl + xr), wA[j]);
+                double t = fma(q[1], z * z, q[3]);
+                double r = fma(q[2], xl + xr, wA[j]);
                 return fma(-t, z, r);
             }
             if (i < m) return yB[m + i];
