@@ -279,10 +279,10 @@ def bench_ks(R, torch, dev):
 
 # FP64 pipe operations per component-step of the KS stencil kernels: per stage
 # and component MM takes 7 (two pair sums, one difference shared by two, four
-# fused operations per half) plus the stage input and accumulator, CGB 10
-# (center 4, radius 6) plus those two; over four stages, minus the first
+# fused operations per half) plus the stage input and accumulator, CGB 9
+# (center 4, radius 5) plus those two; over four stages, minus the first
 # accumulator and the last stage input, plus the final update
-KS_FP64_OPS = {"mm": 35.0, "cgb": 47.0, "mc64_m64": 35.0}
+KS_FP64_OPS = {"mm": 35.0, "cgb": 43.0, "mc64_m64": 35.0}
 
 
 # FP64 pipe operations per component-step of the heat stage kernels (RK4 in

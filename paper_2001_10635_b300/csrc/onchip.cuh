@@ -119,10 +119,10 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                 double lin = fma(a2, yA[im2] + yA[ip2], fma(a1, yA[im1] + yA[ip1], a0 * yA[i]));
                 return fma(-t, dc, lin);
             }
+            // C_ii r_i + |k| r_i (r_{i+1} + r_{i-1}) = r_i (a0 - k dc + 2 |k| sr)
             const double ak = kabs(k), sr = yB[ip1] + yB[im1];
-            const double cii = fma(ak, sr, fma(-k, dc, a0));
-            double acc = fma(kabs(a2), yB[im2] + yB[ip2], cii * yB[i]);
-            acc = fma(ak * yB[i], sr, acc);
+            const double e = fma(2.0 * ak, sr, fma(-k, dc, a0));
+            double acc = fma(kabs(a2), yB[im2] + yB[ip2], e * yB[i]);
             acc = fma(kabs(a1 - t), yB[ip1], acc);
             return fma(kabs(a1 + t), yB[im1], acc);
         }

@@ -564,7 +564,8 @@ __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], c
 
 // CGB: center f(c) and radius C(c, r) r with C the supremum of the Jacobian
 // over the box [c - r, c + r] (R3): C_ii = a0 - k dc + |k| (r_{i+1} + r_{i-1}),
-// C_{i,i+-1} = |a1 -+ k c_i| + |k| r_i, C_{i,i+-2} = |a2|
+// C_{i,i+-1} = |a1 -+ k c_i| + |k| r_i, C_{i,i+-2} = |a2|; the two |k| r_i r_{i+-1}
+// terms fold into the diagonal's factor
 __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC], const double (&rr)[KC],
                                            double (&kc)[KC], double (&kr)[KC]) {
     double C[KC + 4], Rr[KC + 4];
@@ -578,11 +579,10 @@ __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC],
         const double t = p.k * C[c];
         const double lin = fma(p.a2, C[c - 2] + C[c + 2], fma(p.a1, C[c - 1] + C[c + 1], p.a0 * C[c]));
         kc[j] = fma(-t, dc, lin);
+        // C_ii r_i + |k| r_i (r_{i+1} + r_{i-1}) = r_i (a0 - k dc + 2 |k| sr)
         const double sr = Rr[c + 1] + Rr[c - 1];
-        const double cii = fma(ak, sr, fma(nk, dc, p.a0));
-        const double u = ak * Rr[c];
-        double acc = fma(aa2, Rr[c - 2] + Rr[c + 2], cii * Rr[c]);
-        acc = fma(u, sr, acc);
+        const double e = fma(2.0 * ak, sr, fma(nk, dc, p.a0));
+        double acc = fma(aa2, Rr[c - 2] + Rr[c + 2], e * Rr[c]);
         acc = fma(kabs(p.a1 - t), Rr[c + 1], acc);
         kr[j] = fma(kabs(p.a1 + t), Rr[c - 1], acc);
     }
