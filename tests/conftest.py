@@ -9,3 +9,11 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (runs on the B300 box)")
     config.addinivalue_line("markers", "slow: long-running CPU case")
+
+
+def pytest_sessionstart(session):
+    # the tests load the in-tree libreach.so: build it when it is missing or
+    # older than its sources (a no-op otherwise); the package itself never
+    # falls back when it is absent
+    from paper_2001_10635_b300 import build as B
+    B.build()
