@@ -14,6 +14,9 @@ def pytest_configure(config):
 def pytest_sessionstart(session):
     # the tests load the in-tree libreach.so: build it when it is missing or
     # older than its sources (a no-op otherwise); the package itself never
-    # falls back when it is absent
+    # falls back when it is absent.  Parallel workers leave it to the main
+    # process, which starts first.
+    if hasattr(session.config, "workerinput"):
+        return
     from paper_2001_10635_b300 import build as B
     B.build()
