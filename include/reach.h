@@ -136,10 +136,11 @@ REACH_API int64_t reach_input_dim(const reach_system *sys);
    system [x; xh]' = [d(x, p, xh, ph); d(xh, ph, x, p)] from
    [x0_lo; x0_hi] with p = w_lo, ph = w_hi and returns [lo, hi] = [x(T), xh(T)].
    The decomposition function d of each built-in system is the tight one:
-   cooperative traffic uses d = f; KS splits the linear stencil by coefficient
-   sign and bounds u_i u_x with u_i held at its own argument; the oscillator
-   feeds x_i into the v_i row through the hatted argument; linear splits
-   off-diagonal entries of A by sign.
+   cooperative traffic and heat use d = f; KS splits the linear stencil by
+   coefficient sign and bounds u_i u_x with u_i held at its own argument; the
+   oscillator feeds x_i into the v_i row through the hatted argument; linear
+   splits off-diagonal entries of A by sign; the quadrotor bounds its
+   accelerations by their natural interval extension over the angle box.
    x0_lo, x0_hi, lo, hi: n values.  w_lo, w_hi: nw values (may be NULL if
    nw = 0).  lo/hi may not alias x0_lo/x0_hi. */
 REACH_API int reach_mm(const reach_system *sys, const double *x0_lo, const double *x0_hi,
@@ -152,8 +153,10 @@ REACH_API int reach_mm(const reach_system *sys, const double *x0_lo, const doubl
    p* = (w_lo + w_hi)/2, [p] = (w_hi - w_lo)/2 (entering as the input enters
    f), and returns [lo, hi] = [c(T) - r(T), c(T) + r(T)].  C satisfies
    C_ii >= J_ii and C_ij >= |J_ij|: a constant bound valid for every state
-   (traffic, linear) or the supremum of the Jacobian over the current stage
-   box [c - r, c + r] (KS, oscillator).  Arguments as reach_mm. */
+   (traffic by default, linear, heat with C = A) or a bound over the current
+   stage box [c - r, c + r] (KS and oscillator: the supremum of the Jacobian;
+   quadrotor: its natural interval extension; traffic with cgb_local).
+   Arguments as reach_mm. */
 REACH_API int reach_cgb(const reach_system *sys, const double *x0_lo, const double *x0_hi,
               const double *w_lo, const double *w_hi, double t_final, double dt,
               double *lo, double *hi, void *stream);
