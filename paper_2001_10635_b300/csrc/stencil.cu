@@ -784,6 +784,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
         else stencil_traffic_rk4<CGB, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
         REACH_LAUNCHED("stencil_traffic_rk4");
+        return REACH_OK;
     };
     if (N % S == 0 && L >= 2 * C) {
         // Wavefront at both ends: the first C launches and the last C launches
@@ -838,7 +839,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
                     b.tile0 = tile_at(c);
                     b.tcount = tile_at(c + 1) - b.tile0;
                     if (q == 0) REACH_CUDA(cudaStreamWaitEvent(st, ein[c + 1 < C ? c + 1 : C - 1], 0));
-                    launch(b);
+                    if ((rc = launch(b))) return rc;
                     if (q == L - 1) {
                         const int64_t c0 = b.tile0 * a.W, c1 = std::min<int64_t>((b.tile0 + b.tcount) * a.W, n);
                         if (method == CGB) {
@@ -859,7 +860,8 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
             return REACH_OK;
         };
         if ((rc = wavefront(0))) return rc;
-        for (int64_t q = C; q < L - C; ++q) launch(args_for(q));
+        for (int64_t q = C; q < L - C; ++q)
+            if ((rc = launch(args_for(q)))) return rc;
         if ((rc = wavefront(L - C))) return rc;
         REACH_CUDA(cudaEventRecord(eout[0], cl.cs));
         REACH_CUDA(cudaStreamWaitEvent(st, eout[0], 0));
@@ -890,7 +892,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         a.status = sg.status;
         a.vec = (reinterpret_cast<uintptr_t>(buf) % 16) == 0;   // one allocation, even strides
         if (!a.first && !a.last) {
-            launch(a);
+            if ((rc = launch(a))) return rc;
             done += s;
             continue;
         }
@@ -913,7 +915,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
             b.tile0 = tile_at(c);
             b.tcount = tile_at(c + 1) - b.tile0;
             if (a.first) REACH_CUDA(cudaStreamWaitEvent(st, ein[c + 1 < C ? c + 1 : C - 1], 0));
-            if (b.tcount > 0) launch(b);
+            if (b.tcount > 0 && (rc = launch(b))) return rc;
             if (a.last) {
                 const int64_t c0 = b.tile0 * a.W, c1 = std::min<int64_t>((b.tile0 + b.tcount) * a.W, n);
                 if (c1 <= c0) continue;
