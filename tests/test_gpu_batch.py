@@ -157,3 +157,32 @@ def test_full_osc_batch_sampled_queries_match_oracle():
             assert_close(hi, o[1], TOL64, f"query {i} {method} hi")
     for s in systems.values():
         s.close()
+
+
+def test_heat_cubes_in_a_batch():
+    # heat cubes of several sides (one block, and l = 18: 2n = 11664 on a
+    # cluster) in one batch, both methods, against the oracle; the quadrotor
+    # swarm is rejected (one call already runs every agent in one launch)
+    qs, expect, systems = [], [], []
+    T, dt = 0.2, 0.02
+    for l, seed in ((3, 1), (7, 2), (12, 3), (18, 4)):
+        lo, hi = W.random_box(l ** 3, seed=seed, centre=(0.0, 1.0), width=(0.0, 0.1))
+        prm = (0.3 / (6 * dt * l * l), l, 1)
+        s = R.System("heat", l ** 3, params=prm)
+        systems.append(s)
+        for method in ("mm", "cgb"):
+            qs.append(dict(sys=s, method=method, x0_lo=lo, x0_hi=hi, t_final=T, dt=dt))
+            expect.append(O.reach(method, "heat", lo, hi, t_final=T, dt=dt, params=prm))
+    with R.Batch(qs) as b:
+        st, _ = b.run()
+        assert (st == 0).all()
+        for (lo, hi), o in zip(b.outputs, expect):
+            assert_close(lo, o[0], TOL64, "lo")
+            assert_close(hi, o[1], TOL64, "hi")
+    q = W.quad_swarm(2, seed=1)
+    with R.System("quad", 24) as sq:
+        with pytest.raises(R.ReachError):
+            R.Batch([dict(sys=sq, method="mm", x0_lo=q["x_lo"], x0_hi=q["x_hi"], w_lo=q["w_lo"], w_hi=q["w_hi"],
+                          t_final=0.1, dt=0.01)])
+    for s in systems:
+        s.close()
