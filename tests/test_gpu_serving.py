@@ -86,3 +86,38 @@ def test_bounded_wait_times_out_and_the_request_still_completes():
         assert e.value.code == -5
         st, _, run_s = srv.wait(t, timeout_s=300)
         assert st == 0 and run_s > 0 and np.isfinite(lo).all()
+
+
+def test_heat_quad_and_outward_rounded_requests_in_the_mix():
+    # the other kinds through the server, submitted together: each result
+    # equals the same call made alone (bit for bit: same kernels, same inputs)
+    hc = W.heat_cube(20, t_final=0.2)
+    qs = W.quad_swarm(300, seed=2, t_final=0.3)
+    tr = W.traffic_large(9000, seed=4, t_final=0.3)
+    systems = {"heat": R.System("heat", 20 ** 3), "quad": R.System("quad", 3600),
+               "sound": R.System("traffic", 9000, params=(40.0, 0.5, 1 / 6, 320.0, 0, 1)),
+               "local": R.System("traffic", 9000, params=(40.0, 0.5, 1 / 6, 320.0, 1, 0))}
+    jobs = []
+    for method in ("mm", "cgb"):
+        jobs.append(("heat", method, (hc["x_lo"], hc["x_hi"], None, None), 0.2, 0.02))
+        jobs.append(("quad", method, (qs["x_lo"], qs["x_hi"], qs["w_lo"], qs["w_hi"]), 0.3, 0.01))
+        jobs.append(("sound", method, (tr["x_lo"], tr["x_hi"], tr["w_lo"], tr["w_hi"]), 0.3, 0.01))
+    jobs.append(("local", "cgb", (tr["x_lo"], tr["x_hi"], tr["w_lo"], tr["w_hi"]), 0.3, 0.01))
+    jobs.append(("quad", "mc", (qs["x_lo"], qs["x_hi"], qs["w_lo"], qs["w_hi"]), 0.3, 0.01))
+    with R.Server(slots=4, hbm_budget_bytes=4 << 30) as srv:
+        tickets = [srv.submit(systems[k], m, *args, t_final=T, dt=dt, m=64, seed=9, precision=64)
+                   for k, m, args, T, dt in jobs]
+        for (t, (lo, hi)), (k, m, args, T, dt) in zip(tickets, jobs):
+            st, _, _ = srv.wait(t, timeout_s=300)
+            assert st == 0, (k, m, st)
+            s = systems[k]
+            if m == "mm":
+                a = R.reach_mm(s, *args, t_final=T, dt=dt)
+            elif m == "cgb":
+                a = R.reach_cgb(s, *args, t_final=T, dt=dt)
+            else:
+                a = R.reach_mc(s, *args, t_final=T, dt=dt, m=64, seed=9, precision=64)
+            np.testing.assert_array_equal(lo, a[0])
+            np.testing.assert_array_equal(hi, a[1])
+    for s in systems.values():
+        s.close()
