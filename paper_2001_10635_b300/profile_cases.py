@@ -7,6 +7,8 @@ Cases:
   ks_mc32, ks_mc64     KS grid, m samples (default 256 / 32)
   traffic_mm           traffic chain, n cells (default 2^24), T (default 0.02)
   traffic16_mm         traffic chain n = 16, T = 10 (on-chip kernel)
+  traffic_cgbl         traffic CGB with the box-evaluated C, n cells (default 2^24), T (default 0.02)
+  traffic_sound_mm     outward-rounded traffic MM, n cells (default 2^24), T (default 0.02)
   osc_batch            the 4096-query oscillator batch (MM T=5, CGB T=4)
   heat_mm, heat_cgb    heat cube of side l = --n (default 256), --t (default 0.1)
   quad_mm, quad_cgb, quad_mc32   quadrotor swarm of --n agents (default 10^6), --t (default 0.1)
@@ -60,6 +62,15 @@ def main(argv=None):
         with R.System("traffic", n) as s:
             for _ in range(2):
                 R.reach_mm(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    elif a.case in ("traffic_cgbl", "traffic_sound_mm"):
+        n = a.n or (1 << 24)
+        wl = W.traffic_large(n, t_final=a.t or 0.02)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        prm = (40.0, 0.5, 1 / 6, 320.0, 1, 0) if a.case == "traffic_cgbl" else (40.0, 0.5, 1 / 6, 320.0, 0, 1)
+        f = R.reach_cgb if a.case == "traffic_cgbl" else R.reach_mm
+        with R.System("traffic", n, params=prm) as s:
+            for _ in range(2):
+                f(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
     elif a.case == "traffic16_mm":
         wl = W.traffic_small(16)
         with R.System("traffic", 16) as s:
