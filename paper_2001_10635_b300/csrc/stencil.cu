@@ -418,7 +418,7 @@ __device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[
 }
 
 template <int METHOD, int HALF>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_sound_rk4(SoundArgs a, TrafficK p) {
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound_rk4(SoundArgs a, TrafficK p) {
     constexpr int RADIUS = (METHOD == CGB && HALF == 1);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -596,7 +596,7 @@ __device__ __forceinline__ void ks_rhs(const KsK &p, const double (&a)[KC], cons
 }
 
 template <int METHOD>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_ks_rk4(StepArgs a, KsK p) {
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepArgs a, KsK p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
