@@ -377,7 +377,7 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
     // chunks that overlap the first and last steps (the input checks run on
     // the device as for every launch)
     if (sys->kind == REACH_TRAFFIC && !onchip && N > 0 && sys->prm[4] == 0.0 && sys->prm[5] == 0.0 &&
-        n >= 2 * OVERLAP_CHUNKS * 256 && !is_device_ptr(x0_lo) && !is_device_ptr(x0_hi) && !is_device_ptr(lo) &&
+        n >= OVERLAP_MIN_CELLS && !is_device_ptr(x0_lo) && !is_device_ptr(x0_hi) && !is_device_ptr(lo) &&
         !is_device_ptr(hi) && !is_device_ptr(w_lo)) {
         const double wl = w_lo[0], wh = w_hi[0];
         if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;

@@ -82,8 +82,11 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
                     int *status, cudaStream_t st);
 int quad_run(int method, const QuadK &p, int64_t n, const double *xlo, const double *xhi, const double *wlo,
              const double *whi, double *lo, double *hi, double h, int64_t N, int *status, cudaStream_t st);
-// the host-buffer path of the traffic kernel overlaps its copies in this many chunks
+// the host-buffer path of the traffic kernel overlaps its copies in this many
+// chunks, for chains long enough that the copies outweigh a second stream,
+// sixteen events and the chunked launches (2^20 cells: 8 MiB per vector)
 constexpr int OVERLAP_CHUNKS = 8;
+constexpr int64_t OVERLAP_MIN_CELLS = (int64_t)1 << 20;
 int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const double *hxlo, const double *hxhi,
                             double *hlo, double *hhi, double h, int64_t N, int S, Staging &sg);
 int stencil_traffic_sound(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,

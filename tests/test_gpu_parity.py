@@ -386,7 +386,7 @@ def test_host_buffer_overlap_path(method, T, S):
     # first and last launches; it must give the oracle's box and, bit for bit,
     # the box of the same call on device buffers
     import torch
-    n = 20011
+    n = (1 << 20) + 11   # the overlap path starts at 2^20 cells
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
     lo, hi, wlo, whi, _, dt, _, _ = problem("traffic", n, seed=77)
     o = O.reach(method, "traffic", lo, hi, wlo, whi, t_final=T, dt=dt)
