@@ -565,6 +565,8 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
     sus = trace[: max(20, count // 2)]
     scale = 0.7 * capacity / 2000.0
     slat, sspan, sbad, _ = _serve_run(R, sus, systems, scale, slots, budget)
+    # the same arrivals one at a time: a small query waits behind every large one ahead of it
+    sflat, _, sfbad = _fifo_run(R, sus, systems, scale)
     for s in systems.values():
         s.close()
     return {"workload": f"seeded Poisson trace, 2000 q/s offered; first {count} arrivals; traffic n in [1e2, 1e7] "
@@ -579,7 +581,9 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
                                "p50_ms": _pct(flat, 50) * 1e3, "p99_ms": _pct(flat, 99) * 1e3, "failed": fbad},
             "speedup_vs_fifo": fspan / span,
             "sustainable": {"rate_qps": 2000.0 * scale, "queries": len(sus), "p50_ms": _pct(slat, 50) * 1e3,
-                            "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad}}
+                            "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad,
+                            "fifo_p50_ms": _pct(sflat, 50) * 1e3, "fifo_p99_ms": _pct(sflat, 99) * 1e3,
+                            "fifo_failed": sfbad}}
 
 
 def headline_config(n, world):

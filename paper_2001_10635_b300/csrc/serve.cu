@@ -11,15 +11,21 @@
 //              a free slot is needed and its footprint must fit in what is left of
 //              the budget (first fit, so small requests pass a large one that waits
 //              for memory)
-//   slots      each slot is a worker thread with its own CUDA stream that runs the
+//   slots      each slot is a worker thread with its own CUDA streams that runs the
 //              admitted request through the ordinary entry points; requests on
 //              different slots overlap on the GPU (the on-chip kernels of small
 //              requests fill a few SMs, the streaming kernels of large ones share
 //              the rest at block granularity)
+//   priority   a request runs on a stream whose priority falls with its work
+//              (components per step x steps: the greatest below 2^30 component
+//              updates, one level lower per factor 4 above): the block scheduler hands SMs freed by a
+//              large request's short blocks to a small request first, so small
+//              requests finish in their own time rather than in the large one's
 //   wait       bounded: returns REACH_ETIMEOUT when the request has not finished
 //              within the caller's limit
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -39,6 +45,7 @@ struct Job {
     int64_t ticket;
     reach_request r;
     int64_t bytes;
+    int level = 0;   // stream priority level, 0 = greatest
     Clock::time_point submitted, started, finished;
     int status = REACH_OK;
     bool done = false;
@@ -53,6 +60,8 @@ struct reach_server {
     int64_t budget = 0, in_use = 0, peak = 0;
     int64_t next_ticket = 1;
     int nslots = 0, idle = 0;
+    int nlevels = 1;   // stream priority levels (greatest first)
+    int prio_greatest = 0;
     bool stopping = false;
     std::mutex mu;
     std::condition_variable work_cv, done_cv;
@@ -115,10 +124,26 @@ static void dispatch_locked(reach_server *s) {
     if (!s->admitted.empty()) s->work_cv.notify_all();
 }
 
+// priority level of a request: 0 below 2^30 component updates, one more per
+// factor 4 of work above, the largest requests sharing the least priority
+static int work_level(const reach_request *r, int nlevels) {
+    const int64_t n = r->sys->n;
+    const double per_step = r->method == 2 ? (double)n * (double)std::max<int64_t>(r->m, 1) : 2.0 * (double)n;
+    const double steps = r->dt > 0 ? std::ceil(r->t_final / r->dt) : 1.0;
+    const double work = per_step * std::max(steps, 1.0);
+    int level = 0;
+    for (double t = (double)(1LL << 30); work >= t && level < nlevels - 1; t *= 4) ++level;
+    return level;
+}
+
 static void worker_main(reach_server *s) {
     cudaSetDevice(s->device);
-    cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::vector<cudaStream_t> st(s->nlevels, nullptr);
+    for (int k = 0; k < s->nlevels; ++k)
+        if (cudaStreamCreateWithPriority(&st[k], cudaStreamNonBlocking, s->prio_greatest + k) != cudaSuccess) {
+            cudaGetLastError();
+            st[k] = k > 0 ? st[k - 1] : nullptr;
+        }
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         s->idle++;
@@ -133,7 +158,7 @@ static void worker_main(reach_server *s) {
         s->admitted.pop_front();
         j->started = Clock::now();
         lk.unlock();
-        run_job(j, st);
+        run_job(j, st[j->level]);
         lk.lock();
         j->finished = Clock::now();
         j->done = true;
@@ -141,7 +166,8 @@ static void worker_main(reach_server *s) {
         s->n_done++;
         s->done_cv.notify_all();
     }
-    if (st) cudaStreamDestroy(st);
+    for (int k = 0; k < s->nlevels; ++k)
+        if (st[k] && (k == 0 || st[k] != st[k - 1])) cudaStreamDestroy(st[k]);
 }
 
 }  // namespace reach
@@ -165,6 +191,14 @@ extern "C" int reach_server_create(int slots, int64_t hbm_budget_bytes, reach_se
         delete s;
         return REACH_ECUDA;
     }
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    // numerically lower is greater priority
+    s->prio_greatest = greatest;
+    s->nlevels = std::min(8, std::max(1, least - greatest + 1));
     s->budget = hbm_budget_bytes;
     s->nslots = slots;
     for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_main, s);
@@ -185,6 +219,7 @@ extern "C" int reach_server_submit(reach_server *s, const reach_request *r, int6
     j->ticket = s->next_ticket++;
     j->r = *r;
     j->bytes = bytes;
+    j->level = work_level(r, s->nlevels);
     j->submitted = Clock::now();
     s->jobs[j->ticket] = j;
     s->waiting.push_back(j);
