@@ -258,8 +258,11 @@ REACH_API int reach_batch_destroy(reach_batch *b);
    dispatcher admits them, in arrival order with first fit, whenever one of
    the server's slots is free and the request's device-memory footprint
    (reach_request_footprint) fits in what is left of the budget.  Each slot is
-   a worker thread with its own CUDA stream running the request through
-   reach_mm / reach_cgb / reach_mc, so admitted requests overlap on the GPU.
+   a worker thread running the request through reach_mm / reach_cgb / reach_mc
+   on its own CUDA streams, so admitted requests overlap on the GPU.  The
+   stream's priority falls with the request's work (state components per step
+   x steps; greatest below 2^30, one level lower per factor 4 above), so the
+   blocks of small requests are scheduled ahead of those of large ones.
    A request's buffers must stay valid until reach_server_wait has returned
    its result. */
 typedef struct {
@@ -298,6 +301,8 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming kernels: RK4 steps per launch, 1..8; 0 = auto (FP64 1, FP32 MC 2) */
 #define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
 #define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
+#define REACH_OPT_TILE 5             /* streaming traffic / KS MM and CGB: cells per lane, 0 = auto, 2 (64-cell
+                                        warp tiles, taken only while the halo leaves half the tile) or 8 (256) */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

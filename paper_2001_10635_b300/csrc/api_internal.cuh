@@ -45,6 +45,7 @@ int64_t opt_kernel();
 int64_t opt_steps();
 int64_t opt_block();
 int64_t opt_batch_cpt();
+int64_t opt_tile();
 
 // traffic parameters as the streaming kernel sees them (inputs d in [wl, wh])
 TrafficK make_traffic_k(const double *prm, double wl, double wh);

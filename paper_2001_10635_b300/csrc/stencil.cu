@@ -29,15 +29,18 @@
 
 namespace reach {
 
-constexpr int KC = 8;                 // cells per lane
-constexpr int TILE = 32 * KC;         // cells per warp tile
+// cells per lane: a warp tile is 32 * KC cells.  Wide tiles (256 cells) keep
+// the recomputed halo small; narrow ones (64 cells) give four times as many
+// warps to grids too short to fill the GPU with wide ones.
+constexpr int KC_WIDE = 8;
+constexpr int KC_NARROW = 2;
 constexpr int WARPS_PER_BLOCK = 8;
 
 struct StepArgs {
     const double *inA, *inB;   // state, or the input box on the first launch
     double *outA, *outB;
     int64_t n;
-    int64_t W;                 // owned cells per tile = TILE - 2H
+    int64_t W;                 // owned cells per tile = 32 KC - 2H
     int64_t ntiles;            // ceil(n / W), computed on the host
     int64_t tile0, tcount;     // the tiles this launch covers (traffic: a range, for overlapped copies)
     int H;                     // halo cells per side = 4 R S
@@ -52,6 +55,7 @@ struct StepArgs {
 // A lane's KC consecutive cells start at an even cell (tile starts and halos
 // are even), so with 16-byte aligned arrays a run that lies inside [0, n)
 // moves as KC/2 double2 loads or stores.
+template <int KC>
 __device__ __forceinline__ void load_run(const double *src, int64_t g0, int64_t n, bool vec, double (&v)[KC]) {
     if (vec && g0 >= 0 && g0 + KC <= n) {
         const double2 *p = reinterpret_cast<const double2 *>(src + g0);
@@ -69,7 +73,7 @@ __device__ __forceinline__ void load_run(const double *src, int64_t g0, int64_t 
         }
     }
 }
-template <int R>
+template <int R, int KC>
 __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC + 2 * R]) {
     // e[R + j] = y[j];  e[0..R-1] from lane-1, e[R+KC..] from lane+1
 #pragma unroll
@@ -82,7 +86,7 @@ __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC +
 }
 
 // one RK4 stage update of a lane's cells (stage is a compile-time constant)
-template <int STAGE>
+template <int STAGE, int KC>
 __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], double (&acc)[KC],
                                            const double (&k)[KC], double h) {
 #pragma unroll
@@ -98,7 +102,7 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
 // k[j] = f_{g-1} - f_g: flux out of cell g is min(cap, v y_g, w (xbar - y_{g+1}))
 // (min(cap, v y_g) for the last cell), the inflow of cell 0 is d, and cells
 // outside [0, n) carry no flux.
-template <bool POW2>
+template <bool POW2, int KC>
 __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                             int64_t n, double d, double (&k)[KC]) {
     double e[KC + 2];
@@ -138,6 +142,7 @@ __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)
 }
 
 // radius dynamics (C r)_g + [p]_g = v r_{g-1} + w r_{g+1} + [d] at g = 0
+template <int KC>
 __device__ __forceinline__ void traffic_growth(const TrafficK &p, const double (&r)[KC], int64_t g0,
                                                int64_t n, double (&k)[KC]) {
     double e[KC + 2];
@@ -153,7 +158,7 @@ __device__ __forceinline__ void traffic_growth(const TrafficK &p, const double (
 }
 
 // one traffic half per warp: HALF 0 = x / c, HALF 1 = xh / r
-template <int METHOD, int HALF, bool POW2>
+template <int METHOD, int HALF, bool POW2, int KC>
 __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                                  int64_t n, double (&k)[KC]) {
     if (METHOD == MM) traffic_rhs<POW2>(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
@@ -161,7 +166,7 @@ __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double
     else traffic_growth(p, y, g0, n, k);
 }
 
-template <int METHOD, int HALF, bool POW2>
+template <int METHOD, int HALF, bool POW2, int KC>
 __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &p, int64_t t, int lane,
                                              int &flags) {
     const int64_t n = a.n;
@@ -217,16 +222,16 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
     }
 }
 
-template <int METHOD, bool POW2>
+template <int METHOD, bool POW2, int KC>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(StepArgs a, TrafficK p) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t cnt = a.tcount;
     int flags = 0;
     for (int64_t t = warp; t < 2 * cnt; t += nwarps) {
-        if (t < cnt) traffic_tile<METHOD, 0, POW2>(a, p, a.tile0 + t, lane, flags);
-        else traffic_tile<METHOD, 1, POW2>(a, p, a.tile0 + t - cnt, lane, flags);
+        if (t < cnt) traffic_tile<METHOD, 0, POW2, KC>(a, p, a.tile0 + t, lane, flags);
+        else traffic_tile<METHOD, 1, POW2, KC>(a, p, a.tile0 + t - cnt, lane, flags);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
 // evaluation of those expressions would.
 __device__ __forceinline__ bool klt(double a, double b) { return dkey(a) < dkey(b); }
 
+template <int KC>
 __device__ __forceinline__ void traffic_growth_local(const TrafficK &p, const double (&cc)[KC],
                                                      const double (&rr)[KC], int64_t g0, int64_t n,
                                                      double (&k)[KC]) {
@@ -284,9 +290,10 @@ __device__ __forceinline__ void traffic_growth_local(const TrafficK &p, const do
 // both halves per warp: the radius reads the center
 template <bool POW2>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4(StepArgs a, TrafficK p) {
+    constexpr int KC = KC_WIDE;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t n = a.n;
     int flags = 0;
     for (int64_t t = warp; t < a.ntiles; t += nwarps) {
@@ -380,7 +387,7 @@ __device__ __forceinline__ void flux_iv(const TrafficK &p, double yl, double yu,
     }
 }
 
-template <int RADIUS>
+template <int RADIUS, int KC>
 __device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[KC], const double (&yu)[KC],
                                           int64_t g0, int64_t n, double dl, double du, double hp,
                                           double (&kl)[KC], double (&ku)[KC]) {
@@ -419,10 +426,11 @@ __device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[
 
 template <int METHOD, int HALF>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound_rk4(SoundArgs a, TrafficK p) {
+    constexpr int KC = KC_WIDE;
     constexpr int RADIUS = (METHOD == CGB && HALF == 1);
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t n = a.n;
     int flags = 0;
     // inflow of this half: MM the corner's own input, CGB the center's interval
@@ -538,6 +546,7 @@ __device__ __forceinline__ bool sign_differs(double a, double b) {
     return (__double_as_longlong(a) ^ __double_as_longlong(b)) < 0;
 }
 
+template <int KC>
 __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], const double (&xh)[KC],
                                           double (&kx)[KC], double (&kxh)[KC]) {
     double X[KC + 4], XH[KC + 4];
@@ -566,6 +575,7 @@ __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], c
 // over the box [c - r, c + r] (R3): C_ii = a0 - k dc + |k| (r_{i+1} + r_{i-1}),
 // C_{i,i+-1} = |a1 -+ k c_i| + |k| r_i, C_{i,i+-2} = |a2|; the two |k| r_i r_{i+-1}
 // terms fold into the diagonal's factor
+template <int KC>
 __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC], const double (&rr)[KC],
                                            double (&kc)[KC], double (&kr)[KC]) {
     double C[KC + 4], Rr[KC + 4];
@@ -588,18 +598,18 @@ __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC],
     }
 }
 
-template <int METHOD>
+template <int METHOD, int KC>
 __device__ __forceinline__ void ks_rhs(const KsK &p, const double (&a)[KC], const double (&b)[KC],
                                        double (&ka)[KC], double (&kb)[KC]) {
     if (METHOD == MM) ks_mm_rhs(p, a, b, ka, kb);
     else ks_cgb_rhs(p, a, b, ka, kb);
 }
 
-template <int METHOD>
+template <int METHOD, int KC>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepArgs a, KsK p) {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t n = a.n;
     const int64_t ntiles = a.ntiles;
     int flags = 0;
@@ -664,16 +674,52 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepAr
 }
 
 // ------------------------------------------------------------------ host
-static unsigned grid_for(int64_t warps_needed) {
-    int64_t blocks = (warps_needed + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+// Launch shape for a grid of warp tiles.  A tile is one warp's serial FP64
+// work, so a launch with few tiles takes one tile's time only if no two of its
+// warps share an SM sub-partition: below 8 warps per SM the blocks shrink to
+// ceil(warps / 148) warps, one block per SM, each warp on a sub-partition of
+// its own (up to four per SM).
+struct Shape {
+    unsigned grid, threads;
+};
+static Shape shape_for(int64_t warps_needed) {
+    int64_t wpb = (warps_needed + 147) / 148;
+    if (wpb < 1) wpb = 1;
+    if (wpb > WARPS_PER_BLOCK) wpb = WARPS_PER_BLOCK;
+    int64_t blocks = (warps_needed + wpb - 1) / wpb;
     const int64_t cap = 148LL * 64;
-    return (unsigned)(blocks > cap ? cap : blocks);
+    return Shape{(unsigned)(blocks > cap ? cap : blocks), (unsigned)(32 * wpb)};
+}
+
+// Cells per lane for an n-cell grid with a halo of H cells per tile side and
+// `halves` warps per tile: the narrow tile when its estimated time is shorter,
+// the time being the waves of warps over the 592 SM sub-partitions (at least
+// one) times a warp's cells.  The narrow tile is taken only while its halo
+// leaves it at least half its cells.
+static int tile_kc(int64_t n, int H, int halves) {
+    if (2 * H > 32 * KC_NARROW / 2) return KC_WIDE;
+    if (opt_tile() > 0) return opt_tile() == KC_NARROW ? KC_NARROW : KC_WIDE;
+    auto cost = [&](int kc) {
+        const int64_t w = 32 * kc - 2 * H;
+        const double warps = (double)halves * (double)((n + w - 1) / w);
+        return (warps > 592.0 ? warps / 592.0 : 1.0) * kc;
+    };
+    return cost(KC_NARROW) < cost(KC_WIDE) ? KC_NARROW : KC_WIDE;
+}
+
+template <int KC>
+static void launch_traffic_rk4(int method, bool pw, const StepArgs &a, const TrafficK &p, cudaStream_t st) {
+    const Shape g = shape_for(2 * a.tcount);
+    if (method == MM && pw) stencil_traffic_rk4<MM, true, KC><<<g.grid, g.threads, 0, st>>>(a, p);
+    else if (method == MM) stencil_traffic_rk4<MM, false, KC><<<g.grid, g.threads, 0, st>>>(a, p);
+    else if (pw) stencil_traffic_rk4<CGB, true, KC><<<g.grid, g.threads, 0, st>>>(a, p);
+    else stencil_traffic_rk4<CGB, false, KC><<<g.grid, g.threads, 0, st>>>(a, p);
 }
 
 // Integrate N steps with S steps per launch, ping-ponging between the output
 // (lo, hi) and the scratch pair so that the last launch writes the output.
 template <class LaunchFn>
-static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, double *lo, double *hi,
+static int run_steps(int R, int kc, int64_t n, const double *xlo, const double *xhi, double *lo, double *hi,
                      double *sA, double *sB, double h, int64_t N, int S, int *status, LaunchFn launch) {
     const int64_t L = (N + S - 1) / S;
     double *bufA[2] = {lo, sA}, *bufB[2] = {hi, sB};
@@ -683,7 +729,7 @@ static int run_steps(int R, int64_t n, const double *xlo, const double *xhi, dou
         StepArgs a;
         a.n = n;
         a.H = 4 * R * s;
-        a.W = TILE - 2 * a.H;
+        a.W = 32 * kc - 2 * a.H;
         a.ntiles = (n + a.W - 1) / a.W;
         a.tile0 = 0;
         a.tcount = a.ntiles;
@@ -711,20 +757,20 @@ int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st) {
     const bool local = method == CGB && p.local;
-    int rc = run_steps(1, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
+    // the box-evaluated C kernel holds both halves per warp: wide tiles only
+    const int kc = local ? KC_WIDE : tile_kc(n, 4 * S, 2);
+    int rc = run_steps(1, kc, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
         const int64_t ntiles = (n + a.W - 1) / a.W;
         const bool pw = p.v_pow2 != 0;
         if (local) {
-            if (pw) stencil_traffic_cgbl_rk4<true><<<grid_for(ntiles), 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-            else stencil_traffic_cgbl_rk4<false><<<grid_for(ntiles), 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+            const Shape g = shape_for(ntiles);
+            if (pw) stencil_traffic_cgbl_rk4<true><<<g.grid, g.threads, 0, st>>>(a, p);
+            else stencil_traffic_cgbl_rk4<false><<<g.grid, g.threads, 0, st>>>(a, p);
             REACH_LAUNCHED("stencil_traffic_cgbl_rk4");
             return REACH_OK;
         }
-        const unsigned grid = grid_for(2 * ntiles);
-        if (method == MM && pw) stencil_traffic_rk4<MM, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-        else if (method == MM) stencil_traffic_rk4<MM, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-        else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-        else stencil_traffic_rk4<CGB, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+        if (kc == KC_NARROW) launch_traffic_rk4<KC_NARROW>(method, pw, a, p, st);
+        else launch_traffic_rk4<KC_WIDE>(method, pw, a, p, st);
         REACH_LAUNCHED("stencil_traffic_rk4");
         return REACH_OK;
     });
@@ -778,11 +824,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
     const int64_t L = (N + S - 1) / S;
     const bool pw = p.v_pow2 != 0;
     auto launch = [&](const StepArgs &b) {
-        const unsigned grid = grid_for(2 * b.tcount);
-        if (method == MM && pw) stencil_traffic_rk4<MM, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
-        else if (method == MM) stencil_traffic_rk4<MM, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
-        else if (pw) stencil_traffic_rk4<CGB, true><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
-        else stencil_traffic_rk4<CGB, false><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(b, p);
+        launch_traffic_rk4<KC_WIDE>(method, pw, b, p, st);
         REACH_LAUNCHED("stencil_traffic_rk4");
         return REACH_OK;
     };
@@ -800,7 +842,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         StepArgs a;
         a.n = n;
         a.H = 4 * S;
-        a.W = TILE - 2 * a.H;
+        a.W = 32 * KC_WIDE - 2 * a.H;
         a.ntiles = (n + a.W - 1) / a.W;
         a.S = S;
         a.h = h;
@@ -877,7 +919,7 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         StepArgs a;
         a.n = n;
         a.H = 4 * s;
-        a.W = TILE - 2 * a.H;
+        a.W = 32 * KC_WIDE - 2 * a.H;
         a.ntiles = (n + a.W - 1) / a.W;
         a.tile0 = 0;
         a.tcount = a.ntiles;
@@ -980,20 +1022,20 @@ int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const doubl
         a.hi = hi;
         a.n = n;
         a.H = 4 * s;
-        a.W = TILE - 2 * a.H;
+        a.W = 32 * KC_WIDE - 2 * a.H;
         a.ntiles = (n + a.W - 1) / a.W;
         a.S = s;
         a.h = h;
         a.first = q == 0;
         a.last = q == L - 1;
         a.status = sg.status;
-        const unsigned grid = grid_for(a.ntiles);
+        const Shape g = shape_for(a.ntiles);
         if (method == MM) {
-            stencil_traffic_sound_rk4<MM, 0><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
-            stencil_traffic_sound_rk4<MM, 1><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<MM, 0><<<g.grid, g.threads, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<MM, 1><<<g.grid, g.threads, 0, sg.st>>>(a, p);
         } else {
-            stencil_traffic_sound_rk4<CGB, 0><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
-            stencil_traffic_sound_rk4<CGB, 1><<<grid, 32 * WARPS_PER_BLOCK, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<CGB, 0><<<g.grid, g.threads, 0, sg.st>>>(a, p);
+            stencil_traffic_sound_rk4<CGB, 1><<<g.grid, g.threads, 0, sg.st>>>(a, p);
         }
         REACH_LAUNCHED("stencil_traffic_sound_rk4");
         REACH_LAUNCHED("stencil_traffic_sound_rk4");
@@ -1013,11 +1055,13 @@ int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const doubl
 int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
                double *hi, double *sA, double *sB, double h, int64_t N, int S, int *status,
                cudaStream_t st) {
-    return run_steps(2, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
-        const int64_t ntiles = (n + a.W - 1) / a.W;
-        const unsigned grid = grid_for(ntiles);
-        if (method == MM) stencil_ks_rk4<MM><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
-        else stencil_ks_rk4<CGB><<<grid, 32 * WARPS_PER_BLOCK, 0, st>>>(a, p);
+    const int kc = tile_kc(n, 8 * S, 1);
+    return run_steps(2, kc, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
+        const Shape g = shape_for(a.ntiles);
+        if (method == MM && kc == KC_NARROW) stencil_ks_rk4<MM, KC_NARROW><<<g.grid, g.threads, 0, st>>>(a, p);
+        else if (method == MM) stencil_ks_rk4<MM, KC_WIDE><<<g.grid, g.threads, 0, st>>>(a, p);
+        else if (kc == KC_NARROW) stencil_ks_rk4<CGB, KC_NARROW><<<g.grid, g.threads, 0, st>>>(a, p);
+        else stencil_ks_rk4<CGB, KC_WIDE><<<g.grid, g.threads, 0, st>>>(a, p);
         REACH_LAUNCHED("stencil_ks_rk4");
         return REACH_OK;
     });

@@ -27,6 +27,7 @@ def _reset_options():
     R.reach_set_option(R.OPT_KERNEL, 0)
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
     R.reach_set_option(R.OPT_BLOCK, 0)
+    R.reach_set_option(R.OPT_TILE, 0)
 
 
 def gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=None, A=None, **kw):
@@ -81,17 +82,39 @@ STREAM = [("traffic", 300, 1), ("traffic", 1000, 3), ("traffic", 4097, 1), ("tra
           ("ks", 256, 1), ("ks", 777, 2), ("ks", 3001, 1)]
 
 
+@pytest.mark.parametrize("tile", [2, 8])
 @pytest.mark.parametrize("method", ["mm", "cgb"])
 @pytest.mark.parametrize("kind,n,S", STREAM, ids=[f"{k}{n}S{s}" for k, n, s in STREAM])
-def test_streaming_kernel_matches_oracle(method, kind, n, S):
+def test_streaming_kernel_matches_oracle(method, kind, n, S, tile):
+    # both warp-tile widths (64-cell tiles fall back to 256 where the KS halo
+    # of three steps per launch would not leave half the tile)
     lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=n)
     T = 0.37 if kind == "traffic" else 0.005   # 37 / 50 steps: ragged against S
     R.reach_set_option(R.OPT_KERNEL, 1)
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    R.reach_set_option(R.OPT_TILE, tile)
     olo, ohi = O.reach(method, kind, lo, hi, wlo, whi, t_final=T, dt=dt, params=prm)
     glo, ghi = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm)
     assert_close(glo, olo, TOL64, f"{method} {kind} lo")
     assert_close(ghi, ohi, TOL64, f"{method} {kind} hi")
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("kind,n", [("traffic", 100003), ("ks", 50001)])
+def test_tile_widths_agree_bit_for_bit(method, kind, n):
+    # a cell's arithmetic does not depend on the tile that computes it: the
+    # 64-cell and 256-cell tiles give the same box, and it is the oracle's
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=5)
+    T = 0.2 if kind == "traffic" else 0.003
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    R.reach_set_option(R.OPT_TILE, 2)
+    nlo, nhi = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm)
+    R.reach_set_option(R.OPT_TILE, 8)
+    wlo_, whi_ = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm)
+    assert np.array_equal(nlo, wlo_) and np.array_equal(nhi, whi_)
+    olo, ohi = O.reach(method, kind, lo, hi, wlo, whi, t_final=T, dt=dt, params=prm)
+    assert_close(nlo, olo, TOL64, f"{method} {kind} lo")
+    assert_close(nhi, ohi, TOL64, f"{method} {kind} hi")
 
 
 @pytest.mark.parametrize("method", ["mm", "cgb"])
