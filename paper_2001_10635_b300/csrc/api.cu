@@ -454,14 +454,17 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         sB = sA + n;
         // FP64 stencil kernels are bound by the FP64 pipe: recomputing a wider
         // halo costs more than the HBM traffic it saves, so one step per launch
-        const int S = opt_steps() > 0 ? (int)opt_steps() : 1;
+        // unless the grid is too short to fill the GPU
+        int S = opt_steps() > 0 ? (int)opt_steps() : 1;
         if (sys->kind == REACH_TRAFFIC) {
             TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
+            if (opt_steps() == 0 && !p.sound && !(method == CGB && p.local)) S = stencil_short_steps(1, 2, n);
             if (p.sound) rc = stencil_traffic_sound(method, p, n, dxlo, dxhi, dlo, dhi, dt, N, S, sg);
             else rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
         } else {
             KsK p;
             p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
+            if (opt_steps() == 0) S = stencil_short_steps(2, 1, n);
             rc = stencil_ks(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
         }
     }

@@ -78,6 +78,9 @@ struct BatchTask {
     int big;
     int bin[2];
 };
+// RK4 steps per launch of the streaming stencil kernels for an n-cell grid of
+// stencil radius R and `halves` warps per tile
+int stencil_short_steps(int R, int halves, int64_t n);
 int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st);

@@ -707,6 +707,20 @@ static int tile_kc(int64_t n, int H, int halves) {
     return cost(KC_NARROW) < cost(KC_WIDE) ? KC_NARROW : KC_WIDE;
 }
 
+// A grid whose narrow tiles fit in one wave of warps (one per SM
+// sub-partition) takes its time from the fixed cost of each launch, not from
+// the FP64 pipe: it runs the most steps per launch (up to 4) that keep it in
+// one wave and leave the narrow tile half its cells.  Other grids: 1.
+int stencil_short_steps(int R, int halves, int64_t n) {
+    for (int S = 4; S > 1; S /= 2) {
+        const int H = 4 * R * S;
+        if (2 * H > 32 * KC_NARROW / 2) continue;
+        const int64_t w = 32 * KC_NARROW - 2 * H;
+        if ((int64_t)halves * ((n + w - 1) / w) <= 592) return S;
+    }
+    return 1;
+}
+
 template <int KC>
 static void launch_traffic_rk4(int method, bool pw, const StepArgs &a, const TrafficK &p, cudaStream_t st) {
     const Shape g = shape_for(2 * a.tcount);

@@ -78,8 +78,11 @@ def test_onchip_matches_oracle(method, kind, n):
     assert_close(ghi, ohi, TOL64, f"{method} {kind} hi")
 
 
+# S = 0: the library's own choice (4 steps per launch for these short traffic
+# chains, 2 for these KS grids, 1 for the longer ones)
 STREAM = [("traffic", 300, 1), ("traffic", 1000, 3), ("traffic", 4097, 1), ("traffic", 4097, 2),
-          ("ks", 256, 1), ("ks", 777, 2), ("ks", 3001, 1)]
+          ("traffic", 5000, 0), ("traffic", 20011, 0), ("ks", 256, 1), ("ks", 777, 2), ("ks", 3001, 1),
+          ("ks", 3001, 0), ("ks", 30001, 0)]
 
 
 @pytest.mark.parametrize("tile", [2, 8])
