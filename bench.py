@@ -561,12 +561,19 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
     lat, span, bad, peak = _serve_run(R, trace, systems, 1.0, slots, budget)
     flat, fspan, fbad = _fifo_run(R, trace, systems, 1.0)
     capacity = len(trace) / span
-    # a sustainable rate: 70% of the measured serving capacity
+    # latency against offered load: the first half of the trace at 50%, 70% and
+    # 90% of the measured serving capacity, through the server and one at a
+    # time (where a small query waits behind every large one ahead of it)
     sus = trace[: max(20, count // 2)]
-    scale = 0.7 * capacity / 2000.0
-    slat, sspan, sbad, _ = _serve_run(R, sus, systems, scale, slots, budget)
-    # the same arrivals one at a time: a small query waits behind every large one ahead of it
-    sflat, _, sfbad = _fifo_run(R, sus, systems, scale)
+    sweep = []
+    for frac in (0.5, 0.7, 0.9):
+        scale = frac * capacity / 2000.0
+        slat, _, sbad, _ = _serve_run(R, sus, systems, scale, slots, budget)
+        sflat, _, sfbad = _fifo_run(R, sus, systems, scale)
+        sweep.append({"load": frac, "rate_qps": 2000.0 * scale, "queries": len(sus),
+                      "p50_ms": _pct(slat, 50) * 1e3, "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad,
+                      "fifo_p50_ms": _pct(sflat, 50) * 1e3, "fifo_p99_ms": _pct(sflat, 99) * 1e3,
+                      "fifo_failed": sfbad})
     for s in systems.values():
         s.close()
     return {"workload": f"seeded Poisson trace, 2000 q/s offered; first {count} arrivals; traffic n in [1e2, 1e7] "
@@ -580,10 +587,7 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
             "per_query_fifo": {"value": work / fspan, "unit": "comp-steps/s", "makespan_s": fspan,
                                "p50_ms": _pct(flat, 50) * 1e3, "p99_ms": _pct(flat, 99) * 1e3, "failed": fbad},
             "speedup_vs_fifo": fspan / span,
-            "sustainable": {"rate_qps": 2000.0 * scale, "queries": len(sus), "p50_ms": _pct(slat, 50) * 1e3,
-                            "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad,
-                            "fifo_p50_ms": _pct(sflat, 50) * 1e3, "fifo_p99_ms": _pct(sflat, 99) * 1e3,
-                            "fifo_failed": sfbad}}
+            "sustainable": sweep[1], "load_sweep": sweep}
 
 
 def headline_config(n, world):
