@@ -303,6 +303,8 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
 #define REACH_OPT_TILE 5             /* streaming traffic / KS MM and CGB: cells per lane, 0 = auto, 2 (64-cell
                                         warp tiles, taken only while the halo leaves half the tile) or 8 (256) */
+#define REACH_OPT_MC_SB 6            /* on-chip MC: samples per block, 0 = auto (32 from 4736 samples, 8 from 1184,
+                                        else 2), or 2 / 8 / 32 */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

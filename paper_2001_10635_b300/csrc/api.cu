@@ -23,7 +23,8 @@ int cuda_fail(cudaError_t e, const char *where) {
 }
 
 // process-wide options; read by calls on any thread
-static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0};
+static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
+    g_opt_mc_sb{0};
 
 // ---------------------------------------------------------------- memory
 static std::atomic<bool> g_pool_ready[64];
@@ -184,6 +185,7 @@ int64_t opt_steps() { return g_opt_steps; }
 int64_t opt_block() { return g_opt_block; }
 int64_t opt_batch_cpt() { return g_opt_batch_cpt; }
 int64_t opt_tile() { return g_opt_tile; }
+int64_t opt_mc_sb() { return g_opt_mc_sb; }
 
 }  // namespace reach
 
@@ -512,6 +514,10 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value != 0 && value != 2 && value != 8) return REACH_EINVAL;
         g_opt_tile = value;
         return REACH_OK;
+    case REACH_OPT_MC_SB:
+        if (value != 0 && value != 2 && value != 8 && value != 32) return REACH_EINVAL;
+        g_opt_mc_sb = value;
+        return REACH_OK;
     }
     return REACH_EINVAL;
 }
@@ -523,6 +529,7 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_BLOCK: return g_opt_block;
     case REACH_OPT_BATCH_CPT: return g_opt_batch_cpt;
     case REACH_OPT_TILE: return g_opt_tile;
+    case REACH_OPT_MC_SB: return g_opt_mc_sb;
     }
     return REACH_EINVAL;
 }

@@ -46,6 +46,9 @@ int64_t opt_steps();
 int64_t opt_block();
 int64_t opt_batch_cpt();
 int64_t opt_tile();
+int64_t opt_mc_sb();
+// samples per block of the on-chip MC kernel for m samples (2, 8 or 32)
+int mc_onchip_sb(int64_t m);
 
 // traffic parameters as the streaming kernel sees them (inputs d in [wl, wh])
 TrafficK make_traffic_k(const double *prm, double wl, double wh);

@@ -4,8 +4,9 @@
 // integrated with RK4 in binary64 or binary32.  Lane = sample: a warp holds 32
 // samples of the same components, so the stencil never crosses lanes and the
 // final per-component minimum / maximum over samples is a warp shuffle.
-//   mc_onchip : small n, one block = 32 samples x the whole state, all N steps
-//               in shared memory.
+//   mc_onchip : small n, one block = SB samples x the whole state, all N steps
+//               in shared memory (SB = 32, or 8 or 2 when there are too few
+//               samples for blocks of 32 to reach every SM).
 //   mc_stream : large stencil systems; state in HBM, sample-fastest layout
 //               x[i * M + j]; one launch per RK4 step over tiles of 32 samples x
 //               TC components plus a 4R-cell halo; sampling fused into the first
@@ -52,9 +53,9 @@ struct Plain<REACH_TRAFFIC, T> {
         f = (g < -1 || g >= n) ? T(0) : f;
         return f;
     }
-    template <class Row>
-    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t g, int64_t n, const T *P, int lane) {
-        T d = P[lane];
+    template <class Row, class In>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t g, int64_t n, In pin) {
+        T d = pin(0);
         T fin = flux(q, row(c - 1), row(c), g - 1, n, d);
         T fout = flux(q, row(c), row(c + 1), g, n, d);
         return fin - fout;
@@ -64,8 +65,8 @@ struct Plain<REACH_TRAFFIC, T> {
 template <class T>
 struct Plain<REACH_KS, T> {
     static constexpr int R = 2;
-    template <class Row>
-    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
+    template <class Row, class In>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, In) {
         T um2 = row(c - 2), um1 = row(c - 1), u = row(c), up1 = row(c + 1), up2 = row(c + 2);
         // u (a0 - k (u_{i+1} - u_{i-1})) + a1 (u_{i-1} + u_{i+1}) + a2 (u_{i-2} + u_{i+2})
         return tfma(u, tfma(-q[3], up1 - um1, q[0]), tfma(q[1], um1 + up1, q[2] * (um2 + up2)));
@@ -76,8 +77,8 @@ template <class T>
 struct Plain<REACH_OSC, T> {
     static constexpr int R = 0;
     // whole state on chip: rows 0..m-1 positions, m..2m-1 velocities
-    template <class Row>
-    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t n, const T *P, int lane) {
+    template <class Row, class In>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t n, In pin) {
         const int m = (int)(n >> 1);
         if (c < m) return row(m + c);
         const int j = c - m;
@@ -85,7 +86,7 @@ struct Plain<REACH_OSC, T> {
         T xl = (j > 0) ? row(j - 1) : T(0), xr = (j < m - 1) ? row(j + 1) : T(0);
         // -(ka + 2kc + kb z^2) z + kc (xl + xr) + w
         T t = tfma(q[1], z * z, q[3]);
-        T r = tfma(q[2], xl + xr, P[j * 32 + lane]);
+        T r = tfma(q[2], xl + xr, pin(j));
         return tfma(-t, z, r);
     }
 };
@@ -94,8 +95,8 @@ template <class T>
 struct Plain<REACH_HEAT3D, T> {
     static constexpr int R = 0;
     // whole grid on chip; q: kh, l, open face
-    template <class Row>
-    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, const T *, int) {
+    template <class Row, class In>
+    static __device__ __forceinline__ T rhs(const T *q, Row row, int c, int64_t, int64_t, In) {
         const int l = (int)q[1], pl = l * l;
         const int x = c % l, y = (c / l) % l, z = c / pl;
         T s = (x > 0) ? row(c - 1) : T(0);
@@ -112,14 +113,14 @@ struct Plain<REACH_HEAT3D, T> {
 template <class T>
 struct Plain<REACH_LINEAR, T> {
     static constexpr int R = 0;
-    template <class Row>
-    static __device__ __forceinline__ T rhs(const T *, Row row, int c, int64_t, int64_t n, const T *P, int lane,
+    template <class Row, class In>
+    static __device__ __forceinline__ T rhs(const T *, Row row, int c, int64_t, int64_t n, In pin,
                                             const double *A) {
         T acc = T(0);
         const double *Ar = A + (int64_t)c * n;
 #pragma unroll 1
         for (int j = 0; j < (int)n; ++j) acc = tfma((T)__ldg(Ar + j), row(j), acc);
-        return acc + P[c * 32 + lane];
+        return acc + pin(c);
     }
 };
 
@@ -159,6 +160,28 @@ __device__ __forceinline__ void warp_minmax(T v, bool valid, double *plo, double
     if ((threadIdx.x & 31) == 0) { *plo = (double)a; *phi = (double)b; }
 }
 
+// the same over each group of SB consecutive lanes (SB = 2, 8 or 32), every
+// lane taking part; the group's first lane writes.  `active`: the lane holds a
+// row of the state.
+template <int SB, class T>
+__device__ __forceinline__ void group_minmax(T v, bool valid, bool active, double *plo, double *phi,
+                                             int *status) {
+    if (SB == 32) {
+        if (active) warp_minmax<T>(v, valid, plo, phi, status);
+        return;
+    }
+    const T inf = (T)INFINITY;
+    T a = valid ? v : inf, b = valid ? v : -inf;
+    const bool bad = active && valid && !tfinite(v);
+#pragma unroll
+    for (int o = SB / 2; o > 0; o >>= 1) {
+        a = tmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = tmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    if (active && (threadIdx.x % SB) == 0) { *plo = (double)a; *phi = (double)b; }
+}
+
 struct McArgs {
     int64_t n, nw, m, N;
     double h;
@@ -169,34 +192,38 @@ struct McArgs {
 };
 
 // ------------------------------------------------------------------ on-chip
-template <int SYS, class T>
+// A block holds SB samples (smp = threadIdx % SB) of the whole state; its
+// threads form G = blockDim / SB row groups, group g holding rows g, g + G, ...
+// (at most MC_Q).  Sample j = block * SB + smp draws the same Philox numbers
+// whatever SB is, so the box does not depend on the layout.
+template <int SYS, class T, int SB>
 __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
     extern __shared__ unsigned char smraw[];
-    T *Y = (T *)smraw;                    // [n][32]
-    T *P = Y + a.n * 32;                  // [nw][32]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t j = (int64_t)blockIdx.x * 32 + lane;   // sample
+    T *Y = (T *)smraw;                    // [n][SB]
+    T *P = Y + a.n * SB;                  // [nw][SB]
+    const int smp = (int)(threadIdx.x % SB), grp = (int)(threadIdx.x / SB), G = (int)(blockDim.x / SB);
+    const int64_t j = (int64_t)blockIdx.x * SB + smp;   // sample
     const bool valid = j < a.m;
     const int n = (int)a.n;
     T q[4];
     mc_consts<SYS, T>(a.prm, q);
     int flags = 0;
 
-    for (int k = warp; k < (int)a.nw; k += MC_WARPS) {
+    for (int k = grp; k < (int)a.nw; k += G) {
         double lo = a.wlo[k], hi = a.whi[k];
-        if (lane == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
-        P[k * 32 + lane] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)k, 1u)));
+        if (smp == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+        P[k * SB + smp] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)k, 1u)));
     }
     T z[MC_Q], acc[MC_Q], kk[MC_Q];
 #pragma unroll
     for (int s = 0; s < MC_Q; ++s) {
-        int c = warp + s * MC_WARPS;
+        int c = grp + s * G;
         z[s] = acc[s] = T(0);
         if (c < n) {
             double lo = a.xlo[c], hi = a.xhi[c];
-            if (lane == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+            if (smp == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
             z[s] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)c, 0u)));
-            Y[c * 32 + lane] = z[s];
+            Y[c * SB + smp] = z[s];
         }
     }
     __syncthreads();
@@ -204,27 +231,28 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
     auto row = [&](int c) -> T {
         if (wrap) c = c < 0 ? c + n : (c >= n ? c - n : c);
         else if (c < 0 || c >= n) return T(0);
-        return Y[c * 32 + lane];
+        return Y[c * SB + smp];
     };
+    auto pin = [&](int k) -> T { return P[k * SB + smp]; };
     const T h = (T)a.h, hh = (T)(0.5 * a.h), h6 = (T)(a.h / 6.0);
     for (int64_t step = 0; step < a.N; ++step) {
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
 #pragma unroll
             for (int s = 0; s < MC_Q; ++s) {
-                int c = warp + s * MC_WARPS;
+                int c = grp + s * G;
                 if (c < n) {
                     if constexpr (SYS == REACH_LINEAR)
-                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, P, lane, a.prm);
+                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, pin, a.prm);
                     else
-                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, P, lane);
+                        kk[s] = Plain<SYS, T>::rhs(q, row, c, c, a.n, pin);
                 }
             }
             __syncthreads();
             const T cst = (stage == 2) ? h : hh;
 #pragma unroll
             for (int s = 0; s < MC_Q; ++s) {
-                int c = warp + s * MC_WARPS;
+                int c = grp + s * G;
                 if (c < n) {
                     T y;
                     if (stage == 0) acc[s] = kk[s];
@@ -232,7 +260,7 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
                     else acc[s] += kk[s];
                     if (stage < 3) y = tfma(cst, kk[s], z[s]);
                     else { z[s] = tfma(h6, acc[s], z[s]); y = z[s]; }
-                    Y[c * 32 + lane] = y;
+                    Y[c * SB + smp] = y;
                 }
             }
             __syncthreads();
@@ -240,8 +268,12 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
     }
 #pragma unroll
     for (int s = 0; s < MC_Q; ++s) {
-        int c = warp + s * MC_WARPS;
-        if (c < n) warp_minmax<T>(z[s], valid, a.plo + blockIdx.x * a.n + c, a.phi + blockIdx.x * a.n + c, a.status);
+        // every lane of a group takes part in its shuffles (a group's lanes
+        // share their row count, so no lane of a warp leaves early)
+        const int c = grp + s * G;
+        const int cc = c < n ? c : 0;
+        group_minmax<SB, T>(z[s], valid, c < n, a.plo + blockIdx.x * a.n + cc, a.phi + blockIdx.x * a.n + cc,
+                            a.status);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -473,19 +505,46 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
 }
 
 // ------------------------------------------------------------------ host
-template <int SYS, class T>
-static int launch_onchip(const McArgs &a, cudaStream_t st) {
-    int64_t nblk = (a.m + 31) / 32;
-    size_t smem = (size_t)(a.n + a.nw) * 32 * sizeof(T);
+// Samples per block of the on-chip kernel: blocks of 32 samples while there
+// are enough of them for every SM, else 8 or 2, which spreads the same warps
+// over more SMs (one warp per SM sub-partition instead of four).
+int mc_onchip_sb(int64_t m) {
+    if (opt_mc_sb() > 0) return (int)opt_mc_sb();
+    if ((m + 31) / 32 >= 148) return 32;
+    if ((m + 7) / 8 >= 148) return 8;
+    return 2;
+}
+
+template <int SYS, class T, int SB>
+static int launch_onchip_sb(const McArgs &a, cudaStream_t st) {
+    const int64_t nblk = (a.m + SB - 1) / SB;
+    // row groups: 16 with 32 samples (16 warps); otherwise one row per thread
+    // up to MC_THREADS threads, the count a multiple of 32 / SB so that whole
+    // warps launch
+    int64_t G = 16;
+    if (SB < 32) {
+        const int64_t unit = 32 / SB;
+        G = (a.n + unit - 1) / unit * unit;
+        if (G > MC_THREADS / SB) G = MC_THREADS / SB;
+    }
+    if ((a.n + G - 1) / G > MC_Q) return REACH_EINVAL;   // more rows than a thread holds
+    const size_t smem = (size_t)(a.n + a.nw) * SB * sizeof(T);
     static std::atomic<bool> attr{false};   // idempotent: a second setter is harmless
     if (!attr.load()) {
-        int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T>);
+        int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T, SB>);
         if (rc) return rc;
         attr.store(true);
     }
-    mc_onchip<SYS, T><<<(unsigned)nblk, MC_THREADS, smem, st>>>(a);
+    mc_onchip<SYS, T, SB><<<(unsigned)nblk, (unsigned)(SB * G), smem, st>>>(a);
     REACH_LAUNCHED("mc_onchip");
     return REACH_OK;
+}
+
+template <int SYS, class T>
+static int launch_onchip(const McArgs &a, int sb, cudaStream_t st) {
+    if (sb == 2) return launch_onchip_sb<SYS, T, 2>(a, st);
+    if (sb == 8) return launch_onchip_sb<SYS, T, 8>(a, st);
+    return launch_onchip_sb<SYS, T, 32>(a, st);
 }
 
 // warps per block of the streaming kernel: binary64 keeps 2x the registers
@@ -564,17 +623,19 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
     bool onchip = n <= mc_onchip_limit(sys->kind, sizeof(T) == 4 ? 32 : 64);
     if (opt_kernel() == 1 && (sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS) && n >= 16) onchip = false;
     if (!onchip && !(sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS)) return REACH_EINVAL;
-    int64_t nblk = (base.m + 31) / 32;
+    // partial minima / maxima per block of samples
+    const int sb = onchip ? mc_onchip_sb(base.m) : 32;
+    int64_t nblk = (base.m + sb - 1) / sb;
     McArgs a = base;
     if ((rc = sg.scratch(2 * nblk * n * sizeof(double), (void **)&a.plo))) return rc;
     a.phi = a.plo + nblk * n;
     if (onchip) {
         switch (sys->kind) {
-        case REACH_TRAFFIC: rc = launch_onchip<REACH_TRAFFIC, T>(a, sg.st); break;
-        case REACH_KS: rc = launch_onchip<REACH_KS, T>(a, sg.st); break;
-        case REACH_OSC: rc = launch_onchip<REACH_OSC, T>(a, sg.st); break;
-        case REACH_HEAT3D: rc = launch_onchip<REACH_HEAT3D, T>(a, sg.st); break;
-        default: rc = launch_onchip<REACH_LINEAR, T>(a, sg.st); break;
+        case REACH_TRAFFIC: rc = launch_onchip<REACH_TRAFFIC, T>(a, sb, sg.st); break;
+        case REACH_KS: rc = launch_onchip<REACH_KS, T>(a, sb, sg.st); break;
+        case REACH_OSC: rc = launch_onchip<REACH_OSC, T>(a, sb, sg.st); break;
+        case REACH_HEAT3D: rc = launch_onchip<REACH_HEAT3D, T>(a, sb, sg.st); break;
+        default: rc = launch_onchip<REACH_LINEAR, T>(a, sb, sg.st); break;
         }
     } else {
         McStep s;

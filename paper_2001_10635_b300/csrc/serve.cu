@@ -76,7 +76,10 @@ namespace reach {
 
 static int64_t mc_footprint(const reach_system *s, int64_t m, int prec) {
     const int64_t M = (m + 31) / 32 * 32, elt = prec == 32 ? 4 : 8, n = s->n;
-    int64_t partials = 2 * (M / 32) * n * 8;
+    // partial minima / maxima: one row per block of samples (32 per block on
+    // the streaming kernel, 2 to 32 on the on-chip one)
+    const int64_t sb = mc_onchip_sb(m), blocks = std::max(M / 32, (m + sb - 1) / sb);
+    int64_t partials = 2 * blocks * n * 8;
     bool stream_kernel = (s->kind == REACH_TRAFFIC || s->kind == REACH_KS) && n > 128;
     return partials + (stream_kernel ? 2 * n * M * elt : 0);
 }

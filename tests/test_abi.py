@@ -47,7 +47,7 @@ def test_options_are_validated():
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 3)
     assert R.reach_get_option(R.OPT_STEPS_PER_LAUNCH) == 3
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, old)
-    for key, val in [(R.OPT_STEPS_PER_LAUNCH, -1), (R.OPT_KERNEL, 5), (R.OPT_BLOCK, 33), (R.OPT_TILE, 4), (99, 1)]:
+    for key, val in [(R.OPT_STEPS_PER_LAUNCH, -1), (R.OPT_KERNEL, 5), (R.OPT_BLOCK, 33), (R.OPT_TILE, 4), (R.OPT_MC_SB, 4), (99, 1)]:
         with pytest.raises(R.ReachError):
             R.reach_set_option(key, val)
 

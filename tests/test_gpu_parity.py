@@ -28,6 +28,7 @@ def _reset_options():
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
     R.reach_set_option(R.OPT_BLOCK, 0)
     R.reach_set_option(R.OPT_TILE, 0)
+    R.reach_set_option(R.OPT_MC_SB, 0)
 
 
 def gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=None, A=None, **kw):
@@ -168,14 +169,37 @@ MC = [("traffic", 5, 33, 64), ("traffic", 40, 70, 32), ("ks", 64, 70, 64), ("ks"
       ("osc", 8, 100, 64), ("osc", 40, 45, 32), ("linear", 5, 33, 64), ("linear", 12, 1, 32)]
 
 
+@pytest.mark.parametrize("sb", [0, 8, 32])
 @pytest.mark.parametrize("kind,n,m,prec", MC, ids=[f"{k}{n}m{m}p{p}" for k, n, m, p in MC])
-def test_mc_onchip_matches_oracle(kind, n, m, prec):
+def test_mc_onchip_matches_oracle(kind, n, m, prec, sb):
+    # sb: samples per block of the on-chip kernel (0: the library's choice, 2
+    # for these sample counts)
+    R.reach_set_option(R.OPT_MC_SB, sb)
     lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=7)
     o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, A=A, m=m, seed=11, prec=prec)
     g = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, A=A, m=m, seed=11, precision=prec)
     tol = TOL64 if prec == 64 else TOL32
     assert_close(g[0], o[0], tol, "lo")
     assert_close(g[1], o[1], tol, "hi")
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_mc_small_chain_same_box_for_every_block_shape(prec):
+    # the n = 16 chain over T = 10 with 1000 samples: blocks of 2, 8 and 32
+    # samples draw the same samples and give the same box bit for bit, and it
+    # is the oracle's
+    wl = W.traffic_small(16)
+    args = (wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"])
+    boxes = []
+    for sb in (2, 8, 32):
+        R.reach_set_option(R.OPT_MC_SB, sb)
+        boxes.append(gpu_box("mc", "traffic", 16, *args, wl["t_final"], wl["dt"], m=1000, seed=0, precision=prec))
+    for b in boxes[1:]:
+        assert np.array_equal(b[0], boxes[0][0]) and np.array_equal(b[1], boxes[0][1])
+    o = O.reach("mc", "traffic", *args, t_final=wl["t_final"], dt=wl["dt"], m=1000, seed=0, prec=prec)
+    tol = TOL64 if prec == 64 else TOL32
+    assert_close(boxes[0][0], o[0], tol, "lo")
+    assert_close(boxes[0][1], o[1], tol, "hi")
 
 
 MCS = [("traffic", 700, 70, 64), ("traffic", 300, 33, 32), ("ks", 600, 40, 64), ("ks", 513, 65, 32)]
