@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
 // ------------------------------------------------------------------ host
 // Samples per block of the on-chip kernel: blocks of 32 samples while there
 // are enough of them for every SM, else 8 or 2, which spreads the same warps
-// over more SMs (one warp per SM sub-partition instead of four).
+// over more SMs (a few warps per SM instead of sixteen on a few SMs).
 int mc_onchip_sb(int64_t m) {
     if (opt_mc_sb() > 0) return (int)opt_mc_sb();
     if ((m + 31) / 32 >= 148) return 32;

@@ -675,10 +675,10 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepAr
 
 // ------------------------------------------------------------------ host
 // Launch shape for a grid of warp tiles.  A tile is one warp's serial FP64
-// work, so a launch with few tiles takes one tile's time only if no two of its
-// warps share an SM sub-partition: below 8 warps per SM the blocks shrink to
-// ceil(warps / 148) warps, one block per SM, each warp on a sub-partition of
-// its own (up to four per SM).
+// work (a warp issues an FP64 instruction about every 68 clocks, and an SM's
+// FP64 pipe keeps about four warps at that rate), so a launch with few tiles
+// takes one tile's time only if its warps are spread over all SMs: below 8
+// warps per SM the blocks shrink to ceil(warps / 148) warps, one block per SM.
 struct Shape {
     unsigned grid, threads;
 };
@@ -693,9 +693,9 @@ static Shape shape_for(int64_t warps_needed) {
 
 // Cells per lane for an n-cell grid with a halo of H cells per tile side and
 // `halves` warps per tile: the narrow tile when its estimated time is shorter,
-// the time being the waves of warps over the 592 SM sub-partitions (at least
-// one) times a warp's cells.  The narrow tile is taken only while its halo
-// leaves it at least half its cells.
+// the time being the waves of warps over 592 full-rate warp slots (four per
+// SM; at least one wave) times a warp's cells.  The narrow tile is taken only
+// while its halo leaves it at least half its cells.
 static int tile_kc(int64_t n, int H, int halves) {
     if (2 * H > 32 * KC_NARROW / 2) return KC_WIDE;
     if (opt_tile() > 0) return opt_tile() == KC_NARROW ? KC_NARROW : KC_WIDE;
@@ -707,8 +707,8 @@ static int tile_kc(int64_t n, int H, int halves) {
     return cost(KC_NARROW) < cost(KC_WIDE) ? KC_NARROW : KC_WIDE;
 }
 
-// A grid whose narrow tiles fit in one wave of warps (one per SM
-// sub-partition) takes its time from the fixed cost of each launch, not from
+// A grid whose narrow tiles fit in one wave of warps (592, four per SM)
+// takes its time from the fixed cost of each launch, not from
 // the FP64 pipe: it runs the most steps per launch (up to 4) that keep it in
 // one wave and leave the narrow tile half its cells.  Other grids: 1.
 int stencil_short_steps(int R, int halves, int64_t n) {
