@@ -35,6 +35,10 @@ namespace reach {
 constexpr int KC_WIDE = 8;
 constexpr int KC_NARROW = 2;
 constexpr int WARPS_PER_BLOCK = 8;
+// The KS kernel holds both halves per warp: three 4-warp blocks per SM give it
+// 168 registers (a few spilled) where two 8-warp blocks give 128 (more spilled);
+// measured 1% faster (MM 1.263e10 against 1.248e10 comp-steps/s at n = 2^20).
+constexpr int KS_WARPS_PER_BLOCK = 4;
 
 struct StepArgs {
     const double *inA, *inB;   // state, or the input box on the first launch
@@ -606,7 +610,7 @@ __device__ __forceinline__ void ks_rhs(const KsK &p, const double (&a)[KC], cons
 }
 
 template <int METHOD, int KC>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepArgs a, KsK p) {
+__global__ void __launch_bounds__(32 * KS_WARPS_PER_BLOCK, 3) stencil_ks_rk4(StepArgs a, KsK p) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -677,15 +681,16 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_ks_rk4(StepAr
 // Launch shape for a grid of warp tiles.  A tile is one warp's serial FP64
 // work (a warp issues an FP64 instruction about every 68 clocks, and an SM's
 // FP64 pipe keeps about four warps at that rate), so a launch with few tiles
-// takes one tile's time only if its warps are spread over all SMs: below 8
-// warps per SM the blocks shrink to ceil(warps / 148) warps, one block per SM.
+// takes one tile's time only if its warps are spread over all SMs: below
+// max_wpb warps per SM the blocks shrink to ceil(warps / 148) warps, one block
+// per SM.
 struct Shape {
     unsigned grid, threads;
 };
-static Shape shape_for(int64_t warps_needed) {
+static Shape shape_for(int64_t warps_needed, int64_t max_wpb = WARPS_PER_BLOCK) {
     int64_t wpb = (warps_needed + 147) / 148;
     if (wpb < 1) wpb = 1;
-    if (wpb > WARPS_PER_BLOCK) wpb = WARPS_PER_BLOCK;
+    if (wpb > max_wpb) wpb = max_wpb;
     int64_t blocks = (warps_needed + wpb - 1) / wpb;
     const int64_t cap = 148LL * 64;
     return Shape{(unsigned)(blocks > cap ? cap : blocks), (unsigned)(32 * wpb)};
@@ -1071,7 +1076,7 @@ int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const dou
                cudaStream_t st) {
     const int kc = tile_kc(n, 8 * S, 1);
     return run_steps(2, kc, n, xlo, xhi, lo, hi, sA, sB, h, N, S, status, [&](const StepArgs &a) {
-        const Shape g = shape_for(a.ntiles);
+        const Shape g = shape_for(a.ntiles, KS_WARPS_PER_BLOCK);
         if (method == MM && kc == KC_NARROW) stencil_ks_rk4<MM, KC_NARROW><<<g.grid, g.threads, 0, st>>>(a, p);
         else if (method == MM) stencil_ks_rk4<MM, KC_WIDE><<<g.grid, g.threads, 0, st>>>(a, p);
         else if (kc == KC_NARROW) stencil_ks_rk4<CGB, KC_NARROW><<<g.grid, g.threads, 0, st>>>(a, p);
