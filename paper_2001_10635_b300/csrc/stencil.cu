@@ -49,7 +49,7 @@ struct StepArgs {
     int64_t tile0, tcount;     // the tiles this launch covers (traffic: a range, for overlapped copies)
     int H;                     // halo cells per side = 4 R S
     int S;                     // RK4 steps in this launch
-    double h;
+    double h, hh, h6;          // h, h / 2 and h / 6, formed on the host (no FP64 division in the kernel)
     int first, last;           // convert the input box / emit the output box
     int vec;                   // every state pointer is 16-byte aligned: runs move as double2
     int *status;
@@ -92,13 +92,14 @@ __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC +
 // one RK4 stage update of a lane's cells (stage is a compile-time constant)
 template <int STAGE, int KC>
 __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], double (&acc)[KC],
-                                           const double (&k)[KC], double h) {
+                                           const double (&k)[KC], const StepArgs &a) {
+    const double h = a.h, hh = a.hh, h6 = a.h6;
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
-        if (STAGE == 0) { acc[j] = k[j]; y[j] = fma(0.5 * h, k[j], z[j]); }
-        if (STAGE == 1) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(0.5 * h, k[j], z[j]); }
+        if (STAGE == 0) { acc[j] = k[j]; y[j] = fma(hh, k[j], z[j]); }
+        if (STAGE == 1) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(hh, k[j], z[j]); }
         if (STAGE == 2) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(h, k[j], z[j]); }
-        if (STAGE == 3) { acc[j] += k[j]; z[j] = fma(h / 6.0, acc[j], z[j]); y[j] = z[j]; }
+        if (STAGE == 3) { acc[j] += k[j]; z[j] = fma(h6, acc[j], z[j]); y[j] = z[j]; }
     }
 }
 
@@ -197,13 +198,13 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
 #pragma unroll
         for (int j = 0; j < KC; ++j) y[j] = z[j];
         traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
-        rk4_update<0>(z, y, acc, k, a.h);
+        rk4_update<0>(z, y, acc, k, a);
         traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
-        rk4_update<1>(z, y, acc, k, a.h);
+        rk4_update<1>(z, y, acc, k, a);
         traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
-        rk4_update<2>(z, y, acc, k, a.h);
+        rk4_update<2>(z, y, acc, k, a);
         traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
-        rk4_update<3>(z, y, acc, k, a.h);
+        rk4_update<3>(z, y, acc, k, a);
     }
     double *out = HALF ? a.outB : a.outA;
     if (a.last && METHOD == MM) {
@@ -325,20 +326,20 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4
             for (int j = 0; j < KC; ++j) { yc[j] = zc[j]; yr[j] = zr[j]; }
             traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<0>(zc, yc, ac, kc, a.h);
-            rk4_update<0>(zr, yr, ar, kr, a.h);
+            rk4_update<0>(zc, yc, ac, kc, a);
+            rk4_update<0>(zr, yr, ar, kr, a);
             traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<1>(zc, yc, ac, kc, a.h);
-            rk4_update<1>(zr, yr, ar, kr, a.h);
+            rk4_update<1>(zc, yc, ac, kc, a);
+            rk4_update<1>(zr, yr, ar, kr, a);
             traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<2>(zc, yc, ac, kc, a.h);
-            rk4_update<2>(zr, yr, ar, kr, a.h);
+            rk4_update<2>(zc, yc, ac, kc, a);
+            rk4_update<2>(zr, yr, ar, kr, a);
             traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<3>(zc, yc, ac, kc, a.h);
-            rk4_update<3>(zr, yr, ar, kr, a.h);
+            rk4_update<3>(zc, yc, ac, kc, a);
+            rk4_update<3>(zr, yr, ar, kr, a);
         }
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
@@ -644,17 +645,17 @@ __global__ void __launch_bounds__(32 * KS_WARPS_PER_BLOCK, 3) stencil_ks_rk4(Ste
 #pragma unroll
             for (int j = 0; j < KC; ++j) { yA[j] = zA[j]; yB[j] = zB[j]; }
             ks_rhs<METHOD>(p, yA, yB, kA, kB);
-            rk4_update<0>(zA, yA, aA, kA, a.h);
-            rk4_update<0>(zB, yB, aB, kB, a.h);
+            rk4_update<0>(zA, yA, aA, kA, a);
+            rk4_update<0>(zB, yB, aB, kB, a);
             ks_rhs<METHOD>(p, yA, yB, kA, kB);
-            rk4_update<1>(zA, yA, aA, kA, a.h);
-            rk4_update<1>(zB, yB, aB, kB, a.h);
+            rk4_update<1>(zA, yA, aA, kA, a);
+            rk4_update<1>(zB, yB, aB, kB, a);
             ks_rhs<METHOD>(p, yA, yB, kA, kB);
-            rk4_update<2>(zA, yA, aA, kA, a.h);
-            rk4_update<2>(zB, yB, aB, kB, a.h);
+            rk4_update<2>(zA, yA, aA, kA, a);
+            rk4_update<2>(zB, yB, aB, kB, a);
             ks_rhs<METHOD>(p, yA, yB, kA, kB);
-            rk4_update<3>(zA, yA, aA, kA, a.h);
-            rk4_update<3>(zB, yB, aB, kB, a.h);
+            rk4_update<3>(zA, yA, aA, kA, a);
+            rk4_update<3>(zB, yB, aB, kB, a);
         }
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
@@ -754,6 +755,8 @@ static int run_steps(int R, int kc, int64_t n, const double *xlo, const double *
         a.tcount = a.ntiles;
         a.S = s;
         a.h = h;
+        a.hh = 0.5 * h;
+        a.h6 = h / 6.0;
         a.first = (q == 0);
         a.last = (q == L - 1);
         a.inA = (q == 0) ? xlo : bufA[(L - q) % 2];
@@ -865,6 +868,8 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         a.ntiles = (n + a.W - 1) / a.W;
         a.S = S;
         a.h = h;
+        a.hh = 0.5 * h;
+        a.h6 = h / 6.0;
         a.status = sg.status;
         a.vec = (reinterpret_cast<uintptr_t>(buf) % 16) == 0;   // one allocation, even strides
         double *bufA[2] = {dlo, sA}, *bufB[2] = {dhi, sB};
@@ -944,6 +949,8 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         a.tcount = a.ntiles;
         a.S = s;
         a.h = h;
+        a.hh = 0.5 * h;
+        a.h6 = h / 6.0;
         a.first = (q == 0);
         a.last = (q == L - 1);
         a.inA = (q == 0) ? dxlo : bufA[(L - q) % 2];
