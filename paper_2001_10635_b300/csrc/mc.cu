@@ -294,6 +294,9 @@ struct McStep {
     unsigned ntile;           // ceil(n / TC), computed on the host
     int S;                    // RK4 steps in this launch (0: only sample, t_final = 0)
     double h, hh, h6;         // h, h/2, h/6 (computed on the host)
+    float hf[3];              // the same rounded to binary32, and the system
+    float qf[4];              // constants as mc_consts forms them (host-rounded:
+                              // a conversion would occupy the FP64 pipe)
     uint64_t seed;
     const double *xlo, *xhi;  // first launch: the initial box
     double dlo, dhi;          // traffic inflow box
@@ -332,7 +335,12 @@ mc_stream(McStep a, const double *__restrict__ prm) {
     const int64_t own0 = tile * a.TC;
     const int64_t row0 = own0 - a.H + (int64_t)warp * B;   // global row of this warp's first row
     T q[4];
-    mc_consts<SYS, T>(prm, q);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = a.qf[i];
+    } else {
+        mc_consts<SYS, T>(prm, q);
+    }
     int flags = 0;
     T d = T(0);
     if (SYS == REACH_TRAFFIC) d = as_run<T>(box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j, 0u, 1u)));
@@ -368,7 +376,12 @@ mc_stream(McStep a, const double *__restrict__ prm) {
         off += a.M;
         ++gi;
     }
-    const T h = (T)a.h, hh = (T)a.hh, h6 = (T)a.h6;
+    T h = (T)a.h, hh = (T)a.hh, h6 = (T)a.h6;
+    if constexpr (sizeof(T) == 4) {
+        h = a.hf[0];
+        hh = a.hf[1];
+        h6 = a.hf[2];
+    }
     int buf = 0;
     for (int s = 0; s < a.S; ++s) {
         // e[R + r] is the stage input of row r; e[0..R) and e[R+B..) hold the
@@ -652,6 +665,17 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         s.h = base.h;
         s.hh = 0.5 * base.h;
         s.h6 = base.h / 6.0;
+        s.hf[0] = (float)s.h;
+        s.hf[1] = (float)s.hh;
+        s.hf[2] = (float)s.h6;
+        {
+            const double *pr = sys->prm;   // mc_consts's binary32 constants, rounded here
+            const bool tr = sys->kind == REACH_TRAFFIC;
+            s.qf[0] = (float)pr[0];
+            s.qf[1] = (float)pr[1];
+            s.qf[2] = (float)pr[2];
+            s.qf[3] = tr ? (float)(pr[2] * pr[3]) : (float)pr[3];
+        }
         s.seed = base.seed;
         s.xlo = base.xlo;
         s.xhi = base.xhi;
