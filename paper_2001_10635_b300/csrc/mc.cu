@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include <atomic>
+#include <type_traits>
 
 #include "api_internal.cuh"
 #include "quad.cuh"
@@ -309,6 +310,12 @@ struct McStep {
 
 constexpr int MC_B = 16;   // rows per warp
 
+// the same for a cell with a right neighbour inside the chain (0 <= g < n - 1)
+template <class T>
+__device__ __forceinline__ T tr_flux_interior(const T (&q)[4], T y, T yr) {
+    return tmin(q[0], tmin(q[1] * y, tfma(-q[2], yr, q[3])));
+}
+
 // traffic flux out of global cell g from its value y and its right neighbour yr
 template <class T>
 __device__ __forceinline__ T tr_flux(const T (&q)[4], T y, T yr, int64_t g, int64_t n, T d) {
@@ -382,57 +389,70 @@ mc_stream(McStep a, const double *__restrict__ prm) {
         hh = a.hf[1];
         h6 = a.hf[2];
     }
+    // A traffic warp whose fluxes are all between two cells of the chain (rows
+    // row0 - 1 .. row0 + B - 1 inside [0, n - 1)) takes them without the
+    // boundary selects, which cost issue slots in this issue-bound kernel.
+    const bool interior = SYS != REACH_KS && row0 >= 1 && row0 + B <= n - 1;
     int buf = 0;
-    for (int s = 0; s < a.S; ++s) {
-        // e[R + r] is the stage input of row r; e[0..R) and e[R+B..) hold the
-        // neighbouring warps' edge rows
-        T e[B + 2 * R], acc[B];
+    auto steps = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;
+        (void)IN;
+        for (int s = 0; s < a.S; ++s) {
+            // e[R + r] is the stage input of row r; e[0..R) and e[R+B..) hold the
+            // neighbouring warps' edge rows
+            T e[B + 2 * R], acc[B];
 #pragma unroll
-        for (int r = 0; r < B; ++r) e[R + r] = z[r];
+            for (int r = 0; r < B; ++r) e[R + r] = z[r];
 #pragma unroll
-        for (int stage = 0; stage < 4; ++stage) {
+            for (int stage = 0; stage < 4; ++stage) {
 #pragma unroll
-            for (int q2 = 0; q2 < R; ++q2) {
-                edge[buf][warp][q2][lane] = e[R + q2];
-                edge[buf][warp][R + q2][lane] = e[B + q2];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q2 = 0; q2 < R; ++q2) {
-                e[q2] = warp > 0 ? edge[buf][warp - 1][R + q2][lane] : T(0);
-                e[B + R + q2] = warp < WPB - 1 ? edge[buf][warp + 1][q2][lane] : T(0);
-            }
-            buf ^= 1;
-            // derivative of row r, then the update of row r - R, whose stage
-            // input row r was the last to read; only R + 1 derivatives are live
-            T kring[R + 1];
-            T fprev = T(0);
-            if constexpr (SYS != REACH_KS) fprev = tr_flux<T>(q, e[0], e[1], row0 - 1, n, d);   // flux into row 0
-#pragma unroll
-            for (int r = 0; r < B + R; ++r) {
-                if (r < B) {
-                    T kr;
-                    if constexpr (SYS == REACH_KS) {
-                        T um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
-                        kr = tfma(u, tfma(-q[3], up1 - um1, q[0]), tfma(q[1], um1 + up1, q[2] * (um2 + up2)));
-                    } else {
-                        T fout = tr_flux<T>(q, e[r + 1], e[r + 2], row0 + r, n, d);
-                        kr = fprev - fout;
-                        fprev = fout;
-                    }
-                    kring[r % (R + 1)] = kr;
+                for (int q2 = 0; q2 < R; ++q2) {
+                    edge[buf][warp][q2][lane] = e[R + q2];
+                    edge[buf][warp][R + q2][lane] = e[B + q2];
                 }
-                if (r >= R) {
-                    const int u = r - R;
-                    const T k = kring[u % (R + 1)];
-                    if (stage == 0) { acc[u] = k; e[R + u] = tfma(hh, k, z[u]); }
-                    if (stage == 1) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(hh, k, z[u]); }
-                    if (stage == 2) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(h, k, z[u]); }
-                    if (stage == 3) { acc[u] += k; z[u] = tfma(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                __syncthreads();
+#pragma unroll
+                for (int q2 = 0; q2 < R; ++q2) {
+                    e[q2] = warp > 0 ? edge[buf][warp - 1][R + q2][lane] : T(0);
+                    e[B + R + q2] = warp < WPB - 1 ? edge[buf][warp + 1][q2][lane] : T(0);
+                }
+                buf ^= 1;
+                // derivative of row r, then the update of row r - R, whose stage
+                // input row r was the last to read; only R + 1 derivatives are live
+                T kring[R + 1];
+                T fprev = T(0);
+                (void)fprev;
+                if constexpr (SYS != REACH_KS)   // flux into row 0
+                    fprev = IN ? tr_flux_interior<T>(q, e[0], e[1]) : tr_flux<T>(q, e[0], e[1], row0 - 1, n, d);
+#pragma unroll
+                for (int r = 0; r < B + R; ++r) {
+                    if (r < B) {
+                        T kr;
+                        if constexpr (SYS == REACH_KS) {
+                            T um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                            kr = tfma(u, tfma(-q[3], up1 - um1, q[0]), tfma(q[1], um1 + up1, q[2] * (um2 + up2)));
+                        } else {
+                            T fout = IN ? tr_flux_interior<T>(q, e[r + 1], e[r + 2])
+                                        : tr_flux<T>(q, e[r + 1], e[r + 2], row0 + r, n, d);
+                            kr = fprev - fout;
+                            fprev = fout;
+                        }
+                        kring[r % (R + 1)] = kr;
+                    }
+                    if (r >= R) {
+                        const int u = r - R;
+                        const T k = kring[u % (R + 1)];
+                        if (stage == 0) { acc[u] = k; e[R + u] = tfma(hh, k, z[u]); }
+                        if (stage == 1) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(hh, k, z[u]); }
+                        if (stage == 2) { acc[u] = tfma(T(2), k, acc[u]); e[R + u] = tfma(h, k, z[u]); }
+                        if (stage == 3) { acc[u] += k; z[u] = tfma(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                    }
                 }
             }
         }
-    }
+    };
+    if (interior) steps(std::true_type{});
+    else steps(std::false_type{});
     int64_t oo = (int64_t)(int32_t)row0 * (int32_t)a.M + j;   // store offset of row 0 (owned rows are in range)
     const int64_t pb = (int64_t)((uint64_t)(uint32_t)sb * (uint32_t)n);
     double *plo = a.plo + pb + row0, *phi = a.phi + pb + row0;
