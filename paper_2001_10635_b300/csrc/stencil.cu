@@ -106,8 +106,9 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
 // ------------------------------------------------------------------ traffic
 // k[j] = f_{g-1} - f_g: flux out of cell g is min(cap, v y_g, w (xbar - y_{g+1}))
 // (min(cap, v y_g) for the last cell), the inflow of cell 0 is d, and cells
-// outside [0, n) carry no flux.
-template <bool POW2, int KC>
+// outside [0, n) carry no flux.  IN: every flux of the tile is between two
+// cells of the chain, so none of those cases arises and the tests are skipped.
+template <bool POW2, int KC, bool IN = false>
 __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                             int64_t n, double d, double (&k)[KC]) {
     double e[KC + 2];
@@ -135,13 +136,16 @@ __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)
     for (int j = 0; j < KC; ++j) {
         const int64_t g = g0 + j;
         double cong = fma(-p.w, e[2 + j], p.wxbar);
-        cong = (g == n - 1) ? p.cap : cong;          // no congestion term at the outlet
+        if (!IN) cong = (g == n - 1) ? p.cap : cong;          // no congestion term at the outlet
         double fj = kmin(p.cap, kmin(vy[j], cong));
-        fj = (g == -1) ? d : fj;
-        f[j] = (g < -1 || g >= n) ? 0.0 : fj;
+        if (!IN) {
+            fj = (g == -1) ? d : fj;
+            fj = (g < -1 || g >= n) ? 0.0 : fj;
+        }
+        f[j] = fj;
     }
     double fl = __shfl_up_sync(0xffffffffu, f[KC - 1], 1);
-    fl = (g0 == 0) ? d : fl;
+    if (!IN) fl = (g0 == 0) ? d : fl;
 #pragma unroll
     for (int j = 0; j < KC; ++j) k[j] = (j == 0 ? fl : f[j - 1]) - f[j];
 }
@@ -163,15 +167,15 @@ __device__ __forceinline__ void traffic_growth(const TrafficK &p, const double (
 }
 
 // one traffic half per warp: HALF 0 = x / c, HALF 1 = xh / r
-template <int METHOD, int HALF, bool POW2, int KC>
+template <int METHOD, int HALF, bool POW2, int KC, bool IN>
 __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                                  int64_t n, double (&k)[KC]) {
-    if (METHOD == MM) traffic_rhs<POW2>(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
-    else if (HALF == 0) traffic_rhs<POW2>(p, y, g0, n, p.d_c, k);
-    else traffic_growth(p, y, g0, n, k);
+    if (METHOD == MM) traffic_rhs<POW2, KC, IN>(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
+    else if (HALF == 0) traffic_rhs<POW2, KC, IN>(p, y, g0, n, p.d_c, k);
+    else traffic_growth(p, y, g0, n, k);   // the radius keeps its boundary tests
 }
 
-template <int METHOD, int HALF, bool POW2, int KC>
+template <int METHOD, int HALF, bool POW2, int KC, bool IN>
 __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &p, int64_t t, int lane,
                                              int &flags) {
     const int64_t n = a.n;
@@ -197,13 +201,13 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
         double y[KC], acc[KC], k[KC];
 #pragma unroll
         for (int j = 0; j < KC; ++j) y[j] = z[j];
-        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
         rk4_update<0>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
         rk4_update<1>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
         rk4_update<2>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2>(p, y, g0, n, k);
+        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
         rk4_update<3>(z, y, acc, k, a);
     }
     double *out = HALF ? a.outB : a.outA;
@@ -235,8 +239,23 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
     const int64_t cnt = a.tcount;
     int flags = 0;
     for (int64_t t = warp; t < 2 * cnt; t += nwarps) {
-        if (t < cnt) traffic_tile<METHOD, 0, POW2, KC>(a, p, a.tile0 + t, lane, flags);
-        else traffic_tile<METHOD, 1, POW2, KC>(a, p, a.tile0 + t - cnt, lane, flags);
+        const int64_t tile = a.tile0 + (t < cnt ? t : t - cnt);
+        // Inside the chain (every flux of the tile, cells own0 - H - 1 ..
+        // own0 - H + 32 KC - 1, between two of its cells) the boundary tests are
+        // skipped: MM 5% faster.  The CGB radius keeps them (2% slower without).
+        const int64_t c0 = tile * a.W - a.H;
+        const bool in = c0 >= 1 && c0 + 32 * KC <= a.n - 1;
+        if (t < cnt) {
+            if (in) traffic_tile<METHOD, 0, POW2, KC, true>(a, p, tile, lane, flags);
+            else traffic_tile<METHOD, 0, POW2, KC, false>(a, p, tile, lane, flags);
+        } else {
+            if constexpr (METHOD == MM) {
+                if (in) traffic_tile<METHOD, 1, POW2, KC, true>(a, p, tile, lane, flags);
+                else traffic_tile<METHOD, 1, POW2, KC, false>(a, p, tile, lane, flags);
+            } else {
+                traffic_tile<METHOD, 1, POW2, KC, false>(a, p, tile, lane, flags);
+            }
+        }
     }
     if (flags) atomicOr(a.status, flags);
 }
