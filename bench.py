@@ -55,7 +55,7 @@ CPU_SAMPLE_CELLS = 1 << 20
 # DRAM bytes (read + write) of one stencil_traffic_rk4<MM> launch, ncu capture on
 # 2^24 cells (profiles/stencil_traffic_rk4_mm_traffic_n16M.md); the traffic of a
 # launch is proportional to the cells, so it is scaled to the run's n
-NCU_DRAM_BYTES_PER_CELL_LAUNCH = (268.532736e6 + 224.521472e6) / (1 << 24)
+NCU_DRAM_BYTES_PER_CELL_LAUNCH = (268.636928e6 + 224.436736e6) / (1 << 24)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
