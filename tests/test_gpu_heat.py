@@ -56,8 +56,10 @@ def test_small_cube_matches_oracle(l, open_face, method, kernel):
 
 
 @pytest.mark.parametrize("method", ["mm", "cgb"])
-@pytest.mark.parametrize("l", [9, 16, 21, 40])
+@pytest.mark.parametrize("l", [9, 16, 21, 40, 97])
 def test_stage_kernels_match_oracle(l, method):
+    # l = 97: thread blocks (32 x 8 cells of a plane) inside the cube as well as
+    # on each of its faces
     lo, hi = random_cube(l, seed=100 + l)
     alpha = 0.5 / (6 * 0.02 * l * l)   # h 6 kh = 0.5: strong diffusion per step
     prm = (alpha, l, 1)
