@@ -195,9 +195,9 @@ struct McArgs {
 // ------------------------------------------------------------------ on-chip
 // A block holds SB samples (smp = threadIdx % SB) of the whole state; its
 // threads form G = blockDim / SB row groups, group g holding rows g, g + G, ...
-// (at most MC_Q).  Sample j = block * SB + smp draws the same Philox numbers
+// (at most Q <= MC_Q).  Sample j = block * SB + smp draws the same Philox numbers
 // whatever SB is, so the box does not depend on the layout.
-template <int SYS, class T, int SB>
+template <int SYS, class T, int SB, int Q>
 __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
     extern __shared__ unsigned char smraw[];
     T *Y = (T *)smraw;                    // [n][SB]
@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
         if (smp == 0 && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
         P[k * SB + smp] = as_run<T>(box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j, (uint32_t)k, 1u)));
     }
-    T z[MC_Q], acc[MC_Q], kk[MC_Q];
+    T z[Q], acc[Q], kk[Q];
 #pragma unroll
-    for (int s = 0; s < MC_Q; ++s) {
+    for (int s = 0; s < Q; ++s) {
         int c = grp + s * G;
         z[s] = acc[s] = T(0);
         if (c < n) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
 #pragma unroll
-            for (int s = 0; s < MC_Q; ++s) {
+            for (int s = 0; s < Q; ++s) {
                 int c = grp + s * G;
                 if (c < n) {
                     if constexpr (SYS == REACH_LINEAR)
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
             __syncthreads();
             const T cst = (stage == 2) ? h : hh;
 #pragma unroll
-            for (int s = 0; s < MC_Q; ++s) {
+            for (int s = 0; s < Q; ++s) {
                 int c = grp + s * G;
                 if (c < n) {
                     T y;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(MC_THREADS) mc_onchip(McArgs a) {
         }
     }
 #pragma unroll
-    for (int s = 0; s < MC_Q; ++s) {
+    for (int s = 0; s < Q; ++s) {
         // every lane of a group takes part in its shuffles (a group's lanes
         // share their row count, so no lane of a warp leaves early)
         const int c = grp + s * G;
@@ -563,15 +563,27 @@ static int launch_onchip_sb(const McArgs &a, cudaStream_t st) {
         G = (a.n + unit - 1) / unit * unit;
         if (G > MC_THREADS / SB) G = MC_THREADS / SB;
     }
-    if ((a.n + G - 1) / G > MC_Q) return REACH_EINVAL;   // more rows than a thread holds
+    const int64_t rows = (a.n + G - 1) / G;
+    if (rows > MC_Q) return REACH_EINVAL;   // more rows than a thread holds
     const size_t smem = (size_t)(a.n + a.nw) * SB * sizeof(T);
-    static std::atomic<bool> attr{false};   // idempotent: a second setter is harmless
-    if (!attr.load()) {
-        int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T, SB>);
-        if (rc) return rc;
-        attr.store(true);
+    // one row per thread runs a one-row loop: the eight-row one keeps the
+    // absent rows' code in the stage loop
+    static std::atomic<bool> attr1{false}, attr8{false};   // idempotent: a second setter is harmless
+    if (rows == 1) {
+        if (!attr1.load()) {
+            int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T, SB, 1>);
+            if (rc) return rc;
+            attr1.store(true);
+        }
+        mc_onchip<SYS, T, SB, 1><<<(unsigned)nblk, (unsigned)(SB * G), smem, st>>>(a);
+    } else {
+        if (!attr8.load()) {
+            int rc = allow_max_dynamic_smem((const void *)mc_onchip<SYS, T, SB, MC_Q>);
+            if (rc) return rc;
+            attr8.store(true);
+        }
+        mc_onchip<SYS, T, SB, MC_Q><<<(unsigned)nblk, (unsigned)(SB * G), smem, st>>>(a);
     }
-    mc_onchip<SYS, T, SB><<<(unsigned)nblk, (unsigned)(SB * G), smem, st>>>(a);
     REACH_LAUNCHED("mc_onchip");
     return REACH_OK;
 }
