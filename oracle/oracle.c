@@ -392,9 +392,7 @@ typedef struct { double lo, hi; } ival;
 
 #define ORC_PI 3.141592653589793
 #define ORC_HALF_PI 1.5707963267948966
-#define ORC_THREE_HALF_PI 4.71238898038469
 #define ORC_TWO_PI 6.283185307179586
-#define ORC_INV_TWO_PI 0.15915494309189535
 
 static ival iv_hull(double a, double b) { ival r = {min2(a, b), max2(a, b)}; return r; }
 static ival iv_add(ival a, ival b) { ival r = {a.lo + b.lo, a.hi + b.hi}; return r; }
@@ -408,27 +406,28 @@ static ival iv_mul(ival a, ival b)
 static ival iv_scale(double c, ival a) { return iv_mul((ival){c, c}, a); }
 static double iv_mag(ival a) { return max2(fabs(a.lo), fabs(a.hi)); }
 
-/* does c + 2 pi k lie in [a, b] for some integer k (c in [0, 2 pi), b - a
-   < 2 pi): r = a - 2 pi floor(a / 2 pi) is where a falls in [0, 2 pi), and
-   the first such point at or after a lies c - r beyond it (c + 2 pi - r when
-   c < r) */
+/* does c + 2 pi k lie in [a, b] for some integer k: take the smallest k
+   with c + 2 pi k >= a (the first such point at or after a) and test it
+   against b.  The quotient only proposes k; the two loops make the
+   definition hold for the computed points. */
 static int holds_point(double a, double b, double c)
 {
-    double k = floor(a * ORC_INV_TWO_PI);
-    double r = a - ORC_TWO_PI * k;
-    double d = (c >= r) ? c - r : (c + ORC_TWO_PI) - r;
-    return d <= b - a;
+    double k = ceil((a - c) / ORC_TWO_PI);
+    double p = c + ORC_TWO_PI * k;
+    while (p < a) { k += 1.0; p = c + ORC_TWO_PI * k; }
+    while (c + ORC_TWO_PI * (k - 1.0) >= a) { k -= 1.0; p = c + ORC_TWO_PI * k; }
+    return p <= b;
 }
 
 /* range of sin over [a, b]: the endpoints, and +-1 where a maximum
-   (pi/2 + 2 pi k) or minimum (3 pi/2 + 2 pi k) lies inside */
+   (pi/2 + 2 pi k) or minimum (-pi/2 + 2 pi k) lies inside */
 static ival iv_sin(ival a)
 {
     ival r = {-1.0, 1.0};
     double s0, s1;
     if (a.hi - a.lo >= ORC_TWO_PI) return r;
     s0 = sin(a.lo); s1 = sin(a.hi);
-    r.lo = holds_point(a.lo, a.hi, ORC_THREE_HALF_PI) ? -1.0 : min2(s0, s1);
+    r.lo = holds_point(a.lo, a.hi, -ORC_HALF_PI) ? -1.0 : min2(s0, s1);
     r.hi = holds_point(a.lo, a.hi, ORC_HALF_PI) ? 1.0 : max2(s0, s1);
     return r;
 }

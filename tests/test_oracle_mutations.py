@@ -63,6 +63,9 @@ MUTATIONS = [
     ('quad inertia swapped', '        dy[10] = tau[1] / s->Jy;\n        dy[11] = tau[2] / s->Jz;\n    }\n}\n\nstatic void f_sys', '        dy[10] = tau[1] / s->Jx;\n        dy[11] = tau[2] / s->Jz;\n    }\n}\n\nstatic void f_sys'),
     ('quad agent input stride', 'const double *y = x + 12 * k, *tau = p + 3 * k;', 'const double *y = x + 12 * k, *tau = p + 2 * k;'),
     ('quad interval sin misses its maximum', 'r.hi = holds_point(a.lo, a.hi, ORC_HALF_PI) ? 1.0 : max2(s0, s1);', 'r.hi = max2(s0, s1);'),
+    ('quad extremum test takes the point one period before a',
+     'return p <= b;', 'return p - ORC_TWO_PI <= b;'),
+    ('quad extremum test compares with the wrong end', 'return p <= b;', 'return p <= a;'),
     ('quad interval cos minimum point', 'r.lo = holds_point(a.lo, a.hi, ORC_PI) ? -1.0 : min2(c0, c1);', 'r.lo = holds_point(a.lo, a.hi, ORC_HALF_PI) ? -1.0 : min2(c0, c1);'),
     ('quad interval product drops a corner', 'ival r = {min2(min2(p1, p2), min2(p3, p4)), max2(max2(p1, p2), max2(p3, p4))};', 'ival r = {min2(p1, p4), max2(p1, p4)};'),
     ('quad decomposition orientation', 'dy[3] = lower ? an.lo : an.hi;', 'dy[3] = lower ? an.hi : an.lo;'),
