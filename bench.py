@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -52,9 +53,9 @@ FP64_OPS = {"mm": 15.0, "cgb": 15.0}
 SM_COUNT, FP64_PER_SM_CLK, SM_MAX_MHZ = 148, 2, 2032.0
 FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
 CPU_SAMPLE_CELLS = 1 << 20
-# DRAM bytes (read + write) of one stencil_traffic_rk4<MM> launch, ncu capture on
-# 2^24 cells (profiles/stencil_traffic_rk4_mm_traffic_n16M.md); the traffic of a
-# launch is proportional to the cells, so it is scaled to the run's n
+# DRAM bytes (read + write) of one stencil_traffic_rk4<MM> launch, from the ncu
+# capture of one launch on 2^24 cells; the traffic of a launch is proportional
+# to the cells, so it is scaled to the run's n
 NCU_DRAM_BYTES_PER_CELL_LAUNCH = (268.636928e6 + 224.436736e6) / (1 << 24)
 
 
@@ -128,6 +129,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def host_cpu():
+    """The host the oracle runs on: logical CPUs (nproc) and the CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown"}
+
+
 def cpu_oracle_rate(cells: int = CPU_SAMPLE_CELLS):
     """The FP64 oracle (single thread) on the first `cells` cells, both methods."""
     import oracle as O
@@ -153,7 +168,7 @@ def oracle_rates():
         t0 = time.perf_counter()
         fn()
         sec = time.perf_counter() - t0
-        out[label] = {"value": comps / sec, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+        out[label] = {"value": comps / sec, "unit": "comp-steps/s", "cores": 1, **host_cpu(), "kind": "oracle",
                       "sample": sample, "s": sec}
 
     ks = W.ks_grid(1 << 14, t_final=0.005)
@@ -616,11 +631,111 @@ def run_reference(args):
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": headline_config(N_CELLS, world),
-            "cpu_baseline": {"value": value, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "comp-steps/s", "cores": 1, **host_cpu(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "comp-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "vs_baseline": None}
     print(json.dumps(line))
+    return 0
+
+
+def run_profile_case(a):
+    """--profile-case CASE: run one named workload twice (a warm-up call, then
+    the call a profiler captures) and exit; no timing, no JSON line.
+
+    Cases (sizes from --case-n / --case-m / --case-t, else the defaults):
+      ks_mm, ks_cgb        KS grid, n points (default 2^20), T (default 0.05)
+      ks_mc32, ks_mc64     KS grid, m samples (default 256 / 32)
+      traffic_mm           traffic chain, n cells (default 2^24), T (default 0.02)
+      traffic16_mm         traffic chain n = 16, T = 10 (on-chip kernel)
+      traffic_cgbl         traffic CGB with the box-evaluated C, n cells (default 2^24), T (default 0.02)
+      traffic_sound_mm     outward-rounded traffic MM, n cells (default 2^24), T (default 0.02)
+      osc_batch            the 4096-query oscillator batch (MM T=5, CGB T=4)
+      heat_mm, heat_cgb    heat cube of side l = n (default 256), T (default 0.1)
+      quad_mm, quad_cgb, quad_mc32   quadrotor swarm of n agents (default 10^6), T (default 0.1)
+    """
+    import torch
+
+    import paper_2001_10635_b300 as R
+
+    dev = torch.device("cuda", 0)
+    to = lambda v: torch.tensor(v, dtype=torch.float64, device=dev)
+
+    if a.profile_case.startswith("ks_"):
+        n = a.case_n or (1 << 20)
+        wl = W.ks_grid(n, t_final=a.case_t or 0.05)
+        x0, x1 = to(wl["x_lo"]), to(wl["x_hi"])
+        with R.System("ks", n) as s:
+            kw = dict(t_final=wl["t_final"], dt=wl["dt"])
+            if a.profile_case == "ks_mm":
+                f = lambda: R.reach_mm(s, x0, x1, **kw)
+            elif a.profile_case == "ks_cgb":
+                f = lambda: R.reach_cgb(s, x0, x1, **kw)
+            else:
+                prec = 32 if a.profile_case == "ks_mc32" else 64
+                m = a.case_m or (256 if prec == 32 else 32)
+                f = lambda: R.reach_mc(s, x0, x1, **kw, m=m, seed=0, precision=prec)
+            f()
+            f()
+    elif a.profile_case == "traffic_mm":
+        n = a.case_n or (1 << 24)
+        wl = W.traffic_large(n, t_final=a.case_t or 0.02)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        with R.System("traffic", n) as s:
+            for _ in range(2):
+                R.reach_mm(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    elif a.profile_case in ("traffic_cgbl", "traffic_sound_mm"):
+        n = a.case_n or (1 << 24)
+        wl = W.traffic_large(n, t_final=a.case_t or 0.02)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        prm = (40.0, 0.5, 1 / 6, 320.0, 1, 0) if a.profile_case == "traffic_cgbl" else (40.0, 0.5, 1 / 6, 320.0, 0, 1)
+        f = R.reach_cgb if a.profile_case == "traffic_cgbl" else R.reach_mm
+        with R.System("traffic", n, params=prm) as s:
+            for _ in range(2):
+                f(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    elif a.profile_case == "traffic16_mm":
+        wl = W.traffic_small(16)
+        with R.System("traffic", 16) as s:
+            for _ in range(2):
+                R.reach_mm(s, wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=wl["t_final"], dt=wl["dt"])
+    elif a.profile_case in ("heat_mm", "heat_cgb"):
+        l = a.case_n or 256
+        lo, hi = W.heat_cube_torch(l, dev)
+        with R.System("heat", l ** 3) as s:
+            f = R.reach_mm if a.profile_case == "heat_mm" else R.reach_cgb
+            for _ in range(2):
+                f(s, lo, hi, t_final=a.case_t or 0.1, dt=W.HEAT_DT)
+    elif a.profile_case.startswith("quad_"):
+        K = a.case_n or 1_000_000
+        wl = W.quad_swarm(K, seed=0, t_final=a.case_t or 0.1)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        args = (d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"])
+        kw = dict(t_final=wl["t_final"], dt=wl["dt"])
+        with R.System("quad", 12 * K) as s:
+            for _ in range(2):
+                if a.profile_case == "quad_mm":
+                    R.reach_mm(s, *args, **kw)
+                elif a.profile_case == "quad_cgb":
+                    R.reach_cgb(s, *args, **kw)
+                else:
+                    R.reach_mc(s, *args, **kw, m=a.case_m or 32, seed=0, precision=32)
+    elif a.profile_case == "osc_batch":
+        sizes = W.osc_sizes(4096, seed=0)
+        systems, qs = {}, []
+        for k, m in enumerate(sizes):
+            q = W.osc_query(int(m), seed=1000003 + k)
+            s = systems.setdefault(int(m), R.System("osc", 2 * int(m)))
+            d = {kk: to(q[kk]) for kk in ("x_lo", "x_hi", "w_lo", "w_hi")}
+            for method, T in (("mm", W.OSC_T), ("cgb", W.OSC_T_CGB)):
+                qs.append(dict(sys=s, method=method, x0_lo=d["x_lo"], x0_hi=d["x_hi"], w_lo=d["w_lo"],
+                               w_hi=d["w_hi"], t_final=T, dt=W.OSC_DT))
+        with R.Batch(qs) as b:
+            b.run()
+            b.run()
+    else:
+        raise SystemExit(f"unknown case {a.profile_case}")
+    torch.cuda.synchronize()
+    print("done", a.profile_case, R.reach_kernel_launches(), "launches")
     return 0
 
 
@@ -635,7 +750,13 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched, KS and small-config sections")
     ap.add_argument("--cells", type=int, default=N_CELLS,
                     help="chain length (default 2^26; smaller values are for profiler captures only)")
+    ap.add_argument("--profile-case", default="", help="run one named workload for a profiler capture and exit")
+    ap.add_argument("--case-n", type=int, default=0)
+    ap.add_argument("--case-m", type=int, default=0)
+    ap.add_argument("--case-t", type=float, default=0.0)
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -770,7 +891,7 @@ def main():
         if "batched" in line:
             line["cpu_oracle_sections"] = oracle_rates()
         r, sec, cs = cpu_oracle_rate()
-        line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": r, "unit": "comp-steps/s", "cores": 1, **host_cpu(), "kind": "oracle",
                                 "sample": f"first {CPU_SAMPLE_CELLS} cells, MM + CGB, 200 steps ({sec:.1f} s)"}
     sysm.close()
     if rank == 0:

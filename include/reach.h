@@ -200,11 +200,14 @@ REACH_API int64_t reach_mc_samples(int64_t n, double eps, double delta);
    nothing: the kernel's ping-pong state buffer and the status word live in a
    fixed device buffer of the library (16 MiB + 256 B, held on every GPU that
    loads the library until the process exits).
-     - n <= REACH_NOALLOC_MAX_N, else REACH_EINVAL; other kinds: REACH_EINVAL.
+     - n <= REACH_NOALLOC_MAX_N, else REACH_EINVAL; other kinds, and traffic
+       systems created with outward rounding (sound), give REACH_EINVAL.
      - x0_lo, x0_hi, lo, hi must be device pointers (REACH_EINVAL otherwise);
        w_lo, w_hi (traffic inflow) may be host or device.
-     - The first call on each device looks up the buffer's device address
-       (cudaGetSymbolAddress); make that first call before any stream capture.
+     - Every call looks up the buffer's device address on the current
+       device (cudaGetSymbolAddress, which allocates nothing); the first call
+       on a device also makes the runtime load the module that holds the
+       buffer, so make that first call before any stream capture begins.
      - All calls share the buffer: calls whose work overlaps on the GPU (on
        different streams, or from several threads) race and give wrong
        results.  Each call clears the status word before use.

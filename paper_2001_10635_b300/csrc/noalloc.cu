@@ -10,8 +10,6 @@
 // and the status word in a fixed buffer that the library defines at file
 // scope.  Every GPU that loads the library holds this buffer until the
 // process exits.
-#include <mutex>
-
 #include "api_internal.cuh"
 
 namespace reach {
@@ -20,23 +18,15 @@ namespace reach {
 // by the status word
 static __device__ __align__(256) double g_noalloc_scratch[2 * REACH_NOALLOC_MAX_N + 32];
 
-static std::mutex g_noalloc_mu;
-static double *g_noalloc_addr[64];   // device address of the buffer, per device
-
-// Device address of the buffer on the current device.  The name
-// g_noalloc_scratch is only a host-side stand-in: kernels must be given the
-// address the runtime reports for the current device.
+// Device address of the buffer on the current device, looked up on every
+// call (the lookup allocates nothing and stays valid across a device reset,
+// which reloads the module at another address).  The name g_noalloc_scratch
+// is only a host-side stand-in: kernels must be given the address the runtime
+// reports for the current device.
 static int noalloc_buffer(double **out) {
-    int dev = 0;
-    REACH_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return REACH_ENODEV;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        REACH_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = (double *)p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    REACH_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = (double *)p;
     return REACH_OK;
 }
 
@@ -83,11 +73,15 @@ extern "C" int reach_mm_noalloc(const reach_system *sys, const double *x0_lo, co
         }
         if (!(wl <= wh) || !std::isfinite(wl) || !std::isfinite(wh)) return REACH_EINVAL;
         TrafficK p = make_traffic_k(sys->prm, wl, wh);
-        rc = stencil_traffic(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, opt_steps() > 0 ? (int)opt_steps() : 1, status, st);
+        // the launch schedule of reach_mm: several RK4 steps per launch for
+        // grids too short to fill the GPU (the ping-pong buffer is the same)
+        const int S = opt_steps() > 0 ? (int)opt_steps() : stencil_short_steps(1, 2, n);
+        rc = stencil_traffic(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, S, status, st);
     } else {
         KsK p;
         p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
-        rc = stencil_ks(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, opt_steps() > 0 ? (int)opt_steps() : 1, status, st);
+        const int S = opt_steps() > 0 ? (int)opt_steps() : stencil_short_steps(2, 1, n);
+        rc = stencil_ks(MM, p, n, x0_lo, x0_hi, lo, hi, sA, sB, dt, N, S, status, st);
     }
     if (rc) return rc;
     int host_status = 0;

@@ -299,6 +299,27 @@ def _window(i, n, radius_cells):
     return a, b
 
 
+# Cells a 256-cell warp tile owns at one RK4 step per launch: 256 minus a
+# halo of 4 R cells per side (traffic R = 1, KS R = 2).  Tile t owns
+# [t W, (t + 1) W); the first and last tiles take the chain's boundary path,
+# the others the interior path.
+TRAFFIC_OWNED = 256 - 2 * 4
+KS_OWNED = 256 - 2 * 8
+
+
+def _tile_edge_cells(n, W):
+    """Cells at the offsets 0, 1, W/2 - 1, W - 2, W - 1 of the first and last
+    interior tiles and of a middle tile, and the first, second and last cell
+    of the last (ragged) tile."""
+    ntiles = -(-n // W)
+    cells = []
+    for t in (1, ntiles // 2, ntiles - 2):
+        cells += [t * W + o for o in (0, 1, W // 2 - 1, W - 2, W - 1)]
+    last = (ntiles - 1) * W
+    cells += [last, last + 1, n - 1]
+    return [c for c in cells if 0 <= c < n]
+
+
 @pytest.mark.parametrize("method", ["mm", "cgb"])
 def test_traffic_full_size_sampled_cells(method):
     wl = W.traffic_large(1 << 26, seed=0)
@@ -307,7 +328,8 @@ def test_traffic_full_size_sampled_cells(method):
     g = gpu_box(method, "traffic", n, wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], T, dt)
     assert np.isfinite(g[0]).all() and np.isfinite(g[1]).all() and (g[0] <= g[1]).all()
     cells = [0, 1, 5, 4 * N, 12345678, n // 2 + 17, n - 4 * N - 3, n - 2, n - 1]
-    for i in cells:
+    cells += _tile_edge_cells(n, TRAFFIC_OWNED)
+    for i in sorted(set(cells)):
         a, b = _window(i, n, 4 * N + 2)
         olo, ohi = O.reach(method, "traffic", wl["x_lo"][a:b], wl["x_hi"][a:b], wl["w_lo"], wl["w_hi"],
                            t_final=T, dt=dt)
@@ -324,7 +346,7 @@ def test_ks_full_size_sampled_cells(method):
     g = gpu_box(method, "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt)
     assert np.isfinite(g[0]).all() and (g[0] <= g[1]).all()
     L = 16 * N + 8   # periodic window: the wrap travels 8N cells at most in N steps
-    for i in [0, 7, n // 3, n - 1]:
+    for i in sorted(set([0, 7, n // 3, n - 1] + _tile_edge_cells(n, KS_OWNED))):
         idx = (i - L // 2 + np.arange(L)) % n
         olo, ohi = O.reach(method, "ks", wl["x_lo"][idx], wl["x_hi"][idx], t_final=T, dt=dt,
                            params=wl["params"])
@@ -339,8 +361,9 @@ def test_ks_full_size_mc32_inside_mm():
     mm = gpu_box("mm", "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt)
     mc = gpu_box("mc", "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt, m=1024, seed=0, precision=32)
     assert np.isfinite(mc[0]).all() and (mc[0] <= mc[1]).all()
-    # FP32 trajectories are inside the FP64 MM box up to FP32 rounding of the state
-    slack = 1e-5 * np.abs(mm[1]).max()
+    # binary32 trajectories: inside the binary64 MM box up to the binary32
+    # parity tolerance (the reading of the mc32 containment test below)
+    slack = TOL32 * max(np.abs(mm[0]).max(), np.abs(mm[1]).max())
     assert (mc[0] >= mm[0] - slack).all() and (mc[1] <= mm[1] + slack).all()
     assert (mc[1] - mc[0]).min() > 0
 
@@ -447,3 +470,58 @@ def test_host_buffer_overlap_path(method, T, S):
     gd = gpu_box(method, "traffic", n, *d, T, dt)
     np.testing.assert_array_equal(g[0], gd[0].cpu().numpy())
     np.testing.assert_array_equal(g[1], gd[1].cpu().numpy())
+
+
+# ------------------------------------------------------------------ MC samples inside the boxes
+# (kind, n, samples, forced kernel: 0 = the library's choice, 1 = streaming)
+CONTAIN = [("traffic", 40, 300, 0), ("traffic", 700, 64, 1), ("ks", 64, 256, 0), ("ks", 600, 64, 1),
+           ("osc", 8, 300, 0), ("osc", 40, 256, 0), ("linear", 5, 300, 0), ("linear", 12, 256, 0),
+           ("heat", 64, 300, 0), ("heat", 125, 200, 0)]
+
+
+def _containment_problem(kind, n, kernel):
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=21)
+    if kind == "heat":
+        l = round(n ** (1 / 3))
+        prm = (0.05, l, 1)
+    if kernel == 1:
+        T = 0.13 if kind == "traffic" else 0.003
+    return lo, hi, wlo, whi, T, dt, prm, A
+
+
+def _escapes(inner, outer):
+    """Margins of the inner box inside the outer one (negative: an escape)."""
+    return np.asarray(inner[0]) - np.asarray(outer[0]), np.asarray(outer[1]) - np.asarray(inner[1])
+
+
+@pytest.mark.parametrize("kind,n,m,kernel", CONTAIN, ids=[f"{k}{n}m{m}k{s}" for k, n, m, s in CONTAIN])
+def test_mc64_samples_inside_mm_and_cgb_exactly(kind, n, m, kernel):
+    # Sec. 2.1: MM and CGB over-approximate the reachable set, so every
+    # binary64 sample trajectory ends inside both boxes; checked with no slack
+    # (an escape is reported with its margin, never absorbed)
+    lo, hi, wlo, whi, T, dt, prm, A = _containment_problem(kind, n, kernel)
+    R.reach_set_option(R.OPT_KERNEL, kernel)
+    mc = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, params=prm, A=A, m=m, seed=5, precision=64)
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, params=prm, A=A, m=m, seed=5, prec=64)
+    assert_close(mc[0], o[0], TOL64, "mc lo")
+    assert_close(mc[1], o[1], TOL64, "mc hi")
+    for method in ("mm", "cgb"):
+        box = gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=prm, A=A)
+        dlo, dhi = _escapes(mc, box)
+        assert dlo.min() >= 0.0, f"{method}: sample below the box by {-dlo.min()!r} at {int(dlo.argmin())}"
+        assert dhi.min() >= 0.0, f"{method}: sample above the box by {-dhi.min()!r} at {int(dhi.argmin())}"
+
+
+@pytest.mark.parametrize("kind,n,m,kernel", CONTAIN[:6], ids=[f"{k}{n}m{m}k{s}" for k, n, m, s in CONTAIN[:6]])
+def test_mc32_samples_inside_mm_within_the_binary32_tolerance(kind, n, m, kernel):
+    # binary32 trajectories start from the binary32 rounding of each sample
+    # (which may lie outside the binary64 box by half a binary32 unit) and
+    # carry binary32 rounding error: they are held to the box widened by the
+    # binary32 parity tolerance, TOL32 times the box's magnitude
+    lo, hi, wlo, whi, T, dt, prm, A = _containment_problem(kind, n, kernel)
+    R.reach_set_option(R.OPT_KERNEL, kernel)
+    mc = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, params=prm, A=A, m=m, seed=5, precision=32)
+    box = gpu_box("mm", kind, n, lo, hi, wlo, whi, T, dt, params=prm, A=A)
+    slack = TOL32 * max(np.abs(box[0]).max(), np.abs(box[1]).max())
+    dlo, dhi = _escapes(mc, box)
+    assert dlo.min() >= -slack and dhi.min() >= -slack, (dlo.min(), dhi.min(), slack)

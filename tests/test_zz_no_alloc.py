@@ -60,6 +60,28 @@ def test_noalloc_matches_reach_mm_on_two_calls():
             assert_close(hi.cpu().numpy(), ref[1].cpu().numpy(), TOL64, f"call {seed} hi")
 
 
+def test_noalloc_host_inflow_short_grid_and_zero_horizon():
+    # the traffic inflow box from host memory, a grid short enough for several
+    # RK4 steps per launch, and a zero horizon (the box itself)
+    import torch
+    f = _noalloc()
+    n, T, dt = 5000, 0.37, 0.01
+    with R.System("traffic", n) as s:
+        wl, d = _traffic_case(n, 6)
+        lo = torch.empty(n, dtype=torch.float64, device="cuda")
+        hi = torch.empty_like(lo)
+        for _ in range(2):
+            rc = f(s.handle, d["x_lo"].data_ptr(), d["x_hi"].data_ptr(), wl["w_lo"].ctypes.data,
+                   wl["w_hi"].ctypes.data, T, dt, lo.data_ptr(), hi.data_ptr(), None)
+            assert rc == 0, R.strerror(rc)
+            ref = R.reach_mm(s, wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=T, dt=dt)
+            assert_close(lo.cpu().numpy(), ref[0], TOL64, "lo")
+            assert_close(hi.cpu().numpy(), ref[1], TOL64, "hi")
+        rc, lo0, hi0 = _call(f, s, d, 0.0, dt)
+        assert rc == 0
+        assert torch.equal(lo0, d["x_lo"]) and torch.equal(hi0, d["x_hi"])
+
+
 def test_noalloc_ks_at_the_size_limit():
     import torch
     f = _noalloc()
@@ -85,6 +107,15 @@ def test_noalloc_rejects_what_it_cannot_run():
         lo, hi = np.empty(1000), np.empty(1000)
         rc = f(s.handle, wl["x_lo"].ctypes.data, wl["x_hi"].ctypes.data, wl["w_lo"].ctypes.data,
                wl["w_hi"].ctypes.data, 0.1, 0.01, lo.ctypes.data, hi.ctypes.data, None)
+        assert rc == -1
+    with R.System("traffic", 1000) as s:        # inverted inflow box
+        _, d = _traffic_case(1000, 5)
+        d["w_lo"], d["w_hi"] = d["w_hi"], d["w_lo"]
+        rc, _, _ = _call(f, s, d, 0.1, 0.01)
+        assert rc == -1
+    with R.System("traffic", 1000, params=(40.0, 0.5, 1 / 6, 320.0, 0, 1)) as s:   # outward rounding
+        _, d = _traffic_case(1000, 5)
+        rc, _, _ = _call(f, s, d, 0.1, 0.01)
         assert rc == -1
     A = np.eye(3) * -1.0
     with R.System("linear", 3, A=A) as s:       # no streaming kernel for this kind
