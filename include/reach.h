@@ -254,6 +254,50 @@ REACH_API int reach_batch_run(reach_batch *b, void *stream, int *status, double 
 REACH_API int reach_batch_info(const reach_batch *b, int64_t *cpt, int64_t *kernels, double *tune_ms);
 REACH_API int reach_batch_destroy(reach_batch *b);
 
+/* ---- device work queue: small queries run as they arrive ----
+   Algorithms 2 and 3 for queries that arrive one by one while other work
+   runs (the paper runs one query per call; this queue is new).  A query whose
+   2n components fit one block (n <= REACH_QUEUE_MAX_N, and its stage vectors
+   in shared memory) is appended to a ring in page-locked host memory that the
+   GPU reads directly; the blocks of a persistent kernel take the published
+   queries one at a time and integrate each whole horizon on chip, so a queued
+   query costs no kernel launch, no copy call and no stream synchronisation.
+   The queue launches blocks as queries arrive (one per query without a free
+   block, at most max_blocks over all system kinds); a block that finds no
+   query for idle_s seconds leaves by itself, so an idle queue holds no SM
+   (a cudaDeviceSynchronize meanwhile waits up to idle_s for those blocks).
+   Host vectors are staged in a page-locked arena of arena_bytes; the caller's
+   input buffers may be reused when reach_queue_submit returns, its output
+   buffers must stay valid until reach_queue_wait returns for the ticket.
+   The four functions are thread-safe. */
+#define REACH_QUEUE_MAX_N 4096
+typedef struct reach_queue reach_queue;
+REACH_API int reach_queue_create(int max_blocks, double idle_s, int64_t arena_bytes, reach_queue **out);
+/* Queues one MM or CGB query (a reach_query, as for batches).  REACH_EINVAL
+   for an invalid query, a zero horizon, a kind the queue does not run (the
+   quadrotor, outward-rounded traffic) or n above REACH_QUEUE_MAX_N;
+   REACH_EADMIT when 2048 queries of its kind are in flight or the staging
+   arena is full (wait for results first). */
+REACH_API int reach_queue_submit(reach_queue *q, const reach_query *query, int64_t *ticket);
+/* Waits at most timeout_s seconds for a ticket: REACH_ETIMEOUT if it has not
+   finished (it keeps running; wait again).  Otherwise copies staged outputs to
+   the caller's host buffers, sets *status (REACH_OK, REACH_EINVAL for an
+   inverted or non-finite box seen on the device, REACH_ENONFINITE) and
+   forgets the ticket. */
+REACH_API int reach_queue_wait(reach_queue *q, int64_t ticket, double timeout_s, int *status);
+/* Launches `blocks` blocks of kind's persistent kernel now (they also start by
+   themselves when queries are submitted). */
+REACH_API int reach_queue_start(reach_queue *q, int kind, int blocks);
+/* Waits at most timeout_s seconds for every block of the queue to leave:
+   REACH_ETIMEOUT if some are still running.  Otherwise *exit_status tells how
+   the last launch ended: REACH_ETIMEOUT when its blocks left because no query
+   came within idle_s (their bounded wait ran out), REACH_OK when asked to stop. */
+REACH_API int reach_queue_join(reach_queue *q, double timeout_s, int *exit_status);
+/* queries submitted and not yet waited for, blocks running now, blocks launched so far */
+REACH_API int reach_queue_stats(reach_queue *q, int64_t *in_flight, int64_t *alive_blocks, int64_t *launched_blocks);
+/* runs every submitted query to its end, then frees the queue */
+REACH_API int reach_queue_destroy(reach_queue *q);
+
 /* ---- serving: a continuous-batching request loop ----
    The paper serves reachability problems to other tools over a network
    interface (Sec. 1); here that purpose is an in-process server.  Requests of
@@ -301,13 +345,18 @@ REACH_API int reach_server_destroy(reach_server *s);
 
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
-#define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming kernels: RK4 steps per launch, 1..8; 0 = auto (FP64 1, FP32 MC 2) */
+#define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming kernels: RK4 steps per launch, 1..8; 0 = auto (FP64 1, FP32 MC
+                                        2, FP32 MC on KS grids 3) */
 #define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
 #define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
 #define REACH_OPT_TILE 5             /* streaming traffic / KS MM and CGB: cells per lane, 0 = auto, 2 (64-cell
                                         warp tiles, taken only while the halo leaves half the tile) or 8 (256) */
 #define REACH_OPT_MC_SB 6            /* on-chip MC: samples per block, 0 = auto (32 from 4736 samples, 8 from 1184,
                                         else 2), or 2 / 8 / 32 */
+#define REACH_OPT_MC_LAYOUT 7         /* streaming binary32 MC: 0 auto (two samples per lane, packed FP32
+                                        arithmetic, measured block shape), 1 one sample per lane; 2..5 block
+                                        shapes of the two-sample kernel (warps x rows x blocks per SM:
+                                        16x16x1, 32x8x1, 8x16x2, 16x8x2) */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

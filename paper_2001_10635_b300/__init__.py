@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libreach.so")
 
 TRAFFIC, KS, OSC, LINEAR, HEAT3D, QUAD = 0, 1, 2, 3, 4, 5
 KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D, "quad": QUAD}
-OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT, OPT_TILE, OPT_MC_SB = 1, 2, 3, 4, 5, 6
+OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT, OPT_TILE, OPT_MC_SB, OPT_MC_LAYOUT = 1, 2, 3, 4, 5, 6, 7
 BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
           -4: "REACH_ENONFINITE", -5: "REACH_ETIMEOUT", -6: "REACH_ECUDA", -7: "REACH_ENODEV"}
@@ -98,6 +98,13 @@ def lib() -> ctypes.CDLL:
         L.reach_batch_run.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl)]
         L.reach_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         L.reach_batch_destroy.argtypes = [vp]
+        L.reach_queue_create.argtypes = [ctypes.c_int, dbl, i64, ctypes.POINTER(vp)]
+        L.reach_queue_submit.argtypes = [vp, ctypes.POINTER(_Query), ctypes.POINTER(i64)]
+        L.reach_queue_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(ctypes.c_int)]
+        L.reach_queue_start.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.reach_queue_join.argtypes = [vp, dbl, ctypes.POINTER(ctypes.c_int)]
+        L.reach_queue_stats.argtypes = [vp] + [ctypes.POINTER(i64)] * 3
+        L.reach_queue_destroy.argtypes = [vp]
         L.reach_request_footprint.argtypes = [ctypes.POINTER(_Request)]
         L.reach_request_footprint.restype = i64
         L.reach_server_create.argtypes = [ctypes.c_int, i64, ctypes.POINTER(vp)]
@@ -354,6 +361,76 @@ class Batch:
         if self.handle:
             lib().reach_batch_destroy(self.handle)
             self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ------------------------------------------------------------------ device work queue
+QUEUE_MAX_N = 4096
+_KIND_IDS = {"traffic": 0, "ks": 1, "osc": 2, "linear": 3, "heat": 4}
+
+
+class Queue:
+    """reach_queue_create / _submit / _wait / _start / _join / _stats / _destroy."""
+
+    def __init__(self, max_blocks: int = 64, idle_s: float = 0.005, arena_bytes: int = 256 << 20):
+        self.handle = ctypes.c_void_p()
+        _check(lib().reach_queue_create(int(max_blocks), float(idle_s), int(arena_bytes), ctypes.byref(self.handle)),
+               "reach_queue_create")
+        self._keep = {}
+
+    def submit(self, sys_, method, x0_lo, x0_hi, w_lo=None, w_hi=None, *, t_final, dt, lo=None, hi=None):
+        """Returns (ticket, (lo, hi)); the outputs are complete after wait(ticket)."""
+        a = _ptr(x0_lo, sys_.n, "x0_lo")
+        b = _ptr(x0_hi, sys_.n, "x0_hi")
+        c = _ptr(w_lo, sys_.nw, "w_lo") if sys_.nw else (None, None)
+        d = _ptr(w_hi, sys_.nw, "w_hi") if sys_.nw else (None, None)
+        lo = _out(x0_lo, lo, sys_.n, "lo")
+        hi = _out(x0_lo, hi, sys_.n, "hi")
+        q = _Query(sys_.handle.value, _METHOD_IDS[method] if isinstance(method, str) else int(method), a[0], b[0],
+                   c[0], d[0], float(t_final), float(dt), _ptr(lo, sys_.n, "lo")[0], _ptr(hi, sys_.n, "hi")[0])
+        t = ctypes.c_int64()
+        _check(lib().reach_queue_submit(self.handle, ctypes.byref(q), ctypes.byref(t)), "reach_queue_submit")
+        self._keep[t.value] = (sys_, lo, hi)
+        return t.value, (lo, hi)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> int:
+        """Returns the query's status; raises ReachError(REACH_ETIMEOUT) on timeout."""
+        st = ctypes.c_int()
+        _check(lib().reach_queue_wait(self.handle, int(ticket), float(timeout_s), ctypes.byref(st)),
+               "reach_queue_wait")
+        self._keep.pop(ticket, None)
+        return st.value
+
+    def start(self, kind: str, blocks: int):
+        _check(lib().reach_queue_start(self.handle, _KIND_IDS[kind], int(blocks)), "reach_queue_start")
+
+    def join(self, timeout_s: float = 60.0) -> int:
+        """Waits for every block to leave; returns the last launch's exit status."""
+        st = ctypes.c_int()
+        _check(lib().reach_queue_join(self.handle, float(timeout_s), ctypes.byref(st)), "reach_queue_join")
+        return st.value
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(lib().reach_queue_stats(self.handle, *[ctypes.byref(x) for x in v]), "reach_queue_stats")
+        return dict(zip(("in_flight", "alive_blocks", "launched_blocks"), [x.value for x in v]))
+
+    def close(self):
+        if self.handle:
+            lib().reach_queue_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

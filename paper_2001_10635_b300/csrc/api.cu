@@ -24,7 +24,7 @@ int cuda_fail(cudaError_t e, const char *where) {
 
 // process-wide options; read by calls on any thread
 static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
-    g_opt_mc_sb{0};
+    g_opt_mc_sb{0}, g_opt_mc_layout{0};
 
 // ---------------------------------------------------------------- memory
 static std::atomic<bool> g_pool_ready[64];
@@ -186,6 +186,7 @@ int64_t opt_block() { return g_opt_block; }
 int64_t opt_batch_cpt() { return g_opt_batch_cpt; }
 int64_t opt_tile() { return g_opt_tile; }
 int64_t opt_mc_sb() { return g_opt_mc_sb; }
+int64_t opt_mc_layout() { return g_opt_mc_layout; }
 
 }  // namespace reach
 
@@ -518,6 +519,10 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value != 0 && value != 2 && value != 8 && value != 32) return REACH_EINVAL;
         g_opt_mc_sb = value;
         return REACH_OK;
+    case REACH_OPT_MC_LAYOUT:
+        if (value < 0 || value > 5) return REACH_EINVAL;
+        g_opt_mc_layout = value;
+        return REACH_OK;
     }
     return REACH_EINVAL;
 }
@@ -530,6 +535,7 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_BATCH_CPT: return g_opt_batch_cpt;
     case REACH_OPT_TILE: return g_opt_tile;
     case REACH_OPT_MC_SB: return g_opt_mc_sb;
+    case REACH_OPT_MC_LAYOUT: return g_opt_mc_layout;
     }
     return REACH_EINVAL;
 }

@@ -47,11 +47,15 @@ int64_t opt_block();
 int64_t opt_batch_cpt();
 int64_t opt_tile();
 int64_t opt_mc_sb();
+int64_t opt_mc_layout();
 // samples per block of the on-chip MC kernel for m samples (2, 8 or 32)
 int mc_onchip_sb(int64_t m);
 
 // traffic parameters as the streaming kernel sees them (inputs d in [wl, wh])
 TrafficK make_traffic_k(const double *prm, double wl, double wh);
+
+// device work queue: whether a query of this system and method can be queued
+bool queue_accepts(const reach_system *s, int method);
 
 // kernels
 constexpr int BATCH_THREADS = 512;   // threads per block of the batched kernel

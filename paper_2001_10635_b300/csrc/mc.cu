@@ -466,6 +466,177 @@ mc_stream(McStep a, const double *__restrict__ prm) {
     if (flags) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ streaming, two samples per lane
+// The binary32 streaming kernel is issue-bound: one sample per lane spends an
+// issue slot on every FP32 operation.  Blackwell's packed FP32 instructions
+// (__ffma2_rn, __fadd2_rn, __fmul2_rn: two IEEE binary32 operations, each
+// rounded to nearest, in one issue) let a lane carry two adjacent samples
+// j0 = 64 sb + 2 lane and j0 + 1 as a float2, halving the arithmetic
+// instructions per sample and making every state access one 8-byte access per
+// lane.  Each sample sees the same operations in the same order as in
+// mc_stream, so the two kernels give the same box bit for bit.  Minima have no
+// packed form and stay per sample (traffic only).  A block covers 64 samples
+// and WPB * B rows; the state rows hold M samples, M a multiple of 64.
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 min2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 sel2(bool p, float2 a, float2 b) { return p ? a : b; }
+
+struct Q2 {
+    float2 cap, v, nw, wxbar;   // traffic: cap, v, -w, w xbar
+    float2 a0, a1, a2, nk;      // KS: a0, a1, a2, -k
+};
+
+__device__ __forceinline__ float2 tr_flux2_interior(const Q2 &q, float2 y, float2 yr) {
+    return min2(q.cap, min2(mul2(q.v, y), fma2(q.nw, yr, q.wxbar)));
+}
+
+__device__ __forceinline__ float2 tr_flux2(const Q2 &q, float2 y, float2 yr, int64_t g, int64_t n, float2 d) {
+    const float2 cong = (g == n - 1) ? q.cap : fma2(q.nw, yr, q.wxbar);
+    float2 f = min2(q.cap, min2(mul2(q.v, y), cong));
+    f = sel2(g == -1, d, f);
+    return sel2(g < -1 || g >= n, bc2(0.f), f);
+}
+
+// min / max of one component row over the warp's 64 samples (valid ones only)
+__device__ __forceinline__ void warp_minmax2(float2 v, bool v0, bool v1, double *plo, double *phi, int *status) {
+    float a = fminf(v0 ? v.x : INFINITY, v1 ? v.y : INFINITY);
+    float b = fmaxf(v0 ? v.x : -INFINITY, v1 ? v.y : -INFINITY);
+    const bool bad = (v0 && !isfinite(v.x)) || (v1 && !isfinite(v.y));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+    if ((threadIdx.x & 31) == 0) { *plo = (double)a; *phi = (double)b; }
+}
+
+template <int SYS, int WPB, int B, int MINB>
+__global__ void __launch_bounds__(32 * WPB, MINB) mc_stream2(McStep a) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    __shared__ float2 edge[2][WPB][2 * R][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = a.n;
+    const int64_t tile = blockIdx.x % a.ntile, sb = blockIdx.x / a.ntile;   // 32-bit division
+    const int64_t j0 = sb * 64 + 2 * lane;
+    const bool v0 = j0 < a.m, v1 = j0 + 1 < a.m;
+    const int64_t own0 = tile * a.TC;
+    const int64_t row0 = own0 - a.H + (int64_t)warp * B;
+    Q2 q;
+    q.cap = bc2(a.qf[0]); q.v = bc2(a.qf[1]); q.nw = bc2(-a.qf[2]); q.wxbar = bc2(a.qf[3]);
+    q.a0 = bc2(a.qf[0]); q.a1 = bc2(a.qf[1]); q.a2 = bc2(a.qf[2]); q.nk = bc2(-a.qf[3]);
+    int flags = 0;
+    float2 d = bc2(0.f);
+    if (SYS == REACH_TRAFFIC) {
+        d.x = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j0, 0u, 1u));
+        d.y = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)(j0 + 1), 0u, 1u));
+    }
+    const int64_t nM = a.nM;
+    const int64_t wr0 = (SYS == REACH_KS) ? wrap_index(row0, n) : row0;
+    int64_t off = (int64_t)(int32_t)wr0 * (int32_t)a.M + j0;   // in floats; even
+    int64_t gi = wr0;
+    float2 z[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        const int64_t g = row0 + r;
+        bool in = true;
+        if (SYS == REACH_KS) {
+            if (off >= nM) { off -= nM; gi -= n; }
+        } else {
+            in = g >= 0 && g < n;
+        }
+        float2 v = bc2(0.f);
+        if (in) {
+            if (a.first) {
+                const double lo = a.xlo[gi], hi = a.xhi[gi];
+                const bool owned = g >= own0 && g < own0 + a.TC;
+                if (lane == 0 && owned && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+                v.x = (float)box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)j0, (uint32_t)gi, 0u));
+                v.y = (float)box_sample(lo, hi, philox_uniform(a.seed, (uint32_t)(j0 + 1), (uint32_t)gi, 0u));
+            } else {
+                v = *reinterpret_cast<const float2 *>((const float *)a.in + off);
+            }
+        }
+        z[r] = v;
+        off += a.M;
+        ++gi;
+    }
+    const float2 h = bc2(a.hf[0]), hh = bc2(a.hf[1]), h6 = bc2(a.hf[2]), two = bc2(2.f);
+    const bool interior = SYS != REACH_KS && row0 >= 1 && row0 + B <= n - 1;
+    int buf = 0;
+    auto steps = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;
+        (void)IN;
+        for (int s = 0; s < a.S; ++s) {
+            float2 e[B + 2 * R], acc[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) e[R + r] = z[r];
+#pragma unroll
+            for (int stage = 0; stage < 4; ++stage) {
+#pragma unroll
+                for (int q2 = 0; q2 < R; ++q2) {
+                    edge[buf][warp][q2][lane] = e[R + q2];
+                    edge[buf][warp][R + q2][lane] = e[B + q2];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q2 = 0; q2 < R; ++q2) {
+                    e[q2] = warp > 0 ? edge[buf][warp - 1][R + q2][lane] : bc2(0.f);
+                    e[B + R + q2] = warp < WPB - 1 ? edge[buf][warp + 1][q2][lane] : bc2(0.f);
+                }
+                buf ^= 1;
+                float2 kring[R + 1];
+                float2 fprev = bc2(0.f);
+                (void)fprev;
+                if constexpr (SYS != REACH_KS)
+                    fprev = IN ? tr_flux2_interior(q, e[0], e[1]) : tr_flux2(q, e[0], e[1], row0 - 1, n, d);
+#pragma unroll
+                for (int r = 0; r < B + R; ++r) {
+                    if (r < B) {
+                        float2 kr;
+                        if constexpr (SYS == REACH_KS) {
+                            const float2 um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                            kr = fma2(u, fma2(q.nk, sub2(up1, um1), q.a0),
+                                      fma2(q.a1, add2(um1, up1), mul2(q.a2, add2(um2, up2))));
+                        } else {
+                            const float2 fout = IN ? tr_flux2_interior(q, e[r + 1], e[r + 2])
+                                                   : tr_flux2(q, e[r + 1], e[r + 2], row0 + r, n, d);
+                            kr = sub2(fprev, fout);
+                            fprev = fout;
+                        }
+                        kring[r % (R + 1)] = kr;
+                    }
+                    if (r >= R) {
+                        const int u = r - R;
+                        const float2 k = kring[u % (R + 1)];
+                        if (stage == 0) { acc[u] = k; e[R + u] = fma2(hh, k, z[u]); }
+                        if (stage == 1) { acc[u] = fma2(two, k, acc[u]); e[R + u] = fma2(hh, k, z[u]); }
+                        if (stage == 2) { acc[u] = fma2(two, k, acc[u]); e[R + u] = fma2(h, k, z[u]); }
+                        if (stage == 3) { acc[u] = add2(acc[u], k); z[u] = fma2(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                    }
+                }
+            }
+        }
+    };
+    if (interior) steps(std::true_type{});
+    else steps(std::false_type{});
+    int64_t oo = (int64_t)(int32_t)row0 * (int32_t)a.M + j0;
+    const int64_t pb = (int64_t)((uint64_t)(uint32_t)sb * (uint32_t)n);
+    double *plo = a.plo + pb + row0, *phi = a.phi + pb + row0;
+#pragma unroll
+    for (int r = 0; r < B; ++r, oo += a.M) {
+        const int64_t g = row0 + r;
+        if (g < own0 || g >= own0 + a.TC || g >= n) continue;   // warp-uniform
+        if (a.last) warp_minmax2(z[r], v0, v1, plo + r, phi + r, a.status);
+        else *reinterpret_cast<float2 *>((float *)a.out + oo) = z[r];
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
 // ------------------------------------------------------------------ reduce
 __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, int64_t n, double *lo,
                           double *hi) {
@@ -630,6 +801,57 @@ static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, voi
     return REACH_OK;
 }
 
+// binary32 streaming with two samples per lane: a block of WPB warps x B rows
+// x 64 samples, at least MINB blocks per SM
+template <int SYS, int WPB, int B, int MINB>
+static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_auto, cudaStream_t st) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    int S = opt_steps() > 0 ? (int)opt_steps() : S_auto;
+    while (S > 1 && 2 * 4 * R * S >= WPB * B / 2) --S;   // keep the halo below half the block
+    const int64_t L = N > 0 ? (N + S - 1) / S : 1;
+    void *buf[2] = {bufA, bufB};
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = N > 0 ? (int)std::min<int64_t>(S, N - done) : 0;
+        a.S = s;
+        a.H = 4 * R * s;
+        a.TC = WPB * B - 2 * a.H;
+        a.first = (q == 0);
+        a.last = (q == L - 1);
+        a.in = buf[q % 2];
+        a.out = buf[(q + 1) % 2];
+        const int64_t ntile = (a.n + a.TC - 1) / a.TC;
+        const int64_t grid = ntile * (a.M / 64);
+        if (grid > 0x7fffffffLL) return REACH_EINVAL;
+        a.ntile = (unsigned)ntile;
+        mc_stream2<SYS, WPB, B, MINB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a);
+        REACH_LAUNCHED("mc_stream2");
+        done += s;
+    }
+    return REACH_OK;
+}
+
+// Block shapes (REACH_OPT_MC_LAYOUT 2..5) and the measured default per system
+// (1024 samples of the 2^20-point KS grid over 500 steps, 256 of the 2^20-cell
+// chain over 200): the packed kernel is bound by the FP32 FMA pipe (a packed
+// instruction holds it two cycles), so the shape that best overlaps one
+// block's loads with another's arithmetic wins.  KS: one 16-warp block per
+// SM at three steps per launch (0.96 s; two 8-warp blocks at two steps 1.02
+// s, the one-sample kernel 1.05 s at its best S).  Traffic: two 8-warp blocks
+// per SM at two steps (0.084 s against 0.098 s for the one-sample kernel).
+template <int SYS>
+static int launch_stream2(const McStep &a, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
+    int layout = (int)opt_mc_layout();
+    if (layout == 0) layout = SYS == REACH_KS ? 2 : 4;
+    const int S_auto = SYS == REACH_KS ? 3 : 2;
+    switch (layout) {
+    case 3: return launch_stream2_v<SYS, 32, 8, 1>(a, N, bufA, bufB, S_auto, st);
+    case 4: return launch_stream2_v<SYS, 8, 16, 2>(a, N, bufA, bufB, S_auto, st);
+    case 5: return launch_stream2_v<SYS, 16, 8, 2>(a, N, bufA, bufB, S_auto, st);
+    default: return launch_stream2_v<SYS, 16, 16, 1>(a, N, bufA, bufB, S_auto, st);
+    }
+}
+
 int64_t mc_onchip_limit(int kind, int prec) {
     // rows per thread x warps, and shared memory for [n + nw][32]
     int64_t by_regs = (int64_t)MC_Q * MC_WARPS;
@@ -671,8 +893,10 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
     bool onchip = n <= mc_onchip_limit(sys->kind, sizeof(T) == 4 ? 32 : 64);
     if (opt_kernel() == 1 && (sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS) && n >= 16) onchip = false;
     if (!onchip && !(sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS)) return REACH_EINVAL;
+    // binary32 samples on the streaming kernel go two per lane
+    const bool pairs = !onchip && sizeof(T) == 4 && opt_mc_layout() != 1;
     // partial minima / maxima per block of samples
-    const int sb = onchip ? mc_onchip_sb(base.m) : 32;
+    const int sb = onchip ? mc_onchip_sb(base.m) : (pairs ? 64 : 32);
     int64_t nblk = (base.m + sb - 1) / sb;
     McArgs a = base;
     if ((rc = sg.scratch(2 * nblk * n * sizeof(double), (void **)&a.plo))) return rc;
@@ -689,10 +913,10 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         McStep s;
         memset(&s, 0, sizeof s);
         // the kernel forms row offsets by 32 x 32 -> 64-bit products
-        if (n > INT32_MAX - 64 || nblk * 32 > INT32_MAX) return REACH_EINVAL;
+        if (n > INT32_MAX - 64 || nblk * sb > INT32_MAX) return REACH_EINVAL;
         s.n = n;
         s.m = base.m;
-        s.M = nblk * 32;
+        s.M = nblk * sb;
         s.nM = n * s.M;
         s.h = base.h;
         s.hh = 0.5 * base.h;
@@ -721,8 +945,14 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
             if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufA))) return rc;
             if ((rc = sg.scratch((size_t)n * s.M * sizeof(T), &bufB))) return rc;
         }
-        if (sys->kind == REACH_TRAFFIC) rc = launch_stream<REACH_TRAFFIC, T>(s, base.prm, base.N, bufA, bufB, sg.st);
-        else rc = launch_stream<REACH_KS, T>(s, base.prm, base.N, bufA, bufB, sg.st);
+        if (pairs) {
+            if (sys->kind == REACH_TRAFFIC) rc = launch_stream2<REACH_TRAFFIC>(s, base.N, bufA, bufB, sg.st);
+            else rc = launch_stream2<REACH_KS>(s, base.N, bufA, bufB, sg.st);
+        } else if (sys->kind == REACH_TRAFFIC) {
+            rc = launch_stream<REACH_TRAFFIC, T>(s, base.prm, base.N, bufA, bufB, sg.st);
+        } else {
+            rc = launch_stream<REACH_KS, T>(s, base.prm, base.N, bufA, bufB, sg.st);
+        }
     }
     if (rc) return rc;
     int64_t g = (n + 255) / 256;

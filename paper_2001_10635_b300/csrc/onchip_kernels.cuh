@@ -8,6 +8,7 @@
 #include <atomic>
 
 #include "api_internal.cuh"
+#include "queue.cuh"
 
 namespace reach {
 
@@ -203,6 +204,113 @@ int onchip_batch_k(int method, int q, const void *items, const void *slots, cons
     REACH_BQ(QMAX)
 #undef REACH_BQ
     return REACH_EINVAL;
+}
+
+
+// ---------------------------------------------------------------- device work queue
+// Persistent kernel of the work queue (queue.cuh, queue.cu): each block claims
+// one published item at a time from the kind's ring (a compare-and-swap on
+// the device head, so no item is claimed twice and none is lost), runs it
+// with the same whole-horizon device code as onchip_single, and signals its
+// completion in mapped host memory.  Every wait is bounded: a block with no
+// item for idle_ns leaves (exit word QEXIT_IDLE), and one asked to stop
+// leaves at its next idle poll (QEXIT_STOPPED).
+
+// load at system scope with acquire semantics: the host writes an item before
+// it advances the tail past it
+__device__ __forceinline__ long long ld_acquire_sys(const long long *p) {
+    long long v;
+    asm volatile("ld.acquire.sys.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int SYS, int METHOD>
+__device__ __forceinline__ void queue_run(const OnItem &it, double *sm, int active) {
+    const int64_t n = it.n;
+    double *yA = sm, *yB = sm + n, *yA2 = sm + 2 * n, *yB2 = sm + 3 * n, *wA = sm + 4 * n, *wB = wA + it.nw;
+    // the first `active` threads run the item: barrier 1 over them (a warp
+    // syncs itself), so that the other warps wait at the block barrier
+    GroupSync sync{1, active};
+    const int64_t comps = 2 * n;
+    const int t = (int)threadIdx.x;
+    if (comps <= active) onchip_run<SYS, METHOD, 1>(it, yA, yB, yA2, yB2, wA, wB, 0, comps, t, active, sync);
+    else if (comps <= 4 * active) onchip_run<SYS, METHOD, 4>(it, yA, yB, yA2, yB2, wA, wB, 0, comps, t, active, sync);
+    else onchip_run<SYS, METHOD, QMAX>(it, yA, yB, yA2, yB2, wA, wB, 0, comps, t, active, sync);
+}
+
+template <int SYS>
+__global__ void __launch_bounds__(QUEUE_THREADS, 1) queue_kernel(QueueArgs a) {
+    extern __shared__ double sm[];
+    __shared__ long long claimed;
+    __shared__ QueueItem cur;
+    unsigned long long since = global_ns();
+    int code = QEXIT_IDLE;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long c = -1;
+            unsigned ns = 256;
+            for (;;) {
+                const long long t = ld_acquire_sys(a.tail);
+                const unsigned long long h = *(volatile unsigned long long *)a.head;
+                if ((long long)h < t) {
+                    if (atomicCAS(a.head, h, h + 1) == h) { c = (long long)h; break; }
+                    continue;   // another block took item h: try the next one at once
+                }
+                if (*(volatile const int *)a.stop) { c = -QEXIT_STOPPED; break; }
+                if (global_ns() - since > a.idle_ns) { c = -QEXIT_IDLE; break; }
+                __nanosleep(ns);
+                if (ns < 8192) ns *= 2;
+            }
+            if (c >= 0) {
+                const int slot = (int)(c % a.cap);
+                cur = a.ring[slot];
+                a.dstatus[slot] = 0;
+                __threadfence();
+            }
+            claimed = c;
+        }
+        __syncthreads();
+        const long long c = claimed;
+        if (c < 0) {
+            code = (int)-c;
+            break;
+        }
+        const int slot = (int)(c % a.cap);
+        OnItem it = cur.it;
+        it.status = a.dstatus + slot;
+        const int64_t comps = 2 * it.n;
+        const int active = comps < QUEUE_THREADS ? (int)((comps + 31) / 32 * 32) : QUEUE_THREADS;
+        if ((int)threadIdx.x < active) {
+            if (it.method == MM) queue_run<SYS, MM>(it, sm, active);
+            else queue_run<SYS, CGB>(it, sm, active);
+        }
+        // each thread's results reach host memory before the block signals
+        __threadfence_system();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            a.hstatus[slot] = atomicOr(a.dstatus + slot, 0);
+            __threadfence_system();
+            *(volatile long long *)(a.done + slot) = cur.ticket;
+        }
+        since = global_ns();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence_system();
+        *(volatile int *)(a.exited + blockIdx.x) = code;
+    }
+}
+
+template <int SYS>
+int queue_launch_k(const QueueArgs &a, int blocks, size_t smem, cudaStream_t st) {
+    static std::atomic<bool> attr_set{false};   // idempotent: a second setter is harmless
+    if (!attr_set.load()) {
+        int rc = allow_max_dynamic_smem((const void *)queue_kernel<SYS>);
+        if (rc) return rc;
+        attr_set.store(true);
+    }
+    queue_kernel<SYS><<<blocks, QUEUE_THREADS, smem, st>>>(a);
+    REACH_LAUNCHED("queue_kernel");
+    return REACH_OK;
 }
 
 }  // namespace reach

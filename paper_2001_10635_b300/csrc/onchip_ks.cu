@@ -8,4 +8,5 @@ template int onchip_cluster_k<REACH_KS>(const OnItem &, cudaStream_t);
 template int onchip_batch_k<REACH_KS>(int, int, const void *, const void *, const void *, const void *, int,
                                      int *, uint64_t *, int, size_t, cudaStream_t);
 
+template int queue_launch_k<REACH_KS>(const QueueArgs &, int, size_t, cudaStream_t);
 }  // namespace reach

@@ -75,12 +75,13 @@ struct reach_server {
 namespace reach {
 
 static int64_t mc_footprint(const reach_system *s, int64_t m, int prec) {
-    const int64_t M = (m + 31) / 32 * 32, elt = prec == 32 ? 4 : 8, n = s->n;
-    // partial minima / maxima: one row per block of samples (32 per block on
-    // the streaming kernel, 2 to 32 on the on-chip one)
+    // the streaming kernel pads the samples to blocks of 64 (binary32, two per
+    // lane) or 32, the on-chip one uses blocks of 2 to 32
+    const bool stream_kernel = (s->kind == REACH_TRAFFIC || s->kind == REACH_KS) && s->n > 128;
+    const int64_t ss = prec == 32 ? 64 : 32, M = (m + ss - 1) / ss * ss, elt = prec == 32 ? 4 : 8, n = s->n;
+    // partial minima / maxima: one row per block of samples
     const int64_t sb = mc_onchip_sb(m), blocks = std::max(M / 32, (m + sb - 1) / sb);
     int64_t partials = 2 * blocks * n * 8;
-    bool stream_kernel = (s->kind == REACH_TRAFFIC || s->kind == REACH_KS) && n > 128;
     return partials + (stream_kernel ? 2 * n * M * elt : 0);
 }
 

@@ -29,6 +29,7 @@ def _reset_options():
     R.reach_set_option(R.OPT_BLOCK, 0)
     R.reach_set_option(R.OPT_TILE, 0)
     R.reach_set_option(R.OPT_MC_SB, 0)
+    R.reach_set_option(R.OPT_MC_LAYOUT, 0)
 
 
 def gpu_box(method, kind, n, lo, hi, wlo, whi, T, dt, params=None, A=None, **kw):
@@ -525,3 +526,28 @@ def test_mc32_samples_inside_mm_within_the_binary32_tolerance(kind, n, m, kernel
     slack = TOL32 * max(np.abs(box[0]).max(), np.abs(box[1]).max())
     dlo, dhi = _escapes(mc, box)
     assert dlo.min() >= -slack and dhi.min() >= -slack, (dlo.min(), dhi.min(), slack)
+
+
+@pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 100, 2), ("traffic", 1500, 77, 2), ("ks", 600, 64, 1),
+                                        ("traffic", 3001, 130, 3)])
+def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
+    # the packed binary32 kernel (two samples per lane) performs each sample's
+    # operations in the same order as the one-sample kernel: same box, bit for
+    # bit, for every block shape; and it is the oracle's within TOL32
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=13)
+    T = 0.13 if kind == "traffic" else 0.0013
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    boxes = {}
+    try:
+        for layout in (1, 0, 3, 4, 5):
+            R.reach_set_option(R.OPT_MC_LAYOUT, layout)
+            boxes[layout] = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=4, precision=32)
+    finally:
+        R.reach_set_option(R.OPT_MC_LAYOUT, 0)
+    for layout, b in boxes.items():
+        np.testing.assert_array_equal(b[0], boxes[1][0], err_msg=f"layout {layout} lo")
+        np.testing.assert_array_equal(b[1], boxes[1][1], err_msg=f"layout {layout} hi")
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, m=m, seed=4, prec=32)
+    assert_close(boxes[0][0], o[0], TOL32, "lo")
+    assert_close(boxes[0][1], o[1], TOL32, "hi")
