@@ -206,10 +206,12 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
-def bench_batched(R, torch, dev, runs=3, solo_stride=32):
+def bench_batched(R, torch, dev, runs=3, solo_stride=1):
     """4096 oscillator-chain queries x (MM to T=5, CGB to T=4), one graph launch of
     the batched persistent kernels, against the same queries launched one by one
-    (a deterministic subset: every `solo_stride`-th query)."""
+    (all of them by default; every `solo_stride`-th one otherwise).  CGB runs to
+    T=4: its box-supremum growth bound overflows between t=4 and t=5 for every
+    query (oracle and GPU agree)."""
     sizes = W.osc_sizes(4096, seed=0)
     systems, qs = {}, []
     for k, m in enumerate(sizes):
@@ -248,27 +250,35 @@ def bench_batched(R, torch, dev, runs=3, solo_stride=32):
     solo_launches = R.reach_kernel_launches() - launches0
     solo_rate = sum(comp[i] for i in sub) / ts
     info = b.info()
+    layout = b.layout()
     b.close()
     for s in systems.values():
         s.close()
     return {"workload": "4096 oscillator-chain queries, m log-uniform in [4, 4096] (seed 0), MM T=5 + CGB T=4, "
                         "dt=0.005, box half-width 1e-4, w in [-0.01, 0.01]",
+            "cgb_horizon_note": "CGB runs to T=4: the box-supremum growth bound of the chain overflows between "
+                                "t=4 and t=5 for every query (oracle and GPU agree)",
             "queries": len(qs), "comp_steps": int(sum(comp)),
             "value": sum(comp) / tb, "unit": "comp-steps/s", "run_s": tb, "create_s": create_s,
+            "create_s_in_library": layout["create_s"],
+            "value_with_create": sum(comp) / (tb + create_s),
+            "create_note": "create = planning + layout tuning on 24-step horizons + graph capture, once per batch",
             "latency_p50_ms": _pct(fin, 50) * 1e3, "latency_p99_ms": _pct(fin, 99) * 1e3,
             "latency_note": "completion time of each query from the start of the batch (all submitted at once)",
-            "tuned_cpt": info["cpt"], "tune_ms": info["tune_ms"], "kernels_per_run": info["kernels"],
+            "tuned": {"cpt": layout["cpt"], "cluster_from": layout["cluster_from"]},
+            "tune_ms": layout["tune_ms"], "kernels_per_run": info["kernels"],
             "gpu_launches_per_run": batch_launches,
-            "solo": {"queries": len(sub), "sample": f"every {solo_stride}th query", "s": ts, "value": solo_rate,
+            "solo": {"queries": len(sub), "sample": "every query" if solo_stride == 1 else f"every {solo_stride}th query",
+                     "s": ts, "value": solo_rate,
                      "service_p50_ms": _pct(lat, 50) * 1e3, "service_p99_ms": _pct(lat, 99) * 1e3,
-                     "gpu_launches": solo_launches,
-                     "projected_all_s": ts * sum(comp) / sum(comp[i] for i in sub)},
-            "speedup_vs_solo": (sum(comp) / tb) / solo_rate}
+                     "gpu_launches": solo_launches},
+            "speedup_vs_solo": (sum(comp) / tb) / solo_rate,
+            "speedup_vs_solo_with_create": (sum(comp) / (tb + create_s)) / solo_rate}
 
 
 def bench_ks(R, torch, dev):
-    """Kuramoto-Sivashinsky grid n = 2^20 (dt 1e-4, T 0.05): MM, CGB, MC 1024
-    samples in FP32 (full), MC in FP64 on 64 samples (bounded: FP64 pipe)."""
+    """Kuramoto-Sivashinsky grid n = 2^20 (dt 1e-4, T 0.05): MM, CGB, and MC
+    with 1024 samples in FP32 and in FP64, the configured workload in full."""
     n = 1 << 20
     wl = W.ks_grid(n)
     d = {k: torch.tensor(wl[k], dtype=torch.float64, device=dev) for k in ("x_lo", "x_hi")}
@@ -279,7 +289,7 @@ def bench_ks(R, torch, dev):
     with R.System("ks", n) as s:
         for name, fn, kw, comps in (("mm", R.reach_mm, {}, 2 * n), ("cgb", R.reach_cgb, {}, 2 * n),
                                     ("mc32_m1024", R.reach_mc, dict(m=1024, precision=32), 1024 * n),
-                                    ("mc64_m64", R.reach_mc, dict(m=64, precision=64), 64 * n)):
+                                    ("mc64_m1024", R.reach_mc, dict(m=1024, precision=64), 1024 * n)):
             fn(s, d["x_lo"], d["x_hi"], t_final=wl["t_final"], dt=wl["dt"], lo=lo, hi=hi, **kw)   # warm
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -288,7 +298,15 @@ def bench_ks(R, torch, dev):
             out[name] = {"s": sec, "value": comps * N / sec, "unit": "comp-steps/s"}
             if name in KS_FP64_OPS:
                 out[name]["fp64_frac"] = KS_FP64_OPS[name] * comps * N / sec / FP64_PEAK_OPS
+            if name == "mc32_m1024":
+                # binary32: FP32 FMA-pipe fraction, and HBM at the default
+                # three steps per launch (8 B per sample-component-step / S)
+                S = R.reach_get_option(R.OPT_STEPS_PER_LAUNCH) or 3
+                out[name]["fp32_frac"] = KS_FP32_OPS * comps * N / sec / FP32_PEAK_OPS
+                out[name]["steps_per_launch"] = S
+                out[name]["hbm_frac_at_S"] = 8.0 / S * comps * N / sec / (load_peaks().get("hbm_gbs", 6400.0) * 1e9)
     out["fp64_ops_per_comp_step"] = KS_FP64_OPS
+    out["fp32_ops_per_comp_step"] = KS_FP32_OPS
     return out
 
 
@@ -297,7 +315,12 @@ def bench_ks(R, torch, dev):
 # fused operations per half) plus the stage input and accumulator, CGB 9
 # (center 4, radius 5) plus those two; over four stages, minus the first
 # accumulator and the last stage input, plus the final update
-KS_FP64_OPS = {"mm": 35.0, "cgb": 43.0, "mc64_m64": 35.0}
+KS_FP64_OPS = {"mm": 35.0, "cgb": 43.0, "mc64_m1024": 35.0}
+# FP32 operations per sample-component-step of the binary32 KS sample
+# trajectory (the same 35-operation RK4 step, each a lane of a packed
+# instruction), and the FP32 FMA pipe's rate: 128 lanes per SM per clock
+KS_FP32_OPS = 35.0
+FP32_PEAK_OPS = 148 * 128 * 2032e6
 
 
 # FP64 pipe operations per component-step of the heat stage kernels (RK4 in
@@ -494,6 +517,13 @@ def _comp_steps(q):
     return (q.m * n if q.method == "mc" else 2 * n) * q.steps
 
 
+def _failed(bad):
+    """Failed queries by status name (both arms fail the same ones: KS boxes
+    that overflow over the longest horizons give REACH_ENONFINITE)."""
+    import paper_2001_10635_b300 as R
+    return {R.strerror(k): v for k, v in sorted(bad.items())}
+
+
 def _serve_run(R, trace, systems, rate_scale, slots, budget):
     """Arrivals at trace times / rate_scale through the server; returns latencies."""
     import threading as th
@@ -514,7 +544,7 @@ def _serve_run(R, trace, systems, rate_scale, slots, budget):
 
     feeder = th.Thread(target=feed)
     feeder.start()
-    lat, bad = [], 0
+    lat, bad = [], {}
     last = t0
     for i in range(len(trace)):
         while tickets[i] is None:
@@ -522,18 +552,20 @@ def _serve_run(R, trace, systems, rate_scale, slots, budget):
         sub_t, (tk, _) = tickets[i]
         st, qs, rs = srv.wait(tk, timeout_s=600)
         done_t = sub_t + qs + rs
-        bad += st != 0
+        if st != 0:
+            bad[st] = bad.get(st, 0) + 1
         lat.append(done_t - sub_t)
         last = max(last, done_t)
     feeder.join()
     peak = srv.stats()["bytes_peak"]
+    queued = srv.queued()
     srv.close()
-    return lat, last - t0, bad, peak
+    return lat, last - t0, bad, peak, queued
 
 
 def _fifo_run(R, trace, systems, rate_scale):
     """Plain per-query launches: one at a time in arrival order on one stream."""
-    lat, bad = [], 0
+    lat, bad = [], {}
     t0 = time.perf_counter()
     for q in trace:
         at = (q.arrival - trace[0].arrival) / rate_scale
@@ -550,18 +582,20 @@ def _fifo_run(R, trace, systems, rate_scale):
                 R.reach_cgb(s, q.x_lo, q.x_hi, *w, **kw)
             else:
                 R.reach_mc(s, q.x_lo, q.x_hi, *w, **kw, m=q.m, seed=q.seed, precision=q.prec)
-        except R.ReachError:
-            bad += 1
+        except R.ReachError as e:
+            bad[e.code] = bad.get(e.code, 0) + 1
         lat.append(time.perf_counter() - t0 - at)
     return lat, time.perf_counter() - t0, bad
 
 
-def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget=160 << 30):
-    """The seeded 2000 q/s Poisson trace (traffic n in [1e2, 1e7], KS n = 2^10..2^20,
-    MM / CGB / MC-256-FP32, 100..20000 steps), bounded for the benchmark: its
-    first `count` arrivals, horizons scaled by `scale_steps`, n capped at max_n."""
+def bench_serving(R, count=60, sweep_count=30, slots=8, budget=160 << 30):
+    """The seeded 2000 q/s Poisson trace at its stated sizes (traffic n in
+    [1e2, 1e7], KS n = 2^10..2^20, MM / CGB / MC-256-FP32, 100..20000 RK4
+    steps): its first `count` arrivals at the offered rate, and its first
+    `sweep_count` at 50 / 70 / 90% of the measured serving capacity, served
+    and as plain per-query launches in arrival order (FIFO)."""
     # the trace is drawn sequentially, so its first `count` arrivals are those of the full trace
-    trace = W.serving_trace(count=count, rate=2000.0, seed=0, scale_steps=scale_steps, max_n=max_n)
+    trace = W.serving_trace(count=count, rate=2000.0, seed=0)
     systems = {}
     for q in trace:
         if (q.kind, q.n) not in systems:
@@ -573,34 +607,39 @@ def bench_serving(R, count=300, scale_steps=0.05, max_n=1 << 20, slots=8, budget
         kw = dict(t_final=q.dt * 2, dt=q.dt)
         s = systems[(q.kind, q.n)]
         (R.reach_mm if q.method == "mm" else R.reach_cgb)(s, q.x_lo, q.x_hi, *w, **kw)
-    lat, span, bad, peak = _serve_run(R, trace, systems, 1.0, slots, budget)
+    lat, span, bad, peak, queued = _serve_run(R, trace, systems, 1.0, slots, budget)
     flat, fspan, fbad = _fifo_run(R, trace, systems, 1.0)
     capacity = len(trace) / span
-    # latency against offered load: the first half of the trace at 50%, 70% and
-    # 90% of the measured serving capacity, through the server and one at a
-    # time (where a small query waits behind every large one ahead of it)
-    sus = trace[: max(20, count // 2)]
+    # latency against offered load: the first sweep_count arrivals at 50%, 70%
+    # and 90% of the measured serving capacity, through the server and one at
+    # a time (where a small query waits behind every large one ahead of it)
+    sus = trace[:sweep_count]
     sweep = []
     for frac in (0.5, 0.7, 0.9):
         scale = frac * capacity / 2000.0
-        slat, _, sbad, _ = _serve_run(R, sus, systems, scale, slots, budget)
-        sflat, _, sfbad = _fifo_run(R, sus, systems, scale)
+        slat, sspan, sbad, _, _ = _serve_run(R, sus, systems, scale, slots, budget)
+        sflat, sfspan, sfbad = _fifo_run(R, sus, systems, scale)
         sweep.append({"load": frac, "rate_qps": 2000.0 * scale, "queries": len(sus),
-                      "p50_ms": _pct(slat, 50) * 1e3, "p99_ms": _pct(slat, 99) * 1e3, "failed": sbad,
+                      "p50_ms": _pct(slat, 50) * 1e3, "p99_ms": _pct(slat, 99) * 1e3, "failed": _failed(sbad),
+                      "makespan_s": sspan,
                       "fifo_p50_ms": _pct(sflat, 50) * 1e3, "fifo_p99_ms": _pct(sflat, 99) * 1e3,
-                      "fifo_failed": sfbad})
+                      "fifo_makespan_s": sfspan, "fifo_failed": _failed(sfbad)})
     for s in systems.values():
         s.close()
-    return {"workload": f"seeded Poisson trace, 2000 q/s offered; first {count} arrivals; traffic n in [1e2, 1e7] "
-                        f"and KS n = 2^10..2^20 capped at {max_n}; MM / CGB / MC-256-FP32; horizons "
-                        f"logU[100, 20000] x {scale_steps} RK4 steps",
+    return {"workload": f"seeded Poisson trace, 2000 q/s offered, at its stated sizes: traffic n logU[1e2, 1e7], "
+                        f"KS n = 2^10..2^20, box widths logU[1e-4, 1e-1] x scale, MM / CGB / MC-256-FP32, "
+                        f"horizons logU[100, 20000] RK4 steps; the first {count} of its 4000 arrivals at the "
+                        f"offered rate, the first {sweep_count} in the load sweep",
             "queries": len(trace), "comp_steps": int(work), "slots": slots, "hbm_budget_bytes": budget,
+            "queue_blocks": R.reach_get_option(R.OPT_SERVE_QUEUE_BLOCKS),
+            "queue_n": R.reach_get_option(R.OPT_SERVE_QUEUE_N),
+            "max_wide": R.reach_get_option(R.OPT_SERVE_MAX_WIDE),
             "peak_admitted_bytes": peak,
             "served": {"value": work / span, "unit": "comp-steps/s", "makespan_s": span,
                        "queries_per_s": len(trace) / span, "p50_ms": _pct(lat, 50) * 1e3,
-                       "p99_ms": _pct(lat, 99) * 1e3, "failed": bad},
+                       "p99_ms": _pct(lat, 99) * 1e3, "failed": _failed(bad), "on_device_queue": queued},
             "per_query_fifo": {"value": work / fspan, "unit": "comp-steps/s", "makespan_s": fspan,
-                               "p50_ms": _pct(flat, 50) * 1e3, "p99_ms": _pct(flat, 99) * 1e3, "failed": fbad},
+                               "p50_ms": _pct(flat, 50) * 1e3, "p99_ms": _pct(flat, 99) * 1e3, "failed": _failed(fbad)},
             "speedup_vs_fifo": fspan / span,
             "sustainable": sweep[1], "load_sweep": sweep}
 

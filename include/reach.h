@@ -252,6 +252,14 @@ REACH_API int reach_batch_run(reach_batch *b, void *stream, int *status, double 
 /* the tuned components-per-thread target, the kernels per run, and the
    timings (ms) of the four tuning candidates 2, 4, 8, 16 */
 REACH_API int reach_batch_info(const reach_batch *b, int64_t *cpt, int64_t *kernels, double *tune_ms);
+/* the tuned layout: the components-per-thread target, the item size (state
+   components) from which items run on a two-block cluster instead of a bin
+   slot (0: only items too large for one block), the seconds reach_batch_create
+   spent (planning, tuning, graph capture), and the timings (ms) of the
+   candidates tried: cpt 2, 4, 8, 16, then cluster thresholds 4096 and 2048
+   components with the best cpt (0 where not tried) */
+REACH_API int reach_batch_layout(const reach_batch *b, int64_t *cpt, int64_t *cluster_from, double *create_s,
+                                 double *tune_ms);
 REACH_API int reach_batch_destroy(reach_batch *b);
 
 /* ---- device work queue: small queries run as they arrive ----
@@ -301,15 +309,21 @@ REACH_API int reach_queue_destroy(reach_queue *q);
 /* ---- serving: a continuous-batching request loop ----
    The paper serves reachability problems to other tools over a network
    interface (Sec. 1); here that purpose is an in-process server.  Requests of
-   any system, size, method and horizon are submitted as they arrive; a
-   dispatcher admits them, in arrival order with first fit, whenever one of
-   the server's slots is free and the request's device-memory footprint
-   (reach_request_footprint) fits in what is left of the budget.  Each slot is
-   a worker thread running the request through reach_mm / reach_cgb / reach_mc
-   on its own CUDA streams, so admitted requests overlap on the GPU.  The
-   stream's priority falls with the request's work (state components per step
-   x steps; greatest below 2^30, one level lower per factor 4 above), so the
-   blocks of small requests are scheduled ahead of those of large ones.
+   any system, size, method and horizon are submitted as they arrive and
+   start, in arrival order, as capacity frees up:
+     - MM / CGB requests small enough for the device work queue (above) join
+       the server's queue, whose persistent blocks take them while other work
+       runs: always up to REACH_OPT_SERVE_QUEUE_N cells, and up to
+       REACH_QUEUE_MAX_N cells while other requests are running (alone, a
+       streaming kernel spread over every SM finishes those sooner);
+     - every other request needs one of the server's slots and its
+       device-memory footprint (reach_request_footprint) must fit in what is
+       left of the budget (first fit).  Each slot is a worker thread running
+       the request through reach_mm / reach_cgb / reach_mc on its own CUDA
+       streams, so admitted requests overlap on the GPU.  The stream's
+       priority falls with the request's work (state components per step x
+       steps; greatest below 2^30, one level lower per factor 4 above), so the
+       blocks of small requests are scheduled ahead of those of large ones.
    A request's buffers must stay valid until reach_server_wait has returned
    its result. */
 typedef struct {
@@ -340,6 +354,8 @@ REACH_API int reach_server_wait(reach_server *s, int64_t ticket, double timeout_
                                 double *run_s);
 REACH_API int reach_server_stats(reach_server *s, int64_t *waiting, int64_t *running, int64_t *done,
                                  int64_t *bytes_in_use, int64_t *bytes_peak);
+/* requests that went to the server's device work queue so far */
+REACH_API int64_t reach_server_queued(reach_server *s);
 /* finishes every submitted request, then stops the slots */
 REACH_API int reach_server_destroy(reach_server *s);
 
@@ -357,6 +373,23 @@ REACH_API int reach_server_destroy(reach_server *s);
                                         arithmetic, measured block shape), 1 one sample per lane; 2..5 block
                                         shapes of the two-sample kernel (warps x rows x blocks per SM:
                                         16x16x1, 32x8x1, 8x16x2, 16x8x2) */
+#define REACH_OPT_SERVE_QUEUE_BLOCKS 8 /* servers created afterwards: blocks of their device work queue, 0 = no
+                                         queue (default 64) */
+#define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: requests up to this many cells always take
+                                         the queue (default 512; larger ones up to REACH_QUEUE_MAX_N take it
+                                         while the server is busy) */
+#define REACH_OPT_SERVE_MAX_WIDE 10    /* servers created afterwards: requests with 2^20 or more state components
+                                         per step (they fill the GPU alone) running at once, 0 = no limit
+                                         (default 1) */
+#define REACH_OPT_BATCH_CLUSTER_FROM 11 /* batches: items of this many state components or more run on a
+                                          two-block cluster; 0 = tuned (untuned batches: only items too large
+                                          for one block) */
+#define REACH_OPT_KS_FLOW 12           /* KS MM / CGB: 0 auto (every step in one persistent launch for grids of
+                                         one to eight waves of tiles), 1 one launch per step, 2 one launch
+                                         for every grid it can run */
+#define REACH_OPT_SERVE_PRIORITY 13    /* servers created afterwards: stream priority of slot requests, 0 by
+                                         work (smaller first), 1 by arrival (earlier first), 2 none, 3 by work
+                                         (larger first) */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

@@ -24,6 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libreach.so")
 TRAFFIC, KS, OSC, LINEAR, HEAT3D, QUAD = 0, 1, 2, 3, 4, 5
 KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D, "quad": QUAD}
 OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT, OPT_TILE, OPT_MC_SB, OPT_MC_LAYOUT = 1, 2, 3, 4, 5, 6, 7
+OPT_SERVE_QUEUE_BLOCKS, OPT_SERVE_QUEUE_N, OPT_SERVE_MAX_WIDE, OPT_BATCH_CLUSTER_FROM, OPT_KS_FLOW = 8, 9, 10, 11, 12
+OPT_SERVE_PRIORITY = 13
 BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",
           -4: "REACH_ENONFINITE", -5: "REACH_ETIMEOUT", -6: "REACH_ECUDA", -7: "REACH_ENODEV"}
@@ -97,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.reach_batch_create.argtypes = [ctypes.POINTER(_Query), i64, ctypes.c_int, ctypes.POINTER(vp)]
         L.reach_batch_run.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dbl)]
         L.reach_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        L.reach_batch_layout.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                         ctypes.POINTER(dbl)]
         L.reach_batch_destroy.argtypes = [vp]
         L.reach_queue_create.argtypes = [ctypes.c_int, dbl, i64, ctypes.POINTER(vp)]
         L.reach_queue_submit.argtypes = [vp, ctypes.POINTER(_Query), ctypes.POINTER(i64)]
@@ -113,6 +117,8 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(dbl)]
         L.reach_server_stats.argtypes = [vp] + [ctypes.POINTER(i64)] * 5
         L.reach_server_destroy.argtypes = [vp]
+        L.reach_server_queued.argtypes = [vp]
+        L.reach_server_queued.restype = i64
         _lib = L
     return _lib
 
@@ -357,6 +363,18 @@ class Batch:
         _check(lib().reach_batch_info(self.handle, ctypes.byref(cpt), ctypes.byref(kern), tune), "reach_batch_info")
         return {"cpt": cpt.value, "kernels": kern.value, "tune_ms": dict(zip((2, 4, 8, 16), list(tune)))}
 
+    def layout(self):
+        """The tuned layout: cpt, cluster_from (components), create_s, and the
+        candidates' timings (ms)."""
+        cpt, cf = ctypes.c_int64(), ctypes.c_int64()
+        cs = ctypes.c_double()
+        tune = (ctypes.c_double * 6)()
+        _check(lib().reach_batch_layout(self.handle, ctypes.byref(cpt), ctypes.byref(cf), ctypes.byref(cs), tune),
+               "reach_batch_layout")
+        names = ("cpt2", "cpt4", "cpt8", "cpt16", "cluster_from_4096", "cluster_from_2048")
+        return {"cpt": cpt.value, "cluster_from": cf.value, "create_s": cs.value,
+                "tune_ms": {k: v for k, v in zip(names, list(tune)) if v > 0}}
+
     def close(self):
         if self.handle:
             lib().reach_batch_destroy(self.handle)
@@ -490,6 +508,10 @@ class Server:
         _check(rc, "reach_server_wait")
         self._keep.pop(ticket, None)
         return st.value, q.value, r.value
+
+    def queued(self) -> int:
+        """Requests that went to the server's device work queue."""
+        return int(lib().reach_server_queued(self.handle))
 
     def stats(self):
         v = [ctypes.c_int64() for _ in range(5)]

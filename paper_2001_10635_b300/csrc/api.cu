@@ -24,7 +24,9 @@ int cuda_fail(cudaError_t e, const char *where) {
 
 // process-wide options; read by calls on any thread
 static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
-    g_opt_mc_sb{0}, g_opt_mc_layout{0};
+    g_opt_mc_sb{0}, g_opt_mc_layout{0}, g_opt_serve_queue_blocks{64}, g_opt_serve_queue_n{512},
+    g_opt_serve_max_wide{1}, g_opt_batch_cluster_from{0}, g_opt_ks_flow{0},
+    g_opt_serve_priority{0};
 
 // ---------------------------------------------------------------- memory
 static std::atomic<bool> g_pool_ready[64];
@@ -187,6 +189,8 @@ int64_t opt_batch_cpt() { return g_opt_batch_cpt; }
 int64_t opt_tile() { return g_opt_tile; }
 int64_t opt_mc_sb() { return g_opt_mc_sb; }
 int64_t opt_mc_layout() { return g_opt_mc_layout; }
+int64_t opt_batch_cluster_from() { return g_opt_batch_cluster_from; }
+int64_t opt_ks_flow() { return g_opt_ks_flow; }
 
 }  // namespace reach
 
@@ -468,7 +472,13 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
             KsK p;
             p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
             if (opt_steps() == 0) S = stencil_short_steps(2, 1, n);
-            rc = stencil_ks(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+            if (S == 1 && ks_flow_eligible(n, N)) {
+                void *work;
+                if ((rc = sg.scratch((size_t)ks_flow_work_bytes(n), &work))) return rc;
+                rc = stencil_ks_flow_run(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, sg.status, work, sg.st);
+            } else {
+                rc = stencil_ks(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+            }
         }
     }
     if (rc) return rc;
@@ -523,6 +533,30 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value < 0 || value > 5) return REACH_EINVAL;
         g_opt_mc_layout = value;
         return REACH_OK;
+    case REACH_OPT_SERVE_QUEUE_BLOCKS:
+        if (value < 0 || value > 4096) return REACH_EINVAL;
+        g_opt_serve_queue_blocks = value;
+        return REACH_OK;
+    case REACH_OPT_SERVE_QUEUE_N:
+        if (value < 0 || value > REACH_QUEUE_MAX_N) return REACH_EINVAL;
+        g_opt_serve_queue_n = value;
+        return REACH_OK;
+    case REACH_OPT_SERVE_MAX_WIDE:
+        if (value < 0 || value > 256) return REACH_EINVAL;
+        g_opt_serve_max_wide = value;
+        return REACH_OK;
+    case REACH_OPT_BATCH_CLUSTER_FROM:
+        if (value < 0 || value > 16384) return REACH_EINVAL;
+        g_opt_batch_cluster_from = value;
+        return REACH_OK;
+    case REACH_OPT_KS_FLOW:
+        if (value < 0 || value > 2) return REACH_EINVAL;
+        g_opt_ks_flow = value;
+        return REACH_OK;
+    case REACH_OPT_SERVE_PRIORITY:
+        if (value < 0 || value > 3) return REACH_EINVAL;
+        g_opt_serve_priority = value;
+        return REACH_OK;
     }
     return REACH_EINVAL;
 }
@@ -536,6 +570,12 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_TILE: return g_opt_tile;
     case REACH_OPT_MC_SB: return g_opt_mc_sb;
     case REACH_OPT_MC_LAYOUT: return g_opt_mc_layout;
+    case REACH_OPT_SERVE_QUEUE_BLOCKS: return g_opt_serve_queue_blocks;
+    case REACH_OPT_SERVE_QUEUE_N: return g_opt_serve_queue_n;
+    case REACH_OPT_SERVE_MAX_WIDE: return g_opt_serve_max_wide;
+    case REACH_OPT_BATCH_CLUSTER_FROM: return g_opt_batch_cluster_from;
+    case REACH_OPT_KS_FLOW: return g_opt_ks_flow;
+    case REACH_OPT_SERVE_PRIORITY: return g_opt_serve_priority;
     }
     return REACH_EINVAL;
 }

@@ -12,14 +12,18 @@
 // first by an atomic counter (longest-processing-time order).
 //
 // Autotuning.  cpt in {2, 4, 8, 16} trades parallelism inside an item against
-// the number of items running at once; each candidate layout is timed on the
-// real batch with every horizon cut to a few steps, and the fastest is kept.
+// the number of items running at once; then, with the best cpt, mid-size
+// items (from 4096 or from 2048 components) may run on a two-block cluster
+// instead of a bin slot (shorter critical path, fewer items at once).  Each
+// candidate layout is timed on the real batch with every horizon cut to a few
+// steps, and the fastest is kept.
 //
 // Graph.  Input copies (for host-resident queries), counter and status resets,
 // a start stamp, one persistent kernel per (system kind, method) present, and
 // the copies of outputs, statuses and completion stamps back are captured once
 // into a CUDA graph that reach_batch_run replays.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -67,14 +71,17 @@ struct reach_batch {
     int nkernels = 0;
     int cpt = 0;
     int plan_cpt = 16;   // the layout currently planned (tuning tries several)
-    double tune_ms[4] = {0, 0, 0, 0};
+    int64_t cluster_from = 0;   // tuned: items of this many components or more run on a cluster (0: only too-large ones)
+    double tune_ms[6] = {0, 0, 0, 0, 0, 0};
+    double create_s = 0;
 };
 
 namespace reach {
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-static int plan_group(reach_batch *b, Group &g, int cpt, int64_t n_override, std::vector<char> &dev_mem_keep) {
+static int plan_group(reach_batch *b, Group &g, int cpt, int64_t cluster_from, int64_t n_override,
+                      std::vector<char> &dev_mem_keep) {
     (void)dev_mem_keep;
     const int smem_cap = onchip_max_smem() - 64;
     struct Small { int item, warps; int64_t smem, cost; };
@@ -87,8 +94,11 @@ static int plan_group(reach_batch *b, Group &g, int cpt, int64_t n_override, std
         const int64_t N = n_override > 0 ? std::min<int64_t>(n_override, it.N) : it.N;
         const int64_t sm1 = onchip_smem_bytes(it.n, it.nw);
         // a bin slot holds at most cpt components per thread (the kernel is
-        // instantiated for that loop length) and at most one block of warps
-        if (comps <= (int64_t)BIN_WARPS * 32 * cpt && sm1 <= smem_cap) {
+        // instantiated for that loop length) and at most one block of warps;
+        // items from cluster_from components take a cluster when they fit one
+        const bool to_cluster = cluster_from > 0 && comps >= cluster_from && comps <= 2 * ITEM_MAX_BLOCK &&
+                                cluster_smem_bytes(it.n, it.nw) <= smem_cap;
+        if (!to_cluster && comps <= (int64_t)BIN_WARPS * 32 * cpt && sm1 <= smem_cap) {
             const int64_t w = std::max<int64_t>(1, ceil_div(comps, 32LL * cpt));
             small.push_back({qi, (int)w, sm1, ceil_div(comps, 32 * w) * N});
         } else if (comps <= 2 * ITEM_MAX_BLOCK && cluster_smem_bytes(it.n, it.nw) <= smem_cap) {
@@ -185,12 +195,12 @@ static void free_groups(reach_batch *b) {
     }
 }
 
-static int plan_all(reach_batch *b, int cpt, int64_t n_override) {
+static int plan_all(reach_batch *b, int cpt, int64_t cluster_from, int64_t n_override) {
     free_groups(b);
     b->plan_cpt = cpt;
     std::vector<char> keep;
     for (Group &g : b->groups) {
-        int rc = plan_group(b, g, cpt, n_override, keep);
+        int rc = plan_group(b, g, cpt, cluster_from, n_override, keep);
         if (rc) return rc;
     }
     return REACH_OK;
@@ -243,6 +253,7 @@ static void destroy(reach_batch *b) {
 
 extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int flags, reach_batch **out) {
     if (!out || !queries || count < 1 || count > (1 << 24)) return REACH_EINVAL;
+    const auto created0 = std::chrono::steady_clock::now();
     *out = nullptr;
     reach_batch *b = new (std::nothrow) reach_batch();
     if (!b) return REACH_ENOMEM;
@@ -345,9 +356,13 @@ extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int
         return REACH_ENOMEM;
     }
 
-    // autotune the components-per-thread target on short horizons
+    // autotune the layout on short horizons: first the components-per-thread
+    // target, then, with it, whether mid-size items (from 2048 or 4096
+    // components) run on a two-block cluster instead of a bin slot
     const int cands[4] = {2, 4, 8, 16};
+    const int64_t cfrom[2] = {4096, 2048};
     int best = (int)(opt_batch_cpt() > 0 ? opt_batch_cpt() : 8);
+    int64_t best_from = opt_batch_cluster_from();
     if (!(flags & REACH_BATCH_NO_AUTOTUNE) && opt_batch_cpt() == 0) {
         int64_t maxN = *std::max_element(b->N.begin(), b->N.end());
         int64_t nshort = std::max<int64_t>(1, std::min<int64_t>(maxN, 24));
@@ -355,25 +370,40 @@ extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         double best_ms = 1e300;
-        for (int c = 0; c < 4; ++c) {
-            if ((rc = plan_all(b, cands[c], nshort))) break;
+        auto time_layout = [&](int cpt, int64_t from, double *ms_out) -> int {
+            int r = plan_all(b, cpt, from, nshort);
+            if (r) return r;
             // warm once, then time
-            if ((rc = enqueue(b, b->cap, false))) break;
+            if ((r = enqueue(b, b->cap, false))) return r;
             cudaEventRecord(e0, b->cap);
-            if ((rc = enqueue(b, b->cap, false))) break;
+            if ((r = enqueue(b, b->cap, false))) return r;
             cudaEventRecord(e1, b->cap);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = REACH_ECUDA; break; }
+            if (cudaEventSynchronize(e1) != cudaSuccess) return REACH_ECUDA;
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            b->tune_ms[c] = ms;
-            if (ms < best_ms) { best_ms = ms; best = cands[c]; }
+            *ms_out = ms;
+            return REACH_OK;
+        };
+        for (int c = 0; c < 4 && !rc; ++c) {
+            rc = time_layout(cands[c], 0, &b->tune_ms[c]);
+            if (!rc && b->tune_ms[c] < best_ms) { best_ms = b->tune_ms[c]; best = cands[c]; }
+        }
+        // only if some item lies in a candidate's range
+        int64_t max_small = 0;
+        for (const OnItem &it : b->items)
+            if (2 * it.n <= (int64_t)BIN_WARPS * 32 * best) max_small = std::max<int64_t>(max_small, 2 * it.n);
+        for (int c = 0; c < 2 && !rc && opt_batch_cluster_from() == 0; ++c) {
+            if (max_small < cfrom[c]) continue;
+            rc = time_layout(best, cfrom[c], &b->tune_ms[4 + c]);
+            if (!rc && b->tune_ms[4 + c] < best_ms) { best_ms = b->tune_ms[4 + c]; best_from = cfrom[c]; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (rc) { destroy(b); return rc; }
     }
     b->cpt = best;
-    if ((rc = plan_all(b, best, 0))) { destroy(b); return rc; }
+    b->cluster_from = best_from;
+    if ((rc = plan_all(b, best, best_from, 0))) { destroy(b); return rc; }
 
     // capture the whole run once
     cudaGraph_t graph = nullptr;
@@ -397,6 +427,7 @@ extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int
         destroy(b);
         return cuda_fail(ce, "cudaGraphInstantiate");
     }
+    b->create_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - created0).count();
     *out = b;
     return REACH_OK;
 }
@@ -427,6 +458,16 @@ extern "C" int reach_batch_info(const reach_batch *b, int64_t *cpt, int64_t *ker
     if (cpt) *cpt = b->cpt;
     if (kernels) *kernels = b->nkernels;
     if (tune_ms) for (int i = 0; i < 4; ++i) tune_ms[i] = b->tune_ms[i];
+    return REACH_OK;
+}
+
+extern "C" int reach_batch_layout(const reach_batch *b, int64_t *cpt, int64_t *cluster_from, double *create_s,
+                                  double *tune_ms) {
+    if (!b) return REACH_EINVAL;
+    if (cpt) *cpt = b->cpt;
+    if (cluster_from) *cluster_from = b->cluster_from;
+    if (create_s) *create_s = b->create_s;
+    if (tune_ms) for (int i = 0; i < 6; ++i) tune_ms[i] = b->tune_ms[i];
     return REACH_OK;
 }
 

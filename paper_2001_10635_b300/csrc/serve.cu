@@ -3,24 +3,34 @@
 // The paper serves reachability problems to remote tools (Sec. 1, the
 // pFaces REST interface); here that purpose becomes an in-process server:
 // requests of any kind, size, method and horizon are submitted as they
-// arrive, admitted by their device-memory footprint, and run concurrently.
+// arrive, admitted as capacity frees up, and run concurrently.
 //
 //   submit     appends the request to the waiting list (never blocks on GPU work)
 //   dispatch   whenever a request arrives or one finishes, the waiting list is
-//              scanned in arrival order and every request that fits is admitted:
-//              a free slot is needed and its footprint must fit in what is left of
-//              the budget (first fit, so small requests pass a large one that waits
-//              for memory)
-//   slots      each slot is a worker thread with its own CUDA streams that runs the
-//              admitted request through the ordinary entry points; requests on
-//              different slots overlap on the GPU (the on-chip kernels of small
-//              requests fill a few SMs, the streaming kernels of large ones share
-//              the rest at block granularity)
-//   priority   a request runs on a stream whose priority falls with its work
-//              (components per step x steps: the greatest below 2^30 component
-//              updates, one level lower per factor 4 above): the block scheduler hands SMs freed by a
-//              large request's short blocks to a small request first, so small
-//              requests finish in their own time rather than in the large one's
+//              scanned in arrival order and every request that can start does:
+//   queue      an MM / CGB request small enough for one block (2n <= 8192) joins
+//              the server's device work queue (queue.cu): the blocks of a
+//              persistent kernel take it as soon as it is published, beside
+//              whatever else runs, with no launch, copy call or synchronisation
+//              of its own; requests join while others are on the GPU
+//              (continuous batching).  Requests up to REACH_OPT_SERVE_QUEUE_N
+//              cells always go there; larger ones up to 4096 cells only while
+//              other requests are running, because alone a streaming kernel
+//              spread over every SM finishes them sooner than one block
+//   slots      every other request needs a free slot and its device footprint
+//              must fit in what is left of the budget (first fit, so small
+//              requests pass a large one that waits for memory); a slot is a
+//              worker thread with its own CUDA streams running the request
+//              through the ordinary entry points, so admitted requests overlap
+//   wide       a request with 2^20 or more state components per step fills the
+//              GPU alone; at most REACH_OPT_SERVE_MAX_WIDE of them run at once
+//              (in arrival order), so that two large requests do not share the
+//              GPU and both finish late, while smaller requests run beside them
+//   priority   a slot request runs on a stream whose priority falls with its
+//              work (components per step x steps: the greatest below 2^30
+//              component updates, one level lower per factor 4 above): the
+//              block scheduler hands SMs freed by a large request's short
+//              blocks to a small request first
 //   wait       bounded: returns REACH_ETIMEOUT when the request has not finished
 //              within the caller's limit
 #include <algorithm>
@@ -49,6 +59,10 @@ struct Job {
     Clock::time_point submitted, started, finished;
     int status = REACH_OK;
     bool done = false;
+    bool queue_ok = false;   // may run on the device work queue
+    bool wide = false;       // its kernels fill the GPU alone
+    bool in_queue = false;   // submitted to it: qticket is its ticket there
+    int64_t qticket = 0;
 };
 
 }  // namespace reach
@@ -61,6 +75,8 @@ struct reach_server {
     int64_t next_ticket = 1;
     int nslots = 0, idle = 0;
     int nlevels = 1;   // stream priority levels (greatest first)
+    int prio_mode = 0;  // 0: by work (small first), 1: by arrival, 2: one level, 3: by work (large first)
+    int next_level = 0; // arrival order: the level of the next request to start
     int prio_greatest = 0;
     bool stopping = false;
     std::mutex mu;
@@ -70,6 +86,13 @@ struct reach_server {
     std::unordered_map<int64_t, Job *> jobs;
     std::vector<std::thread> workers;
     int64_t n_admitted = 0, n_done = 0, n_rejected = 0;
+    reach_queue *queue = nullptr;   // device work queue of small MM / CGB requests (null: none)
+    int64_t queue_n = 0;            // cells up to which a request always takes the queue
+    int64_t n_queued = 0;           // requests that went to the queue
+    int queue_running = 0;          // requests on the queue and not yet finished
+    int slot_running = 0;           // requests running on slots
+    int wide_running = 0;           // wide requests admitted and not finished
+    int max_wide = 0;               // wide requests at once (0: no limit)
 };
 
 namespace reach {
@@ -109,12 +132,62 @@ static void run_job(Job *j, cudaStream_t st) {
                              r.lo, r.hi, st);
 }
 
-// admit every waiting request that fits, in arrival order (caller holds mu)
+// a request the device work queue can run: MM / CGB of a small system with
+// at least one step
+static bool queue_eligible(const reach_request *r) {
+    if (r->method != MM && r->method != CGB) return false;
+    if (!queue_accepts(r->sys, r->method)) return false;
+    int64_t N;
+    return nsteps(r->t_final, r->dt, &N) == REACH_OK && N >= 1;
+}
+
+static void finish_locked(reach_server *s, Job *j, int status) {
+    j->status = status;
+    j->finished = Clock::now();
+    j->done = true;
+    s->n_done++;
+    s->done_cv.notify_all();
+}
+
+// hand a waiting request to the device work queue; false if the queue cannot
+// take it now (ring or staging arena full) and it must keep waiting
+static bool to_queue_locked(reach_server *s, Job *j) {
+    const reach_request &r = j->r;
+    reach_query q{r.sys, r.method, r.x0_lo, r.x0_hi, r.w_lo, r.w_hi, r.t_final, r.dt, r.lo, r.hi};
+    j->started = Clock::now();
+    const int rc = reach_queue_submit(s->queue, &q, &j->qticket);
+    if (rc == REACH_EADMIT) return false;
+    s->n_admitted++;
+    if (rc != REACH_OK) {
+        finish_locked(s, j, rc);
+        return true;
+    }
+    j->in_queue = true;
+    s->n_queued++;
+    s->queue_running++;
+    s->done_cv.notify_all();   // its waiter continues on the queue
+    return true;
+}
+
+// admit every waiting request that can start, in arrival order (caller holds mu)
 static void dispatch_locked(reach_server *s) {
     int free_slots = s->idle - (int)s->admitted.size();
-    for (auto it = s->waiting.begin(); it != s->waiting.end() && free_slots > 0;) {
+    for (auto it = s->waiting.begin(); it != s->waiting.end();) {
         Job *j = *it;
+        // small requests go to the queue: always below queue_n cells, and up
+        // to its limit while other requests keep the GPU busy
+        if (j->queue_ok && (j->r.sys->n <= s->queue_n || s->slot_running > 0 || s->queue_running > 0 ||
+                            !s->admitted.empty())) {
+            if (to_queue_locked(s, j)) it = s->waiting.erase(it);
+            else ++it;
+            continue;
+        }
+        if (free_slots <= 0 || (j->wide && s->max_wide > 0 && s->wide_running >= s->max_wide)) {
+            ++it;
+            continue;
+        }
         if (s->in_use + j->bytes <= s->budget) {
+            if (j->wide) s->wide_running++;
             s->in_use += j->bytes;
             s->peak = std::max(s->peak, s->in_use);
             s->admitted.push_back(j);
@@ -161,14 +234,25 @@ static void worker_main(reach_server *s) {
         Job *j = s->admitted.front();
         s->admitted.pop_front();
         j->started = Clock::now();
+        if (s->prio_mode == 1) {
+            // arrival order: a request never outranks one that started before
+            // it and still runs; the levels start over when the slots drain
+            if (s->slot_running == 0) s->next_level = 0;
+            j->level = s->next_level;
+            s->next_level = std::min(s->next_level + 1, s->nlevels - 1);
+        } else if (s->prio_mode == 2) {
+            j->level = 0;
+        } else if (s->prio_mode == 3) {
+            j->level = s->nlevels - 1 - j->level;   // largest work first
+        }
+        s->slot_running++;
         lk.unlock();
         run_job(j, st[j->level]);
         lk.lock();
-        j->finished = Clock::now();
-        j->done = true;
+        s->slot_running--;
+        if (j->wide) s->wide_running--;
         s->in_use -= j->bytes;
-        s->n_done++;
-        s->done_cv.notify_all();
+        finish_locked(s, j, j->status);
     }
     for (int k = 0; k < s->nlevels; ++k)
         if (st[k] && (k == 0 || st[k] != st[k - 1])) cudaStreamDestroy(st[k]);
@@ -205,6 +289,17 @@ extern "C" int reach_server_create(int slots, int64_t hbm_budget_bytes, reach_se
     s->nlevels = std::min(8, std::max(1, least - greatest + 1));
     s->budget = hbm_budget_bytes;
     s->nslots = slots;
+    const int64_t qblocks = reach_get_option(REACH_OPT_SERVE_QUEUE_BLOCKS);
+    s->queue_n = reach_get_option(REACH_OPT_SERVE_QUEUE_N);
+    s->max_wide = (int)reach_get_option(REACH_OPT_SERVE_MAX_WIDE);
+    s->prio_mode = (int)reach_get_option(REACH_OPT_SERVE_PRIORITY);
+    if (qblocks > 0) {
+        int rc = reach_queue_create((int)qblocks, 0.005, (int64_t)256 << 20, &s->queue);
+        if (rc) {
+            delete s;
+            return rc;
+        }
+    }
     for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_main, s);
     *out = s;
     return REACH_OK;
@@ -224,6 +319,10 @@ extern "C" int reach_server_submit(reach_server *s, const reach_request *r, int6
     j->r = *r;
     j->bytes = bytes;
     j->level = work_level(r, s->nlevels);
+    j->queue_ok = s->queue && queue_eligible(r);
+    // wide: state components per step enough to fill every SM (2^20)
+    j->wide = (r->method == 2 ? (double)r->sys->n * (double)std::max<int64_t>(r->m, 1) : 2.0 * r->sys->n) >=
+              (double)(1 << 20);
     j->submitted = Clock::now();
     s->jobs[j->ticket] = j;
     s->waiting.push_back(j);
@@ -235,12 +334,27 @@ extern "C" int reach_server_submit(reach_server *s, const reach_request *r, int6
 extern "C" int reach_server_wait(reach_server *s, int64_t ticket, double timeout_s, int *status, double *queue_s,
                                  double *run_s) {
     if (!s) return REACH_EINVAL;
+    const auto t0 = Clock::now();
+    auto limit = std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->jobs.find(ticket);
     if (it == s->jobs.end()) return REACH_EINVAL;
     Job *j = it->second;
-    auto limit = std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
-    if (!s->done_cv.wait_for(lk, limit, [&] { return j->done; })) return REACH_ETIMEOUT;
+    if (!s->done_cv.wait_for(lk, limit, [&] { return j->done || j->in_queue; })) return REACH_ETIMEOUT;
+    if (!j->done) {
+        // on the device work queue: wait there without holding the lock
+        const double left = std::max(0.0, timeout_s - std::chrono::duration<double>(Clock::now() - t0).count());
+        const int64_t qt = j->qticket;
+        lk.unlock();
+        int st = REACH_OK;
+        const int rc = reach_queue_wait(s->queue, qt, left, &st);
+        lk.lock();
+        if (rc == REACH_ETIMEOUT) return REACH_ETIMEOUT;
+        j->in_queue = false;
+        s->queue_running--;
+        finish_locked(s, j, rc ? rc : st);
+        dispatch_locked(s);
+    }
     if (status) *status = j->status;
     if (queue_s) *queue_s = std::chrono::duration<double>(j->started - j->submitted).count();
     if (run_s) *run_s = std::chrono::duration<double>(j->finished - j->started).count();
@@ -261,21 +375,50 @@ extern "C" int reach_server_stats(reach_server *s, int64_t *waiting, int64_t *ru
     return REACH_OK;
 }
 
+extern "C" int64_t reach_server_queued(reach_server *s) {
+    if (!s) return REACH_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->n_queued;
+}
+
 extern "C" int reach_server_destroy(reach_server *s) {
     if (!s) return REACH_EINVAL;
     {
         std::unique_lock<std::mutex> lk(s->mu);
-        // admitted and waiting requests are finished first
-        while (!s->waiting.empty() || !s->admitted.empty() || s->n_admitted > s->n_done) {
-            if (!s->waiting.empty() && s->admitted.empty() && s->n_admitted == s->n_done) break;
+        // admitted and waiting requests are finished first; requests on the
+        // queue are collected there (their staged results copied out)
+        for (;;) {
+            Job *qj = nullptr;
+            for (auto &kv : s->jobs)
+                if (kv.second->in_queue) { qj = kv.second; break; }
+            if (qj) {
+                const int64_t qt = qj->qticket;
+                lk.unlock();
+                int st = REACH_OK;
+                const int rc = reach_queue_wait(s->queue, qt, 3600.0, &st);
+                lk.lock();
+                qj->in_queue = false;
+                s->queue_running--;
+                finish_locked(s, qj, rc ? rc : st);
+                dispatch_locked(s);
+                continue;
+            }
+            if (s->admitted.empty() && s->slot_running == 0) {
+                if (s->waiting.empty()) break;
+                dispatch_locked(s);
+                bool started = !s->admitted.empty() || s->slot_running > 0;
+                for (auto &kv : s->jobs) started |= kv.second->in_queue;
+                if (!started) break;   // nothing left can start
+                continue;
+            }
             s->done_cv.wait_for(lk, std::chrono::milliseconds(50));
         }
         s->stopping = true;
         s->work_cv.notify_all();
     }
     for (std::thread &t : s->workers) t.join();
+    if (s->queue) reach_queue_destroy(s->queue);
     for (auto &kv : s->jobs) delete kv.second;
-    for (Job *j : s->waiting) (void)j;   // owned by jobs
     delete s;
     return REACH_OK;
 }

@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "api_internal.cuh"
 
@@ -697,6 +698,141 @@ __global__ void __launch_bounds__(32 * KS_WARPS_PER_BLOCK, 3) stencil_ks_rk4(Ste
     if (flags) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ KS, all steps in one launch
+// A KS grid of a few waves of warp tiles (2^20 points: 4370 tiles over 1776
+// resident warps) loses the end of every launch: as the last tiles of a step
+// finish, SMs hold fewer warps than keep the FP64 pipe busy, and the next
+// step's launch waits for all of them.  Here one persistent launch runs every
+// step: warps take (step, tile) items in step-major order from a counter, and
+// item (s, t) starts as soon as tiles t - 1, t, t + 1 (the tiles its halo of
+// 4R = 8 cells reaches) have finished step s - 1, so step s + 1 fills the SMs
+// that step s leaves idle.  An item waits only for items handed out before it
+// (to running warps), so no wait is circular; each wait is also bounded
+// (wait_ns), after which the launch records ST_TIMEOUT and stops.  A tile's
+// arithmetic is that of stencil_ks_rk4 at one step per launch, so the box is
+// the same bit for bit.
+struct FlowArgs {
+    StepArgs st;                   // n, W, H = 8, h, hh, h6, status; ntiles
+    const double *xlo, *xhi;       // the input box (step 0)
+    double *bufA[2], *bufB[2];     // step s writes [(N - 1 - s) % 2]: [0] is the output (lo, hi)
+    int64_t N;
+    unsigned long long *next;      // item counter (zeroed before the launch)
+    int *ready;                    // per tile: steps completed (zeroed before the launch)
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int METHOD, int KC>
+__global__ void __launch_bounds__(32 * KS_WARPS_PER_BLOCK, 3) stencil_ks_flow(FlowArgs f, KsK p) {
+    const StepArgs &a = f.st;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = a.n;
+    const uint32_t T = (uint32_t)a.ntiles;
+    const unsigned long long total = (unsigned long long)f.N * T;   // < 2^32 (checked on the host)
+    int flags = 0;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(f.next, 1ULL);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= total) break;
+        const uint32_t s = (uint32_t)i / T, t = (uint32_t)i - s * T;   // 32-bit division
+        if (s > 0) {
+            // wait for the neighbouring tiles' previous step (bounded)
+            int late = 0;
+            if (lane == 0) {
+                const uint32_t tl = t == 0 ? T - 1 : t - 1, tr = t == T - 1 ? 0 : t + 1;
+                const unsigned long long t0 = global_ns();
+                unsigned ns = 64;
+                while (ld_acquire_gpu(f.ready + tl) < (int)s || ld_acquire_gpu(f.ready + t) < (int)s ||
+                       ld_acquire_gpu(f.ready + tr) < (int)s) {
+                    if (global_ns() - t0 > f.wait_ns || (*(volatile int *)a.status & ST_TIMEOUT)) {
+                        late = 1;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 1024) ns *= 2;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, late, 0)) {
+                if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+                return;
+            }
+        }
+        const int64_t own0 = (int64_t)t * a.W;
+        const int64_t g0 = own0 - a.H + (int64_t)lane * KC;
+        const int in = (int)((f.N - s) & 1), out = (int)((f.N - 1 - s) & 1);
+        const double *srcA = s == 0 ? f.xlo : f.bufA[in], *srcB = s == 0 ? f.xhi : f.bufB[in];
+        double zA[KC], zB[KC];
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            const int64_t idx = wrap_index(g, n);
+            // written by other warps during this launch: read through L2
+            double va = __ldcg(srcA + idx), vb = __ldcg(srcB + idx);
+            if (s == 0) {
+                const bool owned = g >= own0 && g < own0 + a.W && g < n && g >= 0;
+                if (owned && !(kle(va, vb) && kfinite(va) && kfinite(vb))) flags |= ST_BADINPUT;
+                if (METHOD == CGB) {
+                    double c = 0.5 * (va + vb), r = 0.5 * (vb - va);
+                    va = c;
+                    vb = r;
+                }
+            }
+            zA[j] = va;
+            zB[j] = vb;
+        }
+        {
+            double yA[KC], yB[KC], aA[KC], aB[KC], kA[KC], kB[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) { yA[j] = zA[j]; yB[j] = zB[j]; }
+            ks_rhs<METHOD>(p, yA, yB, kA, kB);
+            rk4_update<0>(zA, yA, aA, kA, a);
+            rk4_update<0>(zB, yB, aB, kB, a);
+            ks_rhs<METHOD>(p, yA, yB, kA, kB);
+            rk4_update<1>(zA, yA, aA, kA, a);
+            rk4_update<1>(zB, yB, aB, kB, a);
+            ks_rhs<METHOD>(p, yA, yB, kA, kB);
+            rk4_update<2>(zA, yA, aA, kA, a);
+            rk4_update<2>(zB, yB, aB, kB, a);
+            ks_rhs<METHOD>(p, yA, yB, kA, kB);
+            rk4_update<3>(zA, yA, aA, kA, a);
+            rk4_update<3>(zB, yB, aB, kB, a);
+        }
+        const bool last = (int64_t)s == f.N - 1;
+        double *outA = f.bufA[out], *outB = f.bufB[out];
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int64_t g = g0 + j;
+            if (!(g >= own0 && g < own0 + a.W && g < n && g >= 0)) continue;
+            double oa = zA[j], ob = zB[j];
+            if (last) {
+                if (METHOD == CGB) {
+                    if (dkey(ob) < 0) flags |= ST_NEGRADIUS;
+                    double lo = oa - ob, hi = oa + ob;
+                    oa = lo;
+                    ob = hi;
+                }
+                if (!kfinite(oa) || !kfinite(ob)) flags |= ST_NONFINITE;
+            }
+            outA[g] = oa;
+            outB[g] = ob;
+        }
+        // the tile's step s is visible before its flag says so
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu(f.ready + t, (int)s + 1);
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
 // ------------------------------------------------------------------ host
 // Launch shape for a grid of warp tiles.  A tile is one warp's serial FP64
 // work (a warp issues an FP64 instruction about every 68 clocks, and an SM's
@@ -1095,6 +1231,61 @@ int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const doubl
         REACH_LAUNCHED("sound_cgb_box");
     }
     return REACH_OK;
+}
+
+// Whether stencil_ks_flow runs an n-point KS grid over N steps: wide tiles at
+// one step per launch, more tiles than one wave of full-rate warps (592) and
+// few enough waves that the end of each launch costs (up to 8), at least
+// three tiles (a tile's two neighbours differ) and N x tiles < 2^32.
+bool ks_flow_eligible(int64_t n, int64_t N) {
+    if (opt_ks_flow() == 1 || N < 2) return false;
+    if (tile_kc(n, 8, 1) != KC_WIDE) return false;
+    const int64_t W = 32 * KC_WIDE - 16, T = (n + W - 1) / W;
+    if (T < 3 || (uint64_t)N * (uint64_t)T >= (1ULL << 32)) return false;
+    if (opt_ks_flow() == 2) return true;
+    return T > 592 && T <= 8 * 1776;
+}
+
+int stencil_ks_flow_run(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
+                        double *hi, double *sA, double *sB, double h, int64_t N, int *status, void *work,
+                        cudaStream_t st) {
+    FlowArgs f;
+    memset(&f, 0, sizeof f);
+    StepArgs &a = f.st;
+    a.n = n;
+    a.H = 8;
+    a.W = 32 * KC_WIDE - 2 * a.H;
+    a.ntiles = (n + a.W - 1) / a.W;
+    a.tile0 = 0;
+    a.tcount = a.ntiles;
+    a.S = 1;
+    a.h = h;
+    a.hh = 0.5 * h;
+    a.h6 = h / 6.0;
+    a.status = status;
+    f.xlo = xlo;
+    f.xhi = xhi;
+    f.bufA[0] = lo; f.bufB[0] = hi;
+    f.bufA[1] = sA; f.bufB[1] = sB;
+    f.N = N;
+    f.next = (unsigned long long *)work;
+    f.ready = (int *)((char *)work + 16);
+    f.wait_ns = 2000000000ULL;   // 2 s: far beyond any tile's step
+    REACH_CUDA(cudaMemsetAsync(work, 0, ks_flow_work_bytes(n), st));
+    // a resident grid: three 4-warp blocks per SM (the kernel's launch bound)
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(3 * sms);
+    if (method == MM) stencil_ks_flow<MM, KC_WIDE><<<grid, 32 * KS_WARPS_PER_BLOCK, 0, st>>>(f, p);
+    else stencil_ks_flow<CGB, KC_WIDE><<<grid, 32 * KS_WARPS_PER_BLOCK, 0, st>>>(f, p);
+    REACH_LAUNCHED("stencil_ks_flow");
+    return REACH_OK;
+}
+
+int64_t ks_flow_work_bytes(int64_t n) {
+    const int64_t W = 32 * KC_WIDE - 16, T = (n + W - 1) / W;
+    return 16 + 4 * T;
 }
 
 int stencil_ks(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,

@@ -17,6 +17,7 @@ def _reset_options():
     yield
     R.reach_set_option(R.OPT_BATCH_CPT, 0)
     R.reach_set_option(R.OPT_KERNEL, 0)
+    R.reach_set_option(R.OPT_BATCH_CLUSTER_FROM, 0)
 
 
 @pytest.mark.parametrize("method", ["mm", "cgb"])
@@ -60,6 +61,44 @@ def test_osc_batch_matches_oracle_and_solo(autotune):
             fn = R.reach_mm if method == "mm" else R.reach_cgb
             solo = fn(qq["sys"], q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
             assert np.array_equal(solo[0], lo) and np.array_equal(solo[1], hi)
+    for s in systems.values():
+        s.close()
+
+
+@pytest.mark.parametrize("cluster_from", [0, 2048, 4096])
+def test_mid_size_items_on_clusters_give_the_same_boxes(cluster_from):
+    # the layout's second tuned dimension: items from cluster_from components
+    # run on a two-block cluster instead of a bin slot; a component's
+    # arithmetic does not depend on where it runs, so the boxes are the same
+    # bit for bit, and they are the oracle's
+    sizes = [9, 300, 520, 700, 1000, 1500, 2048]
+    T = 0.05
+    R.reach_set_option(R.OPT_BATCH_CPT, 16)
+    R.reach_set_option(R.OPT_BATCH_CLUSTER_FROM, cluster_from)
+    systems, queries, raw = _osc_batch(sizes, T, seed0=300)
+    with R.Batch(queries) as b:
+        st, _ = b.run()
+        lay = b.layout()
+        assert (st == 0).all()
+        assert lay["cpt"] == 16 and lay["cluster_from"] == cluster_from and lay["create_s"] > 0
+        for (lo, hi), (method, q), qq in zip(b.outputs, raw, queries):
+            o = O.reach(method, "osc", q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
+            assert_close(lo, o[0], TOL64, f"{method} m={qq['sys'].n // 2} lo")
+            assert_close(hi, o[1], TOL64, f"{method} m={qq['sys'].n // 2} hi")
+            fn = R.reach_mm if method == "mm" else R.reach_cgb
+            solo = fn(qq["sys"], q["x_lo"], q["x_hi"], q["w_lo"], q["w_hi"], t_final=T, dt=q["dt"])
+            assert np.array_equal(solo[0], lo) and np.array_equal(solo[1], hi)
+    for s in systems.values():
+        s.close()
+
+
+def test_tuner_reports_its_candidates():
+    sizes = [4, 40, 600, 1100, 1500]
+    systems, queries, _ = _osc_batch(sizes, 0.05, seed0=400)
+    with R.Batch(queries) as b:
+        lay = b.layout()
+        assert lay["cpt"] in (2, 4, 8, 16) and lay["cluster_from"] in (0, 2048, 4096)
+        assert {"cpt2", "cpt4", "cpt8", "cpt16"} <= set(lay["tune_ms"])
     for s in systems.values():
         s.close()
 

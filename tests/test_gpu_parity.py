@@ -551,3 +551,42 @@ def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
     o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, m=m, seed=4, prec=32)
     assert_close(boxes[0][0], o[0], TOL32, "lo")
     assert_close(boxes[0][1], o[1], TOL32, "hi")
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("n,T", [(723, 0.003), (3001, 0.0013), (40001, 0.001)])
+def test_ks_all_steps_in_one_launch(method, n, T):
+    # the persistent KS kernel (every step in one launch, items started as
+    # their neighbouring tiles finish the previous step) gives the box of one
+    # launch per step bit for bit, and the oracle's
+    lo, hi, _, _, _, dt, _, _ = problem("ks", n, seed=61)
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    boxes = {}
+    try:
+        for mode in (1, 2):
+            R.reach_set_option(R.OPT_KS_FLOW, mode)
+            boxes[mode] = gpu_box(method, "ks", n, lo, hi, None, None, T, dt)
+    finally:
+        R.reach_set_option(R.OPT_KS_FLOW, 0)
+    np.testing.assert_array_equal(boxes[1][0], boxes[2][0])
+    np.testing.assert_array_equal(boxes[1][1], boxes[2][1])
+    o = O.reach(method, "ks", lo, hi, t_final=T, dt=dt)
+    assert_close(boxes[2][0], o[0], TOL64, "lo")
+    assert_close(boxes[2][1], o[1], TOL64, "hi")
+
+
+def test_ks_one_launch_reports_a_bad_box_and_a_nonfinite_result():
+    n = 3001
+    lo, hi, _, _, _, dt, _, _ = problem("ks", n, seed=62)
+    R.reach_set_option(R.OPT_KS_FLOW, 2)
+    try:
+        with R.System("ks", n) as s:
+            with pytest.raises(R.ReachError) as e:
+                R.reach_mm(s, hi, lo, t_final=0.001, dt=dt)
+            assert e.value.code == -1
+            big = np.full(n, 10.0)
+            with pytest.raises(R.ReachError) as e:
+                R.reach_mm(s, -big, big, t_final=2.0, dt=1e-3)
+            assert e.value.code == -4
+    finally:
+        R.reach_set_option(R.OPT_KS_FLOW, 0)

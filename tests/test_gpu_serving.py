@@ -1,9 +1,11 @@
-"""The continuous-batching server (reach_server_*): results in the mix equal
-results alone, admission keeps within the memory budget, and bounded waits
-time out on the host without touching the GPU."""
+"""The continuous-batching server (reach_server_*): every result in the mix is
+the oracle's (or, for queries too large for the oracle, the same call made
+alone), small requests run on the device work queue, admission keeps within
+the memory budget, and bounded waits time out on the host."""
 import numpy as np
 import pytest
 
+import oracle as O
 import paper_2001_10635_b300 as R
 import workloads as W
 from reachtest import TOL32, TOL64, assert_close, cuda_available
@@ -31,26 +33,89 @@ def _alone(s, q):
     return R.reach_mc(s, q.x_lo, q.x_hi, *w, **kw, m=q.m, seed=q.seed, precision=q.prec)
 
 
-def test_results_in_the_mix_equal_results_alone():
+# oracle work per query (comp-steps) up to which the mix is checked against
+# the oracle; larger queries are checked against the same call made alone
+ORACLE_WORK = 3e7
+
+
+def _oracle(q):
+    kw = dict(t_final=q.steps * q.dt, dt=q.dt, params=q.params or None)
+    w = (q.w_lo, q.w_hi) if q.kind == "traffic" else (None, None)
+    if q.method == "mc":
+        return O.reach("mc", q.kind, q.x_lo, q.x_hi, *w, **kw, m=q.m, seed=q.seed, prec=q.prec)
+    return O.reach(q.method, q.kind, q.x_lo, q.x_hi, *w, **kw)
+
+
+def _work(q):
+    return (q.m * q.n if q.method == "mc" else 2 * q.n) * q.steps
+
+
+def test_results_in_the_mix_match_the_oracle():
+    # all submitted at once: the server must overlap them, send the small MM /
+    # CGB requests to its device work queue and admit the rest as slots free up
     trace = W.serving_trace(count=48, seed=3, traffic_n=(100, 200_000), ks_k=(10, 15), steps=(100, 2000),
                             scale_steps=0.2)
     cache = _systems(trace)
+    checked = 0
     with R.Server(slots=6, hbm_budget_bytes=8 << 30) as srv:
         tickets = []
-        for q in trace:   # all at once: the server must overlap and admit them as slots free up
+        for q in trace:
             w = (q.w_lo, q.w_hi) if q.kind == "traffic" else (None, None)
             tickets.append(srv.submit(cache[(q.kind, q.n)], q.method, q.x_lo, q.x_hi, *w, t_final=q.steps * q.dt,
                                       dt=q.dt, m=q.m, seed=q.seed, precision=q.prec))
         for (t, (lo, hi)), q in zip(tickets, trace):
             st, qs, rs = srv.wait(t, timeout_s=300)
             assert st == 0, (q.kind, q.method, q.n, st)
-            a = _alone(cache[(q.kind, q.n)], q)
             tol = TOL32 if q.method == "mc" and q.prec == 32 else TOL64
-            assert_close(lo, a[0], tol, f"{q.kind} {q.method} n={q.n} lo")
-            assert_close(hi, a[1], tol, f"{q.kind} {q.method} n={q.n} hi")
+            if _work(q) <= ORACLE_WORK:
+                ref = _oracle(q)
+                checked += 1
+            else:
+                ref = _alone(cache[(q.kind, q.n)], q)
+            assert_close(lo, ref[0], tol, f"{q.kind} {q.method} n={q.n} lo")
+            assert_close(hi, ref[1], tol, f"{q.kind} {q.method} n={q.n} hi")
         st = srv.stats()
         assert st["done"] == len(trace) and st["waiting"] == 0 and st["bytes_in_use"] == 0
+        assert srv.queued() > 0   # some requests ran on the device work queue
+    assert checked >= len(trace) // 2
     for s in cache.values():
+        s.close()
+
+
+def test_small_requests_alone_and_in_the_mix_through_the_queue():
+    # small MM / CGB requests (always queued) submitted one at a time and all
+    # together give the same boxes, and they are the oracle's
+    g = np.random.default_rng(12)
+    reqs = []
+    for i in range(24):
+        kind = ("traffic", "ks")[i % 2]
+        n = int(g.integers(10, 500))
+        if kind == "traffic":
+            c = g.uniform(60, 200, n)
+            args = (c - 2, c + 2, np.array([35.0]), np.array([45.0]))
+            T, dt = 1.0, 0.01
+        else:
+            u = W.ks_profile(n) + g.uniform(-0.01, 0.01, n)
+            args = (u - 1e-3, u + 1e-3, None, None)
+            T, dt = 0.01, 1e-4
+        reqs.append((kind, n, ("mm", "cgb")[(i // 2) % 2], args, T, dt))
+    systems = {(k, n): R.System(k, n) for k, n, *_ in reqs}
+    with R.Server(slots=2, hbm_budget_bytes=1 << 30) as srv:
+        alone = []
+        for k, n, m, args, T, dt in reqs:
+            t, out = srv.submit(systems[(k, n)], m, *args, t_final=T, dt=dt)
+            assert srv.wait(t, timeout_s=120)[0] == 0
+            alone.append(out)
+        mix = [srv.submit(systems[(k, n)], m, *args, t_final=T, dt=dt) for k, n, m, args, T, dt in reqs]
+        for (t, out), a, (k, n, m, args, T, dt) in zip(mix, alone, reqs):
+            assert srv.wait(t, timeout_s=120)[0] == 0
+            np.testing.assert_array_equal(out[0], a[0])
+            np.testing.assert_array_equal(out[1], a[1])
+            o = O.reach(m, k, *args, t_final=T, dt=dt)
+            assert_close(out[0], o[0], TOL64, f"{k}{n} {m} lo")
+            assert_close(out[1], o[1], TOL64, f"{k}{n} {m} hi")
+        assert srv.queued() == 2 * len(reqs)
+    for s in systems.values():
         s.close()
 
 
