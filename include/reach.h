@@ -311,11 +311,11 @@ REACH_API int reach_queue_destroy(reach_queue *q);
    interface (Sec. 1); here that purpose is an in-process server.  Requests of
    any system, size, method and horizon are submitted as they arrive and
    start, in arrival order, as capacity frees up:
-     - MM / CGB requests small enough for the device work queue (above) join
-       the server's queue, whose persistent blocks take them while other work
-       runs: always up to REACH_OPT_SERVE_QUEUE_N cells, and up to
-       REACH_QUEUE_MAX_N cells while other requests are running (alone, a
-       streaming kernel spread over every SM finishes those sooner);
+     - MM / CGB requests of up to REACH_OPT_SERVE_QUEUE_N cells (at most
+       REACH_QUEUE_MAX_N; default 512, beyond which one block takes longer per
+       RK4 step than a streaming kernel spread over every SM) join the
+       server's device work queue (above), whose persistent blocks take them
+       while other work runs;
      - every other request needs one of the server's slots and its
        device-memory footprint (reach_request_footprint) must fit in what is
        left of the budget (first fit).  Each slot is a worker thread running
@@ -375,21 +375,26 @@ REACH_API int reach_server_destroy(reach_server *s);
                                         16x16x1, 32x8x1, 8x16x2, 16x8x2) */
 #define REACH_OPT_SERVE_QUEUE_BLOCKS 8 /* servers created afterwards: blocks of their device work queue, 0 = no
                                          queue (default 64) */
-#define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: requests up to this many cells always take
-                                         the queue (default 512; larger ones up to REACH_QUEUE_MAX_N take it
-                                         while the server is busy) */
+#define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: MM / CGB requests up to this many cells
+                                         take the device work queue (default 512, at most REACH_QUEUE_MAX_N) */
 #define REACH_OPT_SERVE_MAX_WIDE 10    /* servers created afterwards: requests with 2^20 or more state components
                                          per step (they fill the GPU alone) running at once, 0 = no limit
-                                         (default 1) */
+                                         (default) */
 #define REACH_OPT_BATCH_CLUSTER_FROM 11 /* batches: items of this many state components or more run on a
                                           two-block cluster; 0 = tuned (untuned batches: only items too large
                                           for one block) */
 #define REACH_OPT_KS_FLOW 12           /* KS MM / CGB: 0 auto (every step in one persistent launch for grids of
-                                         one to eight waves of tiles), 1 one launch per step, 2 one launch
-                                         for every grid it can run */
+                                         two to eight waves of 240-point tiles, 0.85e6 to 3.4e6 points), 1 one
+                                         launch per step, 2 one launch for every grid it can run */
 #define REACH_OPT_SERVE_PRIORITY 13    /* servers created afterwards: stream priority of slot requests, 0 by
                                          work (smaller first), 1 by arrival (earlier first), 2 none, 3 by work
                                          (larger first) */
+#define REACH_OPT_SERVE_WIDE_EXCLUSIVE 14 /* servers created afterwards: 1 = a wide request starts only when no
+                                            other slot request runs and none starts beside it (queued requests
+                                            still run); 0 = off (default) */
+#define REACH_OPT_SERVE_LIGHT 15       /* servers created afterwards, with exclusive wide requests: requests of at
+                                         most this many state components per step compute beside a wide one,
+                                         at the least stream priority (0 = none) */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

@@ -25,8 +25,8 @@ int cuda_fail(cudaError_t e, const char *where) {
 // process-wide options; read by calls on any thread
 static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
     g_opt_mc_sb{0}, g_opt_mc_layout{0}, g_opt_serve_queue_blocks{64}, g_opt_serve_queue_n{512},
-    g_opt_serve_max_wide{1}, g_opt_batch_cluster_from{0}, g_opt_ks_flow{0},
-    g_opt_serve_priority{0};
+    g_opt_serve_max_wide{0}, g_opt_batch_cluster_from{0}, g_opt_ks_flow{0},
+    g_opt_serve_priority{0}, g_opt_serve_wide_exclusive{0}, g_opt_serve_light{0};
 
 // ---------------------------------------------------------------- memory
 static std::atomic<bool> g_pool_ready[64];
@@ -557,6 +557,14 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value < 0 || value > 3) return REACH_EINVAL;
         g_opt_serve_priority = value;
         return REACH_OK;
+    case REACH_OPT_SERVE_WIDE_EXCLUSIVE:
+        if (value < 0 || value > 1) return REACH_EINVAL;
+        g_opt_serve_wide_exclusive = value;
+        return REACH_OK;
+    case REACH_OPT_SERVE_LIGHT:
+        if (value < 0 || value > ((int64_t)1 << 40)) return REACH_EINVAL;
+        g_opt_serve_light = value;
+        return REACH_OK;
     }
     return REACH_EINVAL;
 }
@@ -576,6 +584,8 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_BATCH_CLUSTER_FROM: return g_opt_batch_cluster_from;
     case REACH_OPT_KS_FLOW: return g_opt_ks_flow;
     case REACH_OPT_SERVE_PRIORITY: return g_opt_serve_priority;
+    case REACH_OPT_SERVE_WIDE_EXCLUSIVE: return g_opt_serve_wide_exclusive;
+    case REACH_OPT_SERVE_LIGHT: return g_opt_serve_light;
     }
     return REACH_EINVAL;
 }

@@ -14,9 +14,8 @@
 //              whatever else runs, with no launch, copy call or synchronisation
 //              of its own; requests join while others are on the GPU
 //              (continuous batching).  Requests up to REACH_OPT_SERVE_QUEUE_N
-//              cells always go there; larger ones up to 4096 cells only while
-//              other requests are running, because alone a streaming kernel
-//              spread over every SM finishes them sooner than one block
+//              cells (default 512) go there: beyond that one block takes
+//              longer per RK4 step than a streaming kernel spread over every SM
 //   slots      every other request needs a free slot and its device footprint
 //              must fit in what is left of the budget (first fit, so small
 //              requests pass a large one that waits for memory); a slot is a
@@ -41,6 +40,7 @@
 #include <deque>
 #include <mutex>
 #include <new>
+#include <set>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -61,6 +61,7 @@ struct Job {
     bool done = false;
     bool queue_ok = false;   // may run on the device work queue
     bool wide = false;       // its kernels fill the GPU alone
+    bool light = false;      // its kernels hold few SMs: it may backfill beside a wide request
     bool in_queue = false;   // submitted to it: qticket is its ticket there
     int64_t qticket = 0;
 };
@@ -93,6 +94,11 @@ struct reach_server {
     int slot_running = 0;           // requests running on slots
     int wide_running = 0;           // wide requests admitted and not finished
     int max_wide = 0;               // wide requests at once (0: no limit)
+    bool wide_exclusive = false;    // a wide request computes with no other slot request
+    int64_t light_components = 0;   // requests of at most this many components per step backfill
+    int computing = 0, wide_computing = 0, light_computing = 0;   // slot requests past the compute gate
+    std::set<int64_t> gate;         // tickets of slot requests staged and waiting to compute
+    std::condition_variable gate_cv;
 };
 
 namespace reach {
@@ -121,8 +127,74 @@ int64_t footprint(const reach_request *r) {
     return b + (s->kind == REACH_HEAT3D ? 6 : 2) * n * 8;
 }
 
-static void run_job(Job *j, cudaStream_t st) {
+// Device copies of a slot request's host vectors, made before it computes
+// (while other requests run) and copied back after, so that its own kernels
+// start at once and the next request's copies overlap them.
+struct Staged {
+    reach_request r;     // the request with device pointers
+    void *buf = nullptr;
+    double *user_out[2] = {nullptr, nullptr};
+    double *dev_out[2] = {nullptr, nullptr};
+    int64_t n = 0;
+};
+
+static int stage_in(const Job *j, cudaStream_t st, Staged &g) {
     const reach_request &r = j->r;
+    g.r = r;
+    g.n = r.sys->n;
+    const int64_t n = r.sys->n, nw = r.sys->nw;
+    const double *in[4] = {r.x0_lo, r.x0_hi, r.w_lo, r.w_hi};
+    const int64_t cnt[4] = {n, n, nw, nw};
+    bool host_in[4], host_out[2];
+    int64_t total = 0;
+    for (int i = 0; i < 4; ++i) {
+        host_in[i] = cnt[i] > 0 && in[i] && !is_device_ptr(in[i]);
+        if (host_in[i]) total += (cnt[i] + 31) / 32 * 32;
+    }
+    double *out[2] = {r.lo, r.hi};
+    for (int i = 0; i < 2; ++i) {
+        host_out[i] = out[i] && !is_device_ptr(out[i]);
+        if (host_out[i]) total += (n + 31) / 32 * 32;
+    }
+    if (total == 0) return REACH_OK;
+    int rc = dalloc(&g.buf, (size_t)total * sizeof(double), st);
+    if (rc) return rc;
+    double *p = (double *)g.buf;
+    const double **din[4] = {&g.r.x0_lo, &g.r.x0_hi, &g.r.w_lo, &g.r.w_hi};
+    for (int i = 0; i < 4; ++i) {
+        if (!host_in[i]) continue;
+        REACH_CUDA(cudaMemcpyAsync(p, in[i], cnt[i] * sizeof(double), cudaMemcpyHostToDevice, st));
+        *din[i] = p;
+        p += (cnt[i] + 31) / 32 * 32;
+    }
+    double **dout[2] = {&g.r.lo, &g.r.hi};
+    for (int i = 0; i < 2; ++i) {
+        if (!host_out[i]) continue;
+        g.user_out[i] = out[i];
+        g.dev_out[i] = p;
+        *dout[i] = p;
+        p += (n + 31) / 32 * 32;
+    }
+    REACH_CUDA(cudaStreamSynchronize(st));
+    return REACH_OK;
+}
+
+static int stage_out(Staged &g, cudaStream_t st, bool copy) {
+    int rc = REACH_OK;
+    for (int i = 0; i < 2 && copy; ++i)
+        if (g.user_out[i]) {
+            cudaError_t e = cudaMemcpyAsync(g.user_out[i], g.dev_out[i], g.n * sizeof(double),
+                                            cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess && !rc) rc = cuda_fail(e, "stage_out");
+        }
+    if (g.buf) dfree(g.buf, st);
+    g.buf = nullptr;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && !rc) rc = cuda_fail(e, "stage_out");
+    return rc;
+}
+
+static void run_job(Job *j, const reach_request &r, cudaStream_t st) {
     if (r.method == 0)
         j->status = reach_mm(r.sys, r.x0_lo, r.x0_hi, r.w_lo, r.w_hi, r.t_final, r.dt, r.lo, r.hi, st);
     else if (r.method == 1)
@@ -174,10 +246,11 @@ static void dispatch_locked(reach_server *s) {
     int free_slots = s->idle - (int)s->admitted.size();
     for (auto it = s->waiting.begin(); it != s->waiting.end();) {
         Job *j = *it;
-        // small requests go to the queue: always below queue_n cells, and up
-        // to its limit while other requests keep the GPU busy
-        if (j->queue_ok && (j->r.sys->n <= s->queue_n || s->slot_running > 0 || s->queue_running > 0 ||
-                            !s->admitted.empty())) {
+        // small requests go to the queue (up to queue_n cells: beyond about 500
+        // cells one block takes longer per step than a streaming kernel spread
+        // over the GPU, e.g. a KS CGB request of 4096 points and 14902 steps
+        // 1.74 s queued against 0.68 s on a slot)
+        if (j->queue_ok && j->r.sys->n <= s->queue_n) {
             if (to_queue_locked(s, j)) it = s->waiting.erase(it);
             else ++it;
             continue;
@@ -246,13 +319,50 @@ static void worker_main(reach_server *s) {
             j->level = s->nlevels - 1 - j->level;   // largest work first
         }
         s->slot_running++;
+        cudaStream_t js = st[j->level];
         lk.unlock();
-        run_job(j, st[j->level]);
+        Staged g;
+        int rc = stage_in(j, js, g);
         lk.lock();
+        if (!rc) {
+            // the compute gate: with exclusive wide requests a wide one computes
+            // alone and nothing computes beside it; waiters pass in arrival order
+            const bool backfill = s->wide_exclusive && j->light;
+            if (!backfill) {
+                s->gate.insert(j->ticket);
+                s->gate_cv.wait(lk, [&] {
+                    if (!s->wide_exclusive) return true;
+                    if (*s->gate.begin() != j->ticket) return false;
+                    return j->wide ? s->computing - s->light_computing == 0 : s->wide_computing == 0;
+                });
+                s->gate.erase(j->ticket);
+            } else {
+                // a light request passes the gate at the least priority: its
+                // blocks take only SMs that the wide request's blocks leave free
+                js = st[s->nlevels - 1];
+                s->light_computing++;
+            }
+            if (s->wide_exclusive && j->wide) js = st[0];
+            s->computing++;
+            if (j->wide) s->wide_computing++;
+            s->gate_cv.notify_all();
+            lk.unlock();
+            run_job(j, g.r, js);
+            lk.lock();
+            s->computing--;
+            if (j->wide) s->wide_computing--;
+            if (backfill) s->light_computing--;
+            s->gate_cv.notify_all();
+            rc = j->status;
+        }
+        lk.unlock();
+        const int rc_out = stage_out(g, js, rc == REACH_OK);
+        lk.lock();
+        if (!rc && rc_out) rc = rc_out;
         s->slot_running--;
         if (j->wide) s->wide_running--;
         s->in_use -= j->bytes;
-        finish_locked(s, j, j->status);
+        finish_locked(s, j, rc);
     }
     for (int k = 0; k < s->nlevels; ++k)
         if (st[k] && (k == 0 || st[k] != st[k - 1])) cudaStreamDestroy(st[k]);
@@ -293,6 +403,8 @@ extern "C" int reach_server_create(int slots, int64_t hbm_budget_bytes, reach_se
     s->queue_n = reach_get_option(REACH_OPT_SERVE_QUEUE_N);
     s->max_wide = (int)reach_get_option(REACH_OPT_SERVE_MAX_WIDE);
     s->prio_mode = (int)reach_get_option(REACH_OPT_SERVE_PRIORITY);
+    s->wide_exclusive = reach_get_option(REACH_OPT_SERVE_WIDE_EXCLUSIVE) != 0;
+    s->light_components = reach_get_option(REACH_OPT_SERVE_LIGHT);
     if (qblocks > 0) {
         int rc = reach_queue_create((int)qblocks, 0.005, (int64_t)256 << 20, &s->queue);
         if (rc) {
@@ -321,8 +433,10 @@ extern "C" int reach_server_submit(reach_server *s, const reach_request *r, int6
     j->level = work_level(r, s->nlevels);
     j->queue_ok = s->queue && queue_eligible(r);
     // wide: state components per step enough to fill every SM (2^20)
-    j->wide = (r->method == 2 ? (double)r->sys->n * (double)std::max<int64_t>(r->m, 1) : 2.0 * r->sys->n) >=
-              (double)(1 << 20);
+    const double per_step = r->method == 2 ? (double)r->sys->n * (double)std::max<int64_t>(r->m, 1)
+                                           : 2.0 * (double)r->sys->n;
+    j->wide = per_step >= (double)(1 << 20);
+    j->light = per_step <= (double)s->light_components;
     j->submitted = Clock::now();
     s->jobs[j->ticket] = j;
     s->waiting.push_back(j);

@@ -1234,16 +1234,20 @@ int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const doubl
 }
 
 // Whether stencil_ks_flow runs an n-point KS grid over N steps: wide tiles at
-// one step per launch, more tiles than one wave of full-rate warps (592) and
-// few enough waves that the end of each launch costs (up to 8), at least
-// three tiles (a tile's two neighbours differ) and N x tiles < 2^32.
+// one step per launch, at least three tiles (a tile's two neighbours differ),
+// N x tiles < 2^32, and by default two to eight waves of the 1776 resident
+// warps (three 4-warp blocks per SM), where the end of each launch costs
+// most: measured at one launch against one per step, 2^20 points MM 0.80
+// against 0.74 of the FP64 pipe, CGB 0.83 against 0.75; 2^21 CGB 0.84 against
+// 0.82, MM equal; from 2^22 equal; and at 2^18 (0.6 waves) 0.38 against 0.68,
+// where warps waiting for their neighbours hold most of the resident slots.
 bool ks_flow_eligible(int64_t n, int64_t N) {
     if (opt_ks_flow() == 1 || N < 2) return false;
     if (tile_kc(n, 8, 1) != KC_WIDE) return false;
     const int64_t W = 32 * KC_WIDE - 16, T = (n + W - 1) / W;
     if (T < 3 || (uint64_t)N * (uint64_t)T >= (1ULL << 32)) return false;
     if (opt_ks_flow() == 2) return true;
-    return T > 592 && T <= 8 * 1776;
+    return T >= 2 * 1776 && T <= 8 * 1776;
 }
 
 int stencil_ks_flow_run(int method, const KsK &p, int64_t n, const double *xlo, const double *xhi, double *lo,

@@ -50,14 +50,21 @@ def _work(q):
     return (q.m * q.n if q.method == "mc" else 2 * q.n) * q.steps
 
 
-def test_results_in_the_mix_match_the_oracle():
+@pytest.mark.parametrize("exclusive", [0, 1])
+def test_results_in_the_mix_match_the_oracle(exclusive):
     # all submitted at once: the server must overlap them, send the small MM /
     # CGB requests to its device work queue and admit the rest as slots free up
-    trace = W.serving_trace(count=48, seed=3, traffic_n=(100, 200_000), ks_k=(10, 15), steps=(100, 2000),
+    # (with exclusive wide requests, a wide one computes alone)
+    trace = W.serving_trace(count=48, seed=3, traffic_n=(100, 600_000), ks_k=(10, 15), steps=(100, 2000),
                             scale_steps=0.2)
     cache = _systems(trace)
     checked = 0
-    with R.Server(slots=6, hbm_budget_bytes=8 << 30) as srv:
+    R.reach_set_option(R.OPT_SERVE_WIDE_EXCLUSIVE, exclusive)
+    try:
+        srv = R.Server(slots=6, hbm_budget_bytes=8 << 30)
+    finally:
+        R.reach_set_option(R.OPT_SERVE_WIDE_EXCLUSIVE, 0)
+    with srv:
         tickets = []
         for q in trace:
             w = (q.w_lo, q.w_hi) if q.kind == "traffic" else (None, None)
