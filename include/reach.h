@@ -318,12 +318,21 @@ REACH_API int reach_queue_destroy(reach_queue *q);
        while other work runs;
      - every other request needs one of the server's slots and its
        device-memory footprint (reach_request_footprint) must fit in what is
-       left of the budget (first fit).  Each slot is a worker thread running
-       the request through reach_mm / reach_cgb / reach_mc on its own CUDA
-       streams, so admitted requests overlap on the GPU.  The stream's
-       priority falls with the request's work (state components per step x
-       steps; greatest below 2^30, one level lower per factor 4 above), so the
-       blocks of small requests are scheduled ahead of those of large ones.
+       left of the budget (first fit).  Each slot is a worker thread that
+       copies the request's host vectors to the device, runs it through
+       reach_mm / reach_cgb / reach_mc on its own CUDA streams and copies the
+       box back, so copies and kernels of different requests overlap.
+     - By default a wide request (2^20 or more state components per step: it
+       fills the GPU alone) computes alone: it starts computing when no other
+       slot request computes, and no other starts beside it except light
+       ones (REACH_OPT_SERVE_LIGHT components per step or fewer), which take
+       the least stream priority so that their blocks only fill SMs the wide
+       request leaves free; waiting requests start computing in arrival
+       order.  Sharing the GPU with a wide request would finish both late
+       (REACH_OPT_SERVE_WIDE_EXCLUSIVE = 0 lets them share).  Otherwise a
+       stream's priority falls with the request's work (state components per
+       step x steps; greatest below 2^30, one level lower per factor 4
+       above), so the blocks of small requests are scheduled first.
    A request's buffers must stay valid until reach_server_wait has returned
    its result. */
 typedef struct {
@@ -389,12 +398,12 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_SERVE_PRIORITY 13    /* servers created afterwards: stream priority of slot requests, 0 by
                                          work (smaller first), 1 by arrival (earlier first), 2 none, 3 by work
                                          (larger first) */
-#define REACH_OPT_SERVE_WIDE_EXCLUSIVE 14 /* servers created afterwards: 1 = a wide request starts only when no
-                                            other slot request runs and none starts beside it (queued requests
-                                            still run); 0 = off (default) */
+#define REACH_OPT_SERVE_WIDE_EXCLUSIVE 14 /* servers created afterwards: 1 (default) = a wide request computes
+                                            only when no other slot request computes and none starts computing
+                                            beside it, except light ones (queued requests still run); 0 = off */
 #define REACH_OPT_SERVE_LIGHT 15       /* servers created afterwards, with exclusive wide requests: requests of at
                                          most this many state components per step compute beside a wide one,
-                                         at the least stream priority (0 = none) */
+                                         at the least stream priority (default 2^15; 0 = none) */
 REACH_API int reach_set_option(int key, int64_t value);
 REACH_API int64_t reach_get_option(int key);
 

@@ -26,7 +26,8 @@ int cuda_fail(cudaError_t e, const char *where) {
 static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
     g_opt_mc_sb{0}, g_opt_mc_layout{0}, g_opt_serve_queue_blocks{64}, g_opt_serve_queue_n{512},
     g_opt_serve_max_wide{0}, g_opt_batch_cluster_from{0}, g_opt_ks_flow{0},
-    g_opt_serve_priority{0}, g_opt_serve_wide_exclusive{0}, g_opt_serve_light{0};
+    g_opt_serve_priority{0}, g_opt_serve_wide_exclusive{1},
+    g_opt_serve_light{1 << 15};
 
 // ---------------------------------------------------------------- memory
 static std::atomic<bool> g_pool_ready[64];

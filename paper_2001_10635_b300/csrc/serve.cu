@@ -19,16 +19,23 @@
 //   slots      every other request needs a free slot and its device footprint
 //              must fit in what is left of the budget (first fit, so small
 //              requests pass a large one that waits for memory); a slot is a
-//              worker thread with its own CUDA streams running the request
-//              through the ordinary entry points, so admitted requests overlap
-//   wide       a request with 2^20 or more state components per step fills the
-//              GPU alone; at most REACH_OPT_SERVE_MAX_WIDE of them run at once
-//              (in arrival order), so that two large requests do not share the
-//              GPU and both finish late, while smaller requests run beside them
-//   priority   a slot request runs on a stream whose priority falls with its
-//              work (components per step x steps: the greatest below 2^30
-//              component updates, one level lower per factor 4 above): the
-//              block scheduler hands SMs freed by a large request's short
+//              worker thread with its own CUDA streams that copies the
+//              request's host vectors to the device, runs it through the
+//              ordinary entry points and copies the box back, so copies and
+//              kernels of different requests overlap
+//   gate       a wide request (2^20 or more state components per step) fills
+//              the GPU alone; by default it computes alone, since sharing the
+//              GPU finishes both requests late: it passes the compute gate
+//              when no other slot request computes, and none passes beside it
+//              except light ones (REACH_OPT_SERVE_LIGHT components per step or
+//              fewer, on the least stream priority, so their blocks only fill
+//              SMs the wide request leaves free); waiters pass in arrival
+//              order.  REACH_OPT_SERVE_MAX_WIDE can also cap wide requests at
+//              admission.
+//   priority   otherwise a slot request runs on a stream whose priority falls
+//              with its work (components per step x steps: the greatest below
+//              2^30 component updates, one level lower per factor 4 above):
+//              the block scheduler hands SMs freed by a large request's short
 //              blocks to a small request first
 //   wait       bounded: returns REACH_ETIMEOUT when the request has not finished
 //              within the caller's limit
@@ -94,7 +101,7 @@ struct reach_server {
     int slot_running = 0;           // requests running on slots
     int wide_running = 0;           // wide requests admitted and not finished
     int max_wide = 0;               // wide requests at once (0: no limit)
-    bool wide_exclusive = false;    // a wide request computes with no other slot request
+    bool wide_exclusive = true;     // a wide request computes with no other slot request
     int64_t light_components = 0;   // requests of at most this many components per step backfill
     int computing = 0, wide_computing = 0, light_computing = 0;   // slot requests past the compute gate
     std::set<int64_t> gate;         // tickets of slot requests staged and waiting to compute

@@ -61,6 +61,8 @@ def test_option_defaults():
     assert R.reach_get_option(R.OPT_SERVE_QUEUE_BLOCKS) == 64
     assert R.reach_get_option(R.OPT_SERVE_QUEUE_N) == 512
     assert R.reach_get_option(R.OPT_MC_LAYOUT) == 0 and R.reach_get_option(R.OPT_KS_FLOW) == 0
+    assert R.reach_get_option(R.OPT_SERVE_WIDE_EXCLUSIVE) == 1 and R.reach_get_option(R.OPT_SERVE_LIGHT) == 1 << 15
+    assert R.reach_get_option(R.OPT_SERVE_MAX_WIDE) == 0
 
 
 def test_strerror_names_every_code():

@@ -63,7 +63,7 @@ def test_results_in_the_mix_match_the_oracle(exclusive):
     try:
         srv = R.Server(slots=6, hbm_budget_bytes=8 << 30)
     finally:
-        R.reach_set_option(R.OPT_SERVE_WIDE_EXCLUSIVE, 0)
+        R.reach_set_option(R.OPT_SERVE_WIDE_EXCLUSIVE, 1)
     with srv:
         tickets = []
         for q in trace:
