@@ -371,7 +371,7 @@ REACH_API int reach_server_destroy(reach_server *s);
 /* ---- tuning knobs (process-wide; used by tests, the autotuner, bench) ---- */
 #define REACH_OPT_KERNEL 1           /* 0 auto, 1 streaming stencil, 2 on-chip */
 #define REACH_OPT_STEPS_PER_LAUNCH 2 /* streaming kernels: RK4 steps per launch, 1..8; 0 = auto (FP64 1, FP32 MC
-                                        2, FP32 MC on KS grids 3) */
+                                        3) */
 #define REACH_OPT_BLOCK 3            /* threads per block of the on-chip kernel (0 auto) */
 #define REACH_OPT_BATCH_CPT 4        /* batches: components per thread, 0 = autotune, or 2/4/8/16 */
 #define REACH_OPT_TILE 5             /* streaming traffic / KS MM and CGB: cells per lane, 0 = auto, 2 (64-cell
@@ -379,9 +379,10 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_MC_SB 6            /* on-chip MC: samples per block, 0 = auto (32 from 4736 samples, 8 from 1184,
                                         else 2), or 2 / 8 / 32 */
 #define REACH_OPT_MC_LAYOUT 7         /* streaming binary32 MC: 0 auto (two samples per lane, packed FP32
-                                        arithmetic, measured block shape), 1 one sample per lane; 2..5 block
+                                        arithmetic, measured block shape), 1 one sample per lane; 2..6 block
                                         shapes of the two-sample kernel (warps x rows x blocks per SM:
-                                        16x16x1, 32x8x1, 8x16x2, 16x8x2) */
+                                        16x16x1, 32x8x1, 8x16x2, 16x8x2, and 16x16x1 persistent with the
+                                        next tiles copied ahead by the TMA engine) */
 #define REACH_OPT_SERVE_QUEUE_BLOCKS 8 /* servers created afterwards: blocks of their device work queue, 0 = no
                                          queue (default 64) */
 #define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: MM / CGB requests up to this many cells

@@ -19,6 +19,8 @@
 #include <atomic>
 #include <type_traits>
 
+#include <cuda.h>
+
 #include "api_internal.cuh"
 #include "quad.cuh"
 
@@ -637,6 +639,245 @@ __global__ void __launch_bounds__(32 * WPB, MINB) mc_stream2(McStep a) {
     if (flags) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ streaming, two samples per lane, prefetched
+// mc_stream2 loads a block's state rows when the block starts, so with one
+// block per SM the FP32 pipe waits out every tile's load.  Here the blocks
+// are persistent and the next tiles' rows arrive ahead of time: one thread
+// issues a bulk copy (cp.async.bulk, the TMA engine) of each 256-byte row
+// segment (64 samples) into a double-buffered shared-memory tile, counted on
+// an mbarrier; the warps wait on it, move their rows into registers, and the
+// copy of the tile after next starts into the freed buffer while they
+// compute.  Every wait on an mbarrier is bounded (ST_TIMEOUT).  Used for the
+// launches after the first (the first draws the samples); the arithmetic is
+// mc_stream2's, so the box is the same bit for bit.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+
+// bounded wait for phase `parity` of an mbarrier (about 2 s); false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(b, parity)) {
+        if (global_ns() - t0 > 2000000000ULL) return false;
+    }
+    return true;
+}
+
+// one 2-D tensor copy (TMA) of a box of ROWS rows x 64 samples at (x, y) =
+// (first sample, first row); rows outside the tensor arrive as zeros
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
+
+template <int SYS, int WPB, int B>
+__global__ void __launch_bounds__(32 * WPB, 1) mc_stream2p(McStep a, unsigned long long items,
+                                                          const __grid_constant__ CUtensorMap map) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    constexpr int ROWS = WPB * B;
+    extern __shared__ __align__(128) float2 tbuf[];   // [2][ROWS][32]
+    __shared__ float2 edge[2][WPB][2 * R][32];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int ready;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = a.n;
+    Q2 q;
+    q.cap = bc2(a.qf[0]); q.v = bc2(a.qf[1]); q.nw = bc2(-a.qf[2]); q.wxbar = bc2(a.qf[3]);
+    q.a0 = bc2(a.qf[0]); q.a1 = bc2(a.qf[1]); q.a2 = bc2(a.qf[2]); q.nk = bc2(-a.qf[3]);
+    const float2 h = bc2(a.hf[0]), hh = bc2(a.hf[1]), h6 = bc2(a.hf[2]), two = bc2(2.f);
+    const unsigned long long G = gridDim.x;
+
+    // rows of item it: its tile's first halo row and sample block
+    auto item_rows = [&](unsigned long long it, int64_t &row0b, int64_t &sb) {
+        const int64_t tile = (int64_t)(it % a.ntile);
+        sb = (int64_t)(it / a.ntile);
+        row0b = tile * a.TC - a.H;
+    };
+    // warp 0: the copies of item it into buffer k.  One tensor copy of the
+    // whole box (rows outside a traffic chain arrive as zeros); a KS box that
+    // wraps around the periodic grid takes one row copy per lane in turn
+    // (lane 0 announces the bytes first in both cases)
+    auto issue = [&](unsigned long long it, int k) {
+        int64_t row0b, sb;
+        item_rows(it, row0b, sb);
+        if (SYS != REACH_KS || (row0b >= 0 && row0b + ROWS <= n)) {
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bar[k], (uint32_t)(ROWS * 256));
+                tma_load_2d(tbuf + (size_t)k * ROWS * 32, &map, (int)(sb * 64), (int)row0b, &bar[k]);
+            }
+            __syncwarp();
+            return;
+        }
+        int64_t rows_in = ROWS;
+        if (SYS != REACH_KS) {
+            const int64_t lo = row0b > 0 ? row0b : 0, hi = row0b + ROWS < n ? row0b + ROWS : n;
+            rows_in = hi > lo ? hi - lo : 0;
+        }
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[k], (uint32_t)(rows_in * 256));
+        }
+        __syncwarp();
+        const float *src = (const float *)a.in;
+        for (int r = lane; r < ROWS; r += 32) {
+            const int64_t g = row0b + r;
+            int64_t gi = g;
+            if (SYS == REACH_KS) gi = wrap_index(g, n);
+            else if (g < 0 || g >= n) continue;
+            bulk_g2s(tbuf + ((size_t)k * ROWS + r) * 32, src + gi * a.M + sb * 64, 256, &bar[k]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        if (blockIdx.x < items) issue(blockIdx.x, 0);
+        if (blockIdx.x + G < items) issue(blockIdx.x + G, 1);
+    }
+    uint32_t ph[2] = {0, 0};
+    int flags = 0, buf = 0;
+    bool timed_out = false;
+    int k = 0;
+    for (unsigned long long it = blockIdx.x; it < items; it += G, k ^= 1) {
+        int64_t row0b, sb;
+        item_rows(it, row0b, sb);
+        const int64_t own0 = row0b + a.H;
+        const int64_t j0 = sb * 64 + 2 * lane;
+        const bool v0 = j0 < a.m, v1 = j0 + 1 < a.m;
+        const int64_t row0 = row0b + (int64_t)warp * B;
+        float2 d = bc2(0.f);
+        if (SYS == REACH_TRAFFIC) {
+            d.x = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)j0, 0u, 1u));
+            d.y = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, (uint32_t)(j0 + 1), 0u, 1u));
+        }
+        // thread 0 waits (bounded) and tells the block, so that a timeout
+        // leaves the loop in every thread at the same point
+        if (threadIdx.x == 0) ready = mbar_wait_bounded(&bar[k], ph[k]) ? 1 : 0;
+        __syncthreads();
+        if (!ready) {
+            timed_out = true;
+            break;
+        }
+        // the phase is complete: each thread's own wait returns at once and
+        // makes the copied rows visible to it
+        mbar_wait_bounded(&bar[k], ph[k]);
+        ph[k] ^= 1;
+        float2 z[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            const int64_t g = row0 + r;
+            const bool in = SYS == REACH_KS || (g >= 0 && g < n);
+            z[r] = in ? tbuf[((size_t)k * ROWS + warp * B + r) * 32 + lane] : bc2(0.f);
+        }
+        __syncthreads();   // buffer k is free: the copy of the item after next starts
+        if (warp == 0 && it + 2 * G < items) issue(it + 2 * G, k);
+        const bool interior = SYS != REACH_KS && row0 >= 1 && row0 + B <= n - 1;
+        auto steps = [&](auto in_tag) {
+            constexpr bool IN = decltype(in_tag)::value;
+            (void)IN;
+            for (int s = 0; s < a.S; ++s) {
+                float2 e[B + 2 * R], acc[B];
+#pragma unroll
+                for (int r = 0; r < B; ++r) e[R + r] = z[r];
+#pragma unroll
+                for (int stage = 0; stage < 4; ++stage) {
+#pragma unroll
+                    for (int q2 = 0; q2 < R; ++q2) {
+                        edge[buf][warp][q2][lane] = e[R + q2];
+                        edge[buf][warp][R + q2][lane] = e[B + q2];
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int q2 = 0; q2 < R; ++q2) {
+                        e[q2] = warp > 0 ? edge[buf][warp - 1][R + q2][lane] : bc2(0.f);
+                        e[B + R + q2] = warp < WPB - 1 ? edge[buf][warp + 1][q2][lane] : bc2(0.f);
+                    }
+                    buf ^= 1;
+                    float2 kring[R + 1];
+                    float2 fprev = bc2(0.f);
+                    (void)fprev;
+                    if constexpr (SYS != REACH_KS)
+                        fprev = IN ? tr_flux2_interior(q, e[0], e[1]) : tr_flux2(q, e[0], e[1], row0 - 1, n, d);
+#pragma unroll
+                    for (int r = 0; r < B + R; ++r) {
+                        if (r < B) {
+                            float2 kr;
+                            if constexpr (SYS == REACH_KS) {
+                                const float2 um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                                kr = fma2(u, fma2(q.nk, sub2(up1, um1), q.a0),
+                                          fma2(q.a1, add2(um1, up1), mul2(q.a2, add2(um2, up2))));
+                            } else {
+                                const float2 fout = IN ? tr_flux2_interior(q, e[r + 1], e[r + 2])
+                                                       : tr_flux2(q, e[r + 1], e[r + 2], row0 + r, n, d);
+                                kr = sub2(fprev, fout);
+                                fprev = fout;
+                            }
+                            kring[r % (R + 1)] = kr;
+                        }
+                        if (r >= R) {
+                            const int u = r - R;
+                            const float2 kk = kring[u % (R + 1)];
+                            if (stage == 0) { acc[u] = kk; e[R + u] = fma2(hh, kk, z[u]); }
+                            if (stage == 1) { acc[u] = fma2(two, kk, acc[u]); e[R + u] = fma2(hh, kk, z[u]); }
+                            if (stage == 2) { acc[u] = fma2(two, kk, acc[u]); e[R + u] = fma2(h, kk, z[u]); }
+                            if (stage == 3) { acc[u] = add2(acc[u], kk); z[u] = fma2(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                        }
+                    }
+                }
+            }
+        };
+        if (interior) steps(std::true_type{});
+        else steps(std::false_type{});
+        int64_t oo = (int64_t)(int32_t)row0 * (int32_t)a.M + j0;
+        const int64_t pb = (int64_t)((uint64_t)(uint32_t)sb * (uint32_t)n);
+        double *plo = a.plo + pb + row0, *phi = a.phi + pb + row0;
+#pragma unroll
+        for (int r = 0; r < B; ++r, oo += a.M) {
+            const int64_t g = row0 + r;
+            if (g < own0 || g >= own0 + a.TC || g >= n) continue;   // warp-uniform
+            if (a.last) warp_minmax2(z[r], v0, v1, plo + r, phi + r, a.status);
+            else *reinterpret_cast<float2 *>((float *)a.out + oo) = z[r];
+        }
+    }
+    if (timed_out) {
+        flags |= ST_TIMEOUT;
+        // let copies still in flight land before the block's shared memory goes (bounded)
+        if (threadIdx.x == 0)
+            for (int kk = 0; kk < 2; ++kk) mbar_wait_bounded(&bar[kk], ph[kk]);
+        __syncthreads();
+    }
+    if (flags && (threadIdx.x & 31) == 0) atomicOr(a.status, flags);
+}
+
 // ------------------------------------------------------------------ reduce
 __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, int64_t n, double *lo,
                           double *hi) {
@@ -801,15 +1042,63 @@ static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, voi
     return REACH_OK;
 }
 
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link to
+// the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    EncodeTiledFn f = fn.load();
+    if (!f) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        f = (EncodeTiledFn)p;
+        fn.store(f);
+    }
+    return f;
+}
+
+// the n x M binary32 state buffers as 2-D tensors (M samples per row, the
+// inner dimension), boxes of `rows` rows x 64 samples
+static int state_maps(const McStep &a, void *bufA, void *bufB, int rows, CUtensorMap (&maps)[2]) {
+    EncodeTiledFn f = encode_tiled();
+    if (!f) return REACH_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)a.M, (cuuint64_t)a.n};
+    const cuuint64_t strides[1] = {(cuuint64_t)a.M * sizeof(float)};
+    const cuuint32_t box[2] = {64, (cuuint32_t)rows};
+    const cuuint32_t estr[2] = {1, 1};
+    void *bufs[2] = {bufA, bufB};
+    for (int i = 0; i < 2; ++i)
+        if (f(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bufs[i], dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return REACH_ECUDA;
+    return REACH_OK;
+}
+
 // binary32 streaming with two samples per lane: a block of WPB warps x B rows
 // x 64 samples, at least MINB blocks per SM
-template <int SYS, int WPB, int B, int MINB>
+template <int SYS, int WPB, int B, int MINB, bool PREFETCH = false>
 static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_auto, cudaStream_t st) {
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
     int S = opt_steps() > 0 ? (int)opt_steps() : S_auto;
     while (S > 1 && 2 * 4 * R * S >= WPB * B / 2) --S;   // keep the halo below half the block
     const int64_t L = N > 0 ? (N + S - 1) / S : 1;
     void *buf[2] = {bufA, bufB};
+    // tensor maps of the two state buffers (rows of M binary32 samples), for
+    // the launches that copy their tiles ahead
+    CUtensorMap maps[2];
+    bool maps_ok = false;
+    if constexpr (PREFETCH) {
+        if (L > 1 && bufA && bufB) maps_ok = state_maps(a, bufA, bufB, WPB * B, maps) == REACH_OK;
+    }
+    (void)maps_ok;
     int64_t done = 0;
     for (int64_t q = 0; q < L; ++q) {
         const int s = N > 0 ? (int)std::min<int64_t>(S, N - done) : 0;
@@ -824,30 +1113,55 @@ static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_a
         const int64_t grid = ntile * (a.M / 64);
         if (grid > 0x7fffffffLL) return REACH_EINVAL;
         a.ntile = (unsigned)ntile;
-        mc_stream2<SYS, WPB, B, MINB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a);
-        REACH_LAUNCHED("mc_stream2");
+        bool prefetched = false;
+        if constexpr (PREFETCH) {
+          if (q > 0 && maps_ok) {
+            // persistent blocks, one per SM, the next tiles' rows copied ahead
+            static std::atomic<bool> attr_set{false};   // idempotent: a second setter is harmless
+            if (!attr_set.load()) {
+                int rc = allow_max_dynamic_smem((const void *)mc_stream2p<SYS, WPB, B>);
+                if (rc) return rc;
+                attr_set.store(true);
+            }
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const unsigned pgrid = (unsigned)std::min<int64_t>(grid, sms);
+            const size_t smem = (size_t)2 * WPB * B * 32 * sizeof(float2);
+            mc_stream2p<SYS, WPB, B><<<pgrid, 32 * WPB, smem, st>>>(a, (unsigned long long)grid, maps[q % 2]);
+            REACH_LAUNCHED("mc_stream2p");
+            prefetched = true;
+          }
+        }
+        if (!prefetched) {
+            mc_stream2<SYS, WPB, B, MINB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a);
+            REACH_LAUNCHED("mc_stream2");
+        }
         done += s;
     }
     return REACH_OK;
 }
 
-// Block shapes (REACH_OPT_MC_LAYOUT 2..5) and the measured default per system
+// Block shapes (REACH_OPT_MC_LAYOUT 2..6) and the measured default per system
 // (1024 samples of the 2^20-point KS grid over 500 steps, 256 of the 2^20-cell
 // chain over 200): the packed kernel is bound by the FP32 FMA pipe (a packed
-// instruction holds it two cycles), so the shape that best overlaps one
-// block's loads with another's arithmetic wins.  KS: one 16-warp block per
-// SM at three steps per launch (0.96 s; two 8-warp blocks at two steps 1.02
-// s, the one-sample kernel 1.05 s at its best S).  Traffic: two 8-warp blocks
-// per SM at two steps (0.084 s against 0.098 s for the one-sample kernel).
+// instruction holds it two cycles), so the shape that best hides each tile's
+// load behind arithmetic wins.  KS: persistent 16-warp blocks whose next tiles
+// arrive by tensor copies (layout 6) at three steps per launch, 0.87 s; the
+// same shape loading at block start 0.96 s, two 8-warp blocks per SM 1.02 s
+// (two steps), the one-sample kernel 1.05 s at its best.  Traffic: two 8-warp
+// blocks per SM at three steps, 0.077 s (0.081 s prefetched, 0.098 s for the
+// one-sample kernel).
 template <int SYS>
 static int launch_stream2(const McStep &a, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
     int layout = (int)opt_mc_layout();
-    if (layout == 0) layout = SYS == REACH_KS ? 2 : 4;
-    const int S_auto = SYS == REACH_KS ? 3 : 2;
+    if (layout == 0) layout = SYS == REACH_KS ? 6 : 4;
+    const int S_auto = 3;
     switch (layout) {
     case 3: return launch_stream2_v<SYS, 32, 8, 1>(a, N, bufA, bufB, S_auto, st);
     case 4: return launch_stream2_v<SYS, 8, 16, 2>(a, N, bufA, bufB, S_auto, st);
     case 5: return launch_stream2_v<SYS, 16, 8, 2>(a, N, bufA, bufB, S_auto, st);
+    case 6: return launch_stream2_v<SYS, 16, 16, 1, true>(a, N, bufA, bufB, S_auto, st);
     default: return launch_stream2_v<SYS, 16, 16, 1>(a, N, bufA, bufB, S_auto, st);
     }
 }

@@ -540,7 +540,7 @@ def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
     boxes = {}
     try:
-        for layout in (1, 0, 3, 4, 5):
+        for layout in (1, 0, 3, 4, 5, 6):
             R.reach_set_option(R.OPT_MC_LAYOUT, layout)
             boxes[layout] = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=4, precision=32)
     finally:
