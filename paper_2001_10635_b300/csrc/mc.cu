@@ -330,8 +330,8 @@ __device__ __forceinline__ T tr_flux(const T (&q)[4], T y, T yr, int64_t g, int6
 // Two blocks per SM for every variant: the traffic ones then spill a little
 // (64 / 128 registers) and still run 5% (binary32) and 7% (binary64) faster
 // than one block at 128 / 254 registers; KS binary64 fits 126 registers (+2%).
-template <int SYS, class T, int WPB>
-__global__ void __launch_bounds__(32 * WPB, 2)
+template <int SYS, class T, int WPB, int MINB = 2>
+__global__ void __launch_bounds__(32 * WPB, MINB)
 mc_stream(McStep a, const double *__restrict__ prm) {
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
     constexpr int B = MC_B;
@@ -1011,10 +1011,9 @@ static int launch_onchip(const McArgs &a, int sb, cudaStream_t st) {
 template <class T>
 constexpr int mc_wpb() { return sizeof(T) == 4 ? 16 : 8; }
 
-template <int SYS, class T>
-static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
+template <int SYS, class T, int WPB = mc_wpb<T>(), int MINB = 2>
+static int launch_stream_v(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
-    constexpr int WPB = mc_wpb<T>();
     // binary32 samples: two steps per launch halve the state traffic for a
     // 4R-row halo (measured +27% on the KS grid); binary64 is FP64-pipe bound
     int S = opt_steps() > 0 ? (int)opt_steps() : (sizeof(T) == 4 ? 2 : 1);
@@ -1035,11 +1034,24 @@ static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, voi
         const int64_t grid = ntile * (a.M / 32);
         if (grid > 0x7fffffffLL) return REACH_EINVAL;
         a.ntile = (unsigned)ntile;
-        mc_stream<SYS, T, WPB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a, prm);
+        mc_stream<SYS, T, WPB, MINB><<<(unsigned)grid, 32 * WPB, 0, st>>>(a, prm);
         REACH_LAUNCHED("mc_stream");
         done += s;
     }
     return REACH_OK;
+}
+
+template <int SYS, class T>
+static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
+    // binary64 on KS grids: one 16-warp block per SM halves the 16-row halo
+    // share of two 8-warp blocks (1024 samples of 2^20 points: 0.77 against
+    // 0.74 of the FP64 peak); the traffic chain's one-row halo gains nothing
+    // (2.26e10 against 2.33e10 comp-steps/s).  REACH_OPT_MC_LAYOUT 7 forces
+    // it, 1..6 the 8-warp blocks.
+    const int64_t lay = opt_mc_layout();
+    if (sizeof(T) == 8 && (lay == 7 || (lay == 0 && SYS == REACH_KS)))
+        return launch_stream_v<SYS, T, 16, 1>(a, prm, N, bufA, bufB, st);
+    return launch_stream_v<SYS, T>(a, prm, N, bufA, bufB, st);
 }
 
 // cuTensorMapEncodeTiled, from the driver through the runtime (no link to
