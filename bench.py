@@ -11,9 +11,9 @@ traffic cell-transmission chain with n = 2^26 cells, x0 box centres
   e2e    the same through the public API with host buffers (page-locked,
          passed as numpy arrays): the library's host->device copies and the
          result readback are inside the timed region
-  roofline  the dominant kernel (stencil_traffic_rk4): FP64-pipe operations per
-         launch / its average launch time, against the FP64 issue rate of
-         148 SMs x 2 ops/clk x 2.032 GHz
+  roofline  the dominant kernel (stencil_traffic_flow<MM>, all 200 steps of a
+         call in one launch): FP64-pipe operations per launch / its launch
+         time, against the FP64 issue rate of 148 SMs x 2 ops/clk x 2.032 GHz
   cpu_baseline / --impl reference  the FP64 oracle on one host core, on the
          first 2^20 cells of the same workload (full horizon)
 
@@ -53,10 +53,10 @@ FP64_OPS = {"mm": 15.0, "cgb": 15.0}
 SM_COUNT, FP64_PER_SM_CLK, SM_MAX_MHZ = 148, 2, 2032.0
 FP64_PEAK_OPS = SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6
 CPU_SAMPLE_CELLS = 1 << 20
-# DRAM bytes (read + write) of one stencil_traffic_rk4<MM> launch, from the ncu
-# capture of one launch on 2^24 cells; the traffic of a launch is proportional
-# to the cells, so it is scaled to the run's n
-NCU_DRAM_BYTES_PER_CELL_LAUNCH = (268.636928e6 + 224.436736e6) / (1 << 24)
+# DRAM bytes (read + write) per cell and RK4 step of stencil_traffic_flow<MM>,
+# from the ncu capture of one launch on 2^24 cells over 10 steps; the traffic
+# is proportional to cells x steps, so it is scaled to the run's n and steps
+NCU_DRAM_BYTES_PER_CELL_STEP = (2.827737e9 + 2.646888e9) / ((1 << 24) * 10)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -888,9 +888,10 @@ def main():
     h2d = 2 * (2 * n + 2) * 8
     d2h = 2 * 2 * n * 8
 
-    # dominant kernel: the streaming RK4 kernel, 200 launches per call
-    per_launch_ms = {m: statistics.median(v) / NSTEPS for m, v in method_ms.items()}
-    ops = {m: FP64_OPS[m] * 2 * n for m in method_ms}          # per launch
+    # dominant kernel: the traffic kernel that runs a call's 200 steps in one
+    # launch (the MM call is that launch; CGB adds the box conversion)
+    per_launch_ms = {m: statistics.median(v) for m, v in method_ms.items()}
+    ops = {m: FP64_OPS[m] * 2 * n * NSTEPS for m in method_ms}   # per launch
     achieved = {m: ops[m] / (per_launch_ms[m] * 1e-3) for m in method_ms}
     mm_achieved = achieved["mm"]
     peaks = load_peaks()
@@ -904,10 +905,11 @@ def main():
         "config": headline_config(n, world),
         "e2e": {"value": e2e_value, "unit": "comp-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": mm_achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9,
-                     "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS, "traffic": NCU_DRAM_BYTES_PER_CELL_LAUNCH * n,
-                     "traffic_note": "ncu dram__bytes_read+write of one MM launch on 2^24 cells, scaled to n "
-                                     "(algorithmic: 16 B x 2n)",
-                     "kernel": "stencil_traffic_rk4<MM>",
+                     "unit": "Gop/s (FP64 pipe)", "frac": mm_achieved / FP64_PEAK_OPS,
+                     "traffic": NCU_DRAM_BYTES_PER_CELL_STEP * n * NSTEPS,
+                     "traffic_note": "ncu dram__bytes_read+write of one MM launch on 2^24 cells over 10 steps, "
+                                     "scaled to n cells and 200 steps (algorithmic: 16 B x 2n per step)",
+                     "kernel": "stencil_traffic_flow<MM>",
                      "per_launch_ms": per_launch_ms, "fp64_ops_per_comp_step": FP64_OPS,
                      "cgb_frac": achieved["cgb"] / FP64_PEAK_OPS,
                      "peak_source": "148 SMs x 2 FP64 ops/clk x 2032 MHz (recipe nominal FP64 1.25 TFLOP/s)",

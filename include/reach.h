@@ -395,9 +395,10 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_BATCH_CLUSTER_FROM 11 /* batches: items of this many state components or more run on a
                                           two-block cluster; 0 = tuned (untuned batches: only items too large
                                           for one block) */
-#define REACH_OPT_KS_FLOW 12           /* KS MM / CGB: 0 auto (every step in one persistent launch for grids of
-                                         two to eight waves of 240-point tiles, 0.85e6 to 3.4e6 points), 1 one
-                                         launch per step, 2 one launch for every grid it can run */
+#define REACH_OPT_ONE_LAUNCH 12       /* KS and traffic MM / CGB: 0 auto (every step in one persistent launch:
+                                         KS grids of two to eight waves of warp tiles, 0.85e6 to 3.4e6 points;
+                                         traffic chains from 1.5 waves, 4.4e5 cells), 1 one launch per step,
+                                         2 one launch for every grid it can run */
 #define REACH_OPT_SERVE_PRIORITY 13    /* servers created afterwards: stream priority of slot requests, 0 by
                                          work (smaller first), 1 by arrival (earlier first), 2 none, 3 by work
                                          (larger first) */

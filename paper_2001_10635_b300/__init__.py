@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libreach.so")
 TRAFFIC, KS, OSC, LINEAR, HEAT3D, QUAD = 0, 1, 2, 3, 4, 5
 KINDS = {"traffic": TRAFFIC, "ks": KS, "osc": OSC, "linear": LINEAR, "heat": HEAT3D, "quad": QUAD}
 OPT_KERNEL, OPT_STEPS_PER_LAUNCH, OPT_BLOCK, OPT_BATCH_CPT, OPT_TILE, OPT_MC_SB, OPT_MC_LAYOUT = 1, 2, 3, 4, 5, 6, 7
-OPT_SERVE_QUEUE_BLOCKS, OPT_SERVE_QUEUE_N, OPT_SERVE_MAX_WIDE, OPT_BATCH_CLUSTER_FROM, OPT_KS_FLOW = 8, 9, 10, 11, 12
+OPT_SERVE_QUEUE_BLOCKS, OPT_SERVE_QUEUE_N, OPT_SERVE_MAX_WIDE, OPT_BATCH_CLUSTER_FROM, OPT_ONE_LAUNCH = 8, 9, 10, 11, 12
 OPT_SERVE_PRIORITY, OPT_SERVE_WIDE_EXCLUSIVE, OPT_SERVE_LIGHT = 13, 14, 15
 BATCH_NO_AUTOTUNE = 1
 STATUS = {0: "REACH_OK", -1: "REACH_EINVAL", -2: "REACH_ENOMEM", -3: "REACH_EADMIT",

@@ -25,7 +25,7 @@ int cuda_fail(cudaError_t e, const char *where) {
 // process-wide options; read by calls on any thread
 static std::atomic<int64_t> g_opt_kernel{0}, g_opt_steps{0}, g_opt_block{0}, g_opt_batch_cpt{0}, g_opt_tile{0},
     g_opt_mc_sb{0}, g_opt_mc_layout{0}, g_opt_serve_queue_blocks{64}, g_opt_serve_queue_n{512},
-    g_opt_serve_max_wide{0}, g_opt_batch_cluster_from{0}, g_opt_ks_flow{0},
+    g_opt_serve_max_wide{0}, g_opt_batch_cluster_from{0}, g_opt_one_launch{0},
     g_opt_serve_priority{0}, g_opt_serve_wide_exclusive{1},
     g_opt_serve_light{1 << 15};
 
@@ -191,7 +191,7 @@ int64_t opt_tile() { return g_opt_tile; }
 int64_t opt_mc_sb() { return g_opt_mc_sb; }
 int64_t opt_mc_layout() { return g_opt_mc_layout; }
 int64_t opt_batch_cluster_from() { return g_opt_batch_cluster_from; }
-int64_t opt_ks_flow() { return g_opt_ks_flow; }
+int64_t opt_one_launch() { return g_opt_one_launch; }
 
 }  // namespace reach
 
@@ -467,8 +467,16 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         if (sys->kind == REACH_TRAFFIC) {
             TrafficK p = make_traffic_k(sys->prm, wl_host, wh_host);
             if (opt_steps() == 0 && !p.sound && !(method == CGB && p.local)) S = stencil_short_steps(1, 2, n);
-            if (p.sound) rc = stencil_traffic_sound(method, p, n, dxlo, dxhi, dlo, dhi, dt, N, S, sg);
-            else rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+            if (p.sound) {
+                rc = stencil_traffic_sound(method, p, n, dxlo, dxhi, dlo, dhi, dt, N, S, sg);
+            } else if (S == 1 && traffic_flow_eligible(p, method, n, N)) {
+                void *work;
+                if ((rc = sg.scratch((size_t)traffic_flow_work_bytes(n), &work))) return rc;
+                rc = stencil_traffic_flow_run(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, sg.status, work,
+                                              sg.st);
+            } else {
+                rc = stencil_traffic(method, p, n, dxlo, dxhi, dlo, dhi, sA, sB, dt, N, S, sg.status, sg.st);
+            }
         } else {
             KsK p;
             p.a0 = sys->prm[0]; p.a1 = sys->prm[1]; p.a2 = sys->prm[2]; p.k = sys->prm[3];
@@ -550,9 +558,9 @@ extern "C" int reach_set_option(int key, int64_t value) {
         if (value < 0 || value > 16384) return REACH_EINVAL;
         g_opt_batch_cluster_from = value;
         return REACH_OK;
-    case REACH_OPT_KS_FLOW:
+    case REACH_OPT_ONE_LAUNCH:
         if (value < 0 || value > 2) return REACH_EINVAL;
-        g_opt_ks_flow = value;
+        g_opt_one_launch = value;
         return REACH_OK;
     case REACH_OPT_SERVE_PRIORITY:
         if (value < 0 || value > 3) return REACH_EINVAL;
@@ -583,7 +591,7 @@ extern "C" int64_t reach_get_option(int key) {
     case REACH_OPT_SERVE_QUEUE_N: return g_opt_serve_queue_n;
     case REACH_OPT_SERVE_MAX_WIDE: return g_opt_serve_max_wide;
     case REACH_OPT_BATCH_CLUSTER_FROM: return g_opt_batch_cluster_from;
-    case REACH_OPT_KS_FLOW: return g_opt_ks_flow;
+    case REACH_OPT_ONE_LAUNCH: return g_opt_one_launch;
     case REACH_OPT_SERVE_PRIORITY: return g_opt_serve_priority;
     case REACH_OPT_SERVE_WIDE_EXCLUSIVE: return g_opt_serve_wide_exclusive;
     case REACH_OPT_SERVE_LIGHT: return g_opt_serve_light;

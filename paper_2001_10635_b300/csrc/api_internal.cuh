@@ -49,7 +49,7 @@ int64_t opt_tile();
 int64_t opt_mc_sb();
 int64_t opt_mc_layout();
 int64_t opt_batch_cluster_from();
-int64_t opt_ks_flow();
+int64_t opt_one_launch();
 // samples per block of the on-chip MC kernel for m samples (2, 8 or 32)
 int mc_onchip_sb(int64_t m);
 
@@ -106,6 +106,12 @@ int stencil_traffic_sound(int method, const TrafficK &p, int64_t n, const double
                           double *lo, double *hi, double h, int64_t N, int S, Staging &sg);
 int heat_run(int method, const HeatK &p, int64_t n, const double *xlo, const double *xhi, double *lo,
              double *hi, double h, int64_t N, Staging &sg);
+// traffic MM / CGB with every step in one persistent launch (stencil_traffic_flow)
+bool traffic_flow_eligible(const TrafficK &p, int method, int64_t n, int64_t N);
+int64_t traffic_flow_work_bytes(int64_t n);
+int stencil_traffic_flow_run(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+                             double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int *status,
+                             void *work, cudaStream_t st);
 // KS MM / CGB with every step in one persistent launch (stencil_ks_flow):
 // whether it runs this grid, its scratch (an item counter and one word per
 // tile), and the call

@@ -60,13 +60,15 @@ struct StepArgs {
 // A lane's KC consecutive cells start at an even cell (tile starts and halos
 // are even), so with 16-byte aligned arrays a run that lies inside [0, n)
 // moves as KC/2 double2 loads or stores.
-template <int KC>
+// COH: the data was written by other warps of the same launch, so it is read
+// through L2 (the read-only path may hold a stale line)
+template <int KC, bool COH = false>
 __device__ __forceinline__ void load_run(const double *src, int64_t g0, int64_t n, bool vec, double (&v)[KC]) {
     if (vec && g0 >= 0 && g0 + KC <= n) {
         const double2 *p = reinterpret_cast<const double2 *>(src + g0);
 #pragma unroll
         for (int j = 0; j < KC / 2; ++j) {
-            const double2 t = __ldg(p + j);
+            const double2 t = COH ? __ldcg(p + j) : __ldg(p + j);
             v[2 * j] = t.x;
             v[2 * j + 1] = t.y;
         }
@@ -74,7 +76,7 @@ __device__ __forceinline__ void load_run(const double *src, int64_t g0, int64_t 
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
             const int64_t g = g0 + j;
-            v[j] = (g >= 0 && g < n) ? __ldg(src + g) : 0.0;
+            v[j] = (g >= 0 && g < n) ? (COH ? __ldcg(src + g) : __ldg(src + g)) : 0.0;
         }
     }
 }
@@ -176,7 +178,7 @@ __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double
     else traffic_growth(p, y, g0, n, k);   // the radius keeps its boundary tests
 }
 
-template <int METHOD, int HALF, bool POW2, int KC, bool IN>
+template <int METHOD, int HALF, bool POW2, int KC, bool IN, bool COH = false>
 __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &p, int64_t t, int lane,
                                              int &flags) {
     const int64_t n = a.n;
@@ -185,8 +187,8 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
     double z[KC];
     if (a.first) {
         double lo[KC], hi[KC];
-        load_run(a.inA, g0, n, a.vec, lo);
-        load_run(a.inB, g0, n, a.vec, hi);
+        load_run<KC, COH>(a.inA, g0, n, a.vec, lo);
+        load_run<KC, COH>(a.inB, g0, n, a.vec, hi);
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
             const int64_t g = g0 + j;
@@ -196,7 +198,7 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
             else z[j] = HALF ? 0.5 * (hi[j] - lo[j]) : 0.5 * (lo[j] + hi[j]);
         }
     } else {
-        load_run(HALF ? a.inB : a.inA, g0, n, a.vec, z);
+        load_run<KC, COH>(HALF ? a.inB : a.inA, g0, n, a.vec, z);
     }
     for (int s = 0; s < a.S; ++s) {
         double y[KC], acc[KC], k[KC];
@@ -259,6 +261,96 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
         }
     }
     if (flags) atomicOr(a.status, flags);
+}
+
+// ------------------------------------------------------------------ traffic, all steps in one launch
+// The traffic chain's version of stencil_ks_flow (below): for grids of a few
+// waves of warp tiles, one persistent launch runs every step, item (step,
+// half, tile) starting once tiles t - 1, t, t + 1 of the same half have
+// finished the previous step (the halves are independent: MM's two corner
+// trajectories, CGB's center and its radius under a constant C).  Per-tile
+// step counters with release / acquire ordering, state read through L2,
+// bounded waits (ST_TIMEOUT); a tile's arithmetic is stencil_traffic_rk4's at
+// one step per launch, so the box is the same bit for bit.
+struct TrafficFlowArgs {
+    StepArgs st;                   // n, W, H = 4, h, hh, h6, vec, status; ntiles
+    const double *xlo, *xhi;
+    double *bufA[2], *bufB[2];     // step s writes [(N - 1 - s) % 2]: [0] is the output (lo, hi)
+    int64_t N;
+    unsigned long long *next;      // item counter (zeroed before the launch)
+    int *ready;                    // per half and tile: steps completed (zeroed before the launch)
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu_i(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu_i(int *p, int v) {
+    asm volatile("st.release.gpu.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int METHOD, bool POW2, int KC>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_flow(TrafficFlowArgs f, TrafficK p) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t T = (uint32_t)f.st.ntiles, T2 = 2 * T;
+    const unsigned long long total = (unsigned long long)f.N * T2;   // < 2^32 (checked on the host)
+    int flags = 0;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(f.next, 1ULL);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= total) break;
+        const uint32_t s = (uint32_t)i / T2, r = (uint32_t)i - s * T2;   // 32-bit division
+        const uint32_t half = r >= T ? 1u : 0u, t = r - half * T;
+        int *rd = f.ready + half * T;
+        if (s > 0) {
+            int late = 0;
+            if (lane == 0) {
+                const unsigned long long t0 = global_ns();
+                unsigned ns = 64;
+                while ((t > 0 && ld_acquire_gpu_i(rd + t - 1) < (int)s) || ld_acquire_gpu_i(rd + t) < (int)s ||
+                       (t + 1 < T && ld_acquire_gpu_i(rd + t + 1) < (int)s)) {
+                    if (global_ns() - t0 > f.wait_ns || (*(volatile int *)f.st.status & ST_TIMEOUT)) {
+                        late = 1;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 1024) ns *= 2;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, late, 0)) {
+                if (lane == 0) atomicOr(f.st.status, ST_TIMEOUT);
+                return;
+            }
+        }
+        StepArgs a = f.st;
+        const int in = (int)((f.N - s) & 1), out = (int)((f.N - 1 - s) & 1);
+        a.inA = s == 0 ? f.xlo : f.bufA[in];
+        a.inB = s == 0 ? f.xhi : f.bufB[in];
+        a.outA = f.bufA[out];
+        a.outB = f.bufB[out];
+        a.first = s == 0;
+        a.last = (int64_t)s == f.N - 1;
+        const int64_t c0 = (int64_t)t * a.W - a.H;
+        const bool inner = c0 >= 1 && c0 + 32 * KC <= a.n - 1;
+        if (half == 0) {
+            if (inner) traffic_tile<METHOD, 0, POW2, KC, true, true>(a, p, t, lane, flags);
+            else traffic_tile<METHOD, 0, POW2, KC, false, true>(a, p, t, lane, flags);
+        } else {
+            if constexpr (METHOD == MM) {
+                if (inner) traffic_tile<METHOD, 1, POW2, KC, true, true>(a, p, t, lane, flags);
+                else traffic_tile<METHOD, 1, POW2, KC, false, true>(a, p, t, lane, flags);
+            } else {
+                traffic_tile<METHOD, 1, POW2, KC, false, true>(a, p, t, lane, flags);
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu_i(rd + t, (int)s + 1);
+    }
+    if (flags) atomicOr(f.st.status, flags);
 }
 
 // ------------------------------------------------------------------ traffic, box-evaluated C
@@ -930,6 +1022,78 @@ static int run_steps(int R, int kc, int64_t n, const double *xlo, const double *
     return REACH_OK;
 }
 
+// Whether stencil_traffic_flow runs an n-cell chain over N steps: the plain
+// (not box-evaluated, not outward-rounded) kernel with wide tiles at one step
+// per launch, N x 2 x tiles < 2^32, and by default at least 1.5 waves of the
+// 2368 resident warps (two 8-warp blocks per SM).  Measured at one launch
+// against one per step (fraction of the FP64 peak, MM / CGB): 2^19 cells
+// 0.672 / 0.735 against 0.665 / 0.679, 2^20 0.856 / 0.881 against 0.722 /
+// 0.746, 2^22 0.861 / 0.885 against 0.823 / 0.855, 2^26 0.862 / 0.885 against
+// 0.859 / 0.883; at 2^18 (0.9 waves) 0.386 / 0.451 against 0.571 / 0.625.
+bool traffic_flow_eligible(const TrafficK &p, int method, int64_t n, int64_t N) {
+    if (opt_one_launch() == 1 || N < 2 || p.sound || (method == CGB && p.local)) return false;
+    if (tile_kc(n, 4, 2) != KC_WIDE) return false;
+    const int64_t W = 32 * KC_WIDE - 8, T = (n + W - 1) / W;
+    if (T < 2 || (uint64_t)N * (uint64_t)(2 * T) >= (1ULL << 32)) return false;
+    if (opt_one_launch() == 2) return true;
+    return 2 * T >= 3 * 2368 / 2;
+}
+
+int64_t traffic_flow_work_bytes(int64_t n) {
+    const int64_t W = 32 * KC_WIDE - 8, T = (n + W - 1) / W;
+    return 16 + 8 * T;
+}
+
+int stencil_traffic_flow_run(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+                             double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int *status,
+                             void *work, cudaStream_t st) {
+    TrafficFlowArgs f;
+    memset(&f, 0, sizeof f);
+    StepArgs &a = f.st;
+    a.n = n;
+    a.H = 4;
+    a.W = 32 * KC_WIDE - 2 * a.H;
+    a.ntiles = (n + a.W - 1) / a.W;
+    a.tile0 = 0;
+    a.tcount = a.ntiles;
+    a.S = 1;
+    a.h = h;
+    a.hh = 0.5 * h;
+    a.h6 = h / 6.0;
+    a.status = status;
+    const double *ptrs[6] = {xlo, xhi, lo, hi, sA, sB};
+    a.vec = 1;
+    for (const double *ptr : ptrs)
+        if (reinterpret_cast<uintptr_t>(ptr) % 16) a.vec = 0;
+    f.xlo = xlo;
+    f.xhi = xhi;
+    f.bufA[0] = lo; f.bufB[0] = hi;
+    f.bufA[1] = sA; f.bufB[1] = sB;
+    f.N = N;
+    f.next = (unsigned long long *)work;
+    f.ready = (int *)((char *)work + 16);
+    f.wait_ns = 2000000000ULL;   // 2 s: far beyond any tile's step
+    REACH_CUDA(cudaMemsetAsync(work, 0, traffic_flow_work_bytes(n), st));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(2 * sms);   // two 8-warp blocks per SM: the kernel's launch bound
+    const bool pw = p.v_pow2 != 0;
+    const unsigned threads = 32 * WARPS_PER_BLOCK;
+    if (method == MM && pw) stencil_traffic_flow<MM, true, KC_WIDE><<<grid, threads, 0, st>>>(f, p);
+    else if (method == MM) stencil_traffic_flow<MM, false, KC_WIDE><<<grid, threads, 0, st>>>(f, p);
+    else if (pw) stencil_traffic_flow<CGB, true, KC_WIDE><<<grid, threads, 0, st>>>(f, p);
+    else stencil_traffic_flow<CGB, false, KC_WIDE><<<grid, threads, 0, st>>>(f, p);
+    REACH_LAUNCHED("stencil_traffic_flow");
+    if (method == CGB) {
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 148 * 16) blocks = 148 * 16;
+        cgb_box<<<(unsigned)blocks, 256, 0, st>>>(lo, hi, n, status);
+        REACH_LAUNCHED("cgb_box");
+    }
+    return REACH_OK;
+}
+
 int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st) {
@@ -1242,11 +1406,11 @@ int stencil_traffic_sound(int method, const TrafficK &p0, int64_t n, const doubl
 // 0.82, MM equal; from 2^22 equal; and at 2^18 (0.6 waves) 0.38 against 0.68,
 // where warps waiting for their neighbours hold most of the resident slots.
 bool ks_flow_eligible(int64_t n, int64_t N) {
-    if (opt_ks_flow() == 1 || N < 2) return false;
+    if (opt_one_launch() == 1 || N < 2) return false;
     if (tile_kc(n, 8, 1) != KC_WIDE) return false;
     const int64_t W = 32 * KC_WIDE - 16, T = (n + W - 1) / W;
     if (T < 3 || (uint64_t)N * (uint64_t)T >= (1ULL << 32)) return false;
-    if (opt_ks_flow() == 2) return true;
+    if (opt_one_launch() == 2) return true;
     return T >= 2 * 1776 && T <= 8 * 1776;
 }
 

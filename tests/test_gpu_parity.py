@@ -564,10 +564,10 @@ def test_ks_all_steps_in_one_launch(method, n, T):
     boxes = {}
     try:
         for mode in (1, 2):
-            R.reach_set_option(R.OPT_KS_FLOW, mode)
+            R.reach_set_option(R.OPT_ONE_LAUNCH, mode)
             boxes[mode] = gpu_box(method, "ks", n, lo, hi, None, None, T, dt)
     finally:
-        R.reach_set_option(R.OPT_KS_FLOW, 0)
+        R.reach_set_option(R.OPT_ONE_LAUNCH, 0)
     np.testing.assert_array_equal(boxes[1][0], boxes[2][0])
     np.testing.assert_array_equal(boxes[1][1], boxes[2][1])
     o = O.reach(method, "ks", lo, hi, t_final=T, dt=dt)
@@ -578,7 +578,7 @@ def test_ks_all_steps_in_one_launch(method, n, T):
 def test_ks_one_launch_reports_a_bad_box_and_a_nonfinite_result():
     n = 3001
     lo, hi, _, _, _, dt, _, _ = problem("ks", n, seed=62)
-    R.reach_set_option(R.OPT_KS_FLOW, 2)
+    R.reach_set_option(R.OPT_ONE_LAUNCH, 2)
     try:
         with R.System("ks", n) as s:
             with pytest.raises(R.ReachError) as e:
@@ -589,4 +589,29 @@ def test_ks_one_launch_reports_a_bad_box_and_a_nonfinite_result():
                 R.reach_mm(s, -big, big, t_final=2.0, dt=1e-3)
             assert e.value.code == -4
     finally:
-        R.reach_set_option(R.OPT_KS_FLOW, 0)
+        R.reach_set_option(R.OPT_ONE_LAUNCH, 0)
+
+
+@pytest.mark.parametrize("method", ["mm", "cgb"])
+@pytest.mark.parametrize("n,prm", [(5000, None), (30011, None), (30011, (38.0, 0.45, 0.2, 300.0))])
+def test_traffic_all_steps_in_one_launch(method, n, prm):
+    # the persistent traffic kernel gives the box of one launch per step bit
+    # for bit (both v paths: an exponent shift for v = 0.5, a product for
+    # 0.45), and the oracle's; device buffers, as the one-launch path takes
+    import torch
+    lo, hi, wlo, whi, _, dt, _, _ = problem("traffic", n, seed=63)
+    T = 0.37
+    d = [torch.tensor(v, dtype=torch.float64, device="cuda") for v in (lo, hi, wlo, whi)]
+    boxes = {}
+    try:
+        for mode in (1, 2):
+            R.reach_set_option(R.OPT_ONE_LAUNCH, mode)
+            g = gpu_box(method, "traffic", n, *d, T, dt, params=prm)
+            boxes[mode] = (g[0].cpu().numpy(), g[1].cpu().numpy())
+    finally:
+        R.reach_set_option(R.OPT_ONE_LAUNCH, 0)
+    np.testing.assert_array_equal(boxes[1][0], boxes[2][0])
+    np.testing.assert_array_equal(boxes[1][1], boxes[2][1])
+    o = O.reach(method, "traffic", lo, hi, wlo, whi, t_final=T, dt=dt, params=prm)
+    assert_close(boxes[2][0], o[0], TOL64, "lo")
+    assert_close(boxes[2][1], o[1], TOL64, "hi")
