@@ -687,6 +687,7 @@ def run_profile_case(a):
       ks_mm, ks_cgb        KS grid, n points (default 2^20), T (default 0.05)
       ks_mc32, ks_mc64     KS grid, m samples (default 256 / 32)
       traffic_mm           traffic chain, n cells (default 2^24), T (default 0.02)
+      traffic_mc32         traffic chain, n cells (default 2^20), m samples (default 256), T (default 0.09)
       traffic16_mm         traffic chain n = 16, T = 10 (on-chip kernel)
       traffic_cgbl         traffic CGB with the box-evaluated C, n cells (default 2^24), T (default 0.02)
       traffic_sound_mm     outward-rounded traffic MM, n cells (default 2^24), T (default 0.02)
@@ -717,6 +718,14 @@ def run_profile_case(a):
                 f = lambda: R.reach_mc(s, x0, x1, **kw, m=m, seed=0, precision=prec)
             f()
             f()
+    elif a.profile_case == "traffic_mc32":
+        n = a.case_n or (1 << 20)
+        wl = W.traffic_large(n, t_final=a.case_t or 0.09)
+        d = {k: to(wl[k]) for k in ("x_lo", "x_hi", "w_lo", "w_hi")}
+        with R.System("traffic", n) as s:
+            for _ in range(2):
+                R.reach_mc(s, d["x_lo"], d["x_hi"], d["w_lo"], d["w_hi"], t_final=wl["t_final"], dt=wl["dt"],
+                           m=a.case_m or 256, seed=0, precision=32)
     elif a.profile_case == "traffic_mm":
         n = a.case_n or (1 << 24)
         wl = W.traffic_large(n, t_final=a.case_t or 0.02)

@@ -36,6 +36,14 @@ constexpr int MC_Q = 8;                 // component rows per thread (on-chip)
 // integer pipe.
 __device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double tmin(double a, double b) { return kmin(a, b); }
+// minimum of three: one three-input instruction in binary32 (the traffic flux
+// min(cap, v y, w (xbar - y')) is the kernels' only use of minima)
+__device__ __forceinline__ float tmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double tmin3(double a, double b, double c) { return kmin(a, kmin(b, c)); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 
@@ -51,7 +59,7 @@ struct Plain<REACH_TRAFFIC, T> {
     // flux out of global cell g given its row value y and right neighbour yr
     static __device__ __forceinline__ T flux(const T *q, T y, T yr, int64_t g, int64_t n, T d) {
         T cong = (g == n - 1) ? q[0] : tfma(-q[2], yr, q[3]);
-        T f = tmin(q[0], tmin(q[1] * y, cong));
+        T f = tmin3(q[0], q[1] * y, cong);
         f = (g == -1) ? d : f;
         f = (g < -1 || g >= n) ? T(0) : f;
         return f;
@@ -315,14 +323,14 @@ constexpr int MC_B = 16;   // rows per warp
 // the same for a cell with a right neighbour inside the chain (0 <= g < n - 1)
 template <class T>
 __device__ __forceinline__ T tr_flux_interior(const T (&q)[4], T y, T yr) {
-    return tmin(q[0], tmin(q[1] * y, tfma(-q[2], yr, q[3])));
+    return tmin3(q[0], q[1] * y, tfma(-q[2], yr, q[3]));
 }
 
 // traffic flux out of global cell g from its value y and its right neighbour yr
 template <class T>
 __device__ __forceinline__ T tr_flux(const T (&q)[4], T y, T yr, int64_t g, int64_t n, T d) {
     T cong = (g == n - 1) ? q[0] : tfma(-q[2], yr, q[3]);
-    T f = tmin(q[0], tmin(q[1] * y, cong));
+    T f = tmin3(q[0], q[1] * y, cong);
     f = (g == -1) ? d : f;
     return (g < -1 || g >= n) ? T(0) : f;
 }
@@ -477,14 +485,17 @@ mc_stream(McStep a, const double *__restrict__ prm) {
 // instructions per sample and making every state access one 8-byte access per
 // lane.  Each sample sees the same operations in the same order as in
 // mc_stream, so the two kernels give the same box bit for bit.  Minima have no
-// packed form and stay per sample (traffic only).  A block covers 64 samples
-// and WPB * B rows; the state rows hold M samples, M a multiple of 64.
+// packed form and stay per sample (traffic only: one three-input minimum per
+// flux and sample).  A block covers 64 samples and WPB * B rows; the state
+// rows hold M samples, M a multiple of 64.
 __device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 min2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 min3_2(float2 a, float2 b, float2 c) {
+    return make_float2(tmin3(a.x, b.x, c.x), tmin3(a.y, b.y, c.y));
+}
 __device__ __forceinline__ float2 sel2(bool p, float2 a, float2 b) { return p ? a : b; }
 
 struct Q2 {
@@ -493,12 +504,12 @@ struct Q2 {
 };
 
 __device__ __forceinline__ float2 tr_flux2_interior(const Q2 &q, float2 y, float2 yr) {
-    return min2(q.cap, min2(mul2(q.v, y), fma2(q.nw, yr, q.wxbar)));
+    return min3_2(q.cap, mul2(q.v, y), fma2(q.nw, yr, q.wxbar));
 }
 
 __device__ __forceinline__ float2 tr_flux2(const Q2 &q, float2 y, float2 yr, int64_t g, int64_t n, float2 d) {
     const float2 cong = (g == n - 1) ? q.cap : fma2(q.nw, yr, q.wxbar);
-    float2 f = min2(q.cap, min2(mul2(q.v, y), cong));
+    float2 f = min3_2(q.cap, mul2(q.v, y), cong);
     f = sel2(g == -1, d, f);
     return sel2(g < -1 || g >= n, bc2(0.f), f);
 }
