@@ -180,6 +180,7 @@ TrafficK make_traffic_k(const double *prm, double wl, double wh) {
     p.sound = prm[5] != 0.0;
     // h / 6 rounded down and up (set per call by the caller when sound)
     p.c6l = p.c6u = 0.0;
+    p.one = 1.0;
     return p;
 }
 
@@ -439,6 +440,8 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         it.N = N;
         it.h = dt;
         it.status = sg.status;
+        it.one = 1.0;
+        it.nzero = -0.0;
         if (2 * n <= (int64_t)QMAX * 512) rc = onchip_launch_single(it, onchip_threads(n), sg.st);
         else rc = onchip_launch_cluster(it, sg.st);
         if (rc) return rc;

@@ -25,6 +25,7 @@ struct OnItem {
     int64_t N;
     double h;
     int *status;
+    double one, nzero;     // 1 and -0, read at run time (fadd / fmul)
 };
 
 // group barrier: a warp syncs itself, a larger group uses a named barrier
@@ -41,9 +42,9 @@ struct GroupSync {
 // the inputs (MM: w_lo, w_hi; CGB: center, half-width of the input box).
 
 __device__ __forceinline__ double tr_flux_out(const double *y, int64_t i, int64_t n, double cap,
-                                              double v, double w, double wxbar) {
+                                              double v, double w, double wxbar, double nz) {
     double cong = (i == n - 1) ? cap : fma(-w, y[i + 1], wxbar);
-    return kmin(cap, kmin(v * y[i], cong));
+    return kmin(cap, kmin(fmul(v, y[i], nz), cong));
 }
 
 template <int SYS, int METHOD>
@@ -52,6 +53,7 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                                              const double *wB, const double *prm, const double (&q)[8]) {
     const bool upper = c >= n;
     const int64_t i = upper ? c - n : c;
+    const double one = q[6], nz = q[7];   // 1 and -0 (fadd / fmul)
     if constexpr (SYS == REACH_TRAFFIC) {
         // q: cap, v, w, wxbar, box-evaluated C, xbar
         if (METHOD == CGB && upper && q[4] != 0.0) {
@@ -88,13 +90,13 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
         if (METHOD == MM || !upper) {
             const double *y = upper ? yB : yA;
             double d = upper ? wB[0] : wA[0];
-            double fin = (i == 0) ? d : tr_flux_out(y, i - 1, n, q[0], q[1], q[2], q[3]);
-            return fin - tr_flux_out(y, i, n, q[0], q[1], q[2], q[3]);
+            double fin = (i == 0) ? d : tr_flux_out(y, i - 1, n, q[0], q[1], q[2], q[3], nz);
+            return fadd(-tr_flux_out(y, i, n, q[0], q[1], q[2], q[3], nz), fin, one);
         } else {
             double left = (i > 0) ? yB[i - 1] : 0.0;
             double right = (i < n - 1) ? yB[i + 1] : 0.0;
-            double v = fma(q[1], left, q[2] * right);
-            return (i == 0) ? v + wB[0] : v;
+            double v = fma(q[1], left, fmul(q[2], right, nz));
+            return (i == 0) ? fadd(v, wB[0], one) : v;
         }
     } else if constexpr (SYS == REACH_KS) {
         // q: a0, a1, a2, k
@@ -107,24 +109,24 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             // otherwise (the stencil kernel's form)
             const double *Y = upper ? yB : yA, *O = upper ? yA : yB;   // own / other half
             const bool s1 = a1 >= 0.0, s2 = a2 >= 0.0;
-            double l1 = (s1 ? Y[im1] : O[im1]) + (s1 ? Y[ip1] : O[ip1]);
-            double l2 = (s2 ? Y[im2] : O[im2]) + (s2 ? Y[ip2] : O[ip2]);
-            const double da = Y[ip1] - O[im1], db = O[ip1] - Y[im1];
+            double l1 = fadd(s1 ? Y[im1] : O[im1], s1 ? Y[ip1] : O[ip1], one);
+            double l2 = fadd(s2 ? Y[im2] : O[im2], s2 ? Y[ip2] : O[ip2], one);
+            const double da = fadd(Y[ip1], -O[im1], one), db = fadd(O[ip1], -Y[im1], one);
             const bool qpos = (__double_as_longlong(k) ^ __double_as_longlong(Y[i])) < 0;
-            return fma(Y[i], fma(-k, qpos ? da : db, a0), fma(a1, l1, a2 * l2));
+            return fma(Y[i], fma(-k, qpos ? da : db, a0), fma(a1, l1, fmul(a2, l2, nz)));
         } else {
-            double dc = yA[ip1] - yA[im1];
-            const double t = k * yA[i];
+            double dc = fadd(yA[ip1], -yA[im1], one);
+            const double t = fmul(k, yA[i], nz);
             if (!upper) {
-                double lin = fma(a2, yA[im2] + yA[ip2], fma(a1, yA[im1] + yA[ip1], a0 * yA[i]));
+                double lin = fma(a2, fadd(yA[im2], yA[ip2], one), fma(a1, fadd(yA[im1], yA[ip1], one), fmul(a0, yA[i], nz)));
                 return fma(-t, dc, lin);
             }
             // C_ii r_i + |k| r_i (r_{i+1} + r_{i-1}) = r_i (a0 - k dc + 2 |k| sr)
-            const double ak = kabs(k), sr = yB[ip1] + yB[im1];
+            const double ak = kabs(k), sr = fadd(yB[ip1], yB[im1], one);
             const double e = fma(2.0 * ak, sr, fma(-k, dc, a0));
-            double acc = fma(kabs(a2), yB[im2] + yB[ip2], e * yB[i]);
-            acc = fma(kabs(a1 - t), yB[ip1], acc);
-            return fma(kabs(a1 + t), yB[im1], acc);
+            double acc = fma(kabs(a2), fadd(yB[im2], yB[ip2], one), fmul(e, yB[i], nz));
+            acc = fma(kabs(fadd(-t, a1, one)), yB[ip1], acc);
+            return fma(kabs(fadd(t, a1, one)), yB[im1], acc);
         }
     } else if constexpr (SYS == REACH_OSC) {
         // q: ka, kb, kc, ka + 2 kc, 3 kb, |kc|;  state [x_1..x_m | v_1..v_m]
@@ -137,8 +139,8 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
             double xl = (j > 0) ? Y[j - 1] : 0.0, xr = (j < m - 1) ? Y[j + 1] : 0.0;
             double w = upper ? wB[j] : wA[j];
             // -(ka + kb z^2) z + kc (xl - 2z + xr) + w = -(ka + 2kc + kb z^2) z + kc (xl + xr) + w
-            double t = fma(q[1], z * z, q[3]);
-            double r = fma(q[2], xl + xr, w);
+            double t = fma(q[1], fmul(z, z, nz), q[3]);
+            double r = fma(q[2], fadd(xl, xr, one), w);
             return fma(-t, z, r);
         } else {
             if (!upper) {
@@ -146,16 +148,16 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                 const int64_t j = i - m;
                 double z = yA[j];
                 double xl = (j > 0) ? yA[j - 1] : 0.0, xr = (j < m - 1) ? yA[j + 1] : 0.0;
-                double t = fma(q[1], z * z, q[3]);
-                double r = fma(q[2], xl + xr, wA[j]);
+                double t = fma(q[1], fmul(z, z, nz), q[3]);
+                double r = fma(q[2], fadd(xl, xr, one), wA[j]);
                 return fma(-t, z, r);
             }
             if (i < m) return yB[m + i];
             const int64_t j = i - m;
-            double ax = kabs(yA[j]) + yB[j];
-            double cxx = fma(q[4] * ax, ax, q[3]);   // ka + 2kc + 3 kb (|c| + r)^2
+            double ax = fadd(kabs(yA[j]), yB[j], one);
+            double cxx = fma(fmul(q[4], ax, nz), ax, q[3]);   // ka + 2kc + 3 kb (|c| + r)^2
             double rl = (j > 0) ? yB[j - 1] : 0.0, rr = (j < m - 1) ? yB[j + 1] : 0.0;
-            return fma(cxx, yB[j], fma(q[5], rl + rr, wB[j]));
+            return fma(cxx, yB[j], fma(q[5], fadd(rl, rr, one), wB[j]));
         }
     } else if constexpr (SYS == REACH_HEAT3D) {
         // q: kh, l (integer bits), open face;  both halves (MM: corners, CGB:
@@ -164,13 +166,13 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
         const int l = (int)__double_as_longlong(q[1]), pl = l * l;
         const int ii = (int)i, x = ii % l, y = (ii / l) % l, z = ii / pl;
         double s = (x > 0) ? Y[i - 1] : 0.0;
-        s += (x + 1 < l) ? Y[i + 1] : 0.0;
-        s += (y > 0) ? Y[i - l] : 0.0;
-        s += (y + 1 < l) ? Y[i + l] : 0.0;
-        s += (z > 0) ? Y[i - pl] : 0.0;
-        s += (z + 1 < l) ? Y[i + pl] : 0.0;
+        s = fadd((x + 1 < l) ? Y[i + 1] : 0.0, s, one);
+        s = fadd((y > 0) ? Y[i - l] : 0.0, s, one);
+        s = fadd((y + 1 < l) ? Y[i + l] : 0.0, s, one);
+        s = fadd((z > 0) ? Y[i - pl] : 0.0, s, one);
+        s = fadd((z + 1 < l) ? Y[i + pl] : 0.0, s, one);
         const int m = (x > 0) + (x + 1 < l) + (y > 0) + (y + 1 < l) + (z > 0 || q[2] != 0.0) + (z + 1 < l);
-        return q[0] * fma(-(double)m, Y[i], s);
+        return fmul(q[0], fma(-(double)m, Y[i], s), nz);
     } else {   // REACH_LINEAR, prm = A row-major
         const double *Arow = prm + i * n;
         double acc = 0.0;
@@ -182,19 +184,19 @@ __device__ __forceinline__ double onchip_rhs(int64_t c, int64_t n, const double 
                 double v = (j == i || __double_as_longlong(a) >= 0) ? Y[j] : O[j];
                 acc = fma(a, v, acc);
             }
-            return acc + (upper ? wB[i] : wA[i]);
+            return fadd(acc, upper ? wB[i] : wA[i], one);
         } else {
             if (!upper) {
 #pragma unroll 1
                 for (int64_t j = 0; j < n; ++j) acc = fma(__ldg(Arow + j), yA[j], acc);
-                return acc + wA[i];
+                return fadd(acc, wA[i], one);
             }
 #pragma unroll 1
             for (int64_t j = 0; j < n; ++j) {
                 double a = __ldg(Arow + j);
                 acc = fma(j == i ? a : kabs(a), yB[j], acc);
             }
-            return acc + wB[i];
+            return fadd(acc, wB[i], one);
         }
     }
 }
@@ -235,7 +237,7 @@ __device__ __forceinline__ void onchip_stage(const OnItem &it, const double *yA,
             if (STAGE == 0) { acc[s] = k; y = fma(0.5 * h, k, z[s]); }
             if (STAGE == 1) { acc[s] = fma(2.0, k, acc[s]); y = fma(0.5 * h, k, z[s]); }
             if (STAGE == 2) { acc[s] = fma(2.0, k, acc[s]); y = fma(h, k, z[s]); }
-            if (STAGE == 3) { acc[s] += k; z[s] = fma(h / 6.0, acc[s], z[s]); y = z[s]; }
+            if (STAGE == 3) { acc[s] = fadd(k, acc[s], q[6]); z[s] = fma(h / 6.0, acc[s], z[s]); y = z[s]; }
             (c < n ? oA[c] : oB[c - n]) = y;
         }
     }
@@ -255,6 +257,8 @@ __device__ void onchip_run(const OnItem &it, double *yA, double *yB, double *yA2
     const int64_t n = it.n;
     double q[8];
     load_consts<SYS>(it.prm, q);
+    q[6] = it.one;
+    q[7] = it.nzero;
     int flags = 0;
 
     // inputs: MM takes (w_lo, w_hi), CGB (center, half-width)

@@ -408,6 +408,8 @@ extern "C" int reach_queue_submit(reach_queue *q, const reach_query *qu, int64_t
     it.prm = s->dprm;
     it.N = N;
     it.h = qu->dt;
+    it.one = 1.0;
+    it.nzero = -0.0;
     it.status = nullptr;
     item.ticket = t;
     // publish: the item and the staged inputs are written before the tail

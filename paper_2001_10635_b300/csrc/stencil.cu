@@ -51,6 +51,7 @@ struct StepArgs {
     int H;                     // halo cells per side = 4 R S
     int S;                     // RK4 steps in this launch
     double h, hh, h6;          // h, h / 2 and h / 6, formed on the host (no FP64 division in the kernel)
+    double one, nzero;         // 1 and -0, read at run time (fadd / fmul in common.cuh)
     int first, last;           // convert the input box / emit the output box
     int vec;                   // every state pointer is 16-byte aligned: runs move as double2
     int *status;
@@ -92,8 +93,14 @@ __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC +
     }
 }
 
+// a + b, as a fused multiply-add (FA, see fadd) or plain: the kernel that
+// holds both traffic halves per warp sits at the register limit, where the
+// extra operand spills (19% slower fused)
+template <bool FA>
+__device__ __forceinline__ double dsum(double a, double b, double one) { return FA ? fadd(a, b, one) : a + b; }
+
 // one RK4 stage update of a lane's cells (stage is a compile-time constant)
-template <int STAGE, int KC>
+template <int STAGE, int KC, bool FA = true>
 __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], double (&acc)[KC],
                                            const double (&k)[KC], const StepArgs &a) {
     const double h = a.h, hh = a.hh, h6 = a.h6;
@@ -102,7 +109,7 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
         if (STAGE == 0) { acc[j] = k[j]; y[j] = fma(hh, k[j], z[j]); }
         if (STAGE == 1) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(hh, k[j], z[j]); }
         if (STAGE == 2) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(h, k[j], z[j]); }
-        if (STAGE == 3) { acc[j] += k[j]; z[j] = fma(h6, acc[j], z[j]); y[j] = z[j]; }
+        if (STAGE == 3) { acc[j] = dsum<FA>(k[j], acc[j], a.one); z[j] = fma(h6, acc[j], z[j]); y[j] = z[j]; }
     }
 }
 
@@ -111,7 +118,7 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
 // (min(cap, v y_g) for the last cell), the inflow of cell 0 is d, and cells
 // outside [0, n) carry no flux.  IN: every flux of the tile is between two
 // cells of the chain, so none of those cases arises and the tests are skipped.
-template <bool POW2, int KC, bool IN = false>
+template <bool POW2, int KC, bool IN = false, bool FA = true>
 __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                             int64_t n, double d, double (&k)[KC]) {
     double e[KC + 2];
@@ -150,32 +157,53 @@ __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)
     double fl = __shfl_up_sync(0xffffffffu, f[KC - 1], 1);
     if (!IN) fl = (g0 == 0) ? d : fl;
 #pragma unroll
-    for (int j = 0; j < KC; ++j) k[j] = (j == 0 ? fl : f[j - 1]) - f[j];
+    for (int j = 0; j < KC; ++j) k[j] = dsum<FA>(-f[j], j == 0 ? fl : f[j - 1], p.one);
 }
 
-// radius dynamics (C r)_g + [p]_g = v r_{g-1} + w r_{g+1} + [d] at g = 0
-template <int KC>
-__device__ __forceinline__ void traffic_growth(const TrafficK &p, const double (&r)[KC], int64_t g0,
-                                               int64_t n, double (&k)[KC]) {
-    double e[KC + 2];
-    exchange<1>(r, e);
+// CGB radius of the traffic chain, r' = C r + [p] with the constant C of
+// reading R3 (v to the left neighbour, w to the right, the input half-width
+// into cell 0): a linear system with a constant input, for which one classic
+// RK4 step equals, in exact arithmetic, the nested form
+//   y1 = r + (h/4) f(r), y2 = r + (h/3) f(y1), y3 = r + (h/2) f(y2), r+ = r + h f(y3)
+// (both are r + h f + h^2/2 C f + h^3/6 C^2 f + h^4/24 C^3 f with f = f(r)).
+// Each stage is two fused multiply-adds per cell, 8 per step against 15 for
+// the stage form, and needs no accumulator.  The input enters cell 0 in the
+// place of its missing left neighbour (coefficient c_s instead of c_s v).
+// Cells outside the chain take part in the shuffles only: cell 0 never reads
+// its left neighbour and cell n - 1 never its right one, so their values do
+// not enter the chain.  IN: every cell of the tile lies in [1, n - 2].
+template <int KC, bool IN>
+__device__ __forceinline__ void traffic_radius_step(const TrafficK &p, double (&z)[KC], int64_t g0, int64_t n) {
+    double y[KC];
 #pragma unroll
-    for (int j = 0; j < KC; ++j) {
-        const int64_t g = g0 + j;
-        double left = (g > 0) ? e[j] : 0.0;
-        double right = (g < n - 1) ? e[2 + j] : 0.0;
-        double add = (g == 0) ? p.d_r : 0.0;
-        k[j] = fma(p.v, left, fma(p.w, right, add));
+    for (int j = 0; j < KC; ++j) y[j] = z[j];
+#pragma unroll
+    for (int stage = 0; stage < 4; ++stage) {
+        double e[KC + 2];
+        exchange<1>(y, e);
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            double cl = p.rv[stage], left = e[j], right = e[j + 2];
+            if (!IN) {
+                const int64_t g = g0 + j;
+                cl = (g == 0) ? p.rc[stage] : cl;
+                left = (g == 0) ? p.d_r : (g > 0 ? left : 0.0);
+                right = (g < n - 1) ? right : 0.0;
+            }
+            y[j] = fma(cl, left, fma(p.rw[stage], right, z[j]));
+        }
     }
+#pragma unroll
+    for (int j = 0; j < KC; ++j) z[j] = y[j];
 }
 
-// one traffic half per warp: HALF 0 = x / c, HALF 1 = xh / r
+// one traffic half per warp: HALF 0 = x / c, HALF 1 = xh (the CGB radius r
+// takes traffic_radius_step instead)
 template <int METHOD, int HALF, bool POW2, int KC, bool IN>
 __device__ __forceinline__ void traffic_rhs_half(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                                  int64_t n, double (&k)[KC]) {
     if (METHOD == MM) traffic_rhs<POW2, KC, IN>(p, y, g0, n, HALF ? p.d_hi : p.d_lo, k);
-    else if (HALF == 0) traffic_rhs<POW2, KC, IN>(p, y, g0, n, p.d_c, k);
-    else traffic_growth(p, y, g0, n, k);   // the radius keeps its boundary tests
+    else traffic_rhs<POW2, KC, IN>(p, y, g0, n, p.d_c, k);
 }
 
 template <int METHOD, int HALF, bool POW2, int KC, bool IN, bool COH = false>
@@ -201,17 +229,21 @@ __device__ __forceinline__ void traffic_tile(const StepArgs &a, const TrafficK &
         load_run<KC, COH>(HALF ? a.inB : a.inA, g0, n, a.vec, z);
     }
     for (int s = 0; s < a.S; ++s) {
-        double y[KC], acc[KC], k[KC];
+        if constexpr (METHOD == CGB && HALF == 1) {
+            traffic_radius_step<KC, IN>(p, z, g0, n);
+        } else {
+            double y[KC], acc[KC], k[KC];
 #pragma unroll
-        for (int j = 0; j < KC; ++j) y[j] = z[j];
-        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
-        rk4_update<0>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
-        rk4_update<1>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
-        rk4_update<2>(z, y, acc, k, a);
-        traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
-        rk4_update<3>(z, y, acc, k, a);
+            for (int j = 0; j < KC; ++j) y[j] = z[j];
+            traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
+            rk4_update<0>(z, y, acc, k, a);
+            traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
+            rk4_update<1>(z, y, acc, k, a);
+            traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
+            rk4_update<2>(z, y, acc, k, a);
+            traffic_rhs_half<METHOD, HALF, POW2, KC, IN>(p, y, g0, n, k);
+            rk4_update<3>(z, y, acc, k, a);
+        }
     }
     double *out = HALF ? a.outB : a.outA;
     if (a.last && METHOD == MM) {
@@ -245,19 +277,15 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_rk4(S
         const int64_t tile = a.tile0 + (t < cnt ? t : t - cnt);
         // Inside the chain (every flux of the tile, cells own0 - H - 1 ..
         // own0 - H + 32 KC - 1, between two of its cells) the boundary tests are
-        // skipped: MM 5% faster.  The CGB radius keeps them (2% slower without).
+        // skipped: MM 5% faster.
         const int64_t c0 = tile * a.W - a.H;
         const bool in = c0 >= 1 && c0 + 32 * KC <= a.n - 1;
         if (t < cnt) {
             if (in) traffic_tile<METHOD, 0, POW2, KC, true>(a, p, tile, lane, flags);
             else traffic_tile<METHOD, 0, POW2, KC, false>(a, p, tile, lane, flags);
         } else {
-            if constexpr (METHOD == MM) {
-                if (in) traffic_tile<METHOD, 1, POW2, KC, true>(a, p, tile, lane, flags);
-                else traffic_tile<METHOD, 1, POW2, KC, false>(a, p, tile, lane, flags);
-            } else {
-                traffic_tile<METHOD, 1, POW2, KC, false>(a, p, tile, lane, flags);
-            }
+            if (in) traffic_tile<METHOD, 1, POW2, KC, true>(a, p, tile, lane, flags);
+            else traffic_tile<METHOD, 1, POW2, KC, false>(a, p, tile, lane, flags);
         }
     }
     if (flags) atomicOr(a.status, flags);
@@ -339,12 +367,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_flow(
             if (inner) traffic_tile<METHOD, 0, POW2, KC, true, true>(a, p, t, lane, flags);
             else traffic_tile<METHOD, 0, POW2, KC, false, true>(a, p, t, lane, flags);
         } else {
-            if constexpr (METHOD == MM) {
-                if (inner) traffic_tile<METHOD, 1, POW2, KC, true, true>(a, p, t, lane, flags);
-                else traffic_tile<METHOD, 1, POW2, KC, false, true>(a, p, t, lane, flags);
-            } else {
-                traffic_tile<METHOD, 1, POW2, KC, false, true>(a, p, t, lane, flags);
-            }
+            if (inner) traffic_tile<METHOD, 1, POW2, KC, true, true>(a, p, t, lane, flags);
+            else traffic_tile<METHOD, 1, POW2, KC, false, true>(a, p, t, lane, flags);
         }
         __threadfence();
         __syncwarp();
@@ -436,22 +460,22 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4
             double yc[KC], yr[KC], ac[KC], ar[KC], kc[KC], kr[KC];
 #pragma unroll
             for (int j = 0; j < KC; ++j) { yc[j] = zc[j]; yr[j] = zr[j]; }
-            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<0>(zc, yc, ac, kc, a);
-            rk4_update<0>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<0, KC, false>(zc, yc, ac, kc, a);
+            rk4_update<0, KC, false>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<1>(zc, yc, ac, kc, a);
-            rk4_update<1>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<1, KC, false>(zc, yc, ac, kc, a);
+            rk4_update<1, KC, false>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<2>(zc, yc, ac, kc, a);
-            rk4_update<2>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<2, KC, false>(zc, yc, ac, kc, a);
+            rk4_update<2, KC, false>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<3>(zc, yc, ac, kc, a);
-            rk4_update<3>(zr, yr, ar, kr, a);
+            rk4_update<3, KC, false>(zc, yc, ac, kc, a);
+            rk4_update<3, KC, false>(zr, yr, ar, kr, a);
         }
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
@@ -670,21 +694,21 @@ __device__ __forceinline__ void ks_mm_rhs(const KsK &p, const double (&x)[KC], c
     exchange<2>(x, X);
     exchange<2>(xh, XH);
     const bool s1 = p.a1 >= 0.0, s2 = p.a2 >= 0.0;
-    const double nk = -p.k;
+    const double nk = -p.k, one = p.one, nz = p.nzero;
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int c = j + 2;
-        double l1 = (s1 ? X[c - 1] : XH[c - 1]) + (s1 ? X[c + 1] : XH[c + 1]);
-        double l2 = (s2 ? X[c - 2] : XH[c - 2]) + (s2 ? X[c + 2] : XH[c + 2]);
-        double u1 = (s1 ? XH[c - 1] : X[c - 1]) + (s1 ? XH[c + 1] : X[c + 1]);
-        double u2 = (s2 ? XH[c - 2] : X[c - 2]) + (s2 ? XH[c + 2] : X[c + 2]);
-        const double dL = X[c + 1] - XH[c - 1];   // 2dx * u_x at (x_{i+1}, xh_{i-1})
-        const double dH = XH[c + 1] - X[c - 1];   // 2dx * u_x at (xh_{i+1}, x_{i-1})
+        double l1 = fadd(s1 ? X[c - 1] : XH[c - 1], s1 ? X[c + 1] : XH[c + 1], one);
+        double l2 = fadd(s2 ? X[c - 2] : XH[c - 2], s2 ? X[c + 2] : XH[c + 2], one);
+        double u1 = fadd(s1 ? XH[c - 1] : X[c - 1], s1 ? XH[c + 1] : X[c + 1], one);
+        double u2 = fadd(s2 ? XH[c - 2] : X[c - 2], s2 ? XH[c + 2] : X[c + 2], one);
+        const double dL = fadd(X[c + 1], -XH[c - 1], one);   // 2dx * u_x at (x_{i+1}, xh_{i-1})
+        const double dH = fadd(XH[c + 1], -X[c - 1], one);   // 2dx * u_x at (xh_{i+1}, x_{i-1})
         // -k u >= 0 exactly when the signs of k and u differ
         const double dl = sign_differs(p.k, X[c]) ? dL : dH;
         const double dh = sign_differs(p.k, XH[c]) ? dH : dL;
-        kx[j] = fma(X[c], fma(nk, dl, p.a0), fma(p.a1, l1, p.a2 * l2));
-        kxh[j] = fma(XH[c], fma(nk, dh, p.a0), fma(p.a1, u1, p.a2 * u2));
+        kx[j] = fma(X[c], fma(nk, dl, p.a0), fma(p.a1, l1, fmul(p.a2, l2, nz)));
+        kxh[j] = fma(XH[c], fma(nk, dh, p.a0), fma(p.a1, u1, fmul(p.a2, u2, nz)));
     }
 }
 
@@ -698,20 +722,21 @@ __device__ __forceinline__ void ks_cgb_rhs(const KsK &p, const double (&cc)[KC],
     double C[KC + 4], Rr[KC + 4];
     exchange<2>(cc, C);
     exchange<2>(rr, Rr);
-    const double aa2 = kabs(p.a2), ak = kabs(p.k), nk = -p.k;
+    const double aa2 = kabs(p.a2), ak = kabs(p.k), nk = -p.k, one = p.one, nz = p.nzero;
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int c = j + 2;
-        const double dc = C[c + 1] - C[c - 1];
-        const double t = p.k * C[c];
-        const double lin = fma(p.a2, C[c - 2] + C[c + 2], fma(p.a1, C[c - 1] + C[c + 1], p.a0 * C[c]));
+        const double dc = fadd(C[c + 1], -C[c - 1], one);
+        const double t = fmul(p.k, C[c], nz);
+        const double lin = fma(p.a2, fadd(C[c - 2], C[c + 2], one),
+                               fma(p.a1, fadd(C[c - 1], C[c + 1], one), fmul(p.a0, C[c], nz)));
         kc[j] = fma(-t, dc, lin);
         // C_ii r_i + |k| r_i (r_{i+1} + r_{i-1}) = r_i (a0 - k dc + 2 |k| sr)
-        const double sr = Rr[c + 1] + Rr[c - 1];
+        const double sr = fadd(Rr[c + 1], Rr[c - 1], one);
         const double e = fma(2.0 * ak, sr, fma(nk, dc, p.a0));
-        double acc = fma(aa2, Rr[c - 2] + Rr[c + 2], e * Rr[c]);
-        acc = fma(kabs(p.a1 - t), Rr[c + 1], acc);
-        kr[j] = fma(kabs(p.a1 + t), Rr[c - 1], acc);
+        double acc = fma(aa2, fadd(Rr[c - 2], Rr[c + 2], one), fmul(e, Rr[c], nz));
+        acc = fma(kabs(fadd(-t, p.a1, one)), Rr[c + 1], acc);
+        kr[j] = fma(kabs(fadd(t, p.a1, one)), Rr[c - 1], acc);
     }
 }
 
@@ -1004,6 +1029,8 @@ static int run_steps(int R, int kc, int64_t n, const double *xlo, const double *
         a.h = h;
         a.hh = 0.5 * h;
         a.h6 = h / 6.0;
+        a.one = 1.0;
+        a.nzero = -0.0;
         a.first = (q == 0);
         a.last = (q == L - 1);
         a.inA = (q == 0) ? xlo : bufA[(L - q) % 2];
@@ -1044,9 +1071,21 @@ int64_t traffic_flow_work_bytes(int64_t n) {
     return 16 + 8 * T;
 }
 
-int stencil_traffic_flow_run(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+// the per-call coefficients of traffic_radius_step for step h
+static TrafficK with_radius_coeffs(TrafficK p, double h) {
+    const double c[4] = {0.25 * h, h / 3.0, 0.5 * h, h};
+    for (int s = 0; s < 4; ++s) {
+        p.rc[s] = c[s];
+        p.rv[s] = c[s] * p.v;
+        p.rw[s] = c[s] * p.w;
+    }
+    return p;
+}
+
+int stencil_traffic_flow_run(int method, const TrafficK &p0, int64_t n, const double *xlo, const double *xhi,
                              double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int *status,
                              void *work, cudaStream_t st) {
+    const TrafficK p = with_radius_coeffs(p0, h);
     TrafficFlowArgs f;
     memset(&f, 0, sizeof f);
     StepArgs &a = f.st;
@@ -1060,6 +1099,8 @@ int stencil_traffic_flow_run(int method, const TrafficK &p, int64_t n, const dou
     a.h = h;
     a.hh = 0.5 * h;
     a.h6 = h / 6.0;
+    a.one = 1.0;
+    a.nzero = -0.0;
     a.status = status;
     const double *ptrs[6] = {xlo, xhi, lo, hi, sA, sB};
     a.vec = 1;
@@ -1094,9 +1135,10 @@ int stencil_traffic_flow_run(int method, const TrafficK &p, int64_t n, const dou
     return REACH_OK;
 }
 
-int stencil_traffic(int method, const TrafficK &p, int64_t n, const double *xlo, const double *xhi,
+int stencil_traffic(int method, const TrafficK &p0, int64_t n, const double *xlo, const double *xhi,
                     double *lo, double *hi, double *sA, double *sB, double h, int64_t N, int S,
                     int *status, cudaStream_t st) {
+    const TrafficK p = with_radius_coeffs(p0, h);
     const bool local = method == CGB && p.local;
     // the box-evaluated C kernel holds both halves per warp: wide tiles only
     const int kc = local ? KC_WIDE : tile_kc(n, 4 * S, 2);
@@ -1141,8 +1183,9 @@ struct CopyLane {
 };
 }  // namespace
 
-int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const double *hxlo, const double *hxhi,
+int stencil_traffic_overlap(int method, const TrafficK &p0, int64_t n, const double *hxlo, const double *hxhi,
                             double *hlo, double *hhi, double h, int64_t N, int S, Staging &sg) {
+    const TrafficK p = with_radius_coeffs(p0, h);
     constexpr int C = OVERLAP_CHUNKS;
     double *buf;
     int rc;
@@ -1189,6 +1232,8 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         a.h = h;
         a.hh = 0.5 * h;
         a.h6 = h / 6.0;
+        a.one = 1.0;
+        a.nzero = -0.0;
         a.status = sg.status;
         a.vec = (reinterpret_cast<uintptr_t>(buf) % 16) == 0;   // one allocation, even strides
         double *bufA[2] = {dlo, sA}, *bufB[2] = {dhi, sB};
@@ -1270,6 +1315,8 @@ int stencil_traffic_overlap(int method, const TrafficK &p, int64_t n, const doub
         a.h = h;
         a.hh = 0.5 * h;
         a.h6 = h / 6.0;
+        a.one = 1.0;
+        a.nzero = -0.0;
         a.first = (q == 0);
         a.last = (q == L - 1);
         a.inA = (q == 0) ? dxlo : bufA[(L - q) % 2];
@@ -1430,6 +1477,8 @@ int stencil_ks_flow_run(int method, const KsK &p, int64_t n, const double *xlo, 
     a.h = h;
     a.hh = 0.5 * h;
     a.h6 = h / 6.0;
+    a.one = 1.0;
+    a.nzero = -0.0;
     a.status = status;
     f.xlo = xlo;
     f.xhi = xhi;
