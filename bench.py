@@ -57,7 +57,7 @@ CPU_SAMPLE_CELLS = 1 << 20
 # DRAM bytes (read + write) per cell and RK4 step of stencil_traffic_flow<MM>,
 # from the ncu capture of one launch on 2^24 cells over 10 steps; the traffic
 # is proportional to cells x steps, so it is scaled to the run's n and steps
-NCU_DRAM_BYTES_PER_CELL_STEP = (2.827737e9 + 2.646888e9) / ((1 << 24) * 10)
+NCU_DRAM_BYTES_PER_CELL_STEP = (2.825961e9 + 2.646587e9) / ((1 << 24) * 10)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
