@@ -324,11 +324,13 @@ REACH_API int reach_queue_destroy(reach_queue *q);
        box back, so copies and kernels of different requests overlap.
      - By default a wide request (2^20 or more state components per step: it
        fills the GPU alone) computes alone: it starts computing when no other
-       slot request computes, and no other starts beside it except light
-       ones (REACH_OPT_SERVE_LIGHT components per step or fewer), which take
-       the least stream priority so that their blocks only fill SMs the wide
-       request leaves free; waiting requests start computing in arrival
-       order.  Sharing the GPU with a wide request would finish both late
+       slot request computes (light ones included), and no other starts
+       beside it except light ones (REACH_OPT_SERVE_LIGHT components per step
+       or fewer) that arrive while it computes and no other wide request
+       waits; they take the least stream priority so that their blocks only
+       fill SMs the wide request leaves free.  Waiting requests start
+       computing in arrival order, and no request waits for one that arrived
+       after it.  Sharing the GPU with a wide request would finish both late
        (REACH_OPT_SERVE_WIDE_EXCLUSIVE = 0 lets them share).  Otherwise a
        stream's priority falls with the request's work (state components per
        step x steps; greatest below 2^30, one level lower per factor 4

@@ -26,11 +26,16 @@
 //   gate       a wide request (2^20 or more state components per step) fills
 //              the GPU alone; by default it computes alone, since sharing the
 //              GPU finishes both requests late: it passes the compute gate
-//              when no other slot request computes, and none passes beside it
-//              except light ones (REACH_OPT_SERVE_LIGHT components per step or
-//              fewer, on the least stream priority, so their blocks only fill
-//              SMs the wide request leaves free); waiters pass in arrival
-//              order.  REACH_OPT_SERVE_MAX_WIDE can also cap wide requests at
+//              when no other slot request computes (light ones included), and
+//              none passes beside it except light ones (REACH_OPT_SERVE_LIGHT
+//              components per step or fewer, on the least stream priority, so
+//              their blocks only fill SMs the wide request leaves free) that
+//              reach the gate while it computes and no other wide request
+//              waits; waiters pass in arrival order.  So no request waits for
+//              one that reached the gate after it: a light request that
+//              backfills is never passed by a later wide one, and one that
+//              arrives while a wide request waits queues behind it.
+//              REACH_OPT_SERVE_MAX_WIDE can also cap wide requests at
 //              admission.
 //   priority   otherwise a slot request runs on a stream whose priority falls
 //              with its work (components per step x steps: the greatest below
@@ -103,7 +108,8 @@ struct reach_server {
     int max_wide = 0;               // wide requests at once (0: no limit)
     bool wide_exclusive = true;     // a wide request computes with no other slot request
     int64_t light_components = 0;   // requests of at most this many components per step backfill
-    int computing = 0, wide_computing = 0, light_computing = 0;   // slot requests past the compute gate
+    int computing = 0, wide_computing = 0;   // slot requests past the compute gate
+    int wide_waiting = 0;           // wide requests waiting at the compute gate
     std::set<int64_t> gate;         // tickets of slot requests staged and waiting to compute
     std::condition_variable gate_cv;
 };
@@ -333,21 +339,24 @@ static void worker_main(reach_server *s) {
         lk.lock();
         if (!rc) {
             // the compute gate: with exclusive wide requests a wide one computes
-            // alone and nothing computes beside it; waiters pass in arrival order
-            const bool backfill = s->wide_exclusive && j->light;
+            // alone (after everything that passed before it, light requests
+            // included), and only light requests that arrive while it computes
+            // pass beside it; waiters pass in arrival order
+            const bool backfill = s->wide_exclusive && j->light && s->wide_computing > 0 && s->wide_waiting == 0;
             if (!backfill) {
                 s->gate.insert(j->ticket);
+                if (j->wide) s->wide_waiting++;
                 s->gate_cv.wait(lk, [&] {
                     if (!s->wide_exclusive) return true;
                     if (*s->gate.begin() != j->ticket) return false;
-                    return j->wide ? s->computing - s->light_computing == 0 : s->wide_computing == 0;
+                    return j->wide ? s->computing == 0 : s->wide_computing == 0;
                 });
+                if (j->wide) s->wide_waiting--;
                 s->gate.erase(j->ticket);
             } else {
                 // a light request passes the gate at the least priority: its
                 // blocks take only SMs that the wide request's blocks leave free
                 js = st[s->nlevels - 1];
-                s->light_computing++;
             }
             if (s->wide_exclusive && j->wide) js = st[0];
             s->computing++;
@@ -358,7 +367,6 @@ static void worker_main(reach_server *s) {
             lk.lock();
             s->computing--;
             if (j->wide) s->wide_computing--;
-            if (backfill) s->light_computing--;
             s->gate_cv.notify_all();
             rc = j->status;
         }
