@@ -381,12 +381,15 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_MC_SB 6            /* on-chip MC: samples per block, 0 = auto (32 from 4736 samples, 8 from 1184,
                                         else 2), or 2 / 8 / 32 */
 #define REACH_OPT_MC_LAYOUT 7         /* streaming binary32 MC: 0 auto (two samples per lane, packed FP32
-                                        arithmetic, measured block shape), 1 one sample per lane; 2..6 block
-                                        shapes of the two-sample kernel (warps x rows x blocks per SM:
-                                        16x16x1, 32x8x1, 8x16x2, 16x8x2, and 16x16x1 persistent with the
-                                        next tiles copied ahead by the TMA engine); binary64: 0 auto (KS
-                                        one 16-warp block per SM, traffic two 8-warp blocks), 7 forces the
-                                        16-warp block, other values the 8-warp ones */
+                                        arithmetic, along the rows of a sample pair with 12 rows per lane:
+                                        as 9), 1 one sample per lane; 2..6 block shapes of the two-sample
+                                        kernel on sample rows (warps x rows x blocks per SM: 16x16x1,
+                                        32x8x1, 8x16x2, 16x8x2, and 16x16x1 persistent with the next tiles
+                                        copied ahead by the TMA engine); 8 / 9 / 10 along sample-pair
+                                        rows with 8 / 12 / 16 rows per lane; all give the same box bit for
+                                        bit.  Binary64: 0 auto (KS one 16-warp block per SM, traffic two
+                                        8-warp blocks), 7 forces the 16-warp block, other values the
+                                        8-warp ones */
 #define REACH_OPT_SERVE_QUEUE_BLOCKS 8 /* servers created afterwards: blocks of their device work queue, 0 = no
                                          queue (default 64) */
 #define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: MM / CGB requests up to this many cells

@@ -542,7 +542,7 @@ extern "C" int reach_set_option(int key, int64_t value) {
         g_opt_mc_sb = value;
         return REACH_OK;
     case REACH_OPT_MC_LAYOUT:
-        if (value < 0 || value > 7) return REACH_EINVAL;
+        if (value < 0 || value > 10) return REACH_EINVAL;
         g_opt_mc_layout = value;
         return REACH_OK;
     case REACH_OPT_SERVE_QUEUE_BLOCKS:

@@ -889,6 +889,194 @@ __global__ void __launch_bounds__(32 * WPB, 1) mc_stream2p(McStep a, unsigned lo
     if (flags && (threadIdx.x & 31) == 0) atomicOr(a.status, flags);
 }
 
+// ------------------------------------------------------------------ streaming, sample pairs along the rows
+// State layout: sample pair p (samples 2p and 2p + 1) is a contiguous run of
+// n float2 rows, x[p ns + i] (ns = n rounded up to even, so every run starts
+// on 16 bytes).  A warp owns 32 KC consecutive rows of one pair, KC per lane
+// in registers: stencil neighbours come from the adjacent lanes by shuffles,
+// so a warp never waits for another one (no shared memory, no block barrier,
+// against one barrier per stage in mc_stream2), and a warp tile longer than a
+// lane-per-sample block keeps the recomputed halo of 4 R S rows per side a
+// smaller share.  Persistent warps take (pair, tile) items; the first launch
+// draws the samples, and the per-row minimum and maximum over the samples is
+// one coalesced pass over the final state (mc_rows_reduce).  Each sample sees
+// the operations of mc_stream2 in the same order, so the box is the same bit
+// for bit.
+struct RowStep {
+    int64_t n, ns;            // rows, row stride of a pair's run (even)
+    int64_t m;                // samples (drawn beyond m up to 2P, never reduced)
+    unsigned P;               // sample pairs
+    unsigned ntile;           // ceil(n / W)
+    int W, H;                 // owned rows per warp tile, halo rows per side (4 R S)
+    int S;                    // RK4 steps in this launch (0: only draw the samples)
+    float hf[3];              // h, h/2, h/6 rounded to binary32 on the host
+    float qf[4];              // system constants as mc_stream2 takes them
+    uint64_t seed;
+    const double *xlo, *xhi;  // first launch: the initial box
+    double dlo, dhi;          // traffic inflow box
+    const float2 *in;         // state of the previous launch
+    float2 *out;
+    int first;
+    int *status;
+};
+
+template <int SYS, int KC>
+__global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t items = a.ntile * a.P;   // < 2^32 (checked on the host)
+    const int64_t n = a.n;
+    Q2 q;
+    q.cap = bc2(a.qf[0]); q.v = bc2(a.qf[1]); q.nw = bc2(-a.qf[2]); q.wxbar = bc2(a.qf[3]);
+    q.a0 = bc2(a.qf[0]); q.a1 = bc2(a.qf[1]); q.a2 = bc2(a.qf[2]); q.nk = bc2(-a.qf[3]);
+    const float2 h = bc2(a.hf[0]), hh = bc2(a.hf[1]), h6 = bc2(a.hf[2]), two = bc2(2.f);
+    int flags = 0;
+    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const uint32_t p = it / a.ntile, t = it - p * a.ntile;   // 32-bit division
+        const int64_t own0 = (int64_t)t * a.W;
+        const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
+        const int64_t base = (int64_t)((uint64_t)p * (uint64_t)a.ns);
+        const uint32_t j0 = 2 * p;
+        float2 d = bc2(0.f);
+        if (SYS == REACH_TRAFFIC) {
+            d.x = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, j0, 0u, 1u));
+            d.y = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, j0 + 1, 0u, 1u));
+        }
+        float2 z[KC];
+        const bool whole = g0 >= 0 && g0 + KC <= n;   // the lane's run lies inside [0, n)
+        if (a.first) {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                int64_t g = g0 + r;
+                bool in = true;
+                if (SYS == REACH_KS) g = wrap_index(g, n);
+                else in = g >= 0 && g < n;
+                float2 v = bc2(0.f);
+                if (in) {
+                    const double lo = a.xlo[g], hi = a.xhi[g];
+                    const bool owned = p == 0 && g0 + r >= own0 && g0 + r < own0 + a.W;
+                    if (owned && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+                    v.x = (float)box_sample(lo, hi, philox_uniform(a.seed, j0, (uint32_t)g, 0u));
+                    v.y = (float)box_sample(lo, hi, philox_uniform(a.seed, j0 + 1, (uint32_t)g, 0u));
+                }
+                z[r] = v;
+            }
+        } else if (whole) {
+            const float4 *src = reinterpret_cast<const float4 *>(a.in + base + g0);   // g0 and base even
+#pragma unroll
+            for (int r = 0; r < KC / 2; ++r) {
+                const float4 v = __ldcs(src + r);
+                z[2 * r] = make_float2(v.x, v.y);
+                z[2 * r + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                int64_t g = g0 + r;
+                bool in = true;
+                if (SYS == REACH_KS) g = wrap_index(g, n);
+                else in = g >= 0 && g < n;
+                z[r] = in ? __ldcs(a.in + base + g) : bc2(0.f);
+            }
+        }
+        // every flux of the lane's run between two cells of the chain; the
+        // choice is warp-uniform, since the stages shuffle across the warp
+        const bool interior = SYS != REACH_KS && __all_sync(0xffffffffu, g0 >= 1 && g0 + KC <= n - 1);
+        auto steps = [&](auto in_tag) {
+            constexpr bool IN = decltype(in_tag)::value;
+            (void)IN;
+            for (int s = 0; s < a.S; ++s) {
+                float2 e[KC + 2 * R], acc[KC];
+#pragma unroll
+                for (int r = 0; r < KC; ++r) e[R + r] = z[r];
+#pragma unroll
+                for (int stage = 0; stage < 4; ++stage) {
+                    // the R rows on each side from the neighbouring lanes (the
+                    // warp's outermost halo rows take garbage, which stays in
+                    // the halo)
+#pragma unroll
+                    for (int q2 = 0; q2 < R; ++q2) {
+                        const float2 lo_ = e[KC + q2], hi_ = e[R + q2];
+                        e[q2].x = __shfl_up_sync(0xffffffffu, lo_.x, 1);
+                        e[q2].y = __shfl_up_sync(0xffffffffu, lo_.y, 1);
+                        e[R + KC + q2].x = __shfl_down_sync(0xffffffffu, hi_.x, 1);
+                        e[R + KC + q2].y = __shfl_down_sync(0xffffffffu, hi_.y, 1);
+                    }
+                    float2 kring[R + 1];
+                    float2 fprev = bc2(0.f);
+                    (void)fprev;
+                    if constexpr (SYS != REACH_KS)
+                        fprev = IN ? tr_flux2_interior(q, e[0], e[1]) : tr_flux2(q, e[0], e[1], g0 - 1, n, d);
+#pragma unroll
+                    for (int r = 0; r < KC + R; ++r) {
+                        if (r < KC) {
+                            float2 kr;
+                            if constexpr (SYS == REACH_KS) {
+                                const float2 um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                                kr = fma2(u, fma2(q.nk, sub2(up1, um1), q.a0),
+                                          fma2(q.a1, add2(um1, up1), mul2(q.a2, add2(um2, up2))));
+                            } else {
+                                const float2 fout = IN ? tr_flux2_interior(q, e[r + 1], e[r + 2])
+                                                       : tr_flux2(q, e[r + 1], e[r + 2], g0 + r, n, d);
+                                kr = sub2(fprev, fout);
+                                fprev = fout;
+                            }
+                            kring[r % (R + 1)] = kr;
+                        }
+                        if (r >= R) {
+                            const int u = r - R;
+                            const float2 kk = kring[u % (R + 1)];
+                            if (stage == 0) { acc[u] = kk; e[R + u] = fma2(hh, kk, z[u]); }
+                            if (stage == 1) { acc[u] = fma2(two, kk, acc[u]); e[R + u] = fma2(hh, kk, z[u]); }
+                            if (stage == 2) { acc[u] = fma2(two, kk, acc[u]); e[R + u] = fma2(h, kk, z[u]); }
+                            if (stage == 3) { acc[u] = add2(acc[u], kk); z[u] = fma2(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                        }
+                    }
+                }
+            }
+        };
+        if (interior) steps(std::true_type{});
+        else steps(std::false_type{});
+        // the owned rows of the lane's run
+        if (whole && g0 >= own0 && g0 + KC <= own0 + a.W) {
+            float4 *dst = reinterpret_cast<float4 *>(a.out + base + g0);
+#pragma unroll
+            for (int r = 0; r < KC / 2; ++r) __stcs(dst + r, make_float4(z[2 * r].x, z[2 * r].y, z[2 * r + 1].x, z[2 * r + 1].y));
+        } else {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                const int64_t g = g0 + r;
+                if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(a.out + base + g, z[r]);
+            }
+        }
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// per-row minimum and maximum over the valid samples of the pair-row state,
+// written as binary64 (each bound is one sample's value, so the order of the
+// scan does not matter); a non-finite sample sets ST_NONFINITE
+__global__ void mc_rows_reduce(const float2 *x, int64_t ns, int64_t n, unsigned P, int64_t m, double *lo,
+                               double *hi, int *status) {
+    int flags = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float a = INFINITY, b = -INFINITY;
+        bool bad = false;
+        const float2 *col = x + i;
+        for (unsigned p = 0; p < P; ++p) {
+            const float2 v = __ldcs(col + (int64_t)((uint64_t)p * (uint64_t)ns));
+            const int64_t j = 2 * (int64_t)p;
+            if (j < m) { a = fminf(a, v.x); b = fmaxf(b, v.x); bad |= !isfinite(v.x); }
+            if (j + 1 < m) { a = fminf(a, v.y); b = fmaxf(b, v.y); bad |= !isfinite(v.y); }
+        }
+        lo[i] = (double)a;
+        hi[i] = (double)b;
+        if (bad) flags |= ST_NONFINITE;
+    }
+    if (flags) atomicOr(status, flags);
+}
+
 // ------------------------------------------------------------------ reduce
 __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, int64_t n, double *lo,
                           double *hi) {
@@ -1165,9 +1353,50 @@ static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_a
     return REACH_OK;
 }
 
-// Block shapes (REACH_OPT_MC_LAYOUT 2..6) and the measured default per system
-// (1024 samples of the 2^20-point KS grid over 500 steps, 256 of the 2^20-cell
-// chain over 200): the packed kernel is bound by the FP32 FMA pipe (a packed
+// binary32 streaming on the pair-row layout: persistent mc_rows warps, KC
+// rows per lane, S steps per launch, then the per-row reduction of the final
+// state into (lo, hi)
+template <int SYS, int KC>
+static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double *lo, double *hi, cudaStream_t st) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    int S = opt_steps() > 0 ? (int)opt_steps() : 3;
+    while (S > 1 && 2 * 4 * R * S >= 32 * KC / 2) --S;   // keep the halo below half the warp tile
+    const int64_t L = N > 0 ? (N + S - 1) / S : 1;
+    float2 *buf[2] = {bufA, bufB};
+    int dev = 0, sms = 148, per_sm = 2;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    REACH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_rows<SYS, KC>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = N > 0 ? (int)std::min<int64_t>(S, N - done) : 0;
+        a.S = s;
+        a.H = 4 * R * s;
+        a.W = 32 * KC - 2 * a.H;
+        a.first = (q == 0);
+        a.in = buf[q % 2];
+        a.out = buf[(q + 1) % 2];
+        const int64_t ntile = (a.n + a.W - 1) / a.W;
+        if (ntile * (int64_t)a.P >= (1LL << 32)) return REACH_EINVAL;
+        a.ntile = (unsigned)ntile;
+        const int64_t items = ntile * (int64_t)a.P;
+        const int64_t blocks = std::min<int64_t>((items + 7) / 8, (int64_t)sms * per_sm);
+        mc_rows<SYS, KC><<<(unsigned)blocks, 256, 0, st>>>(a);
+        REACH_LAUNCHED("mc_rows");
+        done += s;
+    }
+    int64_t g = (a.n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    mc_rows_reduce<<<(unsigned)g, 256, 0, st>>>(buf[L % 2], a.ns, a.n, a.P, a.m, lo, hi, a.status);
+    REACH_LAUNCHED("mc_rows_reduce");
+    return REACH_OK;
+}
+
+// Block shapes of the sample-row layout (REACH_OPT_MC_LAYOUT 2..6; the
+// pair-row kernel mc_rows is the default, see mc_dispatch), measured on 1024
+// samples of the 2^20-point KS grid over 500 steps and 256 of the 2^20-cell
+// chain over 200: the packed kernel is bound by the FP32 FMA pipe (a packed
 // instruction holds it two cycles), so the shape that best hides each tile's
 // load behind arithmetic wins.  KS: persistent 16-warp blocks whose next tiles
 // arrive by tensor copies (layout 6) at three steps per launch, 0.87 s; the
@@ -1178,7 +1407,6 @@ static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_a
 template <int SYS>
 static int launch_stream2(const McStep &a, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
     int layout = (int)opt_mc_layout();
-    if (layout == 0) layout = SYS == REACH_KS ? 6 : 4;
     const int S_auto = 3;
     switch (layout) {
     case 3: return launch_stream2_v<SYS, 32, 8, 1>(a, N, bufA, bufB, S_auto, st);
@@ -1232,6 +1460,51 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
     if (!onchip && !(sys->kind == REACH_TRAFFIC || sys->kind == REACH_KS)) return REACH_EINVAL;
     // binary32 samples on the streaming kernel go two per lane
     const bool pairs = !onchip && sizeof(T) == 4 && opt_mc_layout() != 1;
+    const int64_t lay = opt_mc_layout();
+    if (pairs && (lay == 0 || lay >= 8)) {
+        // pair-row layout (mc_rows, the default; 12 rows per lane unless the
+        // option picks 8 or 16): no per-block partials, the reduction reads
+        // the final state.  1024 samples of the 2^20-point KS grid over 500
+        // steps: 0.762 s against 0.870 s for the best block layout (6), 0.876
+        // s with 8 rows per lane (halo 19% of the warp tile), 0.782 s with 16
+        // (spills at 128 registers); 256 samples of the 2^20-cell chain over
+        // 200 steps: 0.062 s against 0.076 s (layout 4).  An L2 prefetch of
+        // each warp's next item gained nothing on the KS grid (2% traffic).
+        if (n > INT32_MAX - 64) return REACH_EINVAL;
+        RowStep r;
+        memset(&r, 0, sizeof r);
+        r.n = n;
+        r.ns = (n + 1) & ~(int64_t)1;
+        r.m = base.m;
+        r.P = (unsigned)((base.m + 1) / 2);
+        r.hf[0] = (float)base.h;
+        r.hf[1] = (float)(0.5 * base.h);
+        r.hf[2] = (float)(base.h / 6.0);
+        const double *pr = sys->prm;   // mc_stream2's binary32 constants
+        const bool tr = sys->kind == REACH_TRAFFIC;
+        r.qf[0] = (float)pr[0];
+        r.qf[1] = (float)pr[1];
+        r.qf[2] = (float)pr[2];
+        r.qf[3] = tr ? (float)(pr[2] * pr[3]) : (float)pr[3];
+        r.seed = base.seed;
+        r.xlo = base.xlo;
+        r.xhi = base.xhi;
+        r.dlo = wl;
+        r.dhi = wh;
+        r.status = base.status;
+        float2 *bufA, *bufB;
+        const size_t bytes = (size_t)r.ns * r.P * sizeof(float2);
+        if ((rc = sg.scratch(bytes, (void **)&bufA)) || (rc = sg.scratch(bytes, (void **)&bufB))) return rc;
+        const int kc = lay == 8 ? 8 : (lay == 10 ? 16 : 12);
+        if (sys->kind == REACH_TRAFFIC) {
+            if (kc == 8) return launch_rows<REACH_TRAFFIC, 8>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+            if (kc == 12) return launch_rows<REACH_TRAFFIC, 12>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+            return launch_rows<REACH_TRAFFIC, 16>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+        }
+        if (kc == 8) return launch_rows<REACH_KS, 8>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+        if (kc == 12) return launch_rows<REACH_KS, 12>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+        return launch_rows<REACH_KS, 16>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+    }
     // partial minima / maxima per block of samples
     const int sb = onchip ? mc_onchip_sb(base.m) : (pairs ? 64 : 32);
     int64_t nblk = (base.m + sb - 1) / sb;

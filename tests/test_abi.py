@@ -48,7 +48,7 @@ def test_options_are_validated():
     assert R.reach_get_option(R.OPT_STEPS_PER_LAUNCH) == 3
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, old)
     bad = [(R.OPT_STEPS_PER_LAUNCH, -1), (R.OPT_KERNEL, 5), (R.OPT_BLOCK, 33), (R.OPT_TILE, 4), (R.OPT_MC_SB, 4),
-           (R.OPT_MC_LAYOUT, 8), (R.OPT_SERVE_QUEUE_BLOCKS, -1), (R.OPT_SERVE_QUEUE_N, 4097),
+           (R.OPT_MC_LAYOUT, 11), (R.OPT_SERVE_QUEUE_BLOCKS, -1), (R.OPT_SERVE_QUEUE_N, 4097),
            (R.OPT_SERVE_MAX_WIDE, -1), (R.OPT_BATCH_CLUSTER_FROM, -1), (R.OPT_ONE_LAUNCH, 3),
            (R.OPT_SERVE_PRIORITY, 4), (R.OPT_SERVE_WIDE_EXCLUSIVE, 2), (99, 1)]
     for key, val in bad:

@@ -531,16 +531,17 @@ def test_mc32_samples_inside_mm_within_the_binary32_tolerance(kind, n, m, kernel
 @pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 100, 2), ("traffic", 1500, 77, 2), ("ks", 600, 64, 1),
                                         ("traffic", 3001, 130, 3)])
 def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
-    # the packed binary32 kernel (two samples per lane) performs each sample's
-    # operations in the same order as the one-sample kernel: same box, bit for
-    # bit, for every block shape; and it is the oracle's within TOL32
+    # the packed binary32 kernels (two samples per lane, in blocks of sample
+    # rows or along the rows of a sample pair) perform each sample's operations
+    # in the same order as the one-sample kernel: same box, bit for bit, for
+    # every layout; and it is the oracle's within TOL32
     lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=13)
     T = 0.13 if kind == "traffic" else 0.0013
     R.reach_set_option(R.OPT_KERNEL, 1)
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
     boxes = {}
     try:
-        for layout in (1, 0, 3, 4, 5, 6):
+        for layout in (1, 0, 3, 4, 5, 6, 8, 9, 10):
             R.reach_set_option(R.OPT_MC_LAYOUT, layout)
             boxes[layout] = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=4, precision=32)
     finally:
