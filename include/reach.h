@@ -387,9 +387,10 @@ REACH_API int reach_server_destroy(reach_server *s);
                                         32x8x1, 8x16x2, 16x8x2, and 16x16x1 persistent with the next tiles
                                         copied ahead by the TMA engine); 8 / 9 / 10 along sample-pair
                                         rows with 8 / 12 / 16 rows per lane; all give the same box bit for
-                                        bit.  Binary64: 0 auto (KS one 16-warp block per SM, traffic two
-                                        8-warp blocks), 7 forces the 16-warp block, other values the
-                                        8-warp ones */
+                                        bit.  Binary64: 0 auto (along the rows of one sample, 16 rows per
+                                        lane: as 10), 8 / 9 / 10 along the rows with 8 / 12 / 16 rows per
+                                        lane, 7 sample-row blocks of 16 warps, other values blocks of 8
+                                        warps; all give the same box bit for bit */
 #define REACH_OPT_SERVE_QUEUE_BLOCKS 8 /* servers created afterwards: blocks of their device work queue, 0 = no
                                          queue (default 64) */
 #define REACH_OPT_SERVE_QUEUE_N 9      /* servers created afterwards: MM / CGB requests up to this many cells

@@ -905,12 +905,14 @@ __global__ void __launch_bounds__(32 * WPB, 1) mc_stream2p(McStep a, unsigned lo
 struct RowStep {
     int64_t n, ns;            // rows, row stride of a pair's run (even)
     int64_t m;                // samples (drawn beyond m up to 2P, never reduced)
-    unsigned P;               // sample pairs
+    unsigned P;               // sample pairs (binary64 kernel: samples)
     unsigned ntile;           // ceil(n / W)
     int W, H;                 // owned rows per warp tile, halo rows per side (4 R S)
     int S;                    // RK4 steps in this launch (0: only draw the samples)
     float hf[3];              // h, h/2, h/6 rounded to binary32 on the host
     float qf[4];              // system constants as mc_stream2 takes them
+    double h, h6;             // binary64 kernel: h and h/6 (the host's)
+    double one, nzero;        // binary64 kernel: 1 and -0 (fadd / fmul)
     uint64_t seed;
     const double *xlo, *xhi;  // first launch: the initial box
     double dlo, dhi;          // traffic inflow box
@@ -1072,6 +1074,157 @@ __global__ void mc_rows_reduce(const float2 *x, int64_t ns, int64_t n, unsigned 
         }
         lo[i] = (double)a;
         hi[i] = (double)b;
+        if (bad) flags |= ST_NONFINITE;
+    }
+    if (flags) atomicOr(status, flags);
+}
+
+// ------------------------------------------------------------------ streaming binary64, samples along the rows
+// The binary64 version of mc_rows: sample j is a contiguous run of n doubles,
+// x[j ns + i], and a warp owns 32 KC consecutive rows of one sample (KC per
+// lane), neighbours by shuffles, no barrier, the 4 R S halo rows recomputed.
+// Each sample sees mc_stream's operations in the same order (sums and products
+// in the fused forms, which round the same), so the box is the same bit for
+// bit.
+template <int SYS, int KC, int MINB>
+__global__ void __launch_bounds__(256, MINB) mc_rows64(RowStep a, const double *__restrict__ prm) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t items = a.ntile * a.P;   // P = samples here; < 2^32 (checked on the host)
+    const int64_t n = a.n;
+    double q[4];
+    mc_consts<SYS, double>(prm, q);
+    const double one = a.one, nz = a.nzero;
+    const double h = a.h, hh = 0.5 * a.h, h6 = a.h6;
+    int flags = 0;
+    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const uint32_t j = it / a.ntile, t = it - j * a.ntile;   // 32-bit division
+        const int64_t own0 = (int64_t)t * a.W;
+        const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
+        const int64_t base = (int64_t)((uint64_t)j * (uint64_t)a.ns);
+        double d = 0.0;
+        if (SYS == REACH_TRAFFIC) d = box_sample(a.dlo, a.dhi, philox_uniform(a.seed, j, 0u, 1u));
+        double z[KC];
+        const bool whole = g0 >= 0 && g0 + KC <= n;
+        const double *in = (const double *)a.in;
+        if (a.first) {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                int64_t g = g0 + r;
+                bool ok = true;
+                if (SYS == REACH_KS) g = wrap_index(g, n);
+                else ok = g >= 0 && g < n;
+                double v = 0.0;
+                if (ok) {
+                    const double lo = a.xlo[g], hi = a.xhi[g];
+                    const bool owned = j == 0 && g0 + r >= own0 && g0 + r < own0 + a.W;
+                    if (owned && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
+                    v = box_sample(lo, hi, philox_uniform(a.seed, j, (uint32_t)g, 0u));
+                }
+                z[r] = v;
+            }
+        } else if (whole) {
+            const double2 *src = reinterpret_cast<const double2 *>(in + base + g0);   // g0 and base even
+#pragma unroll
+            for (int r = 0; r < KC / 2; ++r) {
+                const double2 v = __ldcs(src + r);
+                z[2 * r] = v.x;
+                z[2 * r + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                int64_t g = g0 + r;
+                bool ok = true;
+                if (SYS == REACH_KS) g = wrap_index(g, n);
+                else ok = g >= 0 && g < n;
+                z[r] = ok ? __ldcs(in + base + g) : 0.0;
+            }
+        }
+        const bool interior = SYS != REACH_KS && __all_sync(0xffffffffu, g0 >= 1 && g0 + KC <= n - 1);
+        auto steps = [&](auto in_tag) {
+            constexpr bool IN = decltype(in_tag)::value;
+            (void)IN;
+            for (int s = 0; s < a.S; ++s) {
+                double e[KC + 2 * R], acc[KC];
+#pragma unroll
+                for (int r = 0; r < KC; ++r) e[R + r] = z[r];
+#pragma unroll
+                for (int stage = 0; stage < 4; ++stage) {
+#pragma unroll
+                    for (int q2 = 0; q2 < R; ++q2) {
+                        e[q2] = __shfl_up_sync(0xffffffffu, e[KC + q2], 1);
+                        e[R + KC + q2] = __shfl_down_sync(0xffffffffu, e[R + q2], 1);
+                    }
+                    double kring[R + 1];
+                    double fprev = 0.0;
+                    (void)fprev;
+                    if constexpr (SYS != REACH_KS)
+                        fprev = IN ? tr_flux_interior<double>(q, e[0], e[1])
+                                   : tr_flux<double>(q, e[0], e[1], g0 - 1, n, d);
+#pragma unroll
+                    for (int r = 0; r < KC + R; ++r) {
+                        if (r < KC) {
+                            double kr;
+                            if constexpr (SYS == REACH_KS) {
+                                const double um2 = e[r], um1 = e[r + 1], u = e[r + 2], up1 = e[r + 3], up2 = e[r + 4];
+                                kr = fma(u, fma(-q[3], fadd(up1, -um1, one), q[0]),
+                                         fma(q[1], fadd(um1, up1, one), fmul(q[2], fadd(um2, up2, one), nz)));
+                            } else {
+                                const double fout = IN ? tr_flux_interior<double>(q, e[r + 1], e[r + 2])
+                                                       : tr_flux<double>(q, e[r + 1], e[r + 2], g0 + r, n, d);
+                                kr = fadd(-fout, fprev, one);
+                                fprev = fout;
+                            }
+                            kring[r % (R + 1)] = kr;
+                        }
+                        if (r >= R) {
+                            const int u = r - R;
+                            const double k = kring[u % (R + 1)];
+                            if (stage == 0) { acc[u] = k; e[R + u] = fma(hh, k, z[u]); }
+                            if (stage == 1) { acc[u] = fma(2.0, k, acc[u]); e[R + u] = fma(hh, k, z[u]); }
+                            if (stage == 2) { acc[u] = fma(2.0, k, acc[u]); e[R + u] = fma(h, k, z[u]); }
+                            if (stage == 3) { acc[u] = fadd(k, acc[u], one); z[u] = fma(h6, acc[u], z[u]); e[R + u] = z[u]; }
+                        }
+                    }
+                }
+            }
+        };
+        if (interior) steps(std::true_type{});
+        else steps(std::false_type{});
+        double *out = (double *)a.out;
+        if (whole && g0 >= own0 && g0 + KC <= own0 + a.W) {
+            double2 *dst = reinterpret_cast<double2 *>(out + base + g0);
+#pragma unroll
+            for (int r = 0; r < KC / 2; ++r) __stcs(dst + r, make_double2(z[2 * r], z[2 * r + 1]));
+        } else {
+#pragma unroll
+            for (int r = 0; r < KC; ++r) {
+                const int64_t g = g0 + r;
+                if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(out + base + g, z[r]);
+            }
+        }
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// per-row minimum and maximum over the samples of the binary64 row state
+// (integer-key minima, as mc_stream's warp reduction takes them)
+__global__ void mc_rows64_reduce(const double *x, int64_t ns, int64_t n, int64_t m, double *lo, double *hi,
+                                 int *status) {
+    int flags = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = INFINITY, b = -INFINITY;
+        bool bad = false;
+        for (int64_t j = 0; j < m; ++j) {
+            const double v = __ldcs(x + (int64_t)((uint64_t)j * (uint64_t)ns) + i);
+            a = kmin(a, v);
+            b = kmax(b, v);
+            bad |= !kfinite(v);
+        }
+        lo[i] = a;
+        hi[i] = b;
         if (bad) flags |= ST_NONFINITE;
     }
     if (flags) atomicOr(status, flags);
@@ -1242,13 +1395,14 @@ static int launch_stream_v(McStep a, const double *prm, int64_t N, void *bufA, v
 
 template <int SYS, class T>
 static int launch_stream(McStep a, const double *prm, int64_t N, void *bufA, void *bufB, cudaStream_t st) {
-    // binary64 on KS grids: one 16-warp block per SM halves the 16-row halo
-    // share of two 8-warp blocks (1024 samples of 2^20 points: 0.77 against
+    // binary64 in sample-row blocks (the row layout of mc_rows64 is the
+    // default): one 16-warp block per SM halves the 16-row halo share of two
+    // 8-warp blocks on KS grids (1024 samples of 2^20 points: 0.77 against
     // 0.74 of the FP64 peak); the traffic chain's one-row halo gains nothing
     // (2.26e10 against 2.33e10 comp-steps/s).  REACH_OPT_MC_LAYOUT 7 forces
-    // it, 1..6 the 8-warp blocks.
+    // the 16-warp block, 1..6 the 8-warp blocks.
     const int64_t lay = opt_mc_layout();
-    if (sizeof(T) == 8 && (lay == 7 || (lay == 0 && SYS == REACH_KS)))
+    if (sizeof(T) == 8 && lay == 7)
         return launch_stream_v<SYS, T, 16, 1>(a, prm, N, bufA, bufB, st);
     return launch_stream_v<SYS, T>(a, prm, N, bufA, bufB, st);
 }
@@ -1393,6 +1547,47 @@ static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double 
     return REACH_OK;
 }
 
+// binary64 streaming on the row layout: persistent mc_rows64 warps, KC rows
+// per lane, S steps per launch (default 1: the kernel is bound by the FP64
+// pipe), then the per-row reduction of the final state into (lo, hi)
+template <int SYS, int KC, int MINB>
+static int launch_rows64(RowStep a, const double *prm, int64_t N, double *bufA, double *bufB, double *lo,
+                         double *hi, cudaStream_t st) {
+    constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    int S = opt_steps() > 0 ? (int)opt_steps() : 1;
+    while (S > 1 && 2 * 4 * R * S >= 32 * KC / 2) --S;
+    const int64_t L = N > 0 ? (N + S - 1) / S : 1;
+    double *buf[2] = {bufA, bufB};
+    int dev = 0, sms = 148, per_sm = MINB;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    REACH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_rows64<SYS, KC, MINB>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    int64_t done = 0;
+    for (int64_t q = 0; q < L; ++q) {
+        const int s = N > 0 ? (int)std::min<int64_t>(S, N - done) : 0;
+        a.S = s;
+        a.H = 4 * R * s;
+        a.W = 32 * KC - 2 * a.H;
+        a.first = (q == 0);
+        a.in = (const float2 *)buf[q % 2];
+        a.out = (float2 *)buf[(q + 1) % 2];
+        const int64_t ntile = (a.n + a.W - 1) / a.W;
+        if (ntile * (int64_t)a.P >= (1LL << 32)) return REACH_EINVAL;
+        a.ntile = (unsigned)ntile;
+        const int64_t items = ntile * (int64_t)a.P;
+        const int64_t blocks = std::min<int64_t>((items + 7) / 8, (int64_t)sms * per_sm);
+        mc_rows64<SYS, KC, MINB><<<(unsigned)blocks, 256, 0, st>>>(a, prm);
+        REACH_LAUNCHED("mc_rows64");
+        done += s;
+    }
+    int64_t g = (a.n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    mc_rows64_reduce<<<(unsigned)g, 256, 0, st>>>(buf[L % 2], a.ns, a.n, a.m, lo, hi, a.status);
+    REACH_LAUNCHED("mc_rows64_reduce");
+    return REACH_OK;
+}
+
 // Block shapes of the sample-row layout (REACH_OPT_MC_LAYOUT 2..6; the
 // pair-row kernel mc_rows is the default, see mc_dispatch), measured on 1024
 // samples of the 2^20-point KS grid over 500 steps and 256 of the 2^20-cell
@@ -1461,6 +1656,43 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
     // binary32 samples on the streaming kernel go two per lane
     const bool pairs = !onchip && sizeof(T) == 4 && opt_mc_layout() != 1;
     const int64_t lay = opt_mc_layout();
+    if (!onchip && sizeof(T) == 8 && (lay == 0 || lay >= 8)) {
+        // binary64 on the row layout (mc_rows64, the default: 16 rows per lane
+        // in one 8-warp block per SM at 190 registers; the option picks 8 or
+        // 12 in two blocks per SM).  64 samples of the 2^20-point KS grid over
+        // 100 steps: 0.419 s against 0.515 s for one 16-warp block per SM of
+        // sample rows with a barrier per stage (0.93 against 0.77 of the FP64
+        // peak), 0.431 s with 8 rows per lane; the 2^20-cell chain over 200
+        // steps: 0.513 s against 0.573 s.
+        if (n > INT32_MAX - 64) return REACH_EINVAL;
+        RowStep r;
+        memset(&r, 0, sizeof r);
+        r.n = n;
+        r.ns = (n + 1) & ~(int64_t)1;
+        r.m = base.m;
+        r.P = (unsigned)base.m;
+        r.h = base.h;
+        r.h6 = base.h / 6.0;
+        r.one = 1.0;
+        r.nzero = -0.0;
+        r.seed = base.seed;
+        r.xlo = base.xlo;
+        r.xhi = base.xhi;
+        r.dlo = wl;
+        r.dhi = wh;
+        r.status = base.status;
+        double *bufA, *bufB;
+        const size_t bytes = (size_t)r.ns * r.P * sizeof(double);
+        if ((rc = sg.scratch(bytes, (void **)&bufA)) || (rc = sg.scratch(bytes, (void **)&bufB))) return rc;
+        if (sys->kind == REACH_TRAFFIC) {
+            if (lay == 8) return launch_rows64<REACH_TRAFFIC, 8, 2>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+            if (lay == 9) return launch_rows64<REACH_TRAFFIC, 12, 2>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+            return launch_rows64<REACH_TRAFFIC, 16, 1>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+        }
+        if (lay == 8) return launch_rows64<REACH_KS, 8, 2>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+        if (lay == 9) return launch_rows64<REACH_KS, 12, 2>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+        return launch_rows64<REACH_KS, 16, 1>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
+    }
     if (pairs && (lay == 0 || lay >= 8)) {
         // pair-row layout (mc_rows, the default; 12 rows per lane unless the
         // option picks 8 or 16): no per-block partials, the reduction reads

@@ -554,6 +554,32 @@ def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
     assert_close(boxes[0][1], o[1], TOL32, "hi")
 
 
+@pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 37, 1), ("traffic", 1501, 40, 1), ("ks", 2999, 9, 2),
+                                        ("traffic", 700, 21, 3)])
+def test_mc64_layouts_equal_bit_for_bit(kind, n, m, S):
+    # binary64 streaming MC in sample-row blocks (8- and 16-warp) and along the
+    # rows of one sample (8 / 12 / 16 rows per lane): each sample sees the same
+    # operations in the same order, so every layout gives the same box bit for
+    # bit, and it is the oracle's within TOL64
+    lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=17)
+    T = 0.11 if kind == "traffic" else 0.0011
+    R.reach_set_option(R.OPT_KERNEL, 1)
+    R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, S)
+    boxes = {}
+    try:
+        for layout in (2, 7, 8, 9, 10):
+            R.reach_set_option(R.OPT_MC_LAYOUT, layout)
+            boxes[layout] = gpu_box("mc", kind, n, lo, hi, wlo, whi, T, dt, m=m, seed=6, precision=64)
+    finally:
+        R.reach_set_option(R.OPT_MC_LAYOUT, 0)
+    for layout, b in boxes.items():
+        np.testing.assert_array_equal(b[0], boxes[2][0], err_msg=f"layout {layout} lo")
+        np.testing.assert_array_equal(b[1], boxes[2][1], err_msg=f"layout {layout} hi")
+    o = O.reach("mc", kind, lo, hi, wlo, whi, t_final=T, dt=dt, m=m, seed=6, prec=64)
+    assert_close(boxes[8][0], o[0], TOL64, "lo")
+    assert_close(boxes[8][1], o[1], TOL64, "hi")
+
+
 @pytest.mark.parametrize("method", ["mm", "cgb"])
 @pytest.mark.parametrize("n,T", [(723, 0.003), (3001, 0.0013), (40001, 0.001)])
 def test_ks_all_steps_in_one_launch(method, n, T):
