@@ -1283,12 +1283,26 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
     }
     const T h = (T)a.h, fa = (T)p.a, fg = (T)p.g;
     for (int64_t s = 0; s < a.N; ++s) {
+        // sines and cosines at the step start; the stages' by angle addition
+        // over the small stage increment (as quad_box does)
+        T s0[3], c0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if constexpr (sizeof(T) == 4) sincosf(c.q[d], &s0[d], &c0[d]);
+            else sincos(c.q[d], &s0[d], &c0[d]);
+        }
         QSums<T> m;
 #pragma unroll
         for (int st = 0; st < 4; ++st) {
-            T q[3], acc[3];
+            T q[3], dq[3], sn[3], cs[3], acc[3];
             stage_angles(c, st, h, q);
-            quad_acc_point<T>(q, fa, fg, acc);
+            stage_deltas(c, st, h, dq);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (st == 0) { sn[d] = s0[d]; cs[d] = c0[d]; }
+                else shifted_sincos(q[d], dq[d], s0[d], c0[d], sn[d], cs[d]);
+            }
+            quad_acc_trig<T>(sn, cs, fa, fg, acc);
             add_stage(m, acc, st);
         }
         chain_update(c, m, h);

@@ -115,6 +115,25 @@ __device__ __forceinline__ void shifted_sincos(double ang, double d, double s0, 
     }
 }
 
+// binary32: the same with the series through d^7 and d^6 (for |d| <= 1/16 the
+// first omitted terms are below 2e-16 and 6e-15, under binary32 rounding)
+__device__ __forceinline__ void small_sincos(float d, float &s, float &c) {
+    const float d2 = d * d;
+    s = fmaf(d * d2, fmaf(d2, fmaf(d2, -1.98412698e-4f, 8.33333333e-3f), -0.166666667f), d);
+    c = fmaf(d2, fmaf(d2, fmaf(d2, -1.38888889e-3f, 4.16666667e-2f), -0.5f), 1.0f);
+}
+
+__device__ __forceinline__ void shifted_sincos(float ang, float d, float s0, float c0, float &s, float &c) {
+    if (fabsf(d) <= (float)Q_SMALL) {
+        float sd, cd;
+        small_sincos(d, sd, cd);
+        s = fmaf(s0, cd, c0 * sd);
+        c = fmaf(c0, cd, -(s0 * sd));
+    } else {
+        sincosf(ang, &s, &c);
+    }
+}
+
 // the plain accelerations from the sines and cosines of the attitude
 template <class T>
 __device__ __forceinline__ void quad_acc_trig(const T (&s)[3], const T (&c)[3], T a, T g, T (&acc)[3]) {
@@ -122,18 +141,6 @@ __device__ __forceinline__ void quad_acc_trig(const T (&s)[3], const T (&c)[3], 
     acc[0] = a * (-(cs * c[2]) - s[0] * s[2]);
     acc[1] = a * (-(cs * s[2]) + s[0] * c[2]);
     acc[2] = g - a * (c[0] * c[1]);
-}
-
-// accelerations at one attitude (the plain system), in the run precision
-template <class T>
-__device__ __forceinline__ void quad_acc_point(const T (&q)[3], T a, T g, T (&acc)[3]) {
-    T s[3], c[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        if constexpr (sizeof(T) == 4) sincosf(q[j], &s[j], &c[j]);
-        else sincos(q[j], &s[j], &c[j]);
-    }
-    quad_acc_trig<T>(s, c, a, g, acc);
 }
 
 // MM: natural interval extension of the accelerations over the hull of the
