@@ -529,12 +529,15 @@ def test_mc32_samples_inside_mm_within_the_binary32_tolerance(kind, n, m, kernel
 
 
 @pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 100, 2), ("traffic", 1500, 77, 2), ("ks", 600, 64, 1),
-                                        ("traffic", 3001, 130, 3)])
+                                        ("traffic", 3001, 130, 3), ("ks", 150, 33, 2), ("traffic", 70, 1, 1)])
 def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
     # the packed binary32 kernels (two samples per lane, in blocks of sample
     # rows or along the rows of a sample pair) perform each sample's operations
     # in the same order as the one-sample kernel: same box, bit for bit, for
-    # every layout; and it is the oracle's within TOL32
+    # every layout (grids shorter than one warp tile, where a lane's rows wrap
+    # around the periodic grid or run past the chain, and a single sample,
+    # whose pair has no second sample, included); and it is the oracle's
+    # within TOL32
     lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=13)
     T = 0.13 if kind == "traffic" else 0.0013
     R.reach_set_option(R.OPT_KERNEL, 1)
@@ -555,7 +558,7 @@ def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
 
 
 @pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 37, 1), ("traffic", 1501, 40, 1), ("ks", 2999, 9, 2),
-                                        ("traffic", 700, 21, 3)])
+                                        ("traffic", 700, 21, 3), ("ks", 150, 3, 1), ("traffic", 70, 1, 2)])
 def test_mc64_layouts_equal_bit_for_bit(kind, n, m, S):
     # binary64 streaming MC in sample-row blocks (8- and 16-warp) and along the
     # rows of one sample (8 / 12 / 16 rows per lane): each sample sees the same
