@@ -916,8 +916,8 @@ struct RowStep {
     uint64_t seed;
     const double *xlo, *xhi;  // first launch: the initial box
     double dlo, dhi;          // traffic inflow box
-    const float2 *in;         // state of the previous launch
-    float2 *out;
+    const void *in;           // state of the previous launch (float2 pairs or doubles)
+    void *out;
     int first;
     int *status;
 };
@@ -946,16 +946,18 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
             d.y = (float)box_sample(a.dlo, a.dhi, philox_uniform(a.seed, j0 + 1, 0u, 1u));
         }
         float2 z[KC];
+        const float2 *in = static_cast<const float2 *>(a.in);
+        float2 *out = static_cast<float2 *>(a.out);
         const bool whole = g0 >= 0 && g0 + KC <= n;   // the lane's run lies inside [0, n)
         if (a.first) {
 #pragma unroll
             for (int r = 0; r < KC; ++r) {
                 int64_t g = g0 + r;
-                bool in = true;
+                bool ok = true;
                 if (SYS == REACH_KS) g = wrap_index(g, n);
-                else in = g >= 0 && g < n;
+                else ok = g >= 0 && g < n;
                 float2 v = bc2(0.f);
-                if (in) {
+                if (ok) {
                     const double lo = a.xlo[g], hi = a.xhi[g];
                     const bool owned = p == 0 && g0 + r >= own0 && g0 + r < own0 + a.W;
                     if (owned && !(lo <= hi && isfinite(lo) && isfinite(hi))) flags |= ST_BADINPUT;
@@ -965,7 +967,7 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
                 z[r] = v;
             }
         } else if (whole) {
-            const float4 *src = reinterpret_cast<const float4 *>(a.in + base + g0);   // g0 and base even
+            const float4 *src = reinterpret_cast<const float4 *>(in + base + g0);   // g0 and base even
 #pragma unroll
             for (int r = 0; r < KC / 2; ++r) {
                 const float4 v = __ldcs(src + r);
@@ -976,10 +978,10 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
 #pragma unroll
             for (int r = 0; r < KC; ++r) {
                 int64_t g = g0 + r;
-                bool in = true;
+                bool ok = true;
                 if (SYS == REACH_KS) g = wrap_index(g, n);
-                else in = g >= 0 && g < n;
-                z[r] = in ? __ldcs(a.in + base + g) : bc2(0.f);
+                else ok = g >= 0 && g < n;
+                z[r] = ok ? __ldcs(in + base + g) : bc2(0.f);
             }
         }
         // every flux of the lane's run between two cells of the chain; the
@@ -1042,14 +1044,14 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
         else steps(std::false_type{});
         // the owned rows of the lane's run
         if (whole && g0 >= own0 && g0 + KC <= own0 + a.W) {
-            float4 *dst = reinterpret_cast<float4 *>(a.out + base + g0);
+            float4 *dst = reinterpret_cast<float4 *>(out + base + g0);
 #pragma unroll
             for (int r = 0; r < KC / 2; ++r) __stcs(dst + r, make_float4(z[2 * r].x, z[2 * r].y, z[2 * r + 1].x, z[2 * r + 1].y));
         } else {
 #pragma unroll
             for (int r = 0; r < KC; ++r) {
                 const int64_t g = g0 + r;
-                if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(a.out + base + g, z[r]);
+                if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(out + base + g, z[r]);
             }
         }
     }
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(256, MINB) mc_rows64(RowStep a, const double *
         if (SYS == REACH_TRAFFIC) d = box_sample(a.dlo, a.dhi, philox_uniform(a.seed, j, 0u, 1u));
         double z[KC];
         const bool whole = g0 >= 0 && g0 + KC <= n;
-        const double *in = (const double *)a.in;
+        const double *in = static_cast<const double *>(a.in);
         if (a.first) {
 #pragma unroll
             for (int r = 0; r < KC; ++r) {
@@ -1193,7 +1195,7 @@ __global__ void __launch_bounds__(256, MINB) mc_rows64(RowStep a, const double *
         };
         if (interior) steps(std::true_type{});
         else steps(std::false_type{});
-        double *out = (double *)a.out;
+        double *out = static_cast<double *>(a.out);
         if (whole && g0 >= own0 && g0 + KC <= own0 + a.W) {
             double2 *dst = reinterpret_cast<double2 *>(out + base + g0);
 #pragma unroll
@@ -1584,8 +1586,8 @@ static int launch_rows64(RowStep a, const double *prm, int64_t N, double *bufA, 
         a.H = 4 * R * s;
         a.W = 32 * KC - 2 * a.H;
         a.first = (q == 0);
-        a.in = (const float2 *)buf[q % 2];
-        a.out = (float2 *)buf[(q + 1) % 2];
+        a.in = buf[q % 2];
+        a.out = buf[(q + 1) % 2];
         const int64_t ntile = (a.n + a.W - 1) / a.W;
         if (ntile * (int64_t)a.P >= (1LL << 32)) return REACH_EINVAL;
         a.ntile = (unsigned)ntile;
