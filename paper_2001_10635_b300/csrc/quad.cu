@@ -12,6 +12,9 @@
 
 namespace reach {
 
+// steps between fresh sines and cosines of the step-start angles
+constexpr int64_t QUAD_ANCHOR = 32;
+
 struct QuadArgs {
     const double *xlo, *xhi, *wlo, *whi;
     double *lo, *hi;
@@ -51,20 +54,37 @@ __global__ void __launch_bounds__(128) quad_box(QuadArgs A) {
         }
     }
     const double h = A.h;
+    // sines and cosines at the step start: MM the two chains' attitudes; CGB
+    // the center's and the two ends of the angle box.  A step moves each angle
+    // by a small increment, so the next step's values follow by angle addition
+    // (shifted_sincos); every QUAD_ANCHOR steps they are taken afresh, which
+    // bounds the rounding carried from step to step to that many additions
+    double sa[3], ca[3], sb[3], cb[3], sx[3], cx[3];
+    double pa[3], pb[3], px[3];   // the angles those values belong to
     for (int64_t s = 0; s < A.N; ++s) {
-        // sines and cosines at the step start: MM the two chains' attitudes;
-        // CGB the center's and the two ends of the angle box
-        double sa[3], ca[3], sb[3], cb[3], sx[3], cx[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            if (METHOD == MM) {
-                sincos(c0.q[j], &sa[j], &ca[j]);
-                sincos(c1.q[j], &sb[j], &cb[j]);
+            const double na = METHOD == MM ? c0.q[j] : c0.q[j] - c1.q[j];
+            const double nb = METHOD == MM ? c1.q[j] : c0.q[j] + c1.q[j];
+            if (s % QUAD_ANCHOR == 0) {
+                sincos(na, &sa[j], &ca[j]);
+                sincos(nb, &sb[j], &cb[j]);
+                if (METHOD == CGB) sincos(c0.q[j], &sx[j], &cx[j]);
             } else {
-                sincos(c0.q[j], &sx[j], &cx[j]);
-                sincos(c0.q[j] - c1.q[j], &sa[j], &ca[j]);
-                sincos(c0.q[j] + c1.q[j], &sb[j], &cb[j]);
+                double t0 = sa[j], t1 = ca[j];
+                shifted_sincos(na, na - pa[j], t0, t1, sa[j], ca[j]);
+                t0 = sb[j];
+                t1 = cb[j];
+                shifted_sincos(nb, nb - pb[j], t0, t1, sb[j], cb[j]);
+                if (METHOD == CGB) {
+                    t0 = sx[j];
+                    t1 = cx[j];
+                    shifted_sincos(c0.q[j], c0.q[j] - px[j], t0, t1, sx[j], cx[j]);
+                }
             }
+            pa[j] = na;
+            pb[j] = nb;
+            px[j] = c0.q[j];
         }
         QSums<double> m0, m1;
         // stages in a loop: the trigonometric code is large, and unrolling it
