@@ -442,6 +442,8 @@ static int reach_box(int method, const reach_system *sys, const double *x0_lo, c
         it.status = sg.status;
         it.one = 1.0;
         it.nzero = -0.0;
+        it.hh = 0.5 * dt;
+        it.h6 = dt / 6.0;
         if (2 * n <= (int64_t)QMAX * 512) rc = onchip_launch_single(it, onchip_threads(n), sg.st);
         else rc = onchip_launch_cluster(it, sg.st);
         if (rc) return rc;

@@ -328,6 +328,8 @@ extern "C" int reach_batch_create(const reach_query *queries, int64_t count, int
         it.h = q.dt;
         it.one = 1.0;
         it.nzero = -0.0;
+        it.hh = 0.5 * q.dt;
+        it.h6 = q.dt / 6.0;
         it.xlo = d[0]; it.xhi = d[1]; it.wlo = d[2]; it.whi = d[3];
         it.lo = (double *)d[4]; it.hi = (double *)d[5];
         it.status = b->d_status + i;

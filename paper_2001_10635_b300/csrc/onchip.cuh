@@ -26,6 +26,7 @@ struct OnItem {
     double h;
     int *status;
     double one, nzero;     // 1 and -0, read at run time (fadd / fmul)
+    double hh, h6;         // h / 2 and h / 6, formed on the host (no binary64 division per stage)
 };
 
 // group barrier: a warp syncs itself, a larger group uses a named barrier
@@ -234,10 +235,10 @@ __device__ __forceinline__ void onchip_stage(const OnItem &it, const double *yA,
         if (c < cend) {
             const double k = onchip_rhs<SYS, METHOD>(c, n, yA, yB, wA, wB, it.prm, q);
             double y;
-            if (STAGE == 0) { acc[s] = k; y = fma(0.5 * h, k, z[s]); }
-            if (STAGE == 1) { acc[s] = fma(2.0, k, acc[s]); y = fma(0.5 * h, k, z[s]); }
+            if (STAGE == 0) { acc[s] = k; y = fma(it.hh, k, z[s]); }
+            if (STAGE == 1) { acc[s] = fma(2.0, k, acc[s]); y = fma(it.hh, k, z[s]); }
             if (STAGE == 2) { acc[s] = fma(2.0, k, acc[s]); y = fma(h, k, z[s]); }
-            if (STAGE == 3) { acc[s] = fadd(k, acc[s], q[6]); z[s] = fma(h / 6.0, acc[s], z[s]); y = z[s]; }
+            if (STAGE == 3) { acc[s] = fadd(k, acc[s], q[6]); z[s] = fma(it.h6, acc[s], z[s]); y = z[s]; }
             (c < n ? oA[c] : oB[c - n]) = y;
         }
     }

@@ -410,6 +410,8 @@ extern "C" int reach_queue_submit(reach_queue *q, const reach_query *qu, int64_t
     it.h = qu->dt;
     it.one = 1.0;
     it.nzero = -0.0;
+    it.hh = 0.5 * qu->dt;
+    it.h6 = qu->dt / 6.0;
     it.status = nullptr;
     item.ticket = t;
     // publish: the item and the staged inputs are written before the tail
