@@ -51,7 +51,7 @@ struct StepArgs {
     int H;                     // halo cells per side = 4 R S
     int S;                     // RK4 steps in this launch
     double h, hh, h6;          // h, h / 2 and h / 6, formed on the host (no FP64 division in the kernel)
-    double one, nzero;         // 1 and -0, read at run time (fadd / fmul in common.cuh)
+    double one = 1.0, nzero = -0.0;   // read at run time (fadd / fmul in common.cuh); set again after a memset
     int first, last;           // convert the input box / emit the output box
     int vec;                   // every state pointer is 16-byte aligned: runs move as double2
     int *status;
