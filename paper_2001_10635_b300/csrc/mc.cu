@@ -1,16 +1,23 @@
 // mc.cu -- Monte Carlo reachability (Sec. 2.1, Algorithm 4).
 //
 // Samples are drawn on the device with Philox4x32-10 (common.cuh) and
-// integrated with RK4 in binary64 or binary32.  Lane = sample: a warp holds 32
-// samples of the same components, so the stencil never crosses lanes and the
-// final per-component minimum / maximum over samples is a warp shuffle.
+// integrated with RK4 in binary64 or binary32.
 //   mc_onchip : small n, one block = SB samples x the whole state, all N steps
 //               in shared memory (SB = 32, or 8 or 2 when there are too few
-//               samples for blocks of 32 to reach every SM).
-//   mc_stream : large stencil systems; state in HBM, sample-fastest layout
-//               x[i * M + j]; one launch per RK4 step over tiles of 32 samples x
-//               TC components plus a 4R-cell halo; sampling fused into the first
-//               launch and the min/max into the last.
+//               samples for blocks of 32 to reach every SM); lane = sample,
+//               minima / maxima over samples by warp shuffles.
+//   mc_rows / mc_rows64 (the streaming defaults): large stencil systems, state
+//               in HBM with each sample (binary64) or pair of samples (binary32)
+//               a contiguous run of rows; a lane holds consecutive rows, so the
+//               stencil crosses lanes by shuffles and no warp waits for
+//               another; S RK4 steps per launch with a 4RS-row halo; sampling
+//               fused into the first launch, minima / maxima over samples in a
+//               final pass over the state.
+//   mc_stream / mc_stream2 / mc_stream2p: the same systems in the
+//               sample-fastest layout x[i * M + j] (lane = sample; blocks of
+//               sample rows exchanging edge rows through shared memory), kept
+//               as options.
+//   mc_quad   : the quadrotor swarm, 32 samples of one agent per warp.
 // Per-block partial minima / maxima are combined by mc_reduce (no atomics, so
 // the result does not depend on scheduling).
 #include <algorithm>
