@@ -117,8 +117,11 @@ struct reach_server {
 namespace reach {
 
 static int64_t mc_footprint(const reach_system *s, int64_t m, int prec) {
-    // the streaming kernel pads the samples to blocks of 64 (binary32, two per
-    // lane) or 32, the on-chip one uses blocks of 2 to 32
+    // the sample-row streaming kernels pad the samples to blocks of 64
+    // (binary32, two per lane) or 32, the on-chip one uses blocks of 2 to 32;
+    // the row-layout defaults (mc_rows, mc_rows64) hold the same two state
+    // buffers with rows padded to an even count and no partials, which the
+    // partials term below more than covers
     const bool stream_kernel = (s->kind == REACH_TRAFFIC || s->kind == REACH_KS) && s->n > 128;
     const int64_t ss = prec == 32 ? 64 : 32, M = (m + ss - 1) / ss * ss, elt = prec == 32 ? 4 : 8, n = s->n;
     // partial minima / maxima: one row per block of samples
