@@ -491,6 +491,10 @@ def bench_temporal_blocking(R, torch, dev):
                 R.reach_mc(sk, kd["x_lo"], kd["x_hi"], **kw)
                 sec = time.perf_counter() - t0
                 out[f"ks_mc32_S{S}"] = 256 * (1 << 20) * 120 / sec
+                # algorithmic HBM bytes: one binary32 read and write per sample-component and launch
+                gbs = out[f"ks_mc32_S{S}"] * 8.0 / S / 1e9
+                out[f"ks_mc32_S{S}_hbm_gbs"] = gbs
+                out[f"ks_mc32_S{S}_hbm_frac"] = gbs / load_peaks().get("hbm_gbs", 6400.0)
     R.reach_set_option(R.OPT_STEPS_PER_LAUNCH, 0)
     out["unit"] = "comp-steps/s"
     return out
