@@ -369,6 +369,40 @@ def test_ks_full_size_mc32_inside_mm():
     assert (mc[1] - mc[0]).min() > 0
 
 
+@pytest.mark.parametrize("prec,m,owned", [(32, 24, 32 * 12 - 2 * 24), (64, 8, 32 * 16 - 2 * 8)])
+def test_ks_full_size_mc_sampled_rows(prec, m, owned):
+    # the configured 2^20-point grid over 500 steps in the launch configuration
+    # the bench times (binary32: 12 rows per lane, three steps per launch, W =
+    # 336 owned rows per warp tile; binary64: 16 rows per lane, one step per
+    # launch, W = 496), fewer samples: at sampled rows, the minimum and maximum
+    # over the samples equal the oracle's.  Each sample's initial window is
+    # drawn from the oracle's generator with the grid's own component indices,
+    # and a window of 16N + 8 rows is wide enough that its periodic ends never
+    # reach its centre in N steps.
+    n = 1 << 20
+    wl = W.ks_grid(n)
+    T, dt = wl["t_final"], wl["dt"]
+    N = O.nsteps(T, dt)
+    seed = 21
+    g = gpu_box("mc", "ks", n, wl["x_lo"], wl["x_hi"], None, None, T, dt, m=m, seed=seed, precision=prec)
+    assert np.isfinite(g[0]).all() and (g[0] <= g[1]).all()
+    L = 16 * N + 8
+    rows = [0, n - 1] + _tile_edge_cells(n, owned)[::4]
+    for i in sorted(set(rows)):
+        idx = (i - L // 2 + np.arange(L)) % n
+        lo, hi = wl["x_lo"][idx], wl["x_hi"][idx]
+        centre = []
+        for j in range(m):
+            u = np.array([O.uniform(seed, j, int(k), 0) for k in idx])
+            x0 = lo + (hi - lo) * u
+            if prec == 32:
+                x0 = x0.astype(np.float32).astype(np.float64)
+            centre.append(O.flow("ks", x0, t_final=T, dt=dt, params=wl["params"])[L // 2])
+        tol = TOL64 if prec == 64 else TOL32
+        assert_close(g[0][i:i + 1], np.array([min(centre)]), tol, f"row {i} lo")
+        assert_close(g[1][i:i + 1], np.array([max(centre)]), tol, f"row {i} hi")
+
+
 @pytest.mark.parametrize("v", [0.45, 0.25, 0.5])
 @pytest.mark.parametrize("method", ["mm", "cgb"])
 def test_streaming_traffic_parameters(method, v):
