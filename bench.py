@@ -594,7 +594,7 @@ def _fifo_run(R, trace, systems, rate_scale):
     return lat, time.perf_counter() - t0, bad
 
 
-def bench_serving(R, count=60, sweep_count=30, slots=8, budget=160 << 30):
+def bench_serving(R, count=60, sweep_count=30, slots=8, budget=160 << 30, loads=(0.5, 0.7, 0.9)):
     """The seeded 2000 q/s Poisson trace at its stated sizes (traffic n in
     [1e2, 1e7], KS n = 2^10..2^20, MM / CGB / MC-256-FP32, 100..20000 RK4
     steps): its first `count` arrivals at the offered rate, and its first
@@ -621,7 +621,7 @@ def bench_serving(R, count=60, sweep_count=30, slots=8, budget=160 << 30):
     # a time (where a small query waits behind every large one ahead of it)
     sus = trace[:sweep_count]
     sweep = []
-    for frac in (0.5, 0.7, 0.9):
+    for frac in loads:
         scale = frac * capacity / 2000.0
         slat, sspan, sbad, _, _ = _serve_run(R, sus, systems, scale, slots, budget)
         sflat, sfspan, sfbad = _fifo_run(R, sus, systems, scale)
@@ -647,7 +647,7 @@ def bench_serving(R, count=60, sweep_count=30, slots=8, budget=160 << 30):
             "per_query_fifo": {"value": work / fspan, "unit": "comp-steps/s", "makespan_s": fspan,
                                "p50_ms": _pct(flat, 50) * 1e3, "p99_ms": _pct(flat, 99) * 1e3, "failed": _failed(fbad)},
             "speedup_vs_fifo": fspan / span,
-            "sustainable": sweep[1], "load_sweep": sweep}
+            "sustainable": sweep[len(sweep) // 2] if sweep else None, "load_sweep": sweep}
 
 
 def headline_config(n, world):
@@ -805,12 +805,22 @@ def main():
     ap.add_argument("--cells", type=int, default=N_CELLS,
                     help="chain length (default 2^26; smaller values are for profiler captures only)")
     ap.add_argument("--profile-case", default="", help="run one named workload for a profiler capture and exit")
+    ap.add_argument("--serving-run", default="",
+                    help="COUNT:SWEEP:LOADS, e.g. 400:100:0.9: only the serving comparison, with COUNT arrivals at the "
+                         "offered rate and SWEEP at each comma-free list of loads (0.5/0.7/0.9), printed as JSON")
     ap.add_argument("--case-n", type=int, default=0)
     ap.add_argument("--case-m", type=int, default=0)
     ap.add_argument("--case-t", type=float, default=0.0)
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.serving_run:
+        import paper_2001_10635_b300 as R
+        cnt, sweep, loads = args.serving_run.split(":")
+        res = bench_serving(R, count=int(cnt), sweep_count=int(sweep),
+                            loads=tuple(float(v) for v in loads.split("/")))
+        print(json.dumps({"serving": res}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
 
