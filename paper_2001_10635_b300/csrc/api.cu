@@ -181,6 +181,8 @@ TrafficK make_traffic_k(const double *prm, double wl, double wh) {
     // h / 6 rounded down and up (set per call by the caller when sound)
     p.c6l = p.c6u = 0.0;
     p.one = 1.0;
+    p.pzero = 0.0;
+    p.nzero = -0.0;
     return p;
 }
 

@@ -24,7 +24,8 @@ struct TrafficK {
     int local;           // CGB with the box-evaluated contraction matrix
     int sound;           // outward rounding
     double c6l, c6u;     // h / 6 rounded down and up (outward rounding)
-    double one = 1.0;    // read at run time (fadd)
+    double one = 1.0;    // read at run time (fadd; the directed sums of the outward-rounded kernel)
+    double pzero = 0.0, nzero = -0.0;   // read at run time (the outward-rounded kernel's directed products)
     // CGB radius in nested form (stencil.cu, traffic_radius_step): per stage
     // s the coefficient c_s in (h/4, h/3, h/2, h) and c_s v, c_s w
     double rc[4], rv[4], rw[4];

@@ -515,16 +515,28 @@ struct SoundArgs {
     int *status;
 };
 
+// Directed-rounding sums and products issued as fused multiply-adds:
+// fma_rd(a, 1, b) and fma_ru(a, 1, b) round a + b exactly as the plain
+// directed sums do, and fma_rd(a, b, +0), fma_ru(a, b, -0) round a b exactly
+// as the plain directed products do (an exactly zero product keeps its sign
+// under that addend in that mode), so the box is the same bit for bit; the
+// FP64 pipe retires the fused forms faster.  1, +0 and -0 come from the
+// kernel parameters, or the compiler would fold the fused forms back.
+__device__ __forceinline__ double add_rd(double a, double b, const TrafficK &p) { return __fma_rd(a, p.one, b); }
+__device__ __forceinline__ double add_ru(double a, double b, const TrafficK &p) { return __fma_ru(a, p.one, b); }
+__device__ __forceinline__ double mul_rd(double a, double b, const TrafficK &p) { return __fma_rd(a, b, p.pzero); }
+__device__ __forceinline__ double mul_ru(double a, double b, const TrafficK &p) { return __fma_ru(a, b, p.nzero); }
+
 // flux of R6 out of cell g, as an interval; y?n: the right neighbour
 __device__ __forceinline__ void flux_iv(const TrafficK &p, double yl, double yu, double yln, double yun, int64_t g,
                                         int64_t n, double &fl, double &fu) {
-    const double vl = __dmul_rd(p.v, yl), vu = __dmul_ru(p.v, yu);
+    const double vl = mul_rd(p.v, yl, p), vu = mul_ru(p.v, yu, p);
     if (g == n - 1) {
         fl = kmin(p.cap, vl);
         fu = kmin(p.cap, vu);
     } else {
-        fl = kmin(p.cap, kmin(vl, __dmul_rd(p.w, __dadd_rd(p.xbar, -yun))));
-        fu = kmin(p.cap, kmin(vu, __dmul_ru(p.w, __dadd_ru(p.xbar, -yln))));
+        fl = kmin(p.cap, kmin(vl, mul_rd(p.w, add_rd(p.xbar, -yun, p), p)));
+        fu = kmin(p.cap, kmin(vu, mul_ru(p.w, add_ru(p.xbar, -yln, p), p)));
     }
 }
 
@@ -539,8 +551,8 @@ __device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[
         for (int j = 0; j < KC; ++j) {
             const int64_t g = g0 + j;
             double acc = (g == 0) ? hp : 0.0;
-            if (g > 0) acc = __dadd_ru(acc, __dmul_ru(p.v, EU[j]));
-            if (g < n - 1) acc = __dadd_ru(acc, __dmul_ru(p.w, EU[j + 2]));
+            if (g > 0) acc = add_ru(acc, mul_ru(p.v, EU[j], p), p);
+            if (g < n - 1) acc = add_ru(acc, mul_ru(p.w, EU[j + 2], p), p);
             ku[j] = (g < 0 || g >= n) ? 0.0 : acc;
         }
         return;
@@ -558,7 +570,7 @@ __device__ __forceinline__ void sound_rhs(const TrafficK &p, const double (&yl)[
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
         const int64_t g = g0 + j;
-        const double a = __dadd_rd(fl[j], -fu[j + 1]), b = __dadd_ru(fu[j], -fl[j + 1]);
+        const double a = add_rd(fl[j], -fu[j + 1], p), b = add_ru(fu[j], -fl[j + 1], p);
         const bool in = g >= 0 && g < n;
         kl[j] = in ? a : 0.0;
         ku[j] = in ? b : 0.0;
@@ -577,8 +589,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound
     // inflow of this half: MM the corner's own input, CGB the center's interval
     double dl, du;
     if (METHOD == MM) { dl = du = HALF ? p.d_hi : p.d_lo; }
-    else { dl = 0.5 * __dadd_rd(p.d_lo, p.d_hi); du = 0.5 * __dadd_ru(p.d_lo, p.d_hi); }
-    const double hp = 0.5 * __dadd_ru(p.d_hi, -p.d_lo);
+    else { dl = 0.5 * add_rd(p.d_lo, p.d_hi, p); du = 0.5 * add_ru(p.d_lo, p.d_hi, p); }
+    const double hp = 0.5 * add_ru(p.d_hi, -p.d_lo, p);
     const double hh = 0.5 * a.h;
     for (int64_t t = warp; t < a.ntiles; t += nwarps) {
         const int64_t own0 = t * a.W;
@@ -593,8 +605,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound
                 const bool owned = g >= own0 && g < own0 + a.W && in;
                 if (HALF == 0 && owned && !(kle(lo, hi) && kfinite(lo) && kfinite(hi))) flags |= ST_BADINPUT;
                 if (METHOD == MM) { zl[j] = zu[j] = HALF ? hi : lo; }
-                else if (HALF == 0) { zl[j] = 0.5 * __dadd_rd(lo, hi); zu[j] = 0.5 * __dadd_ru(lo, hi); }
-                else { zl[j] = 0.0; zu[j] = 0.5 * __dadd_ru(hi, -lo); }
+                else if (HALF == 0) { zl[j] = 0.5 * add_rd(lo, hi, p); zu[j] = 0.5 * add_ru(lo, hi, p); }
+                else { zl[j] = 0.0; zu[j] = 0.5 * add_ru(hi, -lo, p); }
             } else {
                 zl[j] = (in && !RADIUS) ? __ldg(a.inL[HALF] + g) : 0.0;
                 zu[j] = in ? __ldg(a.inU[HALF] + g) : 0.0;
@@ -611,11 +623,11 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound
 #pragma unroll
                 for (int j = 0; j < KC; ++j) {
                     if (st == 0) { au[j] = ku[j]; al[j] = kl[j]; }
-                    else if (st == 3) { au[j] = __dadd_ru(au[j], ku[j]); al[j] = __dadd_rd(al[j], kl[j]); }
-                    else { au[j] = __dadd_ru(au[j], 2.0 * ku[j]); al[j] = __dadd_rd(al[j], 2.0 * kl[j]); }
+                    else if (st == 3) { au[j] = add_ru(au[j], ku[j], p); al[j] = add_rd(al[j], kl[j], p); }
+                    else { au[j] = add_ru(au[j], 2.0 * ku[j], p); al[j] = add_rd(al[j], 2.0 * kl[j], p); }
                     if (st < 3) {
-                        yu[j] = __dadd_ru(zu[j], __dmul_ru(cs, ku[j]));
-                        if (!RADIUS) yl[j] = __dadd_rd(zl[j], __dmul_rd(cs, kl[j]));
+                        yu[j] = add_ru(zu[j], mul_ru(cs, ku[j], p), p);
+                        if (!RADIUS) yl[j] = add_rd(zl[j], mul_rd(cs, kl[j], p), p);
                     }
                 }
             }
@@ -623,8 +635,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 2) stencil_traffic_sound
 #pragma unroll
             for (int j = 0; j < KC; ++j) {
                 const double ql = RADIUS ? au[j] : al[j];
-                zu[j] = __dadd_ru(zu[j], __dmul_ru(dkey(au[j]) >= 0 ? p.c6u : p.c6l, au[j]));
-                if (!RADIUS) zl[j] = __dadd_rd(zl[j], __dmul_rd(dkey(ql) >= 0 ? p.c6l : p.c6u, ql));
+                zu[j] = add_ru(zu[j], mul_ru(dkey(au[j]) >= 0 ? p.c6u : p.c6l, au[j], p), p);
+                if (!RADIUS) zl[j] = add_rd(zl[j], mul_rd(dkey(ql) >= 0 ? p.c6l : p.c6u, ql, p), p);
             }
         }
 #pragma unroll
