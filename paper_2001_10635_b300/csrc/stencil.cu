@@ -501,8 +501,10 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4
 // interval [zl, zu] of binary64 numbers containing the exact-arithmetic value
 // (MM halves, CGB center) or, for the CGB radius, only its upper end (all its
 // terms are nonnegative).  The operations are the ones a plain evaluation
-// takes, each with its directed-rounding instruction: products and sums are
-// not fused, so that each result is the directed rounding of the exact one.
+// takes, each rounded once in its direction: no product is fused into a sum,
+// so that each result is the directed rounding of the exact one (a sum or a
+// product alone is issued as a directed fused multiply-add with 1 or a signed
+// zero, which rounds it identically: add_rd and the others below).
 struct SoundArgs {
     const double *xlo, *xhi;
     const double *inL[2], *inU[2];   // interval state per half (previous launch)
