@@ -706,6 +706,9 @@ def run_profile_case(a):
 
     dev = torch.device("cuda", 0)
     to = lambda v: torch.tensor(v, dtype=torch.float64, device=dev)
+    for kv in a.case_opt:
+        key, val = kv.split("=")
+        R.reach_set_option(int(key), int(val))
 
     if a.profile_case.startswith("ks_"):
         n = a.case_n or (1 << 20)
@@ -811,6 +814,9 @@ def main():
     ap.add_argument("--case-n", type=int, default=0)
     ap.add_argument("--case-m", type=int, default=0)
     ap.add_argument("--case-t", type=float, default=0.0)
+    ap.add_argument("--case-opt", action="append", default=[],
+                    help="KEY=VALUE: a library option (reach_set_option) for the profile case, e.g. 12=1 for one "
+                         "launch per RK4 step")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
