@@ -93,14 +93,8 @@ __device__ __forceinline__ void exchange(const double (&y)[KC], double (&e)[KC +
     }
 }
 
-// a + b, as a fused multiply-add (FA, see fadd) or plain: the kernel that
-// holds both traffic halves per warp sits at the register limit, where the
-// extra operand spills (19% slower fused)
-template <bool FA>
-__device__ __forceinline__ double dsum(double a, double b, double one) { return FA ? fadd(a, b, one) : a + b; }
-
 // one RK4 stage update of a lane's cells (stage is a compile-time constant)
-template <int STAGE, int KC, bool FA = true>
+template <int STAGE, int KC>
 __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], double (&acc)[KC],
                                            const double (&k)[KC], const StepArgs &a) {
     const double h = a.h, hh = a.hh, h6 = a.h6;
@@ -109,7 +103,7 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
         if (STAGE == 0) { acc[j] = k[j]; y[j] = fma(hh, k[j], z[j]); }
         if (STAGE == 1) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(hh, k[j], z[j]); }
         if (STAGE == 2) { acc[j] = fma(2.0, k[j], acc[j]); y[j] = fma(h, k[j], z[j]); }
-        if (STAGE == 3) { acc[j] = dsum<FA>(k[j], acc[j], a.one); z[j] = fma(h6, acc[j], z[j]); y[j] = z[j]; }
+        if (STAGE == 3) { acc[j] = fadd(k[j], acc[j], a.one); z[j] = fma(h6, acc[j], z[j]); y[j] = z[j]; }
     }
 }
 
@@ -118,7 +112,7 @@ __device__ __forceinline__ void rk4_update(double (&z)[KC], double (&y)[KC], dou
 // (min(cap, v y_g) for the last cell), the inflow of cell 0 is d, and cells
 // outside [0, n) carry no flux.  IN: every flux of the tile is between two
 // cells of the chain, so none of those cases arises and the tests are skipped.
-template <bool POW2, int KC, bool IN = false, bool FA = true>
+template <bool POW2, int KC, bool IN = false>
 __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)[KC], int64_t g0,
                                             int64_t n, double d, double (&k)[KC]) {
     double e[KC + 2];
@@ -157,7 +151,7 @@ __device__ __forceinline__ void traffic_rhs(const TrafficK &p, const double (&y)
     double fl = __shfl_up_sync(0xffffffffu, f[KC - 1], 1);
     if (!IN) fl = (g0 == 0) ? d : fl;
 #pragma unroll
-    for (int j = 0; j < KC; ++j) k[j] = dsum<FA>(-f[j], j == 0 ? fl : f[j - 1], p.one);
+    for (int j = 0; j < KC; ++j) k[j] = fadd(-f[j], j == 0 ? fl : f[j - 1], p.one);
 }
 
 // CGB radius of the traffic chain, r' = C r + [p] with the constant C of
@@ -460,22 +454,22 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) stencil_traffic_cgbl_rk4
             double yc[KC], yr[KC], ac[KC], ar[KC], kc[KC], kr[KC];
 #pragma unroll
             for (int j = 0; j < KC; ++j) { yc[j] = zc[j]; yr[j] = zr[j]; }
-            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
+            traffic_rhs<POW2, KC>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<0, KC, false>(zc, yc, ac, kc, a);
-            rk4_update<0, KC, false>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<0>(zc, yc, ac, kc, a);
+            rk4_update<0>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<1, KC, false>(zc, yc, ac, kc, a);
-            rk4_update<1, KC, false>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<1>(zc, yc, ac, kc, a);
+            rk4_update<1>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<2, KC, false>(zc, yc, ac, kc, a);
-            rk4_update<2, KC, false>(zr, yr, ar, kr, a);
-            traffic_rhs<POW2, KC, false, false>(p, yc, g0, n, p.d_c, kc);
+            rk4_update<2>(zc, yc, ac, kc, a);
+            rk4_update<2>(zr, yr, ar, kr, a);
+            traffic_rhs<POW2, KC>(p, yc, g0, n, p.d_c, kc);
             traffic_growth_local(p, yc, yr, g0, n, kr);
-            rk4_update<3, KC, false>(zc, yc, ac, kc, a);
-            rk4_update<3, KC, false>(zr, yr, ar, kr, a);
+            rk4_update<3>(zc, yc, ac, kc, a);
+            rk4_update<3>(zr, yr, ar, kr, a);
         }
 #pragma unroll
         for (int j = 0; j < KC; ++j) {
