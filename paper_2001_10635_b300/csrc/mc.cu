@@ -941,8 +941,9 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
     q.a0 = bc2(a.qf[0]); q.a1 = bc2(a.qf[1]); q.a2 = bc2(a.qf[2]); q.nk = bc2(-a.qf[3]);
     const float2 h = bc2(a.hf[0]), hh = bc2(a.hf[1]), h6 = bc2(a.hf[2]), two = bc2(2.f);
     int flags = 0;
-    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
-        const uint32_t p = it / a.ntile, t = it - p * a.ntile;   // 32-bit division
+    // a 64-bit counter: it + nwarps must not wrap below items (< 2^32)
+    for (uint64_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const uint32_t p = (uint32_t)it / a.ntile, t = (uint32_t)it - p * a.ntile;   // 32-bit division
         const int64_t own0 = (int64_t)t * a.W;
         const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
         const int64_t base = (int64_t)((uint64_t)p * (uint64_t)a.ns);
@@ -1107,8 +1108,8 @@ __global__ void __launch_bounds__(256, MINB) mc_rows64(RowStep a, const double *
     const double one = a.one, nz = a.nzero;
     const double h = a.h, hh = 0.5 * a.h, h6 = a.h6;
     int flags = 0;
-    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
-        const uint32_t j = it / a.ntile, t = it - j * a.ntile;   // 32-bit division
+    for (uint64_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const uint32_t j = (uint32_t)it / a.ntile, t = (uint32_t)it - j * a.ntile;   // 32-bit division
         const int64_t own0 = (int64_t)t * a.W;
         const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
         const int64_t base = (int64_t)((uint64_t)j * (uint64_t)a.ns);
