@@ -205,9 +205,10 @@ REACH_API int64_t reach_mc_samples(int64_t n, double eps, double delta);
      - x0_lo, x0_hi, lo, hi must be device pointers (REACH_EINVAL otherwise);
        w_lo, w_hi (traffic inflow) may be host or device.
      - Every call looks up the buffer's device address on the current
-       device (cudaGetSymbolAddress, which allocates nothing); the first call
-       on a device also makes the runtime load the module that holds the
-       buffer, so make that first call before any stream capture begins.
+       device (cudaGetSymbolAddress, which allocates nothing).
+     - No call can be captured into a CUDA graph: each synchronises its
+       stream and copies the status word to the host before it returns.
+       Do not call it while its stream is being captured.
      - All calls share the buffer: calls whose work overlaps on the GPU (on
        different streams, or from several threads) race and give wrong
        results.  Each call clears the status word before use.
