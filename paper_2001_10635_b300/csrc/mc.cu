@@ -927,23 +927,35 @@ struct RowStep {
     void *out;
     int first;
     int *status;
+    unsigned *ctr;            // mc_rows: two item counters; this launch takes ctr[slot]
+    int slot;                 // and clears the other one for the next launch
 };
 
 template <int SYS, int KC>
 __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
     const unsigned lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    const uint32_t items = a.ntile * a.P;   // < 2^32 (checked on the host)
+    const uint32_t items = a.ntile * a.P;   // items + warps < 2^32 (checked on the host)
     const int64_t n = a.n;
+    unsigned *ctr = a.ctr + a.slot;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr[a.slot ^ 1] = 0u;   // the next launch's counter
     Q2 q;
     q.cap = bc2(a.qf[0]); q.v = bc2(a.qf[1]); q.nw = bc2(-a.qf[2]); q.wxbar = bc2(a.qf[3]);
     q.a0 = bc2(a.qf[0]); q.a1 = bc2(a.qf[1]); q.a2 = bc2(a.qf[2]); q.nk = bc2(-a.qf[3]);
     const float2 h = bc2(a.hf[0]), hh = bc2(a.hf[1]), h6 = bc2(a.hf[2]), two = bc2(2.f);
     int flags = 0;
-    // a 64-bit counter: it + nwarps must not wrap below items (< 2^32)
-    for (uint64_t it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += nwarps) {
-        const uint32_t p = (uint32_t)it / a.ntile, t = (uint32_t)it - p * a.ntile;   // 32-bit division
+    // Warps take items from the counter as they finish the previous one, so a
+    // warp that the scheduler favours takes more of them (with a fixed stride
+    // the favoured warps finish first and their SM runs the rest with fewer
+    // warps).  Lane 0 asks for the next item before the warp works on the
+    // current one.  Each warp asks once more than it takes items, so the
+    // counter ends at items + warps.
+    uint32_t nxt = 0;
+    if (lane == 0) nxt = atomicAdd(ctr, 1u);
+    uint32_t it = __shfl_sync(0xffffffffu, nxt, 0);
+    while (it < items) {
+        if (lane == 0) nxt = atomicAdd(ctr, 1u);
+        const uint32_t p = it / a.ntile, t = it - p * a.ntile;
         const int64_t own0 = (int64_t)t * a.W;
         const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
         const int64_t base = (int64_t)((uint64_t)p * (uint64_t)a.ns);
@@ -1062,6 +1074,7 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
                 if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(out + base + g, z[r]);
             }
         }
+        it = __shfl_sync(0xffffffffu, nxt, 0);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -1536,6 +1549,7 @@ static int launch_stream2_v(McStep a, int64_t N, void *bufA, void *bufB, int S_a
 // state into (lo, hi)
 template <int SYS, int KC>
 static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double *lo, double *hi, cudaStream_t st) {
+    REACH_CUDA(cudaMemsetAsync(a.ctr, 0, 2 * sizeof(unsigned), st));
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
     int S = opt_steps() > 0 ? (int)opt_steps() : 3;
     while (S > 1 && 2 * 4 * R * S >= 32 * KC / 2) --S;   // keep the halo below half the warp tile
@@ -1555,11 +1569,12 @@ static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double 
         a.first = (q == 0);
         a.in = buf[q % 2];
         a.out = buf[(q + 1) % 2];
+        a.slot = (int)(q % 2);
         const int64_t ntile = (a.n + a.W - 1) / a.W;
-        if (ntile * (int64_t)a.P >= (1LL << 32)) return REACH_EINVAL;
-        a.ntile = (unsigned)ntile;
         const int64_t items = ntile * (int64_t)a.P;
         const int64_t blocks = std::min<int64_t>((items + 7) / 8, (int64_t)sms * per_sm);
+        if (items + 8 * blocks >= (1LL << 32)) return REACH_EINVAL;   // the 32-bit item counter
+        a.ntile = (unsigned)ntile;
         mc_rows<SYS, KC><<<(unsigned)blocks, 256, 0, st>>>(a);
         REACH_LAUNCHED("mc_rows");
         done += s;
@@ -1750,7 +1765,9 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         r.status = base.status;
         float2 *bufA, *bufB;
         const size_t bytes = (size_t)r.ns * r.P * sizeof(float2);
-        if ((rc = sg.scratch(bytes, (void **)&bufA)) || (rc = sg.scratch(bytes, (void **)&bufB))) return rc;
+        if ((rc = sg.scratch(bytes, (void **)&bufA)) || (rc = sg.scratch(bytes, (void **)&bufB)) ||
+            (rc = sg.scratch(2 * sizeof(unsigned), (void **)&r.ctr)))
+            return rc;
         const int kc = lay == 8 ? 8 : (lay == 10 ? 16 : 12);
         if (sys->kind == REACH_TRAFFIC) {
             if (kc == 8) return launch_rows<REACH_TRAFFIC, 8>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
