@@ -1736,11 +1736,11 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         // pair-row layout (mc_rows, the default; 12 rows per lane unless the
         // option picks 8 or 16): no per-block partials, the reduction reads
         // the final state.  1024 samples of the 2^20-point KS grid over 500
-        // steps: 0.762 s against 0.870 s for the best block layout (6), 0.876
-        // s with 8 rows per lane (halo 19% of the warp tile), 0.782 s with 16
-        // (spills at 128 registers); 256 samples of the 2^20-cell chain over
-        // 200 steps: 0.062 s against 0.076 s (layout 4).  An L2 prefetch of
-        // each warp's next item gained nothing on the KS grid (2% traffic).
+        // steps: 0.699 s against 0.870 s for the best block layout (6), 0.789
+        // s with 8 rows per lane (halo 19% of the warp tile), 0.720 s with
+        // 16; 256 samples of the 2^20-cell chain over 200 steps: 0.061 s
+        // against 0.076 s (layout 4).  An L2 prefetch of each warp's next
+        // item gained nothing on the KS grid (2% traffic).
         if (n > INT32_MAX - 64) return REACH_EINVAL;
         RowStep r;
         memset(&r, 0, sizeof r);
