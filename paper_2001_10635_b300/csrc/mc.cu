@@ -931,11 +931,34 @@ struct RowStep {
     int slot;                 // and clears the other one for the next launch
 };
 
+// 16-byte global -> shared copy by the executing thread (cp.async, cached in
+// L2 only); complete and visible to that thread after cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// mc_rows copies the next item's rows ahead on the traffic chain (2^20 cells,
+// 256 samples, 200 steps: 0.0599 s against 0.0613 s); on the KS grid, bound by
+// the FP32 pipe, the copies cost more than they hide (1024 samples, 500 steps:
+// 0.717 s against 0.699 s), so it loads each item's rows when it starts it
+template <int SYS>
+__host__ __device__ constexpr bool rows_prefetch() { return SYS == REACH_TRAFFIC; }
+// dynamic shared memory of mc_rows: per warp two stage buffers of 32 KC / 2
+// float4 (a lane's rows of one item, r-major so that a warp's accesses to row
+// pair r are 512 contiguous bytes)
+template <int SYS, int KC>
+constexpr size_t rows_stage_bytes() { return rows_prefetch<SYS>() ? 8 * 2 * (KC / 2) * 32 * sizeof(float4) : 0; }
+
 template <int SYS, int KC>
 __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
     constexpr int R = (SYS == REACH_KS) ? 2 : 1;
+    constexpr bool PF = rows_prefetch<SYS>();
+    extern __shared__ float4 rows_stage[];
     const unsigned lane = threadIdx.x & 31;
-    const uint32_t items = a.ntile * a.P;   // items + warps < 2^32 (checked on the host)
+    float4 *stage = rows_stage + (threadIdx.x >> 5) * (2 * (KC / 2) * 32) + lane;
+    const uint32_t items = a.ntile * a.P;   // items + 2 warps < 2^32 (checked on the host)
     const int64_t n = a.n;
     unsigned *ctr = a.ctr + a.slot;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr[a.slot ^ 1] = 0u;   // the next launch's counter
@@ -948,13 +971,24 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
     // warp that the scheduler favours takes more of them (with a fixed stride
     // the favoured warps finish first and their SM runs the rest with fewer
     // warps).  Lane 0 asks for the next item before the warp works on the
-    // current one.  Each warp asks once more than it takes items, so the
-    // counter ends at items + warps.
-    uint32_t nxt = 0;
-    if (lane == 0) nxt = atomicAdd(ctr, 1u);
-    uint32_t it = __shfl_sync(0xffffffffu, nxt, 0);
+    // current one.  With PF a warp knows its next item while it works on the
+    // current one and copies the next item's rows into its other stage buffer
+    // meanwhile (launches after the first, lanes whose run lies inside the
+    // chain), and lane 0 asks for the item after that.  One lane's successive
+    // requests are ordered, so a warp's items increase and it stops at the
+    // first one past the end, having asked once (twice with PF) past the end:
+    // the counter ends at items + warps (items + 2 warps).
+    uint32_t req = 0, req2 = 0;
+    if (lane == 0) {
+        req = atomicAdd(ctr, 1u);
+        if (PF) req2 = atomicAdd(ctr, 1u);
+    }
+    uint32_t it = __shfl_sync(0xffffffffu, req, 0);
+    uint32_t nx = PF ? __shfl_sync(0xffffffffu, req2, 0) : 0u;
+    bool staged = false;   // this lane's rows of item `it` are in stage buffer `sb`
+    int sb = 0;
     while (it < items) {
-        if (lane == 0) nxt = atomicAdd(ctr, 1u);
+        if (lane == 0) req = atomicAdd(ctr, 1u);
         const uint32_t p = it / a.ntile, t = it - p * a.ntile;
         const int64_t own0 = (int64_t)t * a.W;
         const int64_t g0 = own0 - a.H + (int64_t)(lane * KC);
@@ -987,12 +1021,23 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
                 z[r] = v;
             }
         } else if (whole) {
-            const float4 *src = reinterpret_cast<const float4 *>(in + base + g0);   // g0 and base even
+            if (PF && staged) {
+                cp_async_wait_all();
+                const float4 *src = stage + sb * ((KC / 2) * 32);
 #pragma unroll
-            for (int r = 0; r < KC / 2; ++r) {
-                const float4 v = __ldcs(src + r);
-                z[2 * r] = make_float2(v.x, v.y);
-                z[2 * r + 1] = make_float2(v.z, v.w);
+                for (int r = 0; r < KC / 2; ++r) {
+                    const float4 v = src[r * 32];
+                    z[2 * r] = make_float2(v.x, v.y);
+                    z[2 * r + 1] = make_float2(v.z, v.w);
+                }
+            } else {
+                const float4 *src = reinterpret_cast<const float4 *>(in + base + g0);   // g0 and base even
+#pragma unroll
+                for (int r = 0; r < KC / 2; ++r) {
+                    const float4 v = __ldcs(src + r);
+                    z[2 * r] = make_float2(v.x, v.y);
+                    z[2 * r + 1] = make_float2(v.z, v.w);
+                }
             }
         } else {
 #pragma unroll
@@ -1002,6 +1047,22 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
                 if (SYS == REACH_KS) g = wrap_index(g, n);
                 else ok = g >= 0 && g < n;
                 z[r] = ok ? __ldcs(in + base + g) : bc2(0.f);
+            }
+        }
+        // the next item's rows into the other buffer while this one computes
+        // (its g0 is even like this one's: W and H are even)
+        sb ^= 1;
+        staged = false;
+        if (PF && !a.first && nx < items) {
+            const uint32_t p2 = nx / a.ntile, t2 = nx - p2 * a.ntile;
+            const int64_t g2 = (int64_t)t2 * a.W - a.H + (int64_t)(lane * KC);
+            if (g2 >= 0 && g2 + KC <= n) {
+                const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)((uint64_t)p2 * (uint64_t)a.ns) + g2);
+                float4 *dst = stage + sb * ((KC / 2) * 32);
+#pragma unroll
+                for (int r = 0; r < KC / 2; ++r) cp_async16(dst + r * 32, src + r);
+                cp_async_commit();
+                staged = true;
             }
         }
         // every flux of the lane's run between two cells of the chain; the
@@ -1074,8 +1135,14 @@ __global__ void __launch_bounds__(256, 2) mc_rows(RowStep a) {
                 if (g >= own0 && g < own0 + a.W && g >= 0 && g < n) __stcs(out + base + g, z[r]);
             }
         }
-        it = __shfl_sync(0xffffffffu, nxt, 0);
+        if (PF) {
+            it = nx;
+            nx = __shfl_sync(0xffffffffu, req, 0);
+        } else {
+            it = __shfl_sync(0xffffffffu, req, 0);
+        }
     }
+    if (PF) cp_async_wait_all();   // nothing stays in flight (a copy is only made for an item the warp then takes)
     if (flags) atomicOr(a.status, flags);
 }
 
@@ -1558,7 +1625,9 @@ static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double 
     int dev = 0, sms = 148, per_sm = 2;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    REACH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_rows<SYS, KC>, 256, 0));
+    constexpr size_t smem = rows_stage_bytes<SYS, KC>();
+    REACH_CUDA(cudaFuncSetAttribute(mc_rows<SYS, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    REACH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mc_rows<SYS, KC>, 256, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t done = 0;
     for (int64_t q = 0; q < L; ++q) {
@@ -1573,9 +1642,9 @@ static int launch_rows(RowStep a, int64_t N, float2 *bufA, float2 *bufB, double 
         const int64_t ntile = (a.n + a.W - 1) / a.W;
         const int64_t items = ntile * (int64_t)a.P;
         const int64_t blocks = std::min<int64_t>((items + 7) / 8, (int64_t)sms * per_sm);
-        if (items + 8 * blocks >= (1LL << 32)) return REACH_EINVAL;   // the 32-bit item counter
+        if (items + 16 * blocks >= (1LL << 32)) return REACH_EINVAL;   // the 32-bit item counter
         a.ntile = (unsigned)ntile;
-        mc_rows<SYS, KC><<<(unsigned)blocks, 256, 0, st>>>(a);
+        mc_rows<SYS, KC><<<(unsigned)blocks, 256, smem, st>>>(a);
         REACH_LAUNCHED("mc_rows");
         done += s;
     }
@@ -1738,7 +1807,7 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         // the final state.  1024 samples of the 2^20-point KS grid over 500
         // steps: 0.699 s against 0.870 s for the best block layout (6), 0.789
         // s with 8 rows per lane (halo 19% of the warp tile), 0.720 s with
-        // 16; 256 samples of the 2^20-cell chain over 200 steps: 0.061 s
+        // 16; 256 samples of the 2^20-cell chain over 200 steps: 0.060 s
         // against 0.076 s (layout 4).  An L2 prefetch of each warp's next
         // item gained nothing on the KS grid (2% traffic).
         if (n > INT32_MAX - 64) return REACH_EINVAL;
