@@ -1372,14 +1372,23 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
         c.al[d] = tau / (T)J[d];
     }
     const T h = (T)a.h, fa = (T)p.a, fg = (T)p.g;
+    // sines and cosines at the step start: taken afresh every QUAD_ANCHOR
+    // steps and carried by angle addition over each step's increment in
+    // between; the stages' by angle addition over the small stage increment
+    // (as quad_box does).  A sincosf at every step start kept the FP64 pipe
+    // 82% busy in the binary32 kernel (ncu), which set its rate.
+    T s0[3], c0[3], pq[3];   // pq: the angles s0, c0 belong to
     for (int64_t s = 0; s < a.N; ++s) {
-        // sines and cosines at the step start; the stages' by angle addition
-        // over the small stage increment (as quad_box does)
-        T s0[3], c0[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if constexpr (sizeof(T) == 4) sincosf(c.q[d], &s0[d], &c0[d]);
-            else sincos(c.q[d], &s0[d], &c0[d]);
+            if (s % QUAD_ANCHOR == 0) {
+                if constexpr (sizeof(T) == 4) sincosf(c.q[d], &s0[d], &c0[d]);
+                else sincos(c.q[d], &s0[d], &c0[d]);
+            } else {
+                const T t0 = s0[d], t1 = c0[d];
+                shifted_sincos(c.q[d], c.q[d] - pq[d], t0, t1, s0[d], c0[d]);
+            }
+            pq[d] = c.q[d];
         }
         QSums<T> m;
 #pragma unroll

@@ -12,9 +12,6 @@
 
 namespace reach {
 
-// steps between fresh sines and cosines of the step-start angles
-constexpr int64_t QUAD_ANCHOR = 32;
-
 struct QuadArgs {
     const double *xlo, *xhi, *wlo, *whi;
     double *lo, *hi;

@@ -93,6 +93,11 @@ __device__ __forceinline__ void iv_sincos_at(double lo, double hi, double s0, do
 // the rounding of the result); a larger d falls back to sincos.
 constexpr double Q_SMALL = 0.0625;
 
+// steps between fresh sines and cosines of the step-start angles; in between
+// a step's values follow from the previous step's by angle addition, which
+// bounds the rounding carried from step to step to that many additions
+constexpr int64_t QUAD_ANCHOR = 32;
+
 __device__ __forceinline__ void small_sincos(double d, double &s, double &c) {
     const double d2 = d * d;
     const double ps = fma(d2, fma(d2, fma(d2, 2.7557319223985893e-06, -0.0001984126984126984),
