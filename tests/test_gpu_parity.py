@@ -563,15 +563,18 @@ def test_mc32_samples_inside_mm_within_the_binary32_tolerance(kind, n, m, kernel
 
 
 @pytest.mark.parametrize("kind,n,m,S", [("ks", 1500, 100, 2), ("traffic", 1500, 77, 2), ("ks", 600, 64, 1),
-                                        ("traffic", 3001, 130, 3), ("ks", 150, 33, 2), ("traffic", 70, 1, 1)])
+                                        ("traffic", 3001, 130, 3), ("ks", 150, 33, 2), ("traffic", 70, 1, 1),
+                                        ("traffic", 1 << 16, 256, 3), ("ks", 1 << 16, 128, 3)])
 def test_mc32_two_samples_per_lane_equal_one_bit_for_bit(kind, n, m, S):
     # the packed binary32 kernels (two samples per lane, in blocks of sample
     # rows or along the rows of a sample pair) perform each sample's operations
     # in the same order as the one-sample kernel: same box, bit for bit, for
     # every layout (grids shorter than one warp tile, where a lane's rows wrap
     # around the periodic grid or run past the chain, and a single sample,
-    # whose pair has no second sample, included); and it is the oracle's
-    # within TOL32
+    # whose pair has no second sample, included; and grids of 2^16 points,
+    # where each persistent warp of the pair-row kernel takes five to ten items
+    # from the device counter and, on the traffic chain, copies each next
+    # item's rows ahead); and it is the oracle's within TOL32
     lo, hi, wlo, whi, T, dt, prm, A = problem(kind, n, seed=13)
     T = 0.13 if kind == "traffic" else 0.0013
     R.reach_set_option(R.OPT_KERNEL, 1)
