@@ -1335,6 +1335,10 @@ __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, in
 }
 
 // ------------------------------------------------------------------ quadrotor swarm
+// fused multiply-add in the kernel's precision
+__device__ __forceinline__ float qfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double qfma(double a, double b, double c) { return fma(a, b, c); }
+
 // Lane = sample of one agent: a warp integrates 32 samples of agent k (blockIdx.x
 // * 4 + warp) over the whole horizon in registers (the agents are independent)
 // and reduces each of its 12 components over the samples; blockIdx.y is the
@@ -1372,34 +1376,69 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
         c.al[d] = tau / (T)J[d];
     }
     const T h = (T)a.h, fa = (T)p.a, fg = (T)p.g;
-    // sines and cosines at the step start: taken afresh every QUAD_ANCHOR
-    // steps and carried by angle addition over each step's increment in
-    // between; the stages' by angle addition over the small stage increment
-    // (as quad_box does).  A sincosf at every step start kept the FP64 pipe
-    // 82% busy in the binary32 kernel (ncu), which set its rate.
-    T s0[3], c0[3], pq[3];   // pq: the angles s0, c0 belong to
+    // Sines and cosines at the step start: taken afresh every QUAD_ANCHOR
+    // steps, and in between the previous step's last-stage values, those of
+    // q + d_3, which is the new step-start angle up to the rounding of the
+    // state update.  The stages' follow by angle addition over the stage
+    // increments d_1 = (h/2) w and d_2 = (h/2) X (Maclaurin series of sine
+    // and cosine), and d_3 = h X = 2 d_2 exactly (h = 2 (h/2)), so the last
+    // stage takes the double-angle formulas of d_2's sine and cosine; an
+    // increment beyond Q_SMALL falls back to sincos of the stage angle.  (A
+    // sincosf of each angle at every step start kept the FP64 pipe 82% busy
+    // in the binary32 kernel; carrying the step-start values by a separate
+    // angle addition cost 13 operations per angle and step.)
+    T s0[3], c0[3];
     for (int64_t s = 0; s < a.N; ++s) {
+        if (s % QUAD_ANCHOR == 0) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (s % QUAD_ANCHOR == 0) {
+            for (int d = 0; d < 3; ++d) {
                 if constexpr (sizeof(T) == 4) sincosf(c.q[d], &s0[d], &c0[d]);
                 else sincos(c.q[d], &s0[d], &c0[d]);
-            } else {
-                const T t0 = s0[d], t1 = c0[d];
-                shifted_sincos(c.q[d], c.q[d] - pq[d], t0, t1, s0[d], c0[d]);
             }
-            pq[d] = c.q[d];
         }
         QSums<T> m;
+        T sd2[3], cd2[3];   // sine and cosine of d_2, for the last stage
+        bool far2[3];       // d_2 beyond Q_SMALL
 #pragma unroll
         for (int st = 0; st < 4; ++st) {
-            T q[3], dq[3], sn[3], cs[3], acc[3];
-            stage_angles(c, st, h, q);
+            T dq[3], sn[3], cs[3], acc[3];
             stage_deltas(c, st, h, dq);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (st == 0) { sn[d] = s0[d]; cs[d] = c0[d]; }
-                else shifted_sincos(q[d], dq[d], s0[d], c0[d], sn[d], cs[d]);
+                if (st == 0) {
+                    sn[d] = s0[d];
+                    cs[d] = c0[d];
+                    continue;
+                }
+                T sd = T(0), cd = T(1);
+                bool near;
+                if (st == 3) {
+                    near = !far2[d];
+                    const T t = sd2[d] + sd2[d];
+                    sd = t * cd2[d];
+                    cd = qfma(-t, sd2[d], T(1));
+                } else {
+                    near = (dq[d] < T(0) ? -dq[d] : dq[d]) <= T(Q_SMALL);
+                    if (near) small_sincos(dq[d], sd, cd);
+                    if (st == 2) {
+                        sd2[d] = sd;
+                        cd2[d] = cd;
+                        far2[d] = !near;
+                    }
+                }
+                if (near) {
+                    sn[d] = qfma(s0[d], cd, c0[d] * sd);
+                    cs[d] = qfma(c0[d], cd, -(s0[d] * sd));
+                } else {
+                    T q[3];
+                    stage_angles(c, st, h, q);
+                    if constexpr (sizeof(T) == 4) sincosf(q[d], &sn[d], &cs[d]);
+                    else sincos(q[d], &sn[d], &cs[d]);
+                }
+                if (st == 3) {
+                    s0[d] = sn[d];   // the next step's start (unless it takes them afresh)
+                    c0[d] = cs[d];
+                }
             }
             quad_acc_trig<T>(sn, cs, fa, fg, acc);
             add_stage(m, acc, st);
