@@ -1339,6 +1339,68 @@ __global__ void mc_reduce(const double *plo, const double *phi, int64_t nblk, in
 __device__ __forceinline__ float qfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double qfma(double a, double b, double c) { return fma(a, b, c); }
 
+__device__ __forceinline__ float qabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double qabs(double a) { return fabs(a); }
+
+// The four stages of one RK4 step of a sample's chain, their accelerations
+// summed into m.  (s0, c0): the sines and cosines of the step-start angles,
+// replaced by those of the last stage, the next step's start.  The stages'
+// sines and cosines follow by angle addition over the stage increments d_1 =
+// (h/2) w and d_2 = (h/2) X (Maclaurin series of sine and cosine), and d_3 = h
+// X = 2 d_2 exactly (h = 2 (h/2)), so the last stage takes the double-angle
+// formulas of d_2's sine and cosine.  FAR: an increment beyond Q_SMALL may
+// occur; that stage takes sincos of its angle instead.
+template <class T, bool FAR>
+__device__ __forceinline__ void quad_mc_stages(const QChain<T> &c, T h, T fa, T fg, T (&s0)[3], T (&c0)[3],
+                                               QSums<T> &m) {
+    T sd2[3], cd2[3];   // sine and cosine of d_2, for the last stage
+    bool far2[3];       // d_2 beyond Q_SMALL
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        T dq[3], sn[3], cs[3], acc[3];
+        stage_deltas(c, st, h, dq);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (st == 0) {
+                sn[d] = s0[d];
+                cs[d] = c0[d];
+                continue;
+            }
+            T sd = T(0), cd = T(1);
+            bool near = true;
+            if (st == 3) {
+                if (FAR) near = !far2[d];
+                const T t = sd2[d] + sd2[d];
+                sd = t * cd2[d];
+                cd = qfma(-t, sd2[d], T(1));
+            } else {
+                if (FAR) near = qabs(dq[d]) <= T(Q_SMALL);
+                if (near) small_sincos(dq[d], sd, cd);
+                if (st == 2) {
+                    sd2[d] = sd;
+                    cd2[d] = cd;
+                    far2[d] = !near;
+                }
+            }
+            if (!FAR || near) {
+                sn[d] = qfma(s0[d], cd, c0[d] * sd);
+                cs[d] = qfma(c0[d], cd, -(s0[d] * sd));
+            } else {
+                T q[3];
+                stage_angles(c, st, h, q);
+                if constexpr (sizeof(T) == 4) sincosf(q[d], &sn[d], &cs[d]);
+                else sincos(q[d], &sn[d], &cs[d]);
+            }
+            if (st == 3) {
+                s0[d] = sn[d];
+                c0[d] = cs[d];
+            }
+        }
+        quad_acc_trig<T>(sn, cs, fa, fg, acc);
+        add_stage(m, acc, st);
+    }
+}
+
 // Lane = sample of one agent: a warp integrates 32 samples of agent k (blockIdx.x
 // * 4 + warp) over the whole horizon in registers (the agents are independent)
 // and reduces each of its 12 components over the samples; blockIdx.y is the
@@ -1379,14 +1441,13 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
     // Sines and cosines at the step start: taken afresh every QUAD_ANCHOR
     // steps, and in between the previous step's last-stage values, those of
     // q + d_3, which is the new step-start angle up to the rounding of the
-    // state update.  The stages' follow by angle addition over the stage
-    // increments d_1 = (h/2) w and d_2 = (h/2) X (Maclaurin series of sine
-    // and cosine), and d_3 = h X = 2 d_2 exactly (h = 2 (h/2)), so the last
-    // stage takes the double-angle formulas of d_2's sine and cosine; an
-    // increment beyond Q_SMALL falls back to sincos of the stage angle.  (A
-    // sincosf of each angle at every step start kept the FP64 pipe 82% busy
-    // in the binary32 kernel; carrying the step-start values by a separate
-    // angle addition cost 13 operations per angle and step.)
+    // state update (quad_mc_stages).  A step whose stage increments d_1 or d_2
+    // pass Q_SMALL runs the copy of the stages that falls back to sincos; the
+    // common copy holds no sincos call (with the calls in it, the compiler
+    // computed part of them at every stage: 12% more instructions).  (A
+    // sincosf of each angle at every step start kept the FP64 pipe 82% busy in
+    // the binary32 kernel; carrying the step-start values by a separate angle
+    // addition cost 13 operations per angle and step.)
     T s0[3], c0[3];
     for (int64_t s = 0; s < a.N; ++s) {
         if (s % QUAD_ANCHOR == 0) {
@@ -1396,53 +1457,15 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
                 else sincos(c.q[d], &s0[d], &c0[d]);
             }
         }
+        T d1[3], d2[3];
+        stage_deltas(c, 1, h, d1);
+        stage_deltas(c, 2, h, d2);
+        bool far = false;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) far = far || qabs(d1[d]) > T(Q_SMALL) || qabs(d2[d]) > T(Q_SMALL);
         QSums<T> m;
-        T sd2[3], cd2[3];   // sine and cosine of d_2, for the last stage
-        bool far2[3];       // d_2 beyond Q_SMALL
-#pragma unroll
-        for (int st = 0; st < 4; ++st) {
-            T dq[3], sn[3], cs[3], acc[3];
-            stage_deltas(c, st, h, dq);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (st == 0) {
-                    sn[d] = s0[d];
-                    cs[d] = c0[d];
-                    continue;
-                }
-                T sd = T(0), cd = T(1);
-                bool near;
-                if (st == 3) {
-                    near = !far2[d];
-                    const T t = sd2[d] + sd2[d];
-                    sd = t * cd2[d];
-                    cd = qfma(-t, sd2[d], T(1));
-                } else {
-                    near = (dq[d] < T(0) ? -dq[d] : dq[d]) <= T(Q_SMALL);
-                    if (near) small_sincos(dq[d], sd, cd);
-                    if (st == 2) {
-                        sd2[d] = sd;
-                        cd2[d] = cd;
-                        far2[d] = !near;
-                    }
-                }
-                if (near) {
-                    sn[d] = qfma(s0[d], cd, c0[d] * sd);
-                    cs[d] = qfma(c0[d], cd, -(s0[d] * sd));
-                } else {
-                    T q[3];
-                    stage_angles(c, st, h, q);
-                    if constexpr (sizeof(T) == 4) sincosf(q[d], &sn[d], &cs[d]);
-                    else sincos(q[d], &sn[d], &cs[d]);
-                }
-                if (st == 3) {
-                    s0[d] = sn[d];   // the next step's start (unless it takes them afresh)
-                    c0[d] = cs[d];
-                }
-            }
-            quad_acc_trig<T>(sn, cs, fa, fg, acc);
-            add_stage(m, acc, st);
-        }
+        if (far) quad_mc_stages<T, true>(c, h, fa, fg, s0, c0, m);
+        else quad_mc_stages<T, false>(c, h, fa, fg, s0, c0, m);
         chain_update(c, m, h);
     }
     double *plo = a.plo + (int64_t)blockIdx.y * a.n + 12 * k, *phi = a.phi + (int64_t)blockIdx.y * a.n + 12 * k;
