@@ -1342,19 +1342,42 @@ __device__ __forceinline__ double qfma(double a, double b, double c) { return fm
 __device__ __forceinline__ float qabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double qabs(double a) { return fabs(a); }
 
+// sin d and cos d for any d by argument halving (scaling and squaring): d is
+// halved k times into the range of the Maclaurin series, and the series'
+// values are doubled back k times by the double-angle formulas, each of
+// which about doubles the rounding error (k <= 3 for |d| <= 1/2); at most 40
+// halvings, so that an infinite d ends as a non-finite result
+template <class T>
+__device__ __forceinline__ void halved_sincos(T d, T &s, T &c) {
+    int k = 0;
+    while (qabs(d) > T(Q_SMALL) && k < 40) {
+        d = d * T(0.5);
+        ++k;
+    }
+    small_sincos(d, s, c);
+    for (int i = 0; i < k; ++i) {
+        const T t = s + s;
+        const T c2 = qfma(-t, s, T(1));
+        s = t * c;
+        c = c2;
+    }
+}
+
 // The four stages of one RK4 step of a sample's chain, their accelerations
 // summed into m.  (s0, c0): the sines and cosines of the step-start angles,
 // replaced by those of the last stage, the next step's start.  The stages'
 // sines and cosines follow by angle addition over the stage increments d_1 =
-// (h/2) w and d_2 = (h/2) X (Maclaurin series of sine and cosine), and d_3 = h
-// X = 2 d_2 exactly (h = 2 (h/2)), so the last stage takes the double-angle
-// formulas of d_2's sine and cosine.  FAR: an increment beyond Q_SMALL may
-// occur; that stage takes sincos of its angle instead.
+// (h/2) w and d_2 = (h/2) X, and d_3 = h X = 2 d_2 exactly (h = 2 (h/2)), so
+// the last stage takes the double-angle formulas of d_2's sine and cosine.
+// The increments' sines and cosines come from the Maclaurin series, or with
+// FAR (an increment may pass Q_SMALL) from halved_sincos.  Neither copy calls
+// sincos: with the calls in the loop, the compiler computed part of them at
+// every stage (their conversions kept the FP64 pipe 87% busy: 44.1 against
+// 37.2 ms for 10^6 agents x 32 samples x 200 steps).
 template <class T, bool FAR>
 __device__ __forceinline__ void quad_mc_stages(const QChain<T> &c, T h, T fa, T fg, T (&s0)[3], T (&c0)[3],
                                                QSums<T> &m) {
     T sd2[3], cd2[3];   // sine and cosine of d_2, for the last stage
-    bool far2[3];       // d_2 beyond Q_SMALL
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
         T dq[3], sn[3], cs[3], acc[3];
@@ -1366,31 +1389,21 @@ __device__ __forceinline__ void quad_mc_stages(const QChain<T> &c, T h, T fa, T 
                 cs[d] = c0[d];
                 continue;
             }
-            T sd = T(0), cd = T(1);
-            bool near = true;
+            T sd, cd;
             if (st == 3) {
-                if (FAR) near = !far2[d];
                 const T t = sd2[d] + sd2[d];
                 sd = t * cd2[d];
                 cd = qfma(-t, sd2[d], T(1));
             } else {
-                if (FAR) near = qabs(dq[d]) <= T(Q_SMALL);
-                if (near) small_sincos(dq[d], sd, cd);
+                if (FAR) halved_sincos(dq[d], sd, cd);
+                else small_sincos(dq[d], sd, cd);
                 if (st == 2) {
                     sd2[d] = sd;
                     cd2[d] = cd;
-                    far2[d] = !near;
                 }
             }
-            if (!FAR || near) {
-                sn[d] = qfma(s0[d], cd, c0[d] * sd);
-                cs[d] = qfma(c0[d], cd, -(s0[d] * sd));
-            } else {
-                T q[3];
-                stage_angles(c, st, h, q);
-                if constexpr (sizeof(T) == 4) sincosf(q[d], &sn[d], &cs[d]);
-                else sincos(q[d], &sn[d], &cs[d]);
-            }
+            sn[d] = qfma(s0[d], cd, c0[d] * sd);
+            cs[d] = qfma(c0[d], cd, -(s0[d] * sd));
             if (st == 3) {
                 s0[d] = sn[d];
                 c0[d] = cs[d];
@@ -1442,9 +1455,8 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
     // steps, and in between the previous step's last-stage values, those of
     // q + d_3, which is the new step-start angle up to the rounding of the
     // state update (quad_mc_stages).  A step whose stage increments d_1 or d_2
-    // pass Q_SMALL runs the copy of the stages that falls back to sincos; the
-    // common copy holds no sincos call (with the calls in it, the compiler
-    // computed part of them at every stage: 12% more instructions).  (A
+    // pass Q_SMALL takes the copy of the stages that halves them into the
+    // series' range.  (A
     // sincosf of each angle at every step start kept the FP64 pipe 82% busy in
     // the binary32 kernel; carrying the step-start values by a separate angle
     // addition cost 13 operations per angle and step.)

@@ -72,19 +72,21 @@ def test_mc_matches_oracle(prec, tol, m):
 @pytest.mark.parametrize("prec,tol", [(64, TOL64), (32, TOL32)])
 def test_mc_fast_rotation(prec, tol):
     # angular rates around the point where a stage's angle increment h/2 w
-    # passes 1/16 (12.5 rad/s at dt = 0.01): above it the stages take sine and
-    # cosine of the stage angle, below it the series of the increment; rates
-    # of 12.4..12.6 rad/s split one warp's samples between the two, and 50
-    # steps take the step-start values afresh once after the first step
-    wl = W.quad_swarm(4, seed=41)
-    for k, (lo, hi) in enumerate([(19.9, 20.1), (4.9, 5.1), (12.4, 12.6), (-30.1, -29.9)]):
+    # passes 1/16 (12.5 rad/s at dt = 0.01): above it the stages halve the
+    # increment into the range of its sine and cosine series and double the
+    # values back, below it they take the series directly; rates of
+    # 12.4..12.6 rad/s split one warp's samples between the two, 150 rad/s
+    # takes four halvings, and 50 steps take the step-start values afresh once
+    # after the first step
+    wl = W.quad_swarm(5, seed=41)
+    for k, (lo, hi) in enumerate([(19.9, 20.1), (4.9, 5.1), (12.4, 12.6), (-30.1, -29.9), (149.9, 150.1)]):
         for d in range(3):
             wl["x_lo"][12 * k + 9 + d] = lo * (1 - 0.2 * d)
             wl["x_hi"][12 * k + 9 + d] = hi * (1 - 0.2 * d)
     T, dt = 0.5, 0.01
     olo, ohi = O.reach("mc", "quad", wl["x_lo"], wl["x_hi"], wl["w_lo"], wl["w_hi"], t_final=T, dt=dt,
                        params=PRM, m=100, seed=3, prec=prec)
-    glo, ghi = gpu("mc", 48, wl, T, dt, m=100, seed=3, precision=prec)
+    glo, ghi = gpu("mc", 60, wl, T, dt, m=100, seed=3, precision=prec)
     assert_close(glo, olo, tol, f"mc{prec} lo")
     assert_close(ghi, ohi, tol, f"mc{prec} hi")
 
