@@ -382,8 +382,8 @@ REACH_API int reach_server_destroy(reach_server *s);
 #define REACH_OPT_MC_SB 6            /* on-chip MC: samples per block, 0 = auto (32 from 4736 samples, 8 from 1184,
                                         else 2), or 2 / 8 / 32 */
 #define REACH_OPT_MC_LAYOUT 7         /* streaming binary32 MC: 0 auto (two samples per lane, packed FP32
-                                        arithmetic, along the rows of a sample pair with 12 rows per lane:
-                                        as 9), 1 one sample per lane; 2..6 block shapes of the two-sample
+                                        arithmetic, along the rows of a sample pair with 14 rows per lane
+                                        on the KS grid, 12 on the traffic chain), 1 one sample per lane; 2..6 block shapes of the two-sample
                                         kernel on sample rows (warps x rows x blocks per SM: 16x16x1,
                                         32x8x1, 8x16x2, 16x8x2, and 16x16x1 persistent with the next tiles
                                         copied ahead by the TMA engine); 8 / 9 / 10 along sample-pair

@@ -1885,12 +1885,11 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         return launch_rows64<REACH_KS, 16, 1>(r, base.prm, base.N, bufA, bufB, dlo, dhi, sg.st);
     }
     if (pairs && (lay == 0 || lay >= 8)) {
-        // pair-row layout (mc_rows, the default; 12 rows per lane unless the
-        // option picks 8 or 16): no per-block partials, the reduction reads
-        // the final state.  1024 samples of the 2^20-point KS grid over 500
-        // steps: 0.699 s against 0.870 s for the best block layout (6), 0.789
-        // s with 8 rows per lane (halo 19% of the warp tile), 0.720 s with
-        // 16; 256 samples of the 2^20-cell chain over 200 steps: 0.060 s
+        // pair-row layout (mc_rows, the default): no per-block partials, the
+        // reduction reads the final state.  1024 samples of the 2^20-point KS
+        // grid over 500 steps: 0.689 s against 0.870 s for the best block
+        // layout (6), 0.789 s with 8 rows per lane (halo 19% of the warp
+        // tile), 0.699 s with 12, 0.720 s with 16; 256 samples of the 2^20-cell chain over 200 steps: 0.060 s
         // against 0.076 s (layout 4).  An L2 prefetch of each warp's next
         // item gained nothing on the KS grid (2% traffic).
         if (n > INT32_MAX - 64) return REACH_EINVAL;
@@ -1920,14 +1919,19 @@ static int mc_dispatch(const reach_system *sys, Staging &sg, const McArgs &base,
         if ((rc = sg.scratch(bytes, (void **)&bufA)) || (rc = sg.scratch(bytes, (void **)&bufB)) ||
             (rc = sg.scratch(2 * sizeof(unsigned), (void **)&r.ctr)))
             return rc;
-        const int kc = lay == 8 ? 8 : (lay == 10 ? 16 : 12);
-        if (sys->kind == REACH_TRAFFIC) {
+        // rows per lane: the option's 8 / 12 / 16, else 14 on the KS grid
+        // (0.689 s against 0.699 s with 12, same box) and 12 on the chain
+        // (whose 14- and 16-row variants spill)
+        const bool ks = sys->kind == REACH_KS;
+        const int kc = lay == 8 ? 8 : lay == 9 ? 12 : lay == 10 ? 16 : (ks ? 14 : 12);
+        if (!ks) {
             if (kc == 8) return launch_rows<REACH_TRAFFIC, 8>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
             if (kc == 12) return launch_rows<REACH_TRAFFIC, 12>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
             return launch_rows<REACH_TRAFFIC, 16>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
         }
         if (kc == 8) return launch_rows<REACH_KS, 8>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
         if (kc == 12) return launch_rows<REACH_KS, 12>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
+        if (kc == 14) return launch_rows<REACH_KS, 14>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
         return launch_rows<REACH_KS, 16>(r, base.N, bufA, bufB, dlo, dhi, sg.st);
     }
     // partial minima / maxima per block of samples
