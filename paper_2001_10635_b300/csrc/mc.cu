@@ -1456,10 +1456,7 @@ __global__ void __launch_bounds__(128) mc_quad(McArgs a, QuadK p) {
     // q + d_3, which is the new step-start angle up to the rounding of the
     // state update (quad_mc_stages).  A step whose stage increments d_1 or d_2
     // pass Q_SMALL takes the copy of the stages that halves them into the
-    // series' range.  (A
-    // sincosf of each angle at every step start kept the FP64 pipe 82% busy in
-    // the binary32 kernel; carrying the step-start values by a separate angle
-    // addition cost 13 operations per angle and step.)
+    // series' range.
     T s0[3], c0[3];
     for (int64_t s = 0; s < a.N; ++s) {
         if (s % QUAD_ANCHOR == 0) {
